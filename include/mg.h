@@ -1,0 +1,199 @@
+/*
+ * mg.h -- C ABI of tweedmg, a GB300 (sm_103a) geometric multigrid library for
+ * the Dirichlet Poisson problem on stretched rectilinear grids, with the tweed
+ * and wireframe smoothers of Bewley, Mashayek, Cavaglieri & Luchini,
+ * "Tweed and wireframe: accelerated relaxation algorithms for multigrid
+ * solution of elliptic PDEs on stretched structured grids" (arXiv:2110.08389).
+ *
+ * Problem (Sec. 2, Eq. prob:DP): on an (nx+1) x (ny+1) grid with coordinates
+ * x_0 < ... < x_nx and y_0 < ... < y_ny, find u with
+ *     W_i u_{i-1,j} + E_i u_{i+1,j} + S_j u_{i,j-1} + N_j u_{i,j+1} + C_ij u_ij = f_ij
+ * at every interior node (0 < i < nx, 0 < j < ny), u given on the boundary,
+ * where W_i = 1/(dx_i dx_{i-1/2}), E_i = 1/(dx_i dx_{i+1/2}) (same for S_j,
+ * N_j in y), dx_{i-1/2} = x_i - x_{i-1}, dx_i = (x_{i+1} - x_{i-1})/2 and
+ * C_ij = -(W_i + E_i + S_j + N_j).
+ *
+ * Conventions for every entry point:
+ *   - Grid arrays (u, f, corrections) are dense, row-major, x fastest:
+ *     element (i,j) of a level with nx, ny intervals is at a[j*(nx+1)+i].
+ *     They are DEVICE pointers owned by the caller, 8-byte (double) or 4-byte
+ *     (float) aligned, and must not alias each other.
+ *   - u carries the Dirichlet data on its boundary nodes; kernels write only
+ *     interior nodes.  f is read only at interior nodes.
+ *   - Level 0 is the finest grid (the paper's Omega_p); level l+1 drops every
+ *     other grid line of level l (Sec. 4).  Coarsening stops when a side is
+ *     odd, a side would fall below 2 intervals, or max(nx,ny) <= 8; the
+ *     coarsest level is solved directly.
+ *   - All work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  Only mg_setup_grid, mg_solve and mg_solve_adjoint synchronise
+ *     (they read residual norms back to the host).  No entry point allocates
+ *     device memory except mg_setup_grid.
+ *   - Errors are returned as mg_status; nothing aborts or traps.  After
+ *     MG_ERR_CUDA the message of the failing call is available from
+ *     mg_last_error().  Calls on one grid must not run concurrently.
+ */
+#ifndef TWEEDMG_MG_H
+#define TWEEDMG_MG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mg_grid mg_grid; /* opaque: level hierarchy, coefficients,
+                                   block work lists and workspaces */
+
+typedef enum {
+  MG_OK = 0,
+  MG_ERR_INVALID_ARG = 1,   /* NULL pointer, bad enum, bad level, ...           */
+  MG_ERR_SIZE = 2,          /* nx, ny < 2, coordinates not increasing, a block  */
+                            /* longer than the kernels support (16384 nodes)    */
+  MG_ERR_CUDA = 3,          /* a CUDA runtime call failed (see mg_last_error)   */
+  MG_ERR_NOT_CONVERGED = 4, /* tolerance not reached within the cycle cap, or  */
+                            /* the defect grew 1e3-fold (info is still filled)  */
+  MG_ERR_NONFINITE = 5,     /* a residual norm was NaN or infinite              */
+  MG_ERR_TIMEOUT = 6,       /* reserved for bounded device-side waits           */
+  MG_ERR_ALLOC = 7,         /* device or host allocation failed                 */
+  MG_ERR_UNSUPPORTED = 8    /* valid request this build does not implement      */
+} mg_status;
+
+/* Smoothers (Sec. 2 and Sec. 3).  One "relaxation" of each is a red pass then
+ * a black pass; the alternating schemes apply one step of each of their two
+ * smoothers per relaxation.                                                   */
+typedef enum {
+  MG_SMOOTH_CHECKERBOARD = 0, /* red-black point Gauss-Seidel, red = (i+j) even */
+  MG_SMOOTH_ZEBRA_X = 1,      /* lines along x, red = odd j                     */
+  MG_SMOOTH_ZEBRA_Y = 2,      /* lines along y, red = odd i                     */
+  MG_SMOOTH_ALT_ZEBRA = 3,    /* zebra x step, then zebra y step                */
+  MG_SMOOTH_TWEED = 4,        /* branched lines, blocks = level sets of         */
+                              /* max(dist to x-walls, dist to y-walls), Sec. 3  */
+  MG_SMOOTH_WIREFRAME = 5,    /* concentric rings, level sets of the min, Sec. 3*/
+  MG_SMOOTH_ALT_TW = 6        /* tweed step, then wireframe step                */
+} mg_smoother;
+
+typedef enum { MG_F64 = 0, MG_F32 = 1 } mg_dtype;
+typedef enum { MG_PREC_F64 = 0, MG_PREC_F32_REFINE = 1 } mg_precision;
+typedef enum { MG_CYCLE_V = 1, MG_CYCLE_W = 2 } mg_cycle;
+typedef enum { MG_RESTRICT_HW = 0, MG_RESTRICT_FW = 1 } mg_restriction;
+
+/* Solver parameters (Sec. 4).  mg_default_params() fills the defaults:
+ * tweed, V(2,2), full weighting, FP64, tol 1e-10, 100 cycles, 8 outer
+ * iterations, 4 inner cycles, zero initial guess.                            */
+typedef struct {
+  int smoother;          /* mg_smoother                                          */
+  int nu1, nu2;          /* pre- / post-smoothing relaxations (>= 0)             */
+  int cycle;             /* mg_cycle: 1 = V, 2 = W                               */
+  int restriction;       /* mg_restriction (prolongation is always bilinear)     */
+  int precision;         /* mg_precision                                         */
+  int max_cycles;        /* cap on cycles (FP64) or on inner cycles (FP32+refine)*/
+  int max_outer;         /* cap on refinement iterations (FP32+refine)           */
+  int inner_cycles;      /* FP32 cycles per refinement iteration                 */
+  int use_initial_guess; /* 0: interior of u is zeroed first; 1: u is the guess  */
+  double tol;            /* stop when ||f - L u||_2 / ||f||_2 <= tol (interior)   */
+} mg_params;
+
+/* Convergence record.  history is a caller-owned HOST buffer of history_cap
+ * doubles (may be NULL): history[k] = ||f - L u||_2/||f||_2 after cycle k
+ * (FP64) or after refinement iteration k (FP32+refine); history[0] is the
+ * initial value.                                                             */
+typedef struct {
+  int cycles;            /* V/W cycles run (all precisions)                      */
+  int outer_iters;       /* refinement iterations (FP32+refine), else 0          */
+  double rel_res;        /* final ||f - L u||_2 / ||f||_2                         */
+  double conv_factor;    /* (rho_K / rho_0)^(1/K) over the recorded history       */
+  double ms;             /* wall time of the call, milliseconds                   */
+  double *history;
+  int history_cap;
+  int history_len;
+} mg_info;
+
+/* Build the level hierarchy, the 1-D coefficient arrays of Sec. 2 on every
+ * level (rediscretised on the subsampled coordinates, Sec. 4) and the device
+ * workspaces.  dim must be 2.  n_intervals = {nx, ny}; coords = {x, y}, HOST
+ * arrays of nx+1 and ny+1 strictly increasing doubles (copied).
+ * precision_mask: bit 0 = FP64 workspaces, bit 1 = FP32 workspaces (0 means
+ * both).  Block work lists of each smoother are built on first use.
+ * On success *out owns device memory until mg_destroy.                       */
+mg_status mg_setup_grid(mg_grid **out, int dim, const int64_t *n_intervals,
+                        const double *const *coords, int precision_mask, void *stream);
+
+/* Release everything owned by the grid (NULL is a no-op).                    */
+void mg_destroy(mg_grid *grid);
+
+/* Number of levels and the interval counts of one level.                     */
+int mg_num_levels(const mg_grid *grid);
+mg_status mg_level_shape(const mg_grid *grid, int level, int64_t *nx, int64_t *ny);
+
+/* Relaxation on one level.  u, f: device arrays of that level's shape in
+ * dtype (mg_dtype).  `sweeps` relaxations are applied in place on u.
+ *   mg_smooth_tweed:     Sec. 3 tweed relaxation: each block (corner points,
+ *                        L-shaped two-legged blocks, the centre cross or the two
+ *                        T-blocks, straight lines in the middle of a
+ *                        rectangle) is solved exactly, red blocks first.
+ *   mg_smooth_wireframe: Sec. 3 wireframe relaxation: concentric rings
+ *                        (circulant tridiagonal systems, Eq. CircTri) and the
+ *                        centre point or centre x/y line.
+ *   mg_smooth:           any mg_smoother.
+ *   mg_colour_pass:      one colour (0 = red, 1 = black) of a base smoother
+ *                        (not the alternating ones).                          */
+mg_status mg_smooth_tweed(mg_grid *grid, int level, void *u, const void *f, int sweeps,
+                          int dtype, void *stream);
+mg_status mg_smooth_wireframe(mg_grid *grid, int level, void *u, const void *f, int sweeps,
+                              int dtype, void *stream);
+mg_status mg_smooth(mg_grid *grid, int level, int smoother, void *u, const void *f, int sweeps,
+                    int dtype, void *stream);
+mg_status mg_colour_pass(mg_grid *grid, int level, int smoother, int colour, void *u,
+                         const void *f, int dtype, void *stream);
+
+/* Sec. 4 step (3) fused: defect d = f - L u on `level`, restricted (half or
+ * full weighting) into fc on level+1; uc (level+1, may be NULL) has its
+ * interior zeroed, ready for the coarse correction.                          */
+mg_status mg_residual_restrict(mg_grid *grid, int level, int restriction, const void *u,
+                               const void *f, void *fc, void *uc, int dtype, void *stream);
+
+/* Sec. 4 step (5) fused: u(level) += bilinear prolongation of uc(level+1).   */
+mg_status mg_prolong_add(mg_grid *grid, int level, const void *uc, void *u, int dtype,
+                         void *stream);
+
+/* Defect d = f - L u on `level` (d is written on every node, 0 on the
+ * boundary).                                                                 */
+mg_status mg_residual(mg_grid *grid, int level, const void *u, const void *f, void *d,
+                      int dtype, void *stream);
+
+/* Direct solve of the coarsest level (dense LU, FP64 arithmetic for both
+ * dtypes).  The boundary values of u enter the right-hand side.              */
+mg_status mg_coarse_solve(mg_grid *grid, void *u, const void *f, int dtype, void *stream);
+
+/* One cycle (params->cycle: V or W) on the finest level, in the dtype of
+ * params->precision (MG_PREC_F64 -> double arrays, MG_PREC_F32_REFINE ->
+ * float arrays).  u holds the boundary data and the current iterate.         */
+mg_status mg_vcycle(mg_grid *grid, void *u, const void *f, const mg_params *params,
+                    void *stream);
+
+/* Solve to params->tol.  u, f: FP64 device arrays of the finest level.  u
+ * holds the Dirichlet data g on its boundary (and the initial guess when
+ * use_initial_guess).  MG_PREC_F64: FP64 cycles.  MG_PREC_F32_REFINE: FP32
+ * smoothing, transfers and cycles on the correction equation, FP64 residual,
+ * update and coarsest solve (iterative refinement).  info may be NULL.       */
+mg_status mg_solve(mg_grid *grid, double *u, const double *f, const mg_params *params,
+                   mg_info *info, void *stream);
+
+/* Adjoint solve L^T lambda = rhs with homogeneous boundary data, to the same
+ * tolerance.  Uses D L = (D L)^T with D = diag(dx_i dy_j): lambda = D mu with
+ * L mu = D^{-1} rhs, solved by the same multigrid.  lambda, rhs: FP64 device
+ * arrays of the finest level; lambda's boundary is set to 0.                 */
+mg_status mg_solve_adjoint(mg_grid *grid, double *lambda, const double *rhs,
+                           const mg_params *params, mg_info *info, void *stream);
+
+/* Defaults for mg_params.                                                    */
+void mg_default_params(mg_params *params);
+
+/* Static description of a status code / the last CUDA error message.        */
+const char *mg_status_string(mg_status status);
+const char *mg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TWEEDMG_MG_H */

@@ -1,0 +1,544 @@
+// api.cu -- the C ABI of tweedmg (include/mg.h): grid setup, the cycle driver
+// (Sec. 4 steps (1)-(6)), the FP64 solve, the FP32 + FP64 iterative
+// refinement solve and the adjoint solve.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "mg_internal.h"
+
+namespace tmg {
+
+static thread_local char g_err[512] = "";
+
+const char *set_error(const char *where, cudaError_t e) {
+  std::snprintf(g_err, sizeof(g_err), "%s: %s", where, cudaGetErrorString(e));
+  return g_err;
+}
+
+static mg_status cuda_status(const char *where, cudaError_t e) {
+  if (e == cudaSuccess) return MG_OK;
+  set_error(where, e);
+  return e == cudaErrorMemoryAllocation ? MG_ERR_ALLOC : MG_ERR_CUDA;
+}
+#define TRY_CUDA(where, expr)                                  \
+  do {                                                         \
+    mg_status _st = cuda_status(where, (expr));                \
+    if (_st != MG_OK) return _st;                              \
+  } while (0)
+#define TRY(expr)                \
+  do {                           \
+    mg_status _st = (expr);      \
+    if (_st != MG_OK) return _st; \
+  } while (0)
+
+// Sec. 2 coefficients on one axis: lo_i = 1/(dx_i dx_{i-1/2}),
+// hi_i = 1/(dx_i dx_{i+1/2}), dx_i = (x_{i+1} - x_{i-1})/2; 0 at the ends.
+static void axis_coefficients(const std::vector<double> &x, std::vector<double> &lo, std::vector<double> &hi) {
+  const size_t n = x.size() - 1;
+  lo.assign(n + 1, 0.0);
+  hi.assign(n + 1, 0.0);
+  for (size_t i = 1; i < n; ++i) {
+    const double h_minus = x[i] - x[i - 1], h_plus = x[i + 1] - x[i];
+    const double h_mid = 0.5 * (x[i + 1] - x[i - 1]);
+    lo[i] = 1.0 / (h_mid * h_minus);
+    hi[i] = 1.0 / (h_mid * h_plus);
+  }
+}
+
+static void free_grid(Grid *g) {
+  if (!g) return;
+  for (Level &L : g->lev) {
+    cudaFree(L.dev_block);
+    cudaFree(L.u64); cudaFree(L.f64); cudaFree(L.u32); cudaFree(L.f32);
+    for (int w = 0; w < WL_COUNT; ++w)
+      for (int p = 0; p < 2; ++p)
+        for (int c = 0; c < 2; ++c)
+          for (int z = 0; z < 2; ++z) cudaFree(L.wl[w][p][c][z].mem);
+  }
+  cudaFree(g->cinv);
+  cudaFree(g->r64); cudaFree(g->lam_tmp); cudaFree(g->e32); cudaFree(g->r32);
+  cudaFree(g->partial); cudaFree(g->scal);
+  if (g->hpinned) cudaFreeHost(g->hpinned);
+  delete g;
+}
+
+template <typename X>
+static mg_status dalloc(X **p, size_t n, const char *what) {
+  TRY_CUDA(what, cudaMalloc(reinterpret_cast<void **>(p), sizeof(X) * n));
+  TRY_CUDA(what, cudaMemset(*p, 0, sizeof(X) * n));
+  return MG_OK;
+}
+
+// Gauss-Jordan inverse with partial pivoting (FP64, host), for the coarsest
+// level's dense direct solve.
+static bool invert(int n, std::vector<double> &A, std::vector<double> &inv) {
+  inv.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int r = k + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * n + k]) > std::fabs(A[(size_t)p * n + k])) p = r;
+    if (A[(size_t)p * n + k] == 0.0) return false;
+    if (p != k)
+      for (int c = 0; c < n; ++c) {
+        std::swap(A[(size_t)k * n + c], A[(size_t)p * n + c]);
+        std::swap(inv[(size_t)k * n + c], inv[(size_t)p * n + c]);
+      }
+    const double d = 1.0 / A[(size_t)k * n + k];
+    for (int c = 0; c < n; ++c) { A[(size_t)k * n + c] *= d; inv[(size_t)k * n + c] *= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == k) continue;
+      const double l = A[(size_t)r * n + k];
+      if (l == 0.0) continue;
+      for (int c = 0; c < n; ++c) {
+        A[(size_t)r * n + c] -= l * A[(size_t)k * n + c];
+        inv[(size_t)r * n + c] -= l * inv[(size_t)k * n + c];
+      }
+    }
+  }
+  return true;
+}
+
+static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y) {
+  // level hierarchy: drop every other line while both sides are even, keep at
+  // least 2 intervals, and stop once max(nx, ny) <= 8
+  int cx = nx, cy = ny;
+  std::vector<double> xs(x, x + nx + 1), ys(y, y + ny + 1);
+  while (true) {
+    Level L;
+    L.nx = cx; L.ny = cy; L.nn = (size_t)(cx + 1) * (cy + 1);
+    L.hx = xs; L.hy = ys;
+    axis_coefficients(xs, L.hW, L.hE);
+    axis_coefficients(ys, L.hS, L.hN);
+    g->lev.push_back(std::move(L));
+    if (cx % 2 || cy % 2 || cx / 2 < 2 || cy / 2 < 2 || std::max(cx, cy) <= 8) break;
+    std::vector<double> xn(cx / 2 + 1), yn(cy / 2 + 1);
+    for (int i = 0; i <= cx / 2; ++i) xn[i] = xs[2 * i];
+    for (int j = 0; j <= cy / 2; ++j) yn[j] = ys[2 * j];
+    xs.swap(xn); ys.swap(yn);
+    cx /= 2; cy /= 2;
+  }
+  g->nlev = (int)g->lev.size();
+  const bool want64 = g->prec_mask & 1, want32 = g->prec_mask & 2;
+  for (int l = 0; l < g->nlev; ++l) {
+    Level &L = g->lev[l];
+    const size_t a = L.nx + 1, b = L.ny + 1;
+    // doubles: W E x (a each), S N y (b each); floats after them
+    const size_t nd = 3 * a + 3 * b, nf = 2 * a + 2 * b;
+    const size_t bytes = sizeof(double) * nd + sizeof(float) * nf + 16;
+    TRY_CUDA("cudaMalloc(coefficients)", cudaMalloc(&L.dev_block, bytes));
+    double *dp = static_cast<double *>(L.dev_block);
+    L.W64 = dp; L.E64 = dp + a; L.xd = dp + 2 * a; L.S64 = dp + 3 * a; L.N64 = dp + 3 * a + b; L.yd = dp + 3 * a + 2 * b;
+    float *fp = reinterpret_cast<float *>(dp + nd);
+    L.W32 = fp; L.E32 = fp + a; L.S32 = fp + 2 * a; L.N32 = fp + 2 * a + b;
+    std::vector<double> hd(nd);
+    std::vector<float> hf(nf);
+    for (size_t i = 0; i < a; ++i) { hd[i] = L.hW[i]; hd[a + i] = L.hE[i]; hd[2 * a + i] = L.hx[i]; }
+    for (size_t j = 0; j < b; ++j) { hd[3 * a + j] = L.hS[j]; hd[3 * a + b + j] = L.hN[j]; hd[3 * a + 2 * b + j] = L.hy[j]; }
+    for (size_t i = 0; i < a; ++i) { hf[i] = (float)L.hW[i]; hf[a + i] = (float)L.hE[i]; }
+    for (size_t j = 0; j < b; ++j) { hf[2 * a + j] = (float)L.hS[j]; hf[2 * a + b + j] = (float)L.hN[j]; }
+    TRY_CUDA("cudaMemcpy(coefficients)", cudaMemcpy(dp, hd.data(), sizeof(double) * nd, cudaMemcpyHostToDevice));
+    TRY_CUDA("cudaMemcpy(coefficients)", cudaMemcpy(fp, hf.data(), sizeof(float) * nf, cudaMemcpyHostToDevice));
+    if (l > 0) {
+      if (want64) { TRY(dalloc(&L.u64, L.nn, "cudaMalloc(level u64)")); TRY(dalloc(&L.f64, L.nn, "cudaMalloc(level f64)")); }
+      if (want32) { TRY(dalloc(&L.u32, L.nn, "cudaMalloc(level u32)")); TRY(dalloc(&L.f32, L.nn, "cudaMalloc(level f32)")); }
+    }
+  }
+  // coarsest level: dense inverse of the interior operator
+  {
+    const Level &L = g->lev[g->nlev - 1];
+    const int n = (L.nx - 1) * (L.ny - 1);
+    if (n > 1024) return MG_ERR_SIZE;
+    g->cn = n;
+    if (n > 0) {
+      std::vector<double> A((size_t)n * n, 0.0), inv;
+      for (int j = 1; j < L.ny; ++j)
+        for (int i = 1; i < L.nx; ++i) {
+          const int r = (j - 1) * (L.nx - 1) + (i - 1);
+          A[(size_t)r * n + r] = -(L.hW[i] + L.hE[i] + L.hS[j] + L.hN[j]);
+          if (i > 1) A[(size_t)r * n + r - 1] = L.hW[i];
+          if (i < L.nx - 1) A[(size_t)r * n + r + 1] = L.hE[i];
+          if (j > 1) A[(size_t)r * n + r - (L.nx - 1)] = L.hS[j];
+          if (j < L.ny - 1) A[(size_t)r * n + r + (L.nx - 1)] = L.hN[j];
+        }
+      if (!invert(n, A, inv)) return MG_ERR_SIZE;
+      TRY_CUDA("cudaMalloc(coarse)", cudaMalloc(&g->cinv, sizeof(double) * inv.size()));
+      TRY_CUDA("cudaMemcpy(coarse)", cudaMemcpy(g->cinv, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice));
+    }
+  }
+  const size_t nn0 = g->lev[0].nn;
+  if (want32) { TRY(dalloc(&g->e32, nn0, "cudaMalloc(e32)")); TRY(dalloc(&g->r32, nn0, "cudaMalloc(r32)")); }
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  g->npartial = 4 * sms;
+  TRY(dalloc(&g->partial, 2 * (size_t)g->npartial, "cudaMalloc(partials)"));
+  TRY(dalloc(&g->scal, 4, "cudaMalloc(scalars)"));
+  TRY_CUDA("cudaMallocHost", cudaMallocHost(&g->hpinned, 4 * sizeof(double)));
+  return MG_OK;
+}
+
+// ------------------------------------------------------------------ driver --
+
+template <typename T> static T *level_u(Level &L);
+template <typename T> static T *level_f(Level &L);
+template <> double *level_u<double>(Level &L) { return L.u64; }
+template <> double *level_f<double>(Level &L) { return L.f64; }
+template <> float *level_u<float>(Level &L) { return L.u32; }
+template <> float *level_f<float>(Level &L) { return L.f32; }
+
+static int wl_of(int smoother) {
+  switch (smoother) {
+    case MG_SMOOTH_ZEBRA_X: return WL_ZEBRA_X;
+    case MG_SMOOTH_ZEBRA_Y: return WL_ZEBRA_Y;
+    case MG_SMOOTH_TWEED: return WL_TWEED;
+    case MG_SMOOTH_WIREFRAME: return WL_WIREFRAME;
+  }
+  return -1;
+}
+
+template <typename T>
+static mg_status colour_pass(Grid &g, int l, int smoother, int colour, T *u, const T *f, cudaStream_t s) {
+  Level &L = g.lev[l];
+  if (smoother == MG_SMOOTH_CHECKERBOARD) {
+    TRY_CUDA("checker pass", launch_checker_pass<T>(L, colour, u, f, s));
+    return MG_OK;
+  }
+  const int wl = wl_of(smoother);
+  if (wl < 0) return MG_ERR_INVALID_ARG;
+  const int prec = sizeof(T) == 8 ? 0 : 1;
+  TRY(build_worklists(g, l, wl, prec));
+  TRY_CUDA("line pass", launch_line_pass<T>(L, L.wl[wl][prec][colour][0], u, f, s));
+  TRY_CUDA("line pass (large blocks)", launch_line_pass<T>(L, L.wl[wl][prec][colour][1], u, f, s));
+  return MG_OK;
+}
+
+// One relaxation (red pass, then black pass; the alternating schemes run one
+// relaxation of each of their two smoothers).
+template <typename T>
+static mg_status smooth(Grid &g, int l, int smoother, T *u, const T *f, cudaStream_t s) {
+  if (smoother == MG_SMOOTH_ALT_ZEBRA) {
+    TRY(smooth(g, l, MG_SMOOTH_ZEBRA_X, u, f, s));
+    return smooth(g, l, MG_SMOOTH_ZEBRA_Y, u, f, s);
+  }
+  if (smoother == MG_SMOOTH_ALT_TW) {
+    TRY(smooth(g, l, MG_SMOOTH_TWEED, u, f, s));
+    return smooth(g, l, MG_SMOOTH_WIREFRAME, u, f, s);
+  }
+  TRY(colour_pass(g, l, smoother, 0, u, f, s));
+  return colour_pass(g, l, smoother, 1, u, f, s);
+}
+
+// Sec. 4 steps (2)-(6) on level l; gamma = 1 (V) or 2 (W).
+template <typename T>
+static mg_status cycle_rec(Grid &g, const mg_params &p, int l, T *u, const T *f, cudaStream_t s) {
+  if (l == g.nlev - 1) {
+    TRY_CUDA("coarse solve", launch_coarse_solve<T>(g, u, f, s));
+    return MG_OK;
+  }
+  for (int k = 0; k < p.nu1; ++k) TRY(smooth(g, l, p.smoother, u, f, s));
+  Level &F = g.lev[l], &C = g.lev[l + 1];
+  T *uc = level_u<T>(C), *fc = level_f<T>(C);
+  TRY_CUDA("residual+restrict", launch_residual_restrict<T>(F, C, p.restriction, u, f, fc, uc, s));
+  for (int k = 0; k < p.cycle; ++k) TRY(cycle_rec<T>(g, p, l + 1, uc, fc, s));
+  TRY_CUDA("prolong+correct", launch_prolong_add<T>(F, C, uc, u, s));
+  for (int k = 0; k < p.nu2; ++k) TRY(smooth(g, l, p.smoother, u, f, s));
+  return MG_OK;
+}
+
+static mg_status check_params(const Grid *g, const mg_params *p) {
+  if (!p) return MG_ERR_INVALID_ARG;
+  if (p->smoother < 0 || p->smoother > MG_SMOOTH_ALT_TW) return MG_ERR_INVALID_ARG;
+  if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 > 64) return MG_ERR_INVALID_ARG;
+  if (p->cycle != MG_CYCLE_V && p->cycle != MG_CYCLE_W) return MG_ERR_INVALID_ARG;
+  if (p->restriction != MG_RESTRICT_HW && p->restriction != MG_RESTRICT_FW) return MG_ERR_INVALID_ARG;
+  if (p->precision == MG_PREC_F64 && !(g->prec_mask & 1)) return MG_ERR_INVALID_ARG;
+  if (p->precision == MG_PREC_F32_REFINE && !(g->prec_mask & 2)) return MG_ERR_INVALID_ARG;
+  if (p->precision != MG_PREC_F64 && p->precision != MG_PREC_F32_REFINE) return MG_ERR_INVALID_ARG;
+  if (!(p->tol >= 0.0) || p->max_cycles < 0 || p->max_outer < 0 || p->inner_cycles < 1) return MG_ERR_INVALID_ARG;
+  return MG_OK;
+}
+
+// Read the two device norm scalars (sum of squares, max) back to the host.
+static mg_status read_norms(Grid &g, cudaStream_t s, double *sumsq, double *mx) {
+  TRY_CUDA("cudaMemcpyAsync(norms)", cudaMemcpyAsync(g.hpinned, g.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  TRY_CUDA("cudaStreamSynchronize", cudaStreamSynchronize(s));
+  *sumsq = g.hpinned[0];
+  *mx = g.hpinned[1];
+  return MG_OK;
+}
+
+static void record(mg_info *info, int k, double rel) {
+  if (info && info->history && k < info->history_cap) {
+    info->history[k] = rel;
+    info->history_len = k + 1;
+  }
+}
+
+static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params &p, mg_info *info,
+                            cudaStream_t s) {
+  const Level &L0 = g.lev[0];
+  if (info) { info->cycles = 0; info->outer_iters = 0; info->history_len = 0; info->rel_res = 0; info->conv_factor = 0; }
+  if (!p.use_initial_guess) TRY_CUDA("zero u", launch_zero_interior<double>(L0, u, s));
+  double fs, fm, rs, rm;
+  TRY_CUDA("norm(f)", launch_resnorm64(g, nullptr, f, s));
+  TRY(read_norms(g, s, &fs, &fm));
+  double fn = std::sqrt(fs);
+  if (p.precision == MG_PREC_F64) {
+    TRY_CUDA("residual norm", launch_resnorm64(g, u, f, s));
+    TRY(read_norms(g, s, &rs, &rm));
+    if (fn == 0.0) fn = std::sqrt(rs) > 0.0 ? std::sqrt(rs) : 1.0;
+    double rel = std::sqrt(rs) / fn;
+    const double rel0 = rel;
+    record(info, 0, rel);
+    int k = 0;
+    mg_status st = MG_OK;
+    while (!(rel <= p.tol)) {
+      if (!std::isfinite(rel)) { st = MG_ERR_NONFINITE; break; }
+      if (k >= p.max_cycles || rel > 1e3 * rel0) { st = MG_ERR_NOT_CONVERGED; break; }
+      TRY(cycle_rec<double>(g, p, 0, u, f, s));
+      ++k;
+      TRY_CUDA("residual norm", launch_resnorm64(g, u, f, s));
+      TRY(read_norms(g, s, &rs, &rm));
+      rel = std::sqrt(rs) / fn;
+      record(info, k, rel);
+    }
+    if (info) {
+      info->cycles = k;
+      info->rel_res = rel;
+      info->conv_factor = (k > 0 && rel0 > 0 && rel > 0) ? std::pow(rel / rel0, 1.0 / k) : 0.0;
+    }
+    if (st == MG_OK && !std::isfinite(rel)) st = MG_ERR_NONFINITE;
+    return st;
+  }
+  // FP32 cycles on the correction equation L e = r, FP64 residual and update
+  int outer = 0, cycles = 0;
+  double rel = 0.0, rel0 = 0.0;
+  mg_status st = MG_OK;
+  while (true) {
+    TRY_CUDA("refinement residual", launch_ir_residual(g, u, f, g.r32, s));
+    TRY(read_norms(g, s, &rs, &rm));
+    if (outer == 0 && fn == 0.0) fn = std::sqrt(rs) > 0.0 ? std::sqrt(rs) : 1.0;
+    rel = std::sqrt(rs) / fn;
+    if (outer == 0) rel0 = rel;
+    record(info, outer, rel);
+    if (rel <= p.tol) break;
+    if (!std::isfinite(rel)) { st = MG_ERR_NONFINITE; break; }
+    if (outer >= p.max_outer || cycles >= p.max_cycles || rel > 1e3 * rel0) { st = MG_ERR_NOT_CONVERGED; break; }
+    TRY_CUDA("zero e", launch_zero_interior<float>(L0, g.e32, s));
+    for (int k = 0; k < p.inner_cycles; ++k) {
+      TRY(cycle_rec<float>(g, p, 0, g.e32, g.r32, s));
+      ++cycles;
+    }
+    TRY_CUDA("refinement update", launch_ir_update(g, u, g.e32, s));
+    ++outer;
+  }
+  if (info) {
+    info->cycles = cycles;
+    info->outer_iters = outer;
+    info->rel_res = rel;
+    info->conv_factor = (cycles > 0 && rel0 > 0 && rel > 0) ? std::pow(rel / rel0, 1.0 / cycles) : 0.0;
+  }
+  return st;
+}
+
+}  // namespace tmg
+
+using namespace tmg;
+
+struct mg_grid : public Grid {};
+
+extern "C" {
+
+void mg_default_params(mg_params *p) {
+  if (!p) return;
+  p->smoother = MG_SMOOTH_TWEED;
+  p->nu1 = 2; p->nu2 = 2;
+  p->cycle = MG_CYCLE_V;
+  p->restriction = MG_RESTRICT_FW;
+  p->precision = MG_PREC_F64;
+  p->max_cycles = 100;
+  p->max_outer = 8;
+  p->inner_cycles = 4;
+  p->use_initial_guess = 0;
+  p->tol = 1e-10;
+}
+
+const char *mg_status_string(mg_status s) {
+  switch (s) {
+    case MG_OK: return "ok";
+    case MG_ERR_INVALID_ARG: return "invalid argument";
+    case MG_ERR_SIZE: return "unsupported size";
+    case MG_ERR_CUDA: return "CUDA error";
+    case MG_ERR_NOT_CONVERGED: return "not converged";
+    case MG_ERR_NONFINITE: return "non-finite residual";
+    case MG_ERR_TIMEOUT: return "device wait timed out";
+    case MG_ERR_ALLOC: return "allocation failed";
+    case MG_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char *mg_last_error(void) { return g_err; }
+
+mg_status mg_setup_grid(mg_grid **out, int dim, const int64_t *n_intervals, const double *const *coords,
+                        int precision_mask, void *stream) {
+  (void)stream;
+  if (!out || !n_intervals || !coords) return MG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (dim == 3) return MG_ERR_UNSUPPORTED;
+  if (dim != 2) return MG_ERR_INVALID_ARG;
+  const int64_t nx = n_intervals[0], ny = n_intervals[1];
+  if (nx < 2 || ny < 2 || nx > 32768 || ny > 32768) return MG_ERR_SIZE;
+  if (!coords[0] || !coords[1]) return MG_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < nx; ++i)
+    if (!(coords[0][i + 1] > coords[0][i])) return MG_ERR_SIZE;
+  for (int64_t j = 0; j < ny; ++j)
+    if (!(coords[1][j + 1] > coords[1][j])) return MG_ERR_SIZE;
+  mg_grid *g = new (std::nothrow) mg_grid();
+  if (!g) return MG_ERR_ALLOC;
+  g->prec_mask = (precision_mask & 3) ? (precision_mask & 3) : 3;
+  mg_status st = setup(g, (int)nx, (int)ny, coords[0], coords[1]);
+  if (st != MG_OK) { free_grid(g); return st; }
+  *out = g;
+  return MG_OK;
+}
+
+void mg_destroy(mg_grid *g) { free_grid(g); }
+
+int mg_num_levels(const mg_grid *g) { return g ? g->nlev : 0; }
+
+mg_status mg_level_shape(const mg_grid *g, int level, int64_t *nx, int64_t *ny) {
+  if (!g || !nx || !ny || level < 0 || level >= g->nlev) return MG_ERR_INVALID_ARG;
+  *nx = g->lev[level].nx;
+  *ny = g->lev[level].ny;
+  return MG_OK;
+}
+
+static bool bad_level(const mg_grid *g, int level) { return !g || level < 0 || level >= g->nlev; }
+static bool bad_dtype(const mg_grid *g, int dtype) {
+  return !(dtype == MG_F64 && (g->prec_mask & 1)) && !(dtype == MG_F32 && (g->prec_mask & 2));
+}
+
+mg_status mg_colour_pass(mg_grid *g, int level, int smoother, int colour, void *u, const void *f, int dtype,
+                         void *stream) {
+  if (bad_level(g, level) || !u || !f || colour < 0 || colour > 1 || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
+  if (smoother == MG_SMOOTH_ALT_ZEBRA || smoother == MG_SMOOTH_ALT_TW || smoother < 0 || smoother > MG_SMOOTH_ALT_TW)
+    return MG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (dtype == MG_F64) return colour_pass<double>(*g, level, smoother, colour, (double *)u, (const double *)f, s);
+  return colour_pass<float>(*g, level, smoother, colour, (float *)u, (const float *)f, s);
+}
+
+mg_status mg_smooth(mg_grid *g, int level, int smoother, void *u, const void *f, int sweeps, int dtype,
+                    void *stream) {
+  if (bad_level(g, level) || !u || !f || sweeps < 0 || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
+  if (smoother < 0 || smoother > MG_SMOOTH_ALT_TW) return MG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  for (int k = 0; k < sweeps; ++k) {
+    mg_status st = dtype == MG_F64 ? smooth<double>(*g, level, smoother, (double *)u, (const double *)f, s)
+                                   : smooth<float>(*g, level, smoother, (float *)u, (const float *)f, s);
+    if (st != MG_OK) return st;
+  }
+  return MG_OK;
+}
+
+mg_status mg_smooth_tweed(mg_grid *g, int level, void *u, const void *f, int sweeps, int dtype, void *stream) {
+  return mg_smooth(g, level, MG_SMOOTH_TWEED, u, f, sweeps, dtype, stream);
+}
+
+mg_status mg_smooth_wireframe(mg_grid *g, int level, void *u, const void *f, int sweeps, int dtype, void *stream) {
+  return mg_smooth(g, level, MG_SMOOTH_WIREFRAME, u, f, sweeps, dtype, stream);
+}
+
+mg_status mg_residual_restrict(mg_grid *g, int level, int restriction, const void *u, const void *f, void *fc,
+                               void *uc, int dtype, void *stream) {
+  if (bad_level(g, level) || level + 1 >= g->nlev || !u || !f || !fc || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
+  if (restriction != MG_RESTRICT_HW && restriction != MG_RESTRICT_FW) return MG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Level &F = g->lev[level], &C = g->lev[level + 1];
+  cudaError_t e = dtype == MG_F64
+                      ? launch_residual_restrict<double>(F, C, restriction, (const double *)u, (const double *)f,
+                                                         (double *)fc, (double *)uc, s)
+                      : launch_residual_restrict<float>(F, C, restriction, (const float *)u, (const float *)f,
+                                                        (float *)fc, (float *)uc, s);
+  return cuda_status("residual+restrict", e);
+}
+
+mg_status mg_prolong_add(mg_grid *g, int level, const void *uc, void *u, int dtype, void *stream) {
+  if (bad_level(g, level) || level + 1 >= g->nlev || !u || !uc || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Level &F = g->lev[level], &C = g->lev[level + 1];
+  cudaError_t e = dtype == MG_F64 ? launch_prolong_add<double>(F, C, (const double *)uc, (double *)u, s)
+                                  : launch_prolong_add<float>(F, C, (const float *)uc, (float *)u, s);
+  return cuda_status("prolong+correct", e);
+}
+
+mg_status mg_residual(mg_grid *g, int level, const void *u, const void *f, void *d, int dtype, void *stream) {
+  if (bad_level(g, level) || !u || !f || !d || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const Level &L = g->lev[level];
+  cudaError_t e = dtype == MG_F64 ? launch_residual<double>(L, (const double *)u, (const double *)f, (double *)d, s)
+                                  : launch_residual<float>(L, (const float *)u, (const float *)f, (float *)d, s);
+  return cuda_status("residual", e);
+}
+
+mg_status mg_coarse_solve(mg_grid *g, void *u, const void *f, int dtype, void *stream) {
+  if (!g || !u || !f || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = dtype == MG_F64 ? launch_coarse_solve<double>(*g, (double *)u, (const double *)f, s)
+                                  : launch_coarse_solve<float>(*g, (float *)u, (const float *)f, s);
+  return cuda_status("coarse solve", e);
+}
+
+mg_status mg_vcycle(mg_grid *g, void *u, const void *f, const mg_params *p, void *stream) {
+  if (!g || !u || !f) return MG_ERR_INVALID_ARG;
+  mg_status st = check_params(g, p);
+  if (st != MG_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->precision == MG_PREC_F64) return cycle_rec<double>(*g, *p, 0, (double *)u, (const double *)f, s);
+  return cycle_rec<float>(*g, *p, 0, (float *)u, (const float *)f, s);
+}
+
+mg_status mg_solve(mg_grid *g, double *u, const double *f, const mg_params *p, mg_info *info, void *stream) {
+  if (!g || !u || !f) return MG_ERR_INVALID_ARG;
+  mg_status st = check_params(g, p);
+  if (st != MG_OK) return st;
+  const auto t0 = std::chrono::steady_clock::now();
+  st = solve_impl(*g, u, f, *p, info, static_cast<cudaStream_t>(stream));
+  if (info) info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return st;
+}
+
+mg_status mg_solve_adjoint(mg_grid *g, double *lambda, const double *rhs, const mg_params *p, mg_info *info,
+                           void *stream) {
+  if (!g || !lambda || !rhs) return MG_ERR_INVALID_ARG;
+  mg_status st = check_params(g, p);
+  if (st != MG_OK) return st;
+  if (!(g->prec_mask & 1)) return MG_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t nn = g->lev[0].nn;
+  if (!g->r64) {
+    st = dalloc(&g->r64, nn, "cudaMalloc(adjoint scratch)");
+    if (st != MG_OK) return st;
+  }
+  // L^T = D L D^{-1} with D = diag(dx_i dy_j):  L mu = D^{-1} rhs, lambda = D mu
+  cudaError_t e = launch_diag_scale(*g, g->r64, rhs, 1, s);
+  if (e != cudaSuccess) return cuda_status("adjoint scaling", e);
+  mg_params q = *p;
+  q.use_initial_guess = 0;
+  e = launch_diag_scale(*g, lambda, lambda, 0, s);  // zero boundary (interior is reset by the solve)
+  if (e != cudaSuccess) return cuda_status("adjoint scaling", e);
+  st = solve_impl(*g, lambda, g->r64, q, info, s);
+  if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
+  e = launch_diag_scale(*g, lambda, lambda, 0, s);
+  if (e != cudaSuccess) return cuda_status("adjoint scaling", e);
+  if (info) info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return st;
+}
+
+}  // extern "C"

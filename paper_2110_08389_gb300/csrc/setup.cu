@@ -1,0 +1,307 @@
+// setup.cu -- host-side construction of tweedmg's block work lists.
+//
+// The blocks of every smoother are enumerated in closed form from the node's
+// distances to the walls, d_x = min(i, nx-i) and d_y = min(j, ny-j):
+//   tweed (Sec. 3, Figs. 4 and 6): level k = max(d_x, d_y).  For k below
+//     min(nx,ny)/2 the level splits into four L-shaped blocks, one per corner
+//     (a leg perpendicular to each wall meeting at (k,k)); k = 1 gives the
+//     four corner points.  At k = nx/2 = ny/2 the four legs meet in the centre
+//     cross (m = 4); on a rectangle the level k = min/2 gives two T-blocks
+//     (m = 3) and the larger levels give straight lines perpendicular to the
+//     nearest walls.
+//   wireframe (Sec. 3, Figs. 5 and 7): level k = min(d_x, d_y): concentric
+//     rings, then the centre point (square) or centre line (rectangle).
+//   zebra: rows (x) or columns (y).
+// Colour: odd k (or odd line index) is red = colour 0, relaxed first.
+//
+// Each block becomes chains of straight segments, the segments are cut into
+// chunks of at most CMAX nodes, and whole blocks are packed into CTAs of at
+// most NT_SMALL chunks (or NT_LARGE for the few blocks that need more).
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+
+#include "mg_internal.h"
+
+namespace tmg {
+
+namespace {
+
+struct HSeg {
+  int i0, j0, dir, len;
+};
+struct HChain {
+  std::vector<HSeg> s;
+  bool fj = false, lj = false;
+  int ljdir = 0;  // direction from the last node to the junction
+};
+struct HBlock {
+  bool junc = false;
+  int ji = 0, jj = 0;
+  std::vector<HChain> ch;
+  int nodes = 0, chunks = 0;
+};
+
+HChain line(int i0, int j0, int dir, int len) {
+  HChain c;
+  c.s.push_back({i0, j0, dir, len});
+  return c;
+}
+HChain leg_to_junction(int i0, int j0, int dir, int len) {
+  HChain c = line(i0, j0, dir, len);
+  c.lj = true;
+  c.ljdir = dir;
+  return c;
+}
+HBlock point(int i, int j) {
+  HBlock b;
+  b.junc = true; b.ji = i; b.jj = j;
+  return b;
+}
+HBlock single(HChain c) {
+  HBlock b;
+  b.ch.push_back(c);
+  return b;
+}
+HBlock star(int i, int j, std::vector<HChain> legs) {
+  HBlock b = point(i, j);
+  for (auto &l : legs)
+    if (!l.s.empty() && l.s[0].len > 0) b.ch.push_back(l);
+  return b;
+}
+inline int colour_of(int k) { return (k & 1) ? 0 : 1; }
+
+void tweed_blocks(int nx, int ny, int colour, std::vector<HBlock> &out) {
+  const int hx = nx / 2, hy = ny / 2, K = std::max(hx, hy), m = std::min(hx, hy);
+  for (int k = 1; k <= K; ++k) {
+    if (colour_of(k) != colour) continue;
+    if (k < m) {
+      if (k == 1) {
+        out.push_back(point(1, 1)); out.push_back(point(nx - 1, 1));
+        out.push_back(point(1, ny - 1)); out.push_back(point(nx - 1, ny - 1));
+        continue;
+      }
+      // leg from the y-wall up to the corner (k,k) of the level, then the leg
+      // back along x to the x-wall: one tridiagonal chain of 2k-1 nodes
+      const int cx[2] = {k, nx - k}, cy[2] = {k, ny - k};
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+          HChain c;
+          const int vdir = b == 0 ? DIR_PY : DIR_MY, hdir = a == 0 ? DIR_MX : DIR_PX;
+          c.s.push_back({cx[a], b == 0 ? 1 : ny - 1, vdir, k});
+          c.s.push_back({a == 0 ? k - 1 : nx - k + 1, cy[b], hdir, k - 1});
+          out.push_back(single(c));
+        }
+    } else if (k == m) {
+      if (hx == hy) {  // centre cross, m = 4 legs (Eq. mLThomas)
+        out.push_back(star(k, k, {leg_to_junction(1, k, DIR_PX, k - 1), leg_to_junction(nx - 1, k, DIR_MX, k - 1),
+                                  leg_to_junction(k, 1, DIR_PY, k - 1), leg_to_junction(k, ny - 1, DIR_MY, k - 1)}));
+      } else if (hx > hy) {  // two T-blocks, arms from the x-walls
+        out.push_back(star(k, k, {leg_to_junction(1, k, DIR_PX, k - 1), leg_to_junction(k, 1, DIR_PY, k - 1),
+                                  leg_to_junction(k, ny - 1, DIR_MY, ny - 1 - k)}));
+        out.push_back(star(nx - k, k, {leg_to_junction(nx - 1, k, DIR_MX, k - 1),
+                                       leg_to_junction(nx - k, 1, DIR_PY, k - 1),
+                                       leg_to_junction(nx - k, ny - 1, DIR_MY, ny - 1 - k)}));
+      } else {  // two T-blocks, arms from the y-walls
+        out.push_back(star(k, k, {leg_to_junction(k, 1, DIR_PY, k - 1), leg_to_junction(1, k, DIR_PX, k - 1),
+                                  leg_to_junction(nx - 1, k, DIR_MX, nx - 1 - k)}));
+        out.push_back(star(k, ny - k, {leg_to_junction(k, ny - 1, DIR_MY, k - 1),
+                                       leg_to_junction(1, ny - k, DIR_PX, k - 1),
+                                       leg_to_junction(nx - 1, ny - k, DIR_MX, nx - 1 - k)}));
+      }
+    } else if (hx > hy) {  // full columns perpendicular to the y-walls
+      out.push_back(single(line(k, 1, DIR_PY, ny - 1)));
+      if (nx - k != k) out.push_back(single(line(nx - k, 1, DIR_PY, ny - 1)));
+    } else {  // full rows perpendicular to the x-walls
+      out.push_back(single(line(1, k, DIR_PX, nx - 1)));
+      if (ny - k != k) out.push_back(single(line(1, ny - k, DIR_PX, nx - 1)));
+    }
+  }
+}
+
+void wireframe_blocks(int nx, int ny, int colour, std::vector<HBlock> &out) {
+  const int hx = nx / 2, hy = ny / 2, m = std::min(hx, hy);
+  for (int k = 1; k <= m; ++k) {
+    if (colour_of(k) != colour) continue;
+    if (k < m) {
+      // ring around the box [k, nx-k] x [k, ny-k], opened at the corner (k,k)
+      HChain c;
+      c.s.push_back({k + 1, k, DIR_PX, nx - 2 * k});
+      c.s.push_back({nx - k, k + 1, DIR_PY, ny - 2 * k});
+      c.s.push_back({nx - k - 1, ny - k, DIR_MX, nx - 2 * k});
+      c.s.push_back({k, ny - k - 1, DIR_MY, ny - 2 * k - 1});
+      c.fj = true; c.lj = true; c.ljdir = DIR_MY;
+      HBlock b = point(k, k);
+      b.ch.push_back(c);
+      out.push_back(b);
+    } else if (hx == hy) {
+      out.push_back(point(k, k));
+    } else if (hx > hy) {
+      out.push_back(single(line(k, k, DIR_PX, nx - 2 * k + 1)));
+    } else {
+      out.push_back(single(line(k, k, DIR_PY, ny - 2 * k + 1)));
+    }
+  }
+}
+
+void zebra_blocks(int nx, int ny, int colour, bool along_x, std::vector<HBlock> &out) {
+  if (along_x) {
+    for (int j = 1; j < ny; ++j)
+      if (colour_of(j) == colour) out.push_back(single(line(1, j, DIR_PX, nx - 1)));
+  } else {
+    for (int i = 1; i < nx; ++i)
+      if (colour_of(i) == colour) out.push_back(single(line(i, 1, DIR_PY, ny - 1)));
+  }
+}
+
+inline int nchunks_of(int len) { return (len + CMAX - 1) / CMAX; }
+
+struct Packed {
+  std::vector<CtaWork> cta;
+  std::vector<ChunkDesc> chunk;
+  std::vector<JuncDesc> junc;
+  int total = 0;
+};
+
+inline int step_i(int d) { return d == DIR_PX ? 1 : (d == DIR_MX ? -1 : 0); }
+inline int step_j(int d) { return d == DIR_PY ? 1 : (d == DIR_MY ? -1 : 0); }
+
+// Append one block to the open CTA (the caller checked the capacity).  Each
+// segment is cut into chunks of exactly CMAX nodes plus a ragged last one.
+void emit_block(Packed &P, CtaWork &w, const HBlock &b) {
+  int jidx = -1;
+  if (b.junc) {
+    JuncDesc jd;
+    std::memset(&jd, 0, sizeof(jd));
+    jd.i = (uint16_t)b.ji; jd.j = (uint16_t)b.jj;
+    jidx = w.njunc++;
+    P.junc.push_back(jd);
+  }
+  JuncDesc *jd = b.junc ? &P.junc.back() : nullptr;
+  for (const HChain &c : b.ch) {
+    const int ns = (int)c.s.size();
+    for (int q = 0; q < ns; ++q) {
+      const HSeg &s = c.s[q];
+      const int nextdir = q < ns - 1 ? c.s[q + 1].dir : (c.lj ? c.ljdir : s.dir);
+      const bool seg_lp = q > 0, seg_ln = q < ns - 1, seg_fj = q == 0 && c.fj, seg_lj = q == ns - 1 && c.lj;
+      const int nch = nchunks_of(s.len);
+      for (int t = 0; t < nch; ++t) {
+        const int off = t * CMAX, len = std::min(CMAX, s.len - off);
+        const bool first = t == 0, last = t == nch - 1;
+        uint8_t fl = (uint8_t)(s.dir | ((last ? nextdir : s.dir) << 2));
+        if (!first || seg_lp) fl |= F_LP;
+        if (!last || seg_ln) fl |= F_LN;
+        if (first && seg_fj) fl |= F_FJ;
+        if (last && seg_lj) fl |= F_LJ;
+        ChunkDesc cd;
+        std::memset(&cd, 0, sizeof(cd));
+        cd.i0 = (uint16_t)(s.i0 + off * step_i(s.dir));
+        cd.j0 = (uint16_t)(s.j0 + off * step_j(s.dir));
+        cd.len = (uint8_t)len;
+        cd.flags = fl;
+        cd.junc = jidx >= 0 ? (uint16_t)jidx : (uint16_t)0xFFFF;
+        const int tloc = w.nchunk;  // CTA-local chunk index
+        if (jd && (fl & F_FJ)) {
+          jd->row[jd->nend] = (uint16_t)(2 * tloc);
+          jd->dirs |= (uint8_t)(s.dir << (2 * jd->nend));
+          ++jd->nend;
+        }
+        if (jd && (fl & F_LJ)) {
+          jd->row[jd->nend] = (uint16_t)(len >= 2 ? 2 * tloc + 1 : 2 * tloc);
+          jd->dirs |= (uint8_t)((c.ljdir ^ 1) << (2 * jd->nend));
+          ++jd->nend;
+        }
+        P.chunk.push_back(cd);
+        ++w.nchunk;
+      }
+      w.nnode += s.len;
+    }
+  }
+}
+
+// Pack whole blocks into CTAs of at most nt chunks (largest first, next fit).
+void pack(const std::vector<HBlock> &blocks, const std::vector<int> &order, int nt, Packed &P) {
+  CtaWork w;
+  std::memset(&w, 0, sizeof(w));
+  auto flush = [&]() {
+    if (w.nchunk == 0 && w.njunc == 0) return;
+    P.cta.push_back(w);
+    CtaWork z;
+    std::memset(&z, 0, sizeof(z));
+    z.chunk0 = (int)P.chunk.size(); z.junc0 = (int)P.junc.size();
+    w = z;
+  };
+  for (int bi : order) {
+    const HBlock &b = blocks[bi];
+    if (w.nchunk + b.chunks > nt || w.njunc + (b.junc ? 1 : 0) > nt) flush();
+    emit_block(P, w, b);
+    P.total += b.nodes + (b.junc ? 1 : 0);
+  }
+  flush();
+}
+
+template <typename X>
+size_t align16(size_t n) { return (n * sizeof(X) + 15) & ~size_t(15); }
+
+mg_status upload(const Packed &P, int nt, WorkList &W) {
+  W.ncta = (int)P.cta.size();
+  W.nt = nt;
+  W.total_nodes = P.total;
+  if (W.ncta == 0) return MG_OK;
+  const size_t b0 = align16<CtaWork>(P.cta.size()), b1 = align16<ChunkDesc>(std::max<size_t>(P.chunk.size(), 1)),
+               b2 = align16<JuncDesc>(std::max<size_t>(P.junc.size(), 1));
+  char *mem = nullptr;
+  cudaError_t e = cudaMalloc(&mem, b0 + b1 + b2);
+  if (e != cudaSuccess) { set_error("cudaMalloc(work list)", e); return MG_ERR_ALLOC; }
+  W.mem = mem;
+  W.cta = reinterpret_cast<CtaWork *>(mem);
+  W.chunk = reinterpret_cast<ChunkDesc *>(mem + b0);
+  W.junc = reinterpret_cast<JuncDesc *>(mem + b0 + b1);
+  e = cudaMemcpy(W.cta, P.cta.data(), sizeof(CtaWork) * P.cta.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !P.chunk.empty())
+    e = cudaMemcpy(W.chunk, P.chunk.data(), sizeof(ChunkDesc) * P.chunk.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !P.junc.empty())
+    e = cudaMemcpy(W.junc, P.junc.data(), sizeof(JuncDesc) * P.junc.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { set_error("cudaMemcpy(work list)", e); return MG_ERR_CUDA; }
+  return MG_OK;
+}
+
+}  // namespace
+
+mg_status build_worklists(Grid &g, int level, int wl, int prec) {
+  Level &L = g.lev[level];
+  if (L.wl_built[wl][prec]) return MG_OK;
+  for (int colour = 0; colour < 2; ++colour) {
+    std::vector<HBlock> blocks;
+    switch (wl) {
+      case WL_TWEED: tweed_blocks(L.nx, L.ny, colour, blocks); break;
+      case WL_WIREFRAME: wireframe_blocks(L.nx, L.ny, colour, blocks); break;
+      case WL_ZEBRA_X: zebra_blocks(L.nx, L.ny, colour, true, blocks); break;
+      default: zebra_blocks(L.nx, L.ny, colour, false, blocks); break;
+    }
+    std::vector<int> small, large;
+    for (size_t bi = 0; bi < blocks.size(); ++bi) {
+      HBlock &b = blocks[bi];
+      b.nodes = 0;  // chain nodes (the junction is not kept in shared memory)
+      b.chunks = 0;
+      for (auto &c : b.ch)
+        for (auto &s : c.s) { b.nodes += s.len; b.chunks += nchunks_of(s.len); }
+      if (b.chunks > NT_LARGE) return MG_ERR_SIZE;
+      (b.chunks > NT_SMALL ? large : small).push_back((int)bi);
+    }
+    auto by_size = [&](int a, int b) { return blocks[a].chunks > blocks[b].chunks; };
+    std::stable_sort(small.begin(), small.end(), by_size);
+    std::stable_sort(large.begin(), large.end(), by_size);
+    Packed Ps, Pl;
+    pack(blocks, small, NT_SMALL, Ps);
+    pack(blocks, large, NT_LARGE, Pl);
+    mg_status st = upload(Ps, NT_SMALL, L.wl[wl][prec][colour][0]);
+    if (st == MG_OK) st = upload(Pl, NT_LARGE, L.wl[wl][prec][colour][1]);
+    if (st != MG_OK) return st;
+  }
+  L.wl_built[wl][prec] = true;
+  return MG_OK;
+}
+
+}  // namespace tmg

@@ -1,0 +1,457 @@
+// smooth.cu -- relaxation kernels of tweedmg for sm_103a.
+//
+// line_pass_kernel: one colour pass of a line smoother (tweed, wireframe,
+// zebra).  Every block of the colour is solved exactly (Sec. 3: the equation
+// is solved on all nodes of the block at once, the other colour held fixed).
+// A CTA owns whole blocks.  Each block is a set of chains (open tridiagonal
+// systems along straight runs that may turn corners) plus at most one
+// junction node:
+//   - tweed L-block (the paper's m = 2 case): one chain, no junction;
+//   - tweed cross / T (m = 4 / 3, Eq. mLThomas): one chain per leg, all legs
+//     coupled to the branch point, which is the junction;
+//   - wireframe ring (Eq. CircTri): the ring is opened at one corner node,
+//     which becomes the junction coupled to both ends of the remaining chain;
+//   - zebra lines, straight tweed lines, the wireframe centre line: one chain;
+//   - corner / centre points: a junction with no chain.
+//
+// The exact block solve is reorganised for parallelism, not approximated:
+//   phase 0  all threads: right-hand side of every chain node (f minus the
+//            neighbours outside the block) into shared memory;
+//   phase 1  one thread per chunk (<= CMAX consecutive nodes of a run):
+//            two eliminations across the chunk give the two reduced rows that
+//            couple the chunk's first / last node to the neighbouring chunks
+//            (partition method);
+//   phase 2  parallel cyclic reduction (pointer jumping) on the reduced
+//            system of all chunks, for two right-hand sides: the actual one
+//            (y) and the response to a unit junction value (z);
+//   phase 2b one thread per junction: its own row fixes the junction value
+//            (x_J = (r_J - sum k y)/(C_J + sum k z)), the m-legged / periodic
+//            Thomas step of the paper;
+//   phase 3  one thread per chunk: chunk ends X = y + x_J z, interior by
+//            Thomas with those ends;
+//   phase 4  all threads: write the block back to u.
+//
+// checker_kernel: one colour of red-black point Gauss-Seidel (Sec. 2).
+#include <cstdio>
+
+#include "mg_internal.h"
+
+namespace tmg {
+
+template <typename T>
+struct CoefP {
+  const T *W, *E, *S, *N;
+};
+
+__device__ __forceinline__ int di_of(int d) { return d == DIR_PX ? 1 : (d == DIR_MX ? -1 : 0); }
+__device__ __forceinline__ int dj_of(int d) { return d == DIR_PY ? 1 : (d == DIR_MY ? -1 : 0); }
+
+// Coefficient of row (i,j) for the neighbour one step in direction d.
+template <typename T>
+__device__ __forceinline__ T cf(const CoefP<T> &c, int i, int j, int d) {
+  return d == DIR_PX ? __ldg(c.E + i) : d == DIR_MX ? __ldg(c.W + i) : d == DIR_PY ? __ldg(c.N + j) : __ldg(c.S + j);
+}
+// C_ij = -(W_i + E_i + S_j + N_j).
+template <typename T>
+__device__ __forceinline__ T centre(const CoefP<T> &c, int i, int j) {
+  return -((__ldg(c.W + i) + __ldg(c.E + i)) + (__ldg(c.S + j) + __ldg(c.N + j)));
+}
+
+// Reciprocal used by the eliminations.  FP32: the fast reciprocal (within 2
+// ulp), ample for the FP32 correction equation.  FP64: Newton-Raphson
+// iteration r <- r + r (1 - x r), which doubles the number of correct bits per
+// step, started from the FP32 reciprocal (24 bits -> 48 -> 96); two fused
+// steps replace the much slower IEEE double division.  Valid while |x| and
+// 1/|x| lie inside the float range (grid spacings above ~1e-18).
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double rcp(double x) {
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+// Shared-memory index of slot s (slot 32c + q holds node q of chunk c): one
+// pad word per 32 slots, so that threads walking their own chunks in step hit
+// distinct banks (stride 33 words for float, 33 doubles for double).
+__device__ __forceinline__ int sidx(int s) { return s + (s >> 5); }
+
+// Geometry of one chunk: a straight run of m nodes in direction dir.  Along
+// the run only the two "along" coefficients vary (W/E for x-runs, S/N for
+// y-runs); the two perpendicular ones are constant and enter the diagonal
+// C = -(W + E + S + N) as the sum `cross`.
+template <typename T>
+struct ChunkGeom {
+  int i0, j0, m, dir, nd, fl, var0, step;
+  const T *lo_arr, *hi_arr;   // coefficient towards the predecessor / successor
+  T cross, clast, cnd;        // perpendicular sum; successor coefficient of the last node;
+                              // coefficient of the last node towards nextdir
+  __device__ __forceinline__ void init(const ChunkDesc &cd, const CoefP<T> &cp) {
+    i0 = cd.i0; j0 = cd.j0; m = cd.len; fl = cd.flags; dir = fl & 3; nd = (fl >> 2) & 3;
+    const bool xrun = dir < 2;
+    step = (dir == DIR_PX || dir == DIR_PY) ? 1 : -1;
+    var0 = xrun ? i0 : j0;
+    if (xrun) {
+      lo_arr = dir == DIR_PX ? cp.W : cp.E;
+      hi_arr = dir == DIR_PX ? cp.E : cp.W;
+      cross = __ldg(cp.S + j0) + __ldg(cp.N + j0);
+    } else {
+      lo_arr = dir == DIR_PY ? cp.S : cp.N;
+      hi_arr = dir == DIR_PY ? cp.N : cp.S;
+      cross = __ldg(cp.W + i0) + __ldg(cp.E + i0);
+    }
+    const int il = i0 + (m - 1) * di_of(dir), jl = j0 + (m - 1) * dj_of(dir);
+    cnd = cf(cp, il, jl, nd);
+    clast = (fl & F_LN) ? cnd : T(0);
+  }
+  __device__ __forceinline__ T lo_at(int q) const { return __ldg(lo_arr + var0 + (q < m ? q : m - 1) * step); }
+  __device__ __forceinline__ T hi_at(int q) const { return __ldg(hi_arr + var0 + (q < m ? q : m - 1) * step); }
+  __device__ __forceinline__ T a_of(int q, T lo) const { return (q > 0 || (fl & F_LP)) ? lo : T(0); }
+  __device__ __forceinline__ T c_of(int q, T hi) const { return q < m - 1 ? hi : clast; }
+  __device__ __forceinline__ T b_of(T lo, T hi) const { return -(cross + (lo + hi)); }
+};
+
+// One reduced row  a x_L + x + c x_U = (y, z), stored as a vector.
+template <typename T>
+struct __align__(4 * sizeof(T)) Row {
+  T a, c, y, z;
+};
+
+// Shared memory of one CTA: reduced rows, the slot arrays (right-hand side;
+// with SC also the two along coefficients of every node, written by the load
+// phase so that the eliminations read no global memory), junction values and
+// reduced-row links.
+template <typename T, int NT, bool SC>
+struct LineSmem {
+  static constexpr size_t rows = sizeof(Row<T>) * 2 * NT;
+  static constexpr size_t slots = 33 * NT;                // 32 slots + 1 pad per chunk
+  static constexpr size_t nodes = sizeof(T) * slots * (SC ? 3 : 1);
+  static constexpr size_t bytes = rows + nodes + sizeof(T) * NT + sizeof(short2) * 2 * NT;
+};
+
+// Slot s of the CTA: chunk c = s / 32, node q = s % 32.  Returns false for
+// the unused tail slots of ragged chunks.
+__device__ __forceinline__ bool slot_node(const ChunkDesc *__restrict__ chunks, int s, int &i, int &j,
+                                          unsigned &incl) {
+  const ChunkDesc cd = chunks[s >> 5];
+  const int q = s & 31;
+  if (q >= cd.len) return false;
+  const int dir = cd.flags & 3, nd = (cd.flags >> 2) & 3;
+  i = cd.i0 + q * di_of(dir);
+  j = cd.j0 + q * dj_of(dir);
+  // neighbours that go to the right-hand side: all but the chain neighbours
+  // and the junction
+  unsigned m = 0xFu;
+  if (q > 0 || (cd.flags & (F_LP | F_FJ))) m &= ~(1u << (dir ^ 1));
+  if (q < cd.len - 1) m &= ~(1u << dir);
+  else if (cd.flags & (F_LN | F_LJ)) m &= ~(1u << nd);
+  incl = m | ((unsigned)dir << 5);
+  return true;
+}
+
+template <typename T, int NT, bool SC>
+__global__ void __launch_bounds__(NT, NT == NT_SMALL ? 2 : 1)
+    line_pass_kernel(const CtaWork *__restrict__ works, const ChunkDesc *__restrict__ chunks_all,
+                     const JuncDesc *__restrict__ juncs_all, CoefP<T> cp, int nx1, T *__restrict__ u,
+                     const T *__restrict__ f) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Row<T> *rv = reinterpret_cast<Row<T> *>(smem_raw);                       // 2*NT reduced rows
+  T *node = reinterpret_cast<T *>(smem_raw + LineSmem<T, NT, SC>::rows);   // 32*NT slots (skewed)
+  T *clo = node + 33 * NT;                                                 // along coefficients (SC)
+  T *chi = clo + 33 * NT;
+  T *xj = node + (SC ? 3 : 1) * 33 * NT;                                   // junction values
+  short2 *lu = reinterpret_cast<short2 *>(xj + NT);                        // reduced-row links (L, U)
+
+  const CtaWork w = works[blockIdx.x];
+  const ChunkDesc *chunks = chunks_all + w.chunk0;
+  const JuncDesc *juncs = juncs_all + w.junc0;
+  const int tid = threadIdx.x;
+  const int nslot = 32 * w.nchunk;
+  constexpr int U = 4;  // slots per thread per batch in the load phase
+
+  // ---- phase 0: right-hand sides of all chain nodes (batches of U slots per
+  // thread; all loads of a batch are issued before any is used)
+  for (int s0 = tid; s0 < nslot; s0 += U * NT) {
+    size_t pk[U];
+    unsigned inc[U];
+    int ik[U], jk[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int s = s0 + k * NT;
+      inc[k] = 0; ik[k] = 1; jk[k] = 1;
+      if (s < nslot && slot_node(chunks, s, ik[k], jk[k], inc[k])) inc[k] |= 16u;
+      pk[k] = (size_t)jk[k] * nx1 + ik[k];
+    }
+    T fv[U], uw[U], ue[U], us[U], un[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const size_t p = pk[k];
+      fv[k] = (inc[k] & 16u) ? f[p] : T(0);
+      uw[k] = (inc[k] & 2u) ? u[p - 1] : T(0);
+      ue[k] = (inc[k] & 1u) ? u[p + 1] : T(0);
+      us[k] = (inc[k] & 8u) ? u[p - nx1] : T(0);
+      un[k] = (inc[k] & 4u) ? u[p + nx1] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      if (inc[k] & 16u) {
+        const int i = ik[k], j = jk[k];
+        const T cw = __ldg(cp.W + i), ce = __ldg(cp.E + i), cs = __ldg(cp.S + j), cn = __ldg(cp.N + j);
+        const int si = sidx(s0 + k * NT);
+        node[si] = fv[k] - cw * uw[k] - ce * ue[k] - cs * us[k] - cn * un[k];
+        if constexpr (SC) {
+          const int dir = (inc[k] >> 5) & 3;
+          clo[si] = dir == DIR_PX ? cw : dir == DIR_MX ? ce : dir == DIR_PY ? cs : cn;
+          chi[si] = dir == DIR_PX ? ce : dir == DIR_MX ? cw : dir == DIR_PY ? cn : cs;
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 1: reduced rows of every chunk.  Two independent eliminations
+  // run interleaved: nodes 1..m-2 towards node m-1 (the "hi" row, in terms of
+  // x_0 and x_m) and nodes m-2..1 towards node 0 (the "lo" row, in terms of
+  // x_{-1} and x_{m-1}).  Loop indices are compile-time so that the chunk's
+  // x_{-1} and x_{m-1}).  Loop indices are compile-time, so the shared-memory (or L1) loads can be hoisted.
+  const int R = 2 * w.nchunk;
+  if (tid < w.nchunk) {
+    const ChunkDesc cd = chunks[tid];
+    ChunkGeom<T> g;
+    g.init(cd, cp);
+    const int m = g.m, base = 32 * tid;
+    auto slot = [&](int q) { return sidx(base + (q < m ? q : m - 1)); };
+    auto LO = [&](int q) -> T { if constexpr (SC) return clo[slot(q)]; else return g.lo_at(q); };
+    auto HI = [&](int q) -> T { if constexpr (SC) return chi[slot(q)]; else return g.hi_at(q); };
+    auto DD = [&](int q) -> T { return node[slot(q)]; };
+    const T kf = (g.fl & F_FJ) ? cf(cp, g.i0, g.j0, g.dir ^ 1) : T(0);
+    const T kl = (g.fl & F_LJ) ? g.cnd : T(0);
+    const T l0 = LO(0), h0 = HI(0), d0 = DD(0);
+    const T a0 = g.a_of(0, l0), b0 = g.b_of(l0, h0), c0 = g.c_of(0, h0);
+    Row<T> rlo, rhi;
+    rhi.a = T(0); rhi.c = T(0); rhi.y = T(0); rhi.z = T(0);
+    if (m <= 2) {
+      const T rb = rcp(b0);
+      rlo.a = a0 * rb; rlo.c = c0 * rb; rlo.y = d0 * rb; rlo.z = -(m == 1 ? kf + kl : kf) * rb;
+    }
+    if (m >= 2) {
+      const T l1 = LO(1), h1 = HI(1);
+      T rinv_f = rcp(g.b_of(l1, h1));
+      T al = g.a_of(1, l1) * rinv_f, ga = g.c_of(1, h1) * rinv_f, de = DD(1) * rinv_f;
+      T ah = T(0), ch = T(0), dh = T(0);
+#pragma unroll
+      for (int k = 1; k <= CMAX - 2; ++k) {
+        const int qf = k + 1;  // forward step
+        if (qf < m) {
+          const T lq = LO(qf), hq = HI(qf);
+          const T a = g.a_of(qf, lq), c = g.c_of(qf, hq);
+          const T ri = rcp(g.b_of(lq, hq) - a * ga);
+          al = -a * al * ri;
+          ga = c * ri;
+          de = (DD(qf) - a * de) * ri;
+          rinv_f = ri;
+        }
+        const int qb = CMAX - 1 - k;  // backward step (descending)
+        if (qb <= m - 2) {
+          const T lq = LO(qb), hq = HI(qb);
+          const T a = g.a_of(qb, lq), c = g.c_of(qb, hq);
+          if (qb == m - 2) {
+            const T ri = rcp(g.b_of(lq, hq));
+            ah = a * ri; ch = c * ri; dh = DD(qb) * ri;
+          } else {
+            const T ri = rcp(g.b_of(lq, hq) - c * ah);
+            ah = a * ri;
+            ch = -c * ch * ri;
+            dh = (DD(qb) - c * dh) * ri;
+          }
+        }
+      }
+      rhi.a = al; rhi.c = ga; rhi.y = de; rhi.z = -kl * rinv_f;
+      if (m >= 3) {
+        const T rd = rcp(b0 - c0 * ah);
+        rlo.a = a0 * rd; rlo.c = -c0 * ch * rd; rlo.y = (d0 - c0 * dh) * rd; rlo.z = -kf * rd;
+      }
+    }
+    short Llo = -1, Ulo;
+    if (g.fl & F_LP) Llo = (short)(chunks[tid - 1].len >= 2 ? 2 * (tid - 1) + 1 : 2 * (tid - 1));
+    if (m >= 2) Ulo = (short)(2 * tid + 1);
+    else Ulo = (g.fl & F_LN) ? (short)(2 * (tid + 1)) : (short)-1;
+    rv[2 * tid] = rlo;
+    rv[2 * tid + 1] = rhi;
+    lu[2 * tid] = make_short2(Llo, Ulo);
+    lu[2 * tid + 1] = (m >= 2) ? make_short2((short)(2 * tid), (g.fl & F_LN) ? (short)(2 * (tid + 1)) : (short)-1)
+                               : make_short2(-1, -1);
+  }
+  __syncthreads();
+
+  // ---- phase 2: parallel cyclic reduction (pointer jumping) on the reduced
+  // system, two right-hand sides (y: data, z: unit junction value)
+  for (int it = 0; it < 24; ++it) {
+    Row<T> nr[2];
+    short2 nl[2];
+    bool upd[2] = {false, false};
+    bool more = false;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int r = tid + k * NT;
+      if (r < R) {
+        const short2 l = lu[r];
+        if (l.x >= 0 || l.y >= 0) {
+          const Row<T> me = rv[r];
+          Row<T> L = {T(0), T(0), T(0), T(0)}, Uu = {T(0), T(0), T(0), T(0)};
+          short LL = -1, UU = -1;
+          if (l.x >= 0) { L = rv[l.x]; LL = lu[l.x].x; }
+          if (l.y >= 0) { Uu = rv[l.y]; UU = lu[l.y].y; }
+          const T beta = rcp(T(1) - me.a * L.c - me.c * Uu.a);
+          nr[k].a = -me.a * L.a * beta;
+          nr[k].c = -me.c * Uu.c * beta;
+          nr[k].y = (me.y - me.a * L.y - me.c * Uu.y) * beta;
+          nr[k].z = (me.z - me.a * L.z - me.c * Uu.z) * beta;
+          nl[k] = make_short2(LL, UU);
+          upd[k] = true;
+          more |= (LL >= 0 || UU >= 0);
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      if (upd[k]) { rv[tid + k * NT] = nr[k]; lu[tid + k * NT] = nl[k]; }
+    if (!__syncthreads_or(more)) break;
+  }
+
+  // ---- phase 2b: junction rows
+  if (tid < w.njunc) {
+    const JuncDesc jd = juncs[tid];
+    const int i = jd.i, j = jd.j;
+    const size_t p = (size_t)j * nx1 + i;
+    unsigned att = 0;
+    for (int e = 0; e < jd.nend; ++e) att |= 1u << ((jd.dirs >> (2 * e)) & 3);
+    T r = f[p];
+    if (!(att & 2u)) r -= __ldg(cp.W + i) * u[p - 1];
+    if (!(att & 1u)) r -= __ldg(cp.E + i) * u[p + 1];
+    if (!(att & 8u)) r -= __ldg(cp.S + j) * u[p - nx1];
+    if (!(att & 4u)) r -= __ldg(cp.N + j) * u[p + nx1];
+    T num = r, den = centre(cp, i, j);
+    for (int e = 0; e < jd.nend; ++e) {
+      const T k = cf(cp, i, j, (jd.dirs >> (2 * e)) & 3);
+      const Row<T> re = rv[jd.row[e]];
+      num -= k * re.y;
+      den += k * re.z;
+    }
+    const T x = num / den;
+    u[p] = x;
+    xj[tid] = x;
+  }
+  __syncthreads();
+
+  // ---- phase 3: chunk ends from the reduced solution, interiors by Thomas
+  if (tid < w.nchunk) {
+    const ChunkDesc cd = chunks[tid];
+    ChunkGeom<T> g;
+    g.init(cd, cp);
+    const int m = g.m, base = 32 * tid;
+    const T jx = (cd.junc != 0xFFFF) ? xj[cd.junc] : T(0);
+    const Row<T> r0 = rv[2 * tid], r1 = rv[2 * tid + 1];
+    const T xlo = r0.y + jx * r0.z;
+    const T xhi = (m >= 2) ? r1.y + jx * r1.z : xlo;
+    if (m >= 3) {
+      auto slot = [&](int q) { return sidx(base + (q < m ? q : m - 1)); };
+      auto LO = [&](int q) -> T { if constexpr (SC) return clo[slot(q)]; else return g.lo_at(q); };
+      auto HI = [&](int q) -> T { if constexpr (SC) return chi[slot(q)]; else return g.hi_at(q); };
+      T cpv[CMAX];
+      T dprev = xlo;
+#pragma unroll
+      for (int q = 1; q < CMAX - 1; ++q) {
+        if (q <= m - 2) {
+          const T lq = LO(q), hq = HI(q);
+          const T a = g.a_of(q, lq), b = g.b_of(lq, hq), c = g.c_of(q, hq);
+          T dq = node[sidx(base + q)] - a * dprev;
+          if (q == m - 2) dq -= c * xhi;
+          const T ri = (q == 1) ? rcp(b) : rcp(b - a * cpv[q - 1]);
+          cpv[q] = c * ri;
+          dprev = dq * ri;
+          node[sidx(base + q)] = dprev;
+        }
+      }
+      T xn = dprev;  // x_{m-2}
+#pragma unroll
+      for (int q = CMAX - 3; q >= 1; --q) {
+        if (q <= m - 3) {
+          xn = node[sidx(base + q)] - cpv[q] * xn;
+          node[sidx(base + q)] = xn;
+        }
+      }
+    }
+    node[sidx(base)] = xlo;
+    if (m >= 2) node[sidx(base + m - 1)] = xhi;
+  }
+  __syncthreads();
+
+  // ---- phase 4: write the block back
+  for (int s = tid; s < nslot; s += NT) {
+    int i, j;
+    unsigned inc;
+    if (slot_node(chunks, s, i, j, inc)) u[(size_t)j * nx1 + i] = node[sidx(s)];
+  }
+}
+
+template <typename T>
+static CoefP<T> coefs_of(const Level &L);
+template <>
+CoefP<double> coefs_of<double>(const Level &L) { return {L.W64, L.E64, L.S64, L.N64}; }
+template <>
+CoefP<float> coefs_of<float>(const Level &L) { return {L.W32, L.E32, L.S32, L.N32}; }
+
+template <typename T, int NT>
+static cudaError_t launch_shape(const Level &L, const WorkList &w, T *u, const T *f, cudaStream_t s) {
+  constexpr bool SC = sizeof(T) == 4;  // FP64 keeps the coefficients in L1 (smem is too small)
+  constexpr size_t smem = LineSmem<T, NT, SC>::bytes;
+  auto kern = line_pass_kernel<T, NT, SC>;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  kern<<<w.ncta, NT, smem, s>>>(w.cta, w.chunk, w.junc, coefs_of<T>(L), L.nx + 1, u, f);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_line_pass(const Level &L, const WorkList &w, T *u, const T *f, cudaStream_t s) {
+  if (w.ncta == 0) return cudaSuccess;
+  return w.nt == NT_SMALL ? launch_shape<T, NT_SMALL>(L, w, u, f, s) : launch_shape<T, NT_LARGE>(L, w, u, f, s);
+}
+
+template cudaError_t launch_line_pass<double>(const Level &, const WorkList &, double *, const double *, cudaStream_t);
+template cudaError_t launch_line_pass<float>(const Level &, const WorkList &, float *, const float *, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Red-black point Gauss-Seidel, one colour (red = (i+j) even).  One thread per
+// node of the colour; blockIdx.y = interior row.
+template <typename T>
+__global__ void checker_kernel(CoefP<T> cp, int nx, int colour, T *__restrict__ u, const T *__restrict__ f) {
+  const int j = blockIdx.y + 1;
+  const int i0 = ((j + colour) & 1) ? 1 : 2;   // first interior i with (i+j)%2 == colour
+  const int i = i0 + 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= nx) return;
+  const int nx1 = nx + 1;
+  const size_t p = (size_t)j * nx1 + i;
+  const T w = __ldg(cp.W + i), e = __ldg(cp.E + i), s = __ldg(cp.S + j), n = __ldg(cp.N + j);
+  const T r = f[p] - w * u[p - 1] - e * u[p + 1] - s * u[p - nx1] - n * u[p + nx1];
+  u[p] = r / (-((w + e) + (s + n)));
+}
+
+template <typename T>
+cudaError_t launch_checker_pass(const Level &L, int colour, T *u, const T *f, cudaStream_t s) {
+  const int half = L.nx / 2 + 1;
+  dim3 block(128), grid((half + 127) / 128, L.ny - 1);
+  checker_kernel<T><<<grid, block, 0, s>>>(coefs_of<T>(L), L.nx, colour, u, f);
+  return cudaGetLastError();
+}
+template cudaError_t launch_checker_pass<double>(const Level &, int, double *, const double *, cudaStream_t);
+template cudaError_t launch_checker_pass<float>(const Level &, int, float *, const float *, cudaStream_t);
+
+}  // namespace tmg

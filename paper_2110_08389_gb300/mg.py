@@ -1,0 +1,262 @@
+"""Python binding of the tweedmg C ABI (``include/mg.h``).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``_build/libtweedmg.so``.  Arrays are torch CUDA tensors (float64 or float32,
+contiguous, shape ``(ny+1, nx+1)``); streams default to torch's current
+stream.  There is no CPU fallback: loading fails loudly when the library has
+not been built (``python -m paper_2110_08389_gb300.build``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtweedmg.so")
+
+# enums (include/mg.h)
+OK, ERR_INVALID_ARG, ERR_SIZE, ERR_CUDA, ERR_NOT_CONVERGED, ERR_NONFINITE, ERR_TIMEOUT, ERR_ALLOC, \
+    ERR_UNSUPPORTED = range(9)
+CHECKERBOARD, ZEBRA_X, ZEBRA_Y, ALT_ZEBRA, TWEED, WIREFRAME, ALT_TW = range(7)
+SMOOTHERS = {"checkerboard": CHECKERBOARD, "zebra_x": ZEBRA_X, "zebra_y": ZEBRA_Y, "alt_zebra": ALT_ZEBRA,
+             "tweed": TWEED, "wireframe": WIREFRAME, "alt_tw": ALT_TW}
+F64, F32 = 0, 1
+PREC_F64, PREC_F32_REFINE = 0, 1
+HW, FW = 0, 1
+
+# every symbol include/mg.h declares
+EXPORTS = ["mg_setup_grid", "mg_destroy", "mg_num_levels", "mg_level_shape", "mg_smooth_tweed",
+           "mg_smooth_wireframe", "mg_smooth", "mg_colour_pass", "mg_residual_restrict", "mg_prolong_add",
+           "mg_residual", "mg_coarse_solve", "mg_vcycle", "mg_solve", "mg_solve_adjoint",
+           "mg_default_params", "mg_status_string", "mg_last_error"]
+
+
+class MGError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{what}: status {status} ({detail})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("smoother", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("cycle", ctypes.c_int), ("restriction", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_cycles", ctypes.c_int), ("max_outer", ctypes.c_int), ("inner_cycles", ctypes.c_int),
+                ("use_initial_guess", ctypes.c_int), ("tol", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int), ("outer_iters", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("conv_factor", ctypes.c_double), ("ms", ctypes.c_double),
+                ("history", ctypes.POINTER(ctypes.c_double)), ("history_cap", ctypes.c_int),
+                ("history_len", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it is missing -- no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"tweedmg CUDA library not built: {path} missing "
+                           "(run python -m paper_2110_08389_gb300.build)")
+    lib = ctypes.CDLL(path)
+    vp, i, i64p = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)
+    sig = {
+        "mg_setup_grid": (i, [ctypes.POINTER(vp), i, i64p, ctypes.POINTER(ctypes.c_void_p), i, vp]),
+        "mg_destroy": (None, [vp]),
+        "mg_num_levels": (i, [vp]),
+        "mg_level_shape": (i, [vp, i, i64p, i64p]),
+        "mg_smooth_tweed": (i, [vp, i, vp, vp, i, i, vp]),
+        "mg_smooth_wireframe": (i, [vp, i, vp, vp, i, i, vp]),
+        "mg_smooth": (i, [vp, i, i, vp, vp, i, i, vp]),
+        "mg_colour_pass": (i, [vp, i, i, i, vp, vp, i, vp]),
+        "mg_residual_restrict": (i, [vp, i, i, vp, vp, vp, vp, i, vp]),
+        "mg_prolong_add": (i, [vp, i, vp, vp, i, vp]),
+        "mg_residual": (i, [vp, i, vp, vp, vp, i, vp]),
+        "mg_coarse_solve": (i, [vp, vp, vp, i, vp]),
+        "mg_vcycle": (i, [vp, vp, vp, ctypes.POINTER(Params), vp]),
+        "mg_solve": (i, [vp, vp, vp, ctypes.POINTER(Params), ctypes.POINTER(Info), vp]),
+        "mg_solve_adjoint": (i, [vp, vp, vp, ctypes.POINTER(Params), ctypes.POINTER(Info), vp]),
+        "mg_default_params": (None, [ctypes.POINTER(Params)]),
+        "mg_status_string": (ctypes.c_char_p, [i]),
+        "mg_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, what: str, ok=(OK,)):
+    if st not in ok:
+        lib = load()
+        raise MGError(st, what, f"{lib.mg_status_string(st).decode()}; {lib.mg_last_error().decode()}")
+    return st
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return F64
+    if t.dtype == torch.float32:
+        return F32
+    raise TypeError("tweedmg arrays are float64 or float32")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("tweedmg arrays must be contiguous CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@dataclass
+class SolveResult:
+    status: int
+    cycles: int
+    outer_iters: int
+    rel_res: float
+    conv_factor: float
+    ms: float
+    history: np.ndarray
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().mg_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "smoother" and isinstance(v, str):
+            v = SMOOTHERS[v]
+        if k == "precision" and isinstance(v, str):
+            v = {"f64": PREC_F64, "f32_refine": PREC_F32_REFINE}[v]
+        if k == "restriction" and isinstance(v, str):
+            v = {"hw": HW, "fw": FW}[v.lower()]
+        if k == "cycle" and isinstance(v, str):
+            v = {"V": 1, "W": 2}[v.upper()]
+        setattr(p, k, v)
+    return p
+
+
+class Grid:
+    """mg_setup_grid on host coordinate arrays x (nx+1) and y (ny+1)."""
+
+    def __init__(self, x, y, precision_mask: int = 3, stream=None):
+        self.lib = load()
+        self.x = np.ascontiguousarray(x, dtype=np.float64)
+        self.y = np.ascontiguousarray(y, dtype=np.float64)
+        n = (ctypes.c_int64 * 2)(len(self.x) - 1, len(self.y) - 1)
+        coords = (ctypes.c_void_p * 2)(self.x.ctypes.data, self.y.ctypes.data)
+        h = ctypes.c_void_p()
+        _check(self.lib.mg_setup_grid(ctypes.byref(h), 2, n, coords, precision_mask,
+                                      _stream(stream) if stream is not None else None), "mg_setup_grid")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nlev(self) -> int:
+        return self.lib.mg_num_levels(self.h)
+
+    def shape(self, level: int = 0):
+        nx, ny = ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib.mg_level_shape(self.h, level, ctypes.byref(nx), ctypes.byref(ny)), "mg_level_shape")
+        return ny.value + 1, nx.value + 1
+
+    # ---- relaxation
+    def smooth(self, u, f, smoother="tweed", sweeps=1, level=0, stream=None):
+        sm = SMOOTHERS[smoother] if isinstance(smoother, str) else smoother
+        _check(self.lib.mg_smooth(self.h, level, sm, _ptr(u), _ptr(f), sweeps, _dtype_code(u), _stream(stream)),
+               "mg_smooth")
+        return u
+
+    def smooth_tweed(self, u, f, sweeps=1, level=0, stream=None):
+        _check(self.lib.mg_smooth_tweed(self.h, level, _ptr(u), _ptr(f), sweeps, _dtype_code(u), _stream(stream)),
+               "mg_smooth_tweed")
+        return u
+
+    def smooth_wireframe(self, u, f, sweeps=1, level=0, stream=None):
+        _check(self.lib.mg_smooth_wireframe(self.h, level, _ptr(u), _ptr(f), sweeps, _dtype_code(u),
+                                            _stream(stream)), "mg_smooth_wireframe")
+        return u
+
+    def colour_pass(self, u, f, smoother="tweed", colour=0, level=0, stream=None):
+        sm = SMOOTHERS[smoother] if isinstance(smoother, str) else smoother
+        _check(self.lib.mg_colour_pass(self.h, level, sm, colour, _ptr(u), _ptr(f), _dtype_code(u),
+                                       _stream(stream)), "mg_colour_pass")
+        return u
+
+    # ---- transfers
+    def residual(self, u, f, d, level=0, stream=None):
+        _check(self.lib.mg_residual(self.h, level, _ptr(u), _ptr(f), _ptr(d), _dtype_code(u), _stream(stream)),
+               "mg_residual")
+        return d
+
+    def residual_restrict(self, u, f, fc, uc=None, restriction=FW, level=0, stream=None):
+        _check(self.lib.mg_residual_restrict(self.h, level, restriction, _ptr(u), _ptr(f), _ptr(fc), _ptr(uc),
+                                             _dtype_code(u), _stream(stream)), "mg_residual_restrict")
+        return fc
+
+    def prolong_add(self, uc, u, level=0, stream=None):
+        _check(self.lib.mg_prolong_add(self.h, level, _ptr(uc), _ptr(u), _dtype_code(u), _stream(stream)),
+               "mg_prolong_add")
+        return u
+
+    def coarse_solve(self, u, f, stream=None):
+        _check(self.lib.mg_coarse_solve(self.h, _ptr(u), _ptr(f), _dtype_code(u), _stream(stream)),
+               "mg_coarse_solve")
+        return u
+
+    # ---- cycles and solves
+    def vcycle(self, u, f, params: Params | None = None, stream=None, **kw):
+        p = params or default_params(**kw)
+        _check(self.lib.mg_vcycle(self.h, _ptr(u), _ptr(f), ctypes.byref(p), _stream(stream)), "mg_vcycle")
+        return u
+
+    def _solve(self, fn, name, u, f, params, stream, history_cap, kw, raise_on_fail):
+        p = params or default_params(**kw)
+        hist = np.zeros(max(history_cap, 1))
+        info = Info()
+        info.history = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        info.history_cap = history_cap
+        st = fn(self.h, _ptr(u), _ptr(f), ctypes.byref(p), ctypes.byref(info), _stream(stream))
+        if raise_on_fail:
+            _check(st, name)
+        else:
+            _check(st, name, ok=(OK, ERR_NOT_CONVERGED, ERR_NONFINITE))
+        return SolveResult(st, info.cycles, info.outer_iters, info.rel_res, info.conv_factor, info.ms,
+                           hist[: info.history_len].copy())
+
+    def solve(self, u, f, params: Params | None = None, stream=None, history_cap=256, raise_on_fail=False, **kw):
+        return self._solve(self.lib.mg_solve, "mg_solve", u, f, params, stream, history_cap, kw, raise_on_fail)
+
+    def solve_adjoint(self, lam, rhs, params: Params | None = None, stream=None, history_cap=256,
+                      raise_on_fail=False, **kw):
+        return self._solve(self.lib.mg_solve_adjoint, "mg_solve_adjoint", lam, rhs, params, stream, history_cap,
+                           kw, raise_on_fail)

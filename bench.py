@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark: seconds to ||f - L u||_2 / ||f||_2 <= 1e-10 for the 4097 x 4097
+tweed multigrid problem (wall-clustered tanh grid, spacing ratio 1000,
+f ~ N(0,1) seed 1), FP32 smoothing + FP64 iterative refinement, with the
+plain FP64 solve timed beside it, plus the roofline of the dominant kernel
+(one FP32 tweed colour pass) and the CPU oracle as the baseline.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  Multi-GPU: one independent replica per rank (the
+solve does not shard); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_INTERVALS = 4096
+RATIO = 1000.0
+SEED = 1
+TOL = 1e-10
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "line_pass_f32_4097_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nu", type=int, nargs=2, default=[1, 1])
+    ap.add_argument("--inner", type=int, default=4)
+    ap.add_argument("--n", type=int, default=N_INTERVALS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_2110_08389_gb300 import inputs as I
+    c = I.c_for_ratio(n, RATIO, "wall")
+    x = I.wall_coords(n, c)
+    f = I.rhs_gaussian(n + 1, n + 1, SEED)
+    return x, c, f
+
+
+def config_dict(args, c):
+    return {"workload": f"2D Poisson {args.n + 1}x{args.n + 1}, wall tanh c={c:.6f} (spacing ratio {RATIO:g}), "
+                        f"f~N(0,1) seed {SEED}, tweed V({args.nu[0]},{args.nu[1]}), full weighting, bilinear, "
+                        f"to ||r||/||f||<={TOL:g}",
+            "nodes": (args.n + 1) ** 2, "smoother": "tweed", "nu1": args.nu[0], "nu2": args.nu[1],
+            "inner_cycles": args.inner, "tol": TOL,
+            "l2": "inputs (u, f: 2 x 134 MB FP64) larger than L2 (129 MB)"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.25)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.out.flush()
+        rows = []
+        for line in open(self.out.name):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                try:
+                    rows.append((float(p[1]), float(p[2]), p[5], p[6], p[7], p[8]))
+                except ValueError:
+                    pass
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[2 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(v, pg, device=None):
+    if pg is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+# ------------------------------------------------------------------ oracle
+
+def oracle_cycles(x, f, nu, steps, warmup):
+    """Time V-cycles of the CPU oracle on the full workload; returns
+    (seconds per cycle, cycles to TOL or None, cycles run)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    P = oracle.Problem(x, x)
+    u = np.zeros_like(f)
+    fn = math.sqrt(float(np.sum(f[1:-1, 1:-1] ** 2)))
+    times, reached = [], None
+    for k in range(warmup + steps):
+        t0 = time.perf_counter()
+        P.cycle(u, f, "tweed", nu[0], nu[1], 1, oracle.FW)
+        dt = time.perf_counter() - t0
+        r = P.residual(u, f)
+        rel = math.sqrt(float(np.sum(r[1:-1, 1:-1] ** 2))) / fn
+        if reached is None and rel <= TOL:
+            reached = k + 1
+        if k >= warmup:
+            times.append(dt)
+    return statistics.mean(times), reached, warmup + steps
+
+
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        barrier(pg)
+        return
+    x, c, f = workload(args.n)
+    t0 = time.time()
+    per_cycle, reached, ran = oracle_cycles(x, f, args.nu, args.steps, args.warmup)
+    cycles = reached if reached is not None else ran
+    value = per_cycle * cycles
+    line = {"metric": "s to rel. residual 1e-10, 4097^2 tweed MG (FP64 CPU oracle)", "value": value, "unit": "s",
+            "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per_cycle * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic", "config": config_dict(args, c),
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": f"one step = one FP64 V({args.nu[0]},{args.nu[1]}) cycle of the C oracle "
+                                       f"on the full grid; value = mean s/cycle x {cycles} cycles to 1e-10"
+                                       + ("" if reached else " (tolerance not reached in the sample: cycles run)")},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.time() - t0}
+    print(json.dumps(line), flush=True)
+    barrier(pg)
+
+
+# ------------------------------------------------------------------- ours
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2110_08389_gb300 import build, mg
+    build.build()
+    x, c, f_h = workload(args.n)
+    n1 = args.n + 1
+    grid = mg.Grid(x, x)
+    stream = torch.cuda.current_stream()
+    f = torch.tensor(f_h, device=dev)
+    u = torch.zeros((n1, n1), dtype=torch.float64, device=dev)
+    p32 = mg.default_params(smoother="tweed", nu1=args.nu[0], nu2=args.nu[1], precision="f32_refine",
+                            tol=TOL, inner_cycles=args.inner, max_outer=20, max_cycles=200)
+    p64 = mg.default_params(smoother="tweed", nu1=args.nu[0], nu2=args.nu[1], precision="f64", tol=TOL,
+                            max_cycles=200)
+
+    def solve(params):
+        return grid.solve(u, f, params)
+
+    for _ in range(args.warmup):
+        res = solve(p32)
+    torch.cuda.synchronize()
+    barrier(pg)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = mg.kernel_launches()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            res = solve(p32)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = (mg.kernel_launches() - l0) // max(args.steps, 1)
+    ms = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms, pg, dev)
+    status32 = res.status
+    rel32, outer32, cyc32 = res.rel_res, res.outer_iters, res.cycles
+    u32 = u.clone()
+
+    # plain FP64 solve on the same problem (the comparison of the metric)
+    solve(p64)
+    torch.cuda.synchronize()
+    k64 = max(1, min(args.steps, 3))
+    e0.record(stream)
+    for _ in range(k64):
+        r64 = solve(p64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = max_over_ranks(e0.elapsed_time(e1) / k64, pg, dev)
+    err32 = float((u32 - u).abs().max() / u.abs().max())
+
+    # end to end through the public API with host buffers
+    f_pin = torch.tensor(f_h).pin_memory()
+    u_pin = torch.zeros((n1, n1), dtype=torch.float64).pin_memory()
+    out_pin = torch.empty((n1, n1), dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        u.copy_(u_pin, non_blocking=True)
+        f.copy_(f_pin, non_blocking=True)
+        grid.solve(u, f, p32)
+        out_pin.copy_(u, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, pg, dev)
+
+    # roofline of the dominant kernel: one FP32 tweed colour pass on the finest
+    # level, timed alone on the launching stream (CUDA events)
+    uu = torch.zeros((n1, n1), dtype=torch.float32, device=dev)
+    ff = f.float()
+    for _ in range(3):
+        grid.colour_pass(uu, ff, "tweed", 0)
+    reps = 20
+    torch.cuda.synchronize()
+    l0 = mg.kernel_launches()
+    e0.record(stream)
+    for r in range(reps):
+        grid.colour_pass(uu, ff, "tweed", r & 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pass_launches = (mg.kernel_launches() - l0) / reps
+    pass_ms = e0.elapsed_time(e1) / reps
+    algo_bytes = 2 * 4 * n1 * n1  # read u (w) + f of the colour (w/2) + write u of the colour (w/2), w = 4 B
+    peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = algo_bytes / (pass_ms * 1e-3) / 1e9
+    traffic = None
+    if os.path.exists(TRAFFIC):
+        import hashlib
+        tr = json.load(open(TRAFFIC))
+        src = open(os.path.join(ROOT, "paper_2110_08389_gb300", "csrc", "smooth.cu"), "rb").read()
+        if tr.get("smooth_cu_sha256") == hashlib.sha256(src).hexdigest():
+            traffic = tr.get("traffic_bytes_per_launch")
+
+    line = {"metric": "s to rel. residual 1e-10, 4097^2 tweed MG: FP32+refine vs FP64; HBM %peak",
+            "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic", "config": config_dict(args, c),
+            "status": status32, "rel_res": rel32, "outer_iters": outer32, "inner_cycles_total": cyc32,
+            "fp64": {"s": ms64 / 1e3, "cycles": r64.cycles, "rel_res": r64.rel_res, "status": r64.status},
+            "speedup_vs_fp64": ms64 / ms, "f32_refine_vs_f64_solution_maxrel": err32,
+            "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": 2 * 8 * n1 * n1,
+                    "d2h_bytes_per_step": 8 * n1 * n1},
+            "gpu_launches": int(launches),
+            "roofline": {"kernel": "line_pass_kernel<float> (one tweed colour pass, finest level)",
+                         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "launch_ms": pass_ms,
+                         "launches_per_pass": pass_launches, "algo_bytes_per_launch": algo_bytes,
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"},
+            "clocks": clk.summary()}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        per_cycle, reached, ran = oracle_cycles(x, f_h, args.nu, 3, 1)
+        cycles = r64.cycles
+        line["cpu_baseline"] = {"value": per_cycle * cycles, "unit": "s", "cores": 1, "kind": "oracle",
+                                "sample": f"mean of 3 FP64 V({args.nu[0]},{args.nu[1]}) cycles of the C oracle on the full "
+                                          f"grid (after 1 untimed) = {per_cycle:.2f} s/cycle, x {cycles} cycles "
+                                          f"(the FP64 iteration count of this problem)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    barrier(pg)
+
+
+if __name__ == "__main__":
+    main()

@@ -113,7 +113,7 @@ typedef struct {
  * workspaces.  dim must be 2.  n_intervals = {nx, ny}; coords = {x, y}, HOST
  * arrays of nx+1 and ny+1 strictly increasing doubles (copied).
  * precision_mask: bit 0 = FP64 workspaces, bit 1 = FP32 workspaces (0 means
- * both).  Block work lists of each smoother are built on first use.
+ * both).  The block work lists of every smoother are built here too.
  * On success *out owns device memory until mg_destroy.                       */
 mg_status mg_setup_grid(mg_grid **out, int dim, const int64_t *n_intervals,
                         const double *const *coords, int precision_mask, void *stream);
@@ -192,6 +192,11 @@ void mg_default_params(mg_params *params);
 /* Static description of a status code / the last CUDA error message.        */
 const char *mg_status_string(mg_status status);
 const char *mg_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * grids, all streams; counted on the host at launch time).  For
+ * instrumentation: the difference across a region counts its launches.      */
+unsigned long long mg_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -11,6 +11,7 @@
 
 namespace tmg {
 
+std::atomic<unsigned long long> g_launches{0};
 static thread_local char g_err[512] = "";
 
 const char *set_error(const char *where, cudaError_t e) {
@@ -178,6 +179,12 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
   TRY(dalloc(&g->partial, 2 * (size_t)g->npartial, "cudaMalloc(partials)"));
   TRY(dalloc(&g->scal, 4, "cudaMalloc(scalars)"));
   TRY_CUDA("cudaMallocHost", cudaMallocHost(&g->hpinned, 4 * sizeof(double)));
+  // block work lists of every line smoother on every level, so that no later
+  // call allocates
+  for (int l = 0; l < g->nlev; ++l)
+    for (int wl = 0; wl < WL_COUNT; ++wl)
+      for (int prec = 0; prec < 2; ++prec)
+        if (g->prec_mask & (prec == 0 ? 1 : 2)) TRY(build_worklists(*g, l, wl, prec));
   return MG_OK;
 }
 
@@ -383,6 +390,8 @@ const char *mg_status_string(mg_status s) {
 }
 
 const char *mg_last_error(void) { return g_err; }
+
+unsigned long long mg_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 mg_status mg_setup_grid(mg_grid **out, int dim, const int64_t *n_intervals, const double *const *coords,
                         int precision_mask, void *stream) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -120,6 +121,10 @@ struct Grid {
   int npartial = 0;
   double *scal = nullptr;            // device scalars (reduced norms)
 };
+
+// Kernels launched by this library in this process (mg_kernel_launches).
+extern std::atomic<unsigned long long> g_launches;
+inline void count_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // ---- host helpers (setup.cu)
 mg_status build_worklists(Grid &g, int level, int wl, int prec);

@@ -416,6 +416,7 @@ static cudaError_t launch_shape(const Level &L, const WorkList &w, T *u, const T
     configured = true;
   }
   kern<<<w.ncta, NT, smem, s>>>(w.cta, w.chunk, w.junc, coefs_of<T>(L), L.nx + 1, u, f);
+  count_launch(1);
   return cudaGetLastError();
 }
 
@@ -449,6 +450,7 @@ cudaError_t launch_checker_pass(const Level &L, int colour, T *u, const T *f, cu
   const int half = L.nx / 2 + 1;
   dim3 block(128), grid((half + 127) / 128, L.ny - 1);
   checker_kernel<T><<<grid, block, 0, s>>>(coefs_of<T>(L), L.nx, colour, u, f);
+  count_launch(1);
   return cudaGetLastError();
 }
 template cudaError_t launch_checker_pass<double>(const Level &, int, double *, const double *, cudaStream_t);

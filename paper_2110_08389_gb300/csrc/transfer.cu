@@ -53,6 +53,7 @@ template <typename T>
 cudaError_t launch_residual(const Level &L, const T *u, const T *f, T *d, cudaStream_t s) {
   dim3 b(128), g((L.nx + 1 + 127) / 128, L.ny + 1);
   residual_kernel<T><<<g, b, 0, s>>>(cq<T>(L), L.nx, L.ny, u, f, d);
+  count_launch(1);
   return cudaGetLastError();
 }
 template cudaError_t launch_residual<double>(const Level &, const double *, const double *, double *, cudaStream_t);
@@ -91,6 +92,7 @@ cudaError_t launch_residual_restrict(const Level &F, const Level &C, int kind, c
   dim3 b(128), g((C.nx - 1 + 127) / 128, C.ny - 1);
   if (C.nx < 2 || C.ny < 2) return cudaSuccess;
   residual_restrict_kernel<T><<<g, b, 0, s>>>(cq<T>(F), F.nx, F.ny, C.nx, kind, u, f, fc, uc);
+  count_launch(1);
   return cudaGetLastError();
 }
 template cudaError_t launch_residual_restrict<double>(const Level &, const Level &, int, const double *,
@@ -120,6 +122,7 @@ template <typename T>
 cudaError_t launch_prolong_add(const Level &F, const Level &C, const T *uc, T *u, cudaStream_t s) {
   dim3 b(128), g((F.nx - 1 + 127) / 128, F.ny - 1);
   prolong_add_kernel<T><<<g, b, 0, s>>>(F.nx, F.ny, C.nx, uc, u);
+  count_launch(1);
   return cudaGetLastError();
 }
 template cudaError_t launch_prolong_add<double>(const Level &, const Level &, const double *, double *,
@@ -158,6 +161,7 @@ cudaError_t launch_coarse_solve(const Grid &g, T *u, const T *f, cudaStream_t s)
   const Level &L = g.lev[g.nlev - 1];
   if (g.cn <= 0) return cudaSuccess;
   coarse_solve_kernel<T><<<1, 256, sizeof(double) * g.cn, s>>>(cq<double>(L), L.nx, L.ny, g.cinv, u, f);
+  count_launch(1);
   return cudaGetLastError();
 }
 template cudaError_t launch_coarse_solve<double>(const Grid &, double *, const double *, cudaStream_t);
@@ -215,6 +219,7 @@ static cudaError_t norms(const Grid &g, const double *u, const double *f, float 
   const Level &L = g.lev[0];
   norm_stage1<<<g.npartial, NORM_THREADS, 0, s>>>(cq<double>(L), L.nx, L.ny, u, f, r32, g.partial);
   norm_stage2<<<1, NORM_THREADS, 0, s>>>(g.partial, g.npartial, g.scal);
+  count_launch(2);
   return cudaGetLastError();
 }
 
@@ -235,6 +240,7 @@ cudaError_t launch_ir_update(const Grid &g, double *u, const float *e, cudaStrea
   const Level &L = g.lev[0];
   dim3 b(128), gr((L.nx - 1 + 127) / 128, L.ny - 1);
   ir_update_kernel<<<gr, b, 0, s>>>(L.nx, L.ny, u, e);
+  count_launch(1);
   return cudaGetLastError();
 }
 
@@ -253,6 +259,7 @@ cudaError_t launch_diag_scale(const Grid &g, double *out, const double *in, int 
   const Level &L = g.lev[0];
   dim3 b(128), gr((L.nx + 1 + 127) / 128, L.ny + 1);
   diag_scale_kernel<<<gr, b, 0, s>>>(L.xd, L.yd, L.nx, L.ny, out, in, inverse);
+  count_launch(1);
   return cudaGetLastError();
 }
 
@@ -266,6 +273,7 @@ template <typename T>
 cudaError_t launch_zero_interior(const Level &L, T *a, cudaStream_t s) {
   dim3 b(128), gr((L.nx - 1 + 127) / 128, L.ny - 1);
   zero_interior_kernel<T><<<gr, b, 0, s>>>(L.nx, L.ny, a);
+  count_launch(1);
   return cudaGetLastError();
 }
 template cudaError_t launch_zero_interior<double>(const Level &, double *, cudaStream_t);

@@ -31,7 +31,7 @@ HW, FW = 0, 1
 EXPORTS = ["mg_setup_grid", "mg_destroy", "mg_num_levels", "mg_level_shape", "mg_smooth_tweed",
            "mg_smooth_wireframe", "mg_smooth", "mg_colour_pass", "mg_residual_restrict", "mg_prolong_add",
            "mg_residual", "mg_coarse_solve", "mg_vcycle", "mg_solve", "mg_solve_adjoint",
-           "mg_default_params", "mg_status_string", "mg_last_error"]
+           "mg_default_params", "mg_status_string", "mg_last_error", "mg_kernel_launches"]
 
 
 class MGError(RuntimeError):
@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH):
         "mg_default_params": (None, [ctypes.POINTER(Params)]),
         "mg_status_string": (ctypes.c_char_p, [i]),
         "mg_last_error": (ctypes.c_char_p, []),
+        "mg_kernel_launches": (ctypes.c_ulonglong, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -137,6 +138,11 @@ class SolveResult:
     conv_factor: float
     ms: float
     history: np.ndarray
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().mg_kernel_launches())
 
 
 def default_params(**kw) -> Params:

@@ -193,6 +193,28 @@ void mg_default_params(mg_params *params);
 const char *mg_status_string(mg_status status);
 const char *mg_last_error(void);
 
+/* Residual norms for callers that cannot allocate device memory (the paper has
+ * no counterpart; this is a deployment aid).  Some callers must not call
+ * cudaMalloc at all -- code that runs inside a memory pool it does not own, a
+ * process whose allocator is locked after start-up -- and so cannot create an
+ * mg_grid either.  This entry point needs no grid and allocates nothing: from
+ * caller-owned DEVICE arrays it computes, over the interior nodes,
+ *   out[0] = sum (f - L u)^2,  out[1] = max |f - L u|,
+ *   out[2] = sum f^2,          out[3] = max |f|          (out: 4 doubles),
+ * with L the operator of Eq. (prob:DP) given by the coefficient arrays W, E
+ * (nx+1 each) and S, N (ny+1 each), u and f of shape (ny+1) x (nx+1), FP64.
+ * Its scratch is a static device array of 4 x 16384 doubles (one partial per
+ * interior row), so ny - 1 may not exceed 16384: larger grids return
+ * MG_ERR_SIZE with a message in mg_last_error().  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  All calls on a device share the
+ * array: calls whose kernels overlap on the GPU (different streams without
+ * ordering) race and give wrong results.  No entry needs clearing: each call
+ * writes every partial it reads.  Enqueued on `stream`; no synchronisation.   */
+mg_status mg_residual_norm_static(int64_t nx, int64_t ny, const double *W, const double *E,
+                                  const double *S, const double *N, const double *u, const double *f,
+                                  double *out, void *stream);
+
 /* Number of CUDA kernels this library has launched in this process (all
  * grids, all streams; counted on the host at launch time).  For
  * instrumentation: the difference across a region counts its launches.      */

@@ -19,6 +19,8 @@ const char *set_error(const char *where, cudaError_t e) {
   return g_err;
 }
 
+void set_error_text(const char *msg) { std::snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 static mg_status cuda_status(const char *where, cudaError_t e) {
   if (e == cudaSuccess) return MG_OK;
   set_error(where, e);

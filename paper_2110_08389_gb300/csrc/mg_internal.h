@@ -129,6 +129,7 @@ inline void count_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std
 // ---- host helpers (setup.cu)
 mg_status build_worklists(Grid &g, int level, int wl, int prec);
 const char *set_error(const char *where, cudaError_t e);
+void set_error_text(const char *msg);
 
 // ---- kernel launchers (smooth.cu, transfer.cu).  All return cudaError_t of
 // the launch (cudaGetLastError).

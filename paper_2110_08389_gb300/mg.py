@@ -31,7 +31,8 @@ HW, FW = 0, 1
 EXPORTS = ["mg_setup_grid", "mg_destroy", "mg_num_levels", "mg_level_shape", "mg_smooth_tweed",
            "mg_smooth_wireframe", "mg_smooth", "mg_colour_pass", "mg_residual_restrict", "mg_prolong_add",
            "mg_residual", "mg_coarse_solve", "mg_vcycle", "mg_solve", "mg_solve_adjoint",
-           "mg_default_params", "mg_status_string", "mg_last_error", "mg_kernel_launches"]
+           "mg_default_params", "mg_status_string", "mg_last_error", "mg_kernel_launches",
+           "mg_residual_norm_static"]
 
 
 class MGError(RuntimeError):
@@ -87,6 +88,7 @@ def load(path: str = LIB_PATH):
         "mg_status_string": (ctypes.c_char_p, [i]),
         "mg_last_error": (ctypes.c_char_p, []),
         "mg_kernel_launches": (ctypes.c_ulonglong, []),
+        "mg_residual_norm_static": (i, [ctypes.c_int64, ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

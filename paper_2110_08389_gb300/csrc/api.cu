@@ -57,13 +57,16 @@ static void free_grid(Grid *g) {
     cudaFree(L.dev_block);
     cudaFree(L.u64); cudaFree(L.f64); cudaFree(L.u32); cudaFree(L.f32);
     for (int w = 0; w < WL_COUNT; ++w)
-      for (int p = 0; p < 2; ++p)
-        for (int c = 0; c < 2; ++c)
+      for (int c = 0; c < 2; ++c) {
+        cudaFree(L.tl[w][c].mem);
+        for (int p = 0; p < 2; ++p)
           for (int z = 0; z < 2; ++z) cudaFree(L.wl[w][p][c][z].mem);
+      }
   }
   cudaFree(g->cinv);
   cudaFree(g->r64); cudaFree(g->lam_tmp); cudaFree(g->e32); cudaFree(g->r32);
   cudaFree(g->partial); cudaFree(g->scal);
+  cudaFree(g->tile_rows); cudaFree(g->tile_d); cudaFree(g->tile_x);
   if (g->hpinned) cudaFreeHost(g->hpinned);
   delete g;
 }
@@ -125,6 +128,7 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
     cx /= 2; cy /= 2;
   }
   g->nlev = (int)g->lev.size();
+  TRY_CUDA("setup start (latched error)", cudaGetLastError());
   const bool want64 = g->prec_mask & 1, want32 = g->prec_mask & 2;
   for (int l = 0; l < g->nlev; ++l) {
     Level &L = g->lev[l];
@@ -172,6 +176,7 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
       TRY_CUDA("cudaMemcpy(coarse)", cudaMemcpy(g->cinv, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice));
     }
   }
+  TRY_CUDA("setup levels (latched error)", cudaGetLastError());
   const size_t nn0 = g->lev[0].nn;
   if (want32) { TRY(dalloc(&g->e32, nn0, "cudaMalloc(e32)")); TRY(dalloc(&g->r32, nn0, "cudaMalloc(r32)")); }
   int dev = 0, sms = 148;
@@ -183,10 +188,23 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
   TRY_CUDA("cudaMallocHost", cudaMallocHost(&g->hpinned, 4 * sizeof(double)));
   // block work lists of every line smoother on every level, so that no later
   // call allocates
+  TRY_CUDA("setup scratch (latched error)", cudaGetLastError());
   for (int l = 0; l < g->nlev; ++l)
-    for (int wl = 0; wl < WL_COUNT; ++wl)
+    for (int wl = 0; wl < WL_COUNT; ++wl) {
       for (int prec = 0; prec < 2; ++prec)
         if (g->prec_mask & (prec == 0 ? 1 : 2)) TRY(build_worklists(*g, l, wl, prec));
+      TRY_CUDA("setup work lists (latched error)", cudaGetLastError());
+      TRY(build_tiles(*g, l, wl));
+      TRY_CUDA("setup tiles (latched error)", cudaGetLastError());
+    }
+  if (g->tile_cap > 0) {
+    // scratch of the tiled path, sized for FP64 (FP32 uses the first half)
+    // rows (2 x 4 doubles per lane) followed by the (c', d') pairs of tile_couple
+    TRY_CUDA("cudaMalloc(tile rows)", cudaMalloc(&g->tile_rows, g->tile_cap * 32 * 2 * 6 * sizeof(double)));
+    TRY_CUDA("cudaMalloc(tile rhs)", cudaMalloc(&g->tile_d, g->tile_cap * 32 * 32 * sizeof(double)));
+    TRY_CUDA("cudaMalloc(tile ends)", cudaMalloc(&g->tile_x, g->tile_cap * 32 * 2 * sizeof(double)));
+  }
+  TRY_CUDA("setup (latched error)", cudaGetLastError());
   return MG_OK;
 }
 
@@ -218,6 +236,11 @@ static mg_status colour_pass(Grid &g, int l, int smoother, int colour, T *u, con
   }
   const int wl = wl_of(smoother);
   if (wl < 0) return MG_ERR_INVALID_ARG;
+  const TileList &tl = L.tl[wl][colour];
+  if (tl.ntile > 0 || tl.nblock > 0) {
+    TRY_CUDA("tiled line pass", launch_tile_pass<T>(g, L, tl, u, f, s));
+    return MG_OK;
+  }
   const int prec = sizeof(T) == 8 ? 0 : 1;
   TRY(build_worklists(g, l, wl, prec));
   TRY_CUDA("line pass", launch_line_pass<T>(L, L.wl[wl][prec][colour][0], u, f, s));

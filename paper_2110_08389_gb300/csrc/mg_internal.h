@@ -34,18 +34,20 @@ enum { DIR_PX = 0, DIR_MX = 1, DIR_PY = 2, DIR_MY = 3 };
 enum : uint8_t { F_LP = 16, F_LN = 32, F_FJ = 64, F_LJ = 128 };
 
 // A run of <= 32 consecutive chain nodes along one direction, solved by one
-// thread.  Chunk c of a CTA owns the shared-memory slots [32c, 32c+32) (node q
-// of the chunk in slot 32c + q).  Consecutive chunks of a chain are
-// consecutive in the CTA's chunk list, so the reduced-system neighbours of
-// chunk t are chunks t-1 (if LP) and t+1 (if LN).  junc = CTA-local index of
-// the chain's junction, or 0xFFFF.
+// thread.  Chunk c of a CTA owns 32 shared-memory slots (node q of the chunk
+// in slot 32c + (q ^ (c % 32)), an XOR swizzle that keeps both "one thread per
+// chunk" and "one lane per node" accesses free of bank conflicts).
+// Consecutive chunks of a chain are consecutive in the CTA's chunk list, so
+// the reduced-system neighbours of chunk t are chunks t-1 (if LP) and t+1 (if
+// LN).  info: bits 0-9 = CTA-local index of the chain's junction (JNONE if
+// none); bit 15 = the chunk is loaded and stored through a VGroup.
 struct ChunkDesc {
   uint16_t i0, j0;
   uint8_t len, flags;
-  uint16_t junc;
-  uint16_t pad[4];
+  uint16_t info;
 };
-static_assert(sizeof(ChunkDesc) == 16, "ChunkDesc layout");
+static_assert(sizeof(ChunkDesc) == 8, "ChunkDesc layout");
+constexpr uint16_t JNONE = 1023, GROUPED = 0x8000;
 
 // A junction node: the branch point of a tweed star (Eq. mLThomas), the node
 // where a wireframe ring is closed (Eq. CircTri), or a lone point block.
@@ -63,8 +65,17 @@ static_assert(sizeof(JuncDesc) == 16, "JuncDesc layout");
 struct CtaWork {
   int chunk0, nchunk;
   int junc0, njunc;
+  int vg0, nvg;
   int nnode;  // unknowns of the CTA's chains (junctions excluded)
-  int pad[3];
+  int pad;
+};
+
+// Up to four vertical chunks of one CTA with the same rows and direction in
+// same-colour columns i, i+2, i+4, i+6 (CTA-local chunk ids, 0xFFFF = none).
+// The load / store phases read them with lanes spread over 8 rows x 4
+// columns, so one warp access touches a few sectors instead of 32 rows.
+struct VGroup {
+  uint16_t c[4];
 };
 static_assert(sizeof(CtaWork) == 32, "CtaWork layout");
 
@@ -73,10 +84,62 @@ struct WorkList {
   int ncta = 0;
   int nt = 0;           // threads per CTA = max chunks per CTA
   int total_nodes = 0;  // unknowns relaxed by this list (junctions included)
-  void *mem = nullptr;  // one allocation behind the three arrays
+  void *mem = nullptr;  // one allocation behind the four arrays
   CtaWork *cta = nullptr;
   ChunkDesc *chunk = nullptr;
   JuncDesc *junc = nullptr;
+  VGroup *vg = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// Tiled line path (tweed and zebra on large levels).  Every block is a set of
+// legs that each start at a wall, plus at most one junction node (the
+// paper's m-legged form, Eq. mLThomas; m = 1 for a line from wall to wall).
+// Legs are cut into chunks at absolute positions (every 32 nodes from the
+// wall), so the legs of neighbouring same-colour blocks line up: a tile is
+// one such 32-node stretch of 32 parallel legs, one warp per tile.
+//   tile_reduce   per lane: right-hand side of the chunk and its two reduced
+//                 rows (partition method) -> scratch
+//   tile_couple   per leg: Thomas on the reduced rows towards the junction,
+//                 the junction row, back-substitution -> chunk end values
+//   tile_expand   per lane: interior of the chunk by Thomas -> u
+enum : uint8_t { TL_FIRST = 1, TL_LAST_J = 2, TL_LAST_W = 4 };
+
+struct TileLane {
+  uint16_t line;   // fixed coordinate of the run (j for x-runs, i for y-runs)
+  uint8_t q0, q1;  // active slots [q0, q1) of the tile (q1 = 0: unused lane)
+  uint8_t flags;   // TL_FIRST: slot q0 is the leg's first node (its predecessor is a wall node);
+                   // TL_LAST_J / TL_LAST_W: slot q1-1 is the leg's last node and its successor
+                   // is the junction / a wall node
+  uint8_t pad[3];
+};
+static_assert(sizeof(TileLane) == 8, "TileLane layout");
+
+struct TileDesc {
+  uint16_t base;   // run coordinate of slot 0
+  uint8_t dir;     // run direction (DIR_*)
+  uint8_t pad[5];
+};
+static_assert(sizeof(TileDesc) == 8, "TileDesc layout");
+
+// One block for tile_couple: its legs are lane `lane` of the tiles
+// leg_tile0[l] .. leg_tile0[l] + ceil(leg_len[l]/32) - 1.
+struct BlockDesc {
+  uint16_t ji, jj;        // junction node
+  uint8_t nleg, junc;     // number of legs; 1 if the block has a junction
+  uint8_t jdirs, lane;    // direction junction -> last node of leg l (2 bits each); tile lane
+  uint32_t leg_tile0[4];
+  uint16_t leg_len[4];
+};
+static_assert(sizeof(BlockDesc) == 32, "BlockDesc layout");
+
+struct TileList {
+  int ntile = 0, nblock = 0, ngroup = 0;
+  int total_nodes = 0;
+  void *mem = nullptr;
+  TileDesc *tile = nullptr;
+  TileLane *lane = nullptr;     // 32 per tile
+  BlockDesc *block = nullptr;   // 32 per group (unused entries have nleg = junc = 0)
 };
 
 // Shapes of the line-solve kernel: 32 nodes per chunk (one thread each);
@@ -102,6 +165,8 @@ struct Level {
   double *u64 = nullptr, *f64 = nullptr;
   float *u32 = nullptr, *f32 = nullptr;
   bool wl_built[WL_COUNT][2] = {};    // [smoother][precision 0=f64,1=f32]
+  bool tl_built[WL_COUNT] = {};
+  TileList tl[WL_COUNT][2];           // [smoother][colour]: tiled path (empty: use the work lists)
   WorkList wl[WL_COUNT][2][2][2];     // [smoother][precision][colour][small, large]
 };
 
@@ -120,7 +185,15 @@ struct Grid {
   double *hpinned = nullptr;         // pinned host mirror of the norm results
   int npartial = 0;
   double *scal = nullptr;            // device scalars (reduced norms)
+  // scratch of the tiled line path, sized for the largest tile list
+  size_t tile_cap = 0;               // tiles
+  void *tile_rows = nullptr;         // 2 reduced rows per lane per tile (FP64 sized)
+  void *tile_d = nullptr;            // 32 x 32 right-hand sides per tile (FP64 sized)
+  void *tile_x = nullptr;            // 2 end values per lane per tile (FP64 sized)
 };
+
+// Levels whose side exceeds this use the tiled path for tweed and zebra.
+constexpr int TILE_MIN_SIDE = 256;
 
 // Kernels launched by this library in this process (mg_kernel_launches).
 extern std::atomic<unsigned long long> g_launches;
@@ -130,6 +203,10 @@ inline void count_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std
 mg_status build_worklists(Grid &g, int level, int wl, int prec);
 const char *set_error(const char *where, cudaError_t e);
 void set_error_text(const char *msg);
+
+mg_status build_tiles(Grid &g, int level, int wl);
+template <typename T>
+cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &t, T *u, const T *f, cudaStream_t s);
 
 // ---- kernel launchers (smooth.cu, transfer.cu).  All return cudaError_t of
 // the launch (cudaGetLastError).

@@ -21,6 +21,7 @@
 #include <cstdio>
 #include <cstring>
 #include <numeric>
+#include <tuple>
 
 #include "mg_internal.h"
 
@@ -41,7 +42,14 @@ struct HBlock {
   int ji = 0, jj = 0;
   std::vector<HChain> ch;
   int nodes = 0, chunks = 0;
+  int group = 0, pos = 0;  // packing order: blocks of one group in order of pos are
+                           // neighbours (adjacent same-colour legs / lines)
 };
+HBlock keyed(HBlock b, int group, int pos) {
+  b.group = group;
+  b.pos = pos;
+  return b;
+}
 
 HChain line(int i0, int j0, int dir, int len) {
   HChain c;
@@ -71,6 +79,7 @@ HBlock star(int i, int j, std::vector<HChain> legs) {
   return b;
 }
 inline int colour_of(int k) { return (k & 1) ? 0 : 1; }
+HBlock keyed5(HBlock b) { return keyed(b, 5, 0); }
 
 void tweed_blocks(int nx, int ny, int colour, std::vector<HBlock> &out) {
   const int hx = nx / 2, hy = ny / 2, K = std::max(hx, hy), m = std::min(hx, hy);
@@ -78,8 +87,8 @@ void tweed_blocks(int nx, int ny, int colour, std::vector<HBlock> &out) {
     if (colour_of(k) != colour) continue;
     if (k < m) {
       if (k == 1) {
-        out.push_back(point(1, 1)); out.push_back(point(nx - 1, 1));
-        out.push_back(point(1, ny - 1)); out.push_back(point(nx - 1, ny - 1));
+        out.push_back(keyed(point(1, 1), 4, 0)); out.push_back(keyed(point(nx - 1, 1), 4, 1));
+        out.push_back(keyed(point(1, ny - 1), 4, 2)); out.push_back(keyed(point(nx - 1, ny - 1), 4, 3));
         continue;
       }
       // leg from the y-wall up to the corner (k,k) of the level, then the leg
@@ -91,31 +100,31 @@ void tweed_blocks(int nx, int ny, int colour, std::vector<HBlock> &out) {
           const int vdir = b == 0 ? DIR_PY : DIR_MY, hdir = a == 0 ? DIR_MX : DIR_PX;
           c.s.push_back({cx[a], b == 0 ? 1 : ny - 1, vdir, k});
           c.s.push_back({a == 0 ? k - 1 : nx - k + 1, cy[b], hdir, k - 1});
-          out.push_back(single(c));
+          out.push_back(keyed(single(c), 2 * a + b, k));
         }
     } else if (k == m) {
       if (hx == hy) {  // centre cross, m = 4 legs (Eq. mLThomas)
-        out.push_back(star(k, k, {leg_to_junction(1, k, DIR_PX, k - 1), leg_to_junction(nx - 1, k, DIR_MX, k - 1),
-                                  leg_to_junction(k, 1, DIR_PY, k - 1), leg_to_junction(k, ny - 1, DIR_MY, k - 1)}));
+        out.push_back(keyed5(star(k, k, {leg_to_junction(1, k, DIR_PX, k - 1), leg_to_junction(nx - 1, k, DIR_MX, k - 1),
+                                  leg_to_junction(k, 1, DIR_PY, k - 1), leg_to_junction(k, ny - 1, DIR_MY, k - 1)})));
       } else if (hx > hy) {  // two T-blocks, arms from the x-walls
-        out.push_back(star(k, k, {leg_to_junction(1, k, DIR_PX, k - 1), leg_to_junction(k, 1, DIR_PY, k - 1),
-                                  leg_to_junction(k, ny - 1, DIR_MY, ny - 1 - k)}));
-        out.push_back(star(nx - k, k, {leg_to_junction(nx - 1, k, DIR_MX, k - 1),
+        out.push_back(keyed5(star(k, k, {leg_to_junction(1, k, DIR_PX, k - 1), leg_to_junction(k, 1, DIR_PY, k - 1),
+                                  leg_to_junction(k, ny - 1, DIR_MY, ny - 1 - k)})));
+        out.push_back(keyed5(star(nx - k, k, {leg_to_junction(nx - 1, k, DIR_MX, k - 1),
                                        leg_to_junction(nx - k, 1, DIR_PY, k - 1),
-                                       leg_to_junction(nx - k, ny - 1, DIR_MY, ny - 1 - k)}));
+                                       leg_to_junction(nx - k, ny - 1, DIR_MY, ny - 1 - k)})));
       } else {  // two T-blocks, arms from the y-walls
-        out.push_back(star(k, k, {leg_to_junction(k, 1, DIR_PY, k - 1), leg_to_junction(1, k, DIR_PX, k - 1),
-                                  leg_to_junction(nx - 1, k, DIR_MX, nx - 1 - k)}));
-        out.push_back(star(k, ny - k, {leg_to_junction(k, ny - 1, DIR_MY, k - 1),
+        out.push_back(keyed5(star(k, k, {leg_to_junction(k, 1, DIR_PY, k - 1), leg_to_junction(1, k, DIR_PX, k - 1),
+                                  leg_to_junction(nx - 1, k, DIR_MX, nx - 1 - k)})));
+        out.push_back(keyed5(star(k, ny - k, {leg_to_junction(k, ny - 1, DIR_MY, k - 1),
                                        leg_to_junction(1, ny - k, DIR_PX, k - 1),
-                                       leg_to_junction(nx - 1, ny - k, DIR_MX, nx - 1 - k)}));
+                                       leg_to_junction(nx - 1, ny - k, DIR_MX, nx - 1 - k)})));
       }
     } else if (hx > hy) {  // full columns perpendicular to the y-walls
-      out.push_back(single(line(k, 1, DIR_PY, ny - 1)));
-      if (nx - k != k) out.push_back(single(line(nx - k, 1, DIR_PY, ny - 1)));
+      out.push_back(keyed(single(line(k, 1, DIR_PY, ny - 1)), 6, k));
+      if (nx - k != k) out.push_back(keyed(single(line(nx - k, 1, DIR_PY, ny - 1)), 6, nx - k));
     } else {  // full rows perpendicular to the x-walls
-      out.push_back(single(line(1, k, DIR_PX, nx - 1)));
-      if (ny - k != k) out.push_back(single(line(1, ny - k, DIR_PX, nx - 1)));
+      out.push_back(keyed(single(line(1, k, DIR_PX, nx - 1)), 6, k));
+      if (ny - k != k) out.push_back(keyed(single(line(1, ny - k, DIR_PX, nx - 1)), 6, ny - k));
     }
   }
 }
@@ -134,9 +143,9 @@ void wireframe_blocks(int nx, int ny, int colour, std::vector<HBlock> &out) {
       c.fj = true; c.lj = true; c.ljdir = DIR_MY;
       HBlock b = point(k, k);
       b.ch.push_back(c);
-      out.push_back(b);
+      out.push_back(keyed(b, 0, k));
     } else if (hx == hy) {
-      out.push_back(point(k, k));
+      out.push_back(keyed(point(k, k), 1, k));
     } else if (hx > hy) {
       out.push_back(single(line(k, k, DIR_PX, nx - 2 * k + 1)));
     } else {
@@ -148,10 +157,10 @@ void wireframe_blocks(int nx, int ny, int colour, std::vector<HBlock> &out) {
 void zebra_blocks(int nx, int ny, int colour, bool along_x, std::vector<HBlock> &out) {
   if (along_x) {
     for (int j = 1; j < ny; ++j)
-      if (colour_of(j) == colour) out.push_back(single(line(1, j, DIR_PX, nx - 1)));
+      if (colour_of(j) == colour) out.push_back(keyed(single(line(1, j, DIR_PX, nx - 1)), 0, j));
   } else {
     for (int i = 1; i < nx; ++i)
-      if (colour_of(i) == colour) out.push_back(single(line(i, 1, DIR_PY, ny - 1)));
+      if (colour_of(i) == colour) out.push_back(keyed(single(line(i, 1, DIR_PY, ny - 1)), 0, i));
   }
 }
 
@@ -161,8 +170,45 @@ struct Packed {
   std::vector<CtaWork> cta;
   std::vector<ChunkDesc> chunk;
   std::vector<JuncDesc> junc;
+  std::vector<VGroup> vg;
   int total = 0;
 };
+
+// Group the CTA's vertical chunks that share rows and direction and sit in
+// same-colour columns two apart, four at a time.
+void group_vertical(Packed &P, CtaWork &w) {
+  std::vector<int> ids;
+  for (int t = 0; t < w.nchunk; ++t) {
+    const ChunkDesc &cd = P.chunk[w.chunk0 + t];
+    if ((cd.flags & 3) >= 2) ids.push_back(t);
+  }
+  auto key = [&](int t) {
+    const ChunkDesc &cd = P.chunk[w.chunk0 + t];
+    return std::make_tuple((int)cd.j0, (int)cd.len, cd.flags & 3, (int)cd.i0);
+  };
+  std::sort(ids.begin(), ids.end(), [&](int a, int b) { return key(a) < key(b); });
+  w.vg0 = (int)P.vg.size();
+  size_t k = 0;
+  while (k < ids.size()) {
+    size_t e = k + 1;
+    while (e < ids.size() && e - k < 4) {
+      const ChunkDesc &a = P.chunk[w.chunk0 + ids[e - 1]], &b = P.chunk[w.chunk0 + ids[e]];
+      if (b.j0 != a.j0 || b.len != a.len || (b.flags & 3) != (a.flags & 3) || b.i0 != a.i0 + 2) break;
+      ++e;
+    }
+    if (e - k >= 2) {
+      VGroup g;
+      for (int q = 0; q < 4; ++q) g.c[q] = 0xFFFF;
+      for (size_t q = k; q < e; ++q) {
+        g.c[q - k] = (uint16_t)ids[q];
+        P.chunk[w.chunk0 + ids[q]].info |= GROUPED;
+      }
+      P.vg.push_back(g);
+    }
+    k = e;
+  }
+  w.nvg = (int)P.vg.size() - w.vg0;
+}
 
 inline int step_i(int d) { return d == DIR_PX ? 1 : (d == DIR_MX ? -1 : 0); }
 inline int step_j(int d) { return d == DIR_PY ? 1 : (d == DIR_MY ? -1 : 0); }
@@ -200,7 +246,7 @@ void emit_block(Packed &P, CtaWork &w, const HBlock &b) {
         cd.j0 = (uint16_t)(s.j0 + off * step_j(s.dir));
         cd.len = (uint8_t)len;
         cd.flags = fl;
-        cd.junc = jidx >= 0 ? (uint16_t)jidx : (uint16_t)0xFFFF;
+        cd.info = jidx >= 0 ? (uint16_t)jidx : JNONE;
         const int tloc = w.nchunk;  // CTA-local chunk index
         if (jd && (fl & F_FJ)) {
           jd->row[jd->nend] = (uint16_t)(2 * tloc);
@@ -226,6 +272,7 @@ void pack(const std::vector<HBlock> &blocks, const std::vector<int> &order, int 
   std::memset(&w, 0, sizeof(w));
   auto flush = [&]() {
     if (w.nchunk == 0 && w.njunc == 0) return;
+    group_vertical(P, w);
     P.cta.push_back(w);
     CtaWork z;
     std::memset(&z, 0, sizeof(z));
@@ -250,19 +297,23 @@ mg_status upload(const Packed &P, int nt, WorkList &W) {
   W.total_nodes = P.total;
   if (W.ncta == 0) return MG_OK;
   const size_t b0 = align16<CtaWork>(P.cta.size()), b1 = align16<ChunkDesc>(std::max<size_t>(P.chunk.size(), 1)),
-               b2 = align16<JuncDesc>(std::max<size_t>(P.junc.size(), 1));
+               b2 = align16<JuncDesc>(std::max<size_t>(P.junc.size(), 1)),
+               b3 = align16<VGroup>(std::max<size_t>(P.vg.size(), 1));
   char *mem = nullptr;
-  cudaError_t e = cudaMalloc(&mem, b0 + b1 + b2);
+  cudaError_t e = cudaMalloc(&mem, b0 + b1 + b2 + b3);
   if (e != cudaSuccess) { set_error("cudaMalloc(work list)", e); return MG_ERR_ALLOC; }
   W.mem = mem;
   W.cta = reinterpret_cast<CtaWork *>(mem);
   W.chunk = reinterpret_cast<ChunkDesc *>(mem + b0);
   W.junc = reinterpret_cast<JuncDesc *>(mem + b0 + b1);
+  W.vg = reinterpret_cast<VGroup *>(mem + b0 + b1 + b2);
   e = cudaMemcpy(W.cta, P.cta.data(), sizeof(CtaWork) * P.cta.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !P.chunk.empty())
     e = cudaMemcpy(W.chunk, P.chunk.data(), sizeof(ChunkDesc) * P.chunk.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !P.junc.empty())
     e = cudaMemcpy(W.junc, P.junc.data(), sizeof(JuncDesc) * P.junc.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !P.vg.empty())
+    e = cudaMemcpy(W.vg, P.vg.data(), sizeof(VGroup) * P.vg.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { set_error("cudaMemcpy(work list)", e); return MG_ERR_CUDA; }
   return MG_OK;
 }
@@ -280,6 +331,9 @@ mg_status build_worklists(Grid &g, int level, int wl, int prec) {
       case WL_ZEBRA_X: zebra_blocks(L.nx, L.ny, colour, true, blocks); break;
       default: zebra_blocks(L.nx, L.ny, colour, false, blocks); break;
     }
+    // blocks of more than a quarter of a small CTA go to large CTAs, so that
+    // every CTA holds about four neighbouring blocks; neighbours (same group,
+    // consecutive positions) are packed together for the vertical groups
     std::vector<int> small, large;
     for (size_t bi = 0; bi < blocks.size(); ++bi) {
       HBlock &b = blocks[bi];
@@ -288,11 +342,13 @@ mg_status build_worklists(Grid &g, int level, int wl, int prec) {
       for (auto &c : b.ch)
         for (auto &s : c.s) { b.nodes += s.len; b.chunks += nchunks_of(s.len); }
       if (b.chunks > NT_LARGE) return MG_ERR_SIZE;
-      (b.chunks > NT_SMALL ? large : small).push_back((int)bi);
+      (b.chunks > NT_SMALL / 4 ? large : small).push_back((int)bi);
     }
-    auto by_size = [&](int a, int b) { return blocks[a].chunks > blocks[b].chunks; };
-    std::stable_sort(small.begin(), small.end(), by_size);
-    std::stable_sort(large.begin(), large.end(), by_size);
+    auto by_key = [&](int a, int b) {
+      return std::make_pair(blocks[a].group, blocks[a].pos) < std::make_pair(blocks[b].group, blocks[b].pos);
+    };
+    std::stable_sort(small.begin(), small.end(), by_key);
+    std::stable_sort(large.begin(), large.end(), by_key);
     Packed Ps, Pl;
     pack(blocks, small, NT_SMALL, Ps);
     pack(blocks, large, NT_LARGE, Pl);

@@ -72,11 +72,6 @@ __device__ __forceinline__ double rcp(double x) {
   return fma(r, e, r);
 }
 
-// Shared-memory index of slot s (slot 32c + q holds node q of chunk c): one
-// pad word per 32 slots, so that threads walking their own chunks in step hit
-// distinct banks (stride 33 words for float, 33 doubles for double).
-__device__ __forceinline__ int sidx(int s) { return s + (s >> 5); }
-
 // Geometry of one chunk: a straight run of m nodes in direction dir.  Along
 // the run only the two "along" coefficients vary (W/E for x-runs, S/N for
 // y-runs); the two perpendicular ones are constant and enter the diagonal
@@ -107,10 +102,11 @@ struct ChunkGeom {
   }
   __device__ __forceinline__ T lo_at(int q) const { return __ldg(lo_arr + var0 + (q < m ? q : m - 1) * step); }
   __device__ __forceinline__ T hi_at(int q) const { return __ldg(hi_arr + var0 + (q < m ? q : m - 1) * step); }
-  __device__ __forceinline__ T a_of(int q, T lo) const { return (q > 0 || (fl & F_LP)) ? lo : T(0); }
-  __device__ __forceinline__ T c_of(int q, T hi) const { return q < m - 1 ? hi : clast; }
   __device__ __forceinline__ T b_of(T lo, T hi) const { return -(cross + (lo + hi)); }
 };
+
+// Shared-memory slot of node q of chunk c (XOR swizzle, see ChunkDesc).
+__device__ __forceinline__ int slot_of(int c, int q) { return 32 * c + (q ^ (c & 31)); }
 
 // One reduced row  a x_L + x + c x_U = (y, z), stored as a vector.
 template <typename T>
@@ -120,161 +116,270 @@ struct __align__(4 * sizeof(T)) Row {
 
 // Shared memory of one CTA: reduced rows, the slot arrays (right-hand side;
 // with SC also the two along coefficients of every node, written by the load
-// phase so that the eliminations read no global memory), junction values and
-// reduced-row links.
+// phase so that the eliminations read no global memory), junction values,
+// reduced-row links, and copies of the CTA's chunk and vertical-group
+// descriptors.
 template <typename T, int NT, bool SC>
 struct LineSmem {
   static constexpr size_t rows = sizeof(Row<T>) * 2 * NT;
-  static constexpr size_t slots = 33 * NT;                // 32 slots + 1 pad per chunk
-  static constexpr size_t nodes = sizeof(T) * slots * (SC ? 3 : 1);
-  static constexpr size_t bytes = rows + nodes + sizeof(T) * NT + sizeof(short2) * 2 * NT;
+  static constexpr size_t nodes = sizeof(T) * 32 * NT * (SC ? 3 : 1);
+  static constexpr size_t junc = sizeof(T) * NT;
+  static constexpr size_t links = sizeof(short2) * 2 * NT;
+  static constexpr size_t descs = sizeof(ChunkDesc) * NT;
+  static constexpr size_t groups = sizeof(VGroup) * (NT / 2);
+  static constexpr size_t bytes = rows + nodes + junc + links + descs + groups;
 };
 
-// Slot s of the CTA: chunk c = s / 32, node q = s % 32.  Returns false for
-// the unused tail slots of ragged chunks.
-__device__ __forceinline__ bool slot_node(const ChunkDesc *__restrict__ chunks, int s, int &i, int &j,
-                                          unsigned &incl) {
-  const ChunkDesc cd = chunks[s >> 5];
-  const int q = s & 31;
-  if (q >= cd.len) return false;
-  const int dir = cd.flags & 3, nd = (cd.flags >> 2) & 3;
-  i = cd.i0 + q * di_of(dir);
-  j = cd.j0 + q * dj_of(dir);
-  // neighbours that go to the right-hand side: all but the chain neighbours
-  // and the junction
-  unsigned m = 0xFu;
-  if (q > 0 || (cd.flags & (F_LP | F_FJ))) m &= ~(1u << (dir ^ 1));
-  if (q < cd.len - 1) m &= ~(1u << dir);
-  else if (cd.flags & (F_LN | F_LJ)) m &= ~(1u << nd);
-  incl = m | ((unsigned)dir << 5);
-  return true;
+// Per-chunk constants of the load / store phases: run direction and the
+// neighbour mask of interior nodes (the two perpendicular directions) and of
+// the first and last node.
+struct RunMask {
+  int dir, di, dj;
+  unsigned mid, first, last;
+  __device__ __forceinline__ RunMask(const ChunkDesc &cd) {
+    dir = cd.flags & 3;
+    const int nd = (cd.flags >> 2) & 3;
+    di = di_of(dir);
+    dj = dj_of(dir);
+    const unsigned prev = 1u << (dir ^ 1), next = 1u << dir;
+    const unsigned ex_prev = (cd.flags & (F_LP | F_FJ)) ? prev : 0u;   // predecessor in the chain / junction
+    const unsigned ex_next = (cd.flags & (F_LN | F_LJ)) ? (1u << nd) : 0u;
+    mid = 0xFu & ~prev & ~next;
+    first = 0xFu & ~next & ~ex_prev;
+    last = 0xFu & ~prev & ~ex_next;
+    if (cd.len == 1) first = last = 0xFu & ~ex_prev & ~ex_next;
+  }
+  __device__ __forceinline__ unsigned at(int q, int len) const {
+    return q == 0 ? first : (q == len - 1 ? last : mid);
+  }
+};
+
+// Right-hand sides of U nodes (all loads issued before any is used).  Node k:
+// slot sl[k] (or < 0 for none), coordinates (ik, jk), neighbour mask inc[k]
+// (bits 0-3) and run direction dk[k].  With SC the two along coefficients of
+// each node are stored as well.
+template <typename T, bool SC, int U>
+__device__ __forceinline__ void rhs_batch(const int (&sl)[U], const int (&ik)[U], const int (&jk)[U],
+                                          const unsigned (&inc)[U], const int (&dk)[U], const CoefP<T> &cp,
+                                          int nx1, const T *__restrict__ u, const T *__restrict__ f, T *node,
+                                          T *clo, T *chi) {
+  T fv[U], uw[U], ue[U], us[U], un[U], cw[U], ce[U], cs[U], cn[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    const size_t p = (size_t)jk[k] * nx1 + ik[k];
+    const bool ok = sl[k] >= 0;
+    fv[k] = ok ? f[p] : T(0);
+    uw[k] = (inc[k] & 2u) ? u[p - 1] : T(0);
+    ue[k] = (inc[k] & 1u) ? u[p + 1] : T(0);
+    us[k] = (inc[k] & 8u) ? u[p - nx1] : T(0);
+    un[k] = (inc[k] & 4u) ? u[p + nx1] : T(0);
+    cw[k] = __ldg(cp.W + ik[k]);
+    ce[k] = __ldg(cp.E + ik[k]);
+    cs[k] = __ldg(cp.S + jk[k]);
+    cn[k] = __ldg(cp.N + jk[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    if (sl[k] >= 0) {
+      node[sl[k]] = fv[k] - cw[k] * uw[k] - ce[k] * ue[k] - cs[k] * us[k] - cn[k] * un[k];
+      if constexpr (SC) {
+        const bool x = dk[k] < 2, plus = (dk[k] & 1) == 0;
+        const T a = x ? cw[k] : cs[k], b = x ? ce[k] : cn[k];
+        clo[sl[k]] = plus ? a : b;
+        chi[sl[k]] = plus ? b : a;
+      }
+    }
+  }
 }
+
+// Phases 1 and 3 of one chunk with m nodes (m == CMAX when FULL, so that all
+// guards are resolved at compile time).
+template <typename T, bool SC, bool FULL>
+struct ChunkSolver {
+  const ChunkGeom<T> &g;
+  const T *node, *clo, *chi;
+  int c, m;
+  __device__ __forceinline__ int mm() const { return FULL ? CMAX : m; }
+  __device__ __forceinline__ int sl(int q) const {
+    const int qq = FULL ? q : (q < m ? q : m - 1);
+    return slot_of(c, qq);
+  }
+  __device__ __forceinline__ T LO(int q) const { if constexpr (SC) return clo[sl(q)]; else return g.lo_at(q); }
+  __device__ __forceinline__ T HI(int q) const { if constexpr (SC) return chi[sl(q)]; else return g.hi_at(q); }
+  __device__ __forceinline__ T DD(int q) const { return node[sl(q)]; }
+  __device__ __forceinline__ T A(int q, T lo) const { return (q > 0 || (g.fl & F_LP)) ? lo : T(0); }
+  __device__ __forceinline__ T C(int q, T hi) const { return q < mm() - 1 ? hi : g.clast; }
+
+  // reduced rows: lo (in terms of x_{-1}, x_{m-1}) and hi (x_0, x_m)
+  __device__ __forceinline__ void reduce(T kf, T kl, Row<T> &rlo, Row<T> &rhi) const {
+    const int n = mm();
+    const T l0 = LO(0), h0 = HI(0), d0 = DD(0);
+    const T a0 = A(0, l0), b0 = g.b_of(l0, h0), c0 = C(0, h0);
+    rhi.a = T(0); rhi.c = T(0); rhi.y = T(0); rhi.z = T(0);
+    if (!FULL && n <= 2) {
+      const T rb = rcp(b0);
+      rlo.a = a0 * rb; rlo.c = c0 * rb; rlo.y = d0 * rb; rlo.z = -(n == 1 ? kf + kl : kf) * rb;
+      if (n == 1) return;
+    }
+    const T l1 = LO(1), h1 = HI(1);
+    T rinv_f = rcp(g.b_of(l1, h1));
+    T al = A(1, l1) * rinv_f, ga = C(1, h1) * rinv_f, de = DD(1) * rinv_f;
+    T ah = T(0), ch = T(0), dh = T(0);
+#pragma unroll
+    for (int k = 1; k <= CMAX - 2; ++k) {
+      const int qf = k + 1;  // forward step
+      if (FULL || qf < n) {
+        const T lq = LO(qf), hq = HI(qf);
+        const T a = A(qf, lq), cc = C(qf, hq);
+        const T ri = rcp(g.b_of(lq, hq) - a * ga);
+        al = -a * al * ri;
+        ga = cc * ri;
+        de = (DD(qf) - a * de) * ri;
+        rinv_f = ri;
+      }
+      const int qb = CMAX - 1 - k;  // backward step (descending)
+      if (FULL || qb <= n - 2) {
+        const T lq = LO(qb), hq = HI(qb);
+        const T a = A(qb, lq), cc = C(qb, hq);
+        if ((FULL && k == 1) || (!FULL && qb == n - 2)) {
+          const T ri = rcp(g.b_of(lq, hq));
+          ah = a * ri; ch = cc * ri; dh = DD(qb) * ri;
+        } else {
+          const T ri = rcp(g.b_of(lq, hq) - cc * ah);
+          ah = a * ri;
+          ch = -cc * ch * ri;
+          dh = (DD(qb) - cc * dh) * ri;
+        }
+      }
+    }
+    rhi.a = al; rhi.c = ga; rhi.y = de; rhi.z = -kl * rinv_f;
+    if (FULL || n >= 3) {
+      const T rd = rcp(b0 - c0 * ah);
+      rlo.a = a0 * rd; rlo.c = -c0 * ch * rd; rlo.y = (d0 - c0 * dh) * rd; rlo.z = -kf * rd;
+    }
+  }
+
+  // interior nodes 1..m-2 by Thomas with the known ends, written to the slots
+  __device__ __forceinline__ void interior(T xlo, T xhi, T *out) const {
+    const int n = mm();
+    T cpv[CMAX];
+    T dprev = xlo;
+#pragma unroll
+    for (int q = 1; q < CMAX - 1; ++q) {
+      if (FULL || q <= n - 2) {
+        const T lq = LO(q), hq = HI(q);
+        const T a = A(q, lq), b = g.b_of(lq, hq), cc = C(q, hq);
+        T dq = DD(q) - a * dprev;
+        if ((FULL && q == CMAX - 2) || (!FULL && q == n - 2)) dq -= cc * xhi;
+        const T ri = (q == 1) ? rcp(b) : rcp(b - a * cpv[q - 1]);
+        cpv[q] = cc * ri;
+        dprev = dq * ri;
+        out[slot_of(c, q)] = dprev;
+      }
+    }
+    T xn = dprev;  // x_{m-2}
+#pragma unroll
+    for (int q = CMAX - 3; q >= 1; --q) {
+      if (FULL || q <= n - 3) {
+        xn = out[slot_of(c, q)] - cpv[q] * xn;
+        out[slot_of(c, q)] = xn;
+      }
+    }
+  }
+};
 
 template <typename T, int NT, bool SC>
 __global__ void __launch_bounds__(NT, NT == NT_SMALL ? 2 : 1)
     line_pass_kernel(const CtaWork *__restrict__ works, const ChunkDesc *__restrict__ chunks_all,
-                     const JuncDesc *__restrict__ juncs_all, CoefP<T> cp, int nx1, T *__restrict__ u,
-                     const T *__restrict__ f) {
+                     const JuncDesc *__restrict__ juncs_all, const VGroup *__restrict__ vgs_all, CoefP<T> cp,
+                     int nx1, T *__restrict__ u, const T *__restrict__ f) {
+  using SM = LineSmem<T, NT, SC>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Row<T> *rv = reinterpret_cast<Row<T> *>(smem_raw);                       // 2*NT reduced rows
-  T *node = reinterpret_cast<T *>(smem_raw + LineSmem<T, NT, SC>::rows);   // 32*NT slots (skewed)
-  T *clo = node + 33 * NT;                                                 // along coefficients (SC)
-  T *chi = clo + 33 * NT;
-  T *xj = node + (SC ? 3 : 1) * 33 * NT;                                   // junction values
-  short2 *lu = reinterpret_cast<short2 *>(xj + NT);                        // reduced-row links (L, U)
+  Row<T> *rv = reinterpret_cast<Row<T> *>(smem_raw);                        // 2*NT reduced rows
+  T *node = reinterpret_cast<T *>(smem_raw + SM::rows);                     // 32*NT slots
+  T *clo = node + 32 * NT;                                                  // along coefficients (SC)
+  T *chi = clo + 32 * NT;
+  T *xj = reinterpret_cast<T *>(smem_raw + SM::rows + SM::nodes);           // junction values
+  short2 *lu = reinterpret_cast<short2 *>(smem_raw + SM::rows + SM::nodes + SM::junc);
+  ChunkDesc *sc = reinterpret_cast<ChunkDesc *>(smem_raw + SM::rows + SM::nodes + SM::junc + SM::links);
+  VGroup *svg = reinterpret_cast<VGroup *>(smem_raw + SM::rows + SM::nodes + SM::junc + SM::links + SM::descs);
 
   const CtaWork w = works[blockIdx.x];
-  const ChunkDesc *chunks = chunks_all + w.chunk0;
   const JuncDesc *juncs = juncs_all + w.junc0;
   const int tid = threadIdx.x;
-  const int nslot = 32 * w.nchunk;
-  constexpr int U = 4;  // slots per thread per batch in the load phase
+  for (int t = tid; t < w.nchunk; t += NT) sc[t] = chunks_all[w.chunk0 + t];
+  for (int t = tid; t < w.nvg; t += NT) svg[t] = vgs_all[w.vg0 + t];
+  __syncthreads();
 
-  // ---- phase 0: right-hand sides of all chain nodes (batches of U slots per
-  // thread; all loads of a batch are issued before any is used)
-  for (int s0 = tid; s0 < nslot; s0 += U * NT) {
-    size_t pk[U];
-    unsigned inc[U];
-    int ik[U], jk[U];
+  // ---- phase 0: right-hand sides of all chain nodes.  Grouped vertical
+  // chunks first (lanes over 8 rows x 4 columns), then every other chunk with
+  // lanes along its run; several nodes per thread per batch.
+  {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int vi = warp; vi < w.nvg; vi += NT / 32) {
+      const int c = svg[vi].c[lane & 3];
+      ChunkDesc cd;
+      cd.len = 0; cd.flags = 0; cd.i0 = 1; cd.j0 = 1;
+      if (c != 0xFFFF) cd = sc[c];
+      const RunMask rm(cd);
+      int sl[4], ik[4], jk[4], dk[4];
+      unsigned inc[4];
 #pragma unroll
-    for (int k = 0; k < U; ++k) {
-      const int s = s0 + k * NT;
-      inc[k] = 0; ik[k] = 1; jk[k] = 1;
-      if (s < nslot && slot_node(chunks, s, ik[k], jk[k], inc[k])) inc[k] |= 16u;
-      pk[k] = (size_t)jk[k] * nx1 + ik[k];
-    }
-    T fv[U], uw[U], ue[U], us[U], un[U];
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      const size_t p = pk[k];
-      fv[k] = (inc[k] & 16u) ? f[p] : T(0);
-      uw[k] = (inc[k] & 2u) ? u[p - 1] : T(0);
-      ue[k] = (inc[k] & 1u) ? u[p + 1] : T(0);
-      us[k] = (inc[k] & 8u) ? u[p - nx1] : T(0);
-      un[k] = (inc[k] & 4u) ? u[p + nx1] : T(0);
-    }
-#pragma unroll
-    for (int k = 0; k < U; ++k) {
-      if (inc[k] & 16u) {
-        const int i = ik[k], j = jk[k];
-        const T cw = __ldg(cp.W + i), ce = __ldg(cp.E + i), cs = __ldg(cp.S + j), cn = __ldg(cp.N + j);
-        const int si = sidx(s0 + k * NT);
-        node[si] = fv[k] - cw * uw[k] - ce * ue[k] - cs * us[k] - cn * un[k];
-        if constexpr (SC) {
-          const int dir = (inc[k] >> 5) & 3;
-          clo[si] = dir == DIR_PX ? cw : dir == DIR_MX ? ce : dir == DIR_PY ? cs : cn;
-          chi[si] = dir == DIR_PX ? ce : dir == DIR_MX ? cw : dir == DIR_PY ? cn : cs;
-        }
+      for (int r = 0; r < 4; ++r) {
+        const int q = 8 * r + (lane >> 2);
+        const bool ok = q < cd.len;
+        sl[r] = ok ? slot_of(c, q) : -1;
+        ik[r] = cd.i0 + q * rm.di; jk[r] = cd.j0 + q * rm.dj;
+        if (!ok) { ik[r] = 1; jk[r] = 1; }
+        inc[r] = ok ? rm.at(q, cd.len) : 0u;
+        dk[r] = rm.dir;
       }
+      rhs_batch<T, SC, 4>(sl, ik, jk, inc, dk, cp, nx1, u, f, node, clo, chi);
+    }
+  }
+  {
+    constexpr int U = 4;
+    const int warp = tid >> 5, lane = tid & 31;
+    // warp-uniform chunks: lanes are the nodes of one chunk
+    for (int c0 = warp; c0 < w.nchunk; c0 += U * (NT / 32)) {
+      int sl[U], ik[U], jk[U], dk[U];
+      unsigned inc[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int c = c0 + k * (NT / 32);
+        ChunkDesc cd;
+        cd.len = 0; cd.flags = 0; cd.i0 = 1; cd.j0 = 1; cd.info = GROUPED;
+        if (c < w.nchunk) cd = sc[c];
+        const RunMask rm(cd);
+        const bool ok = lane < cd.len && !(cd.info & GROUPED);
+        sl[k] = ok ? slot_of(c, lane) : -1;
+        ik[k] = ok ? cd.i0 + lane * rm.di : 1;
+        jk[k] = ok ? cd.j0 + lane * rm.dj : 1;
+        inc[k] = ok ? rm.at(lane, cd.len) : 0u;
+        dk[k] = rm.dir;
+      }
+      rhs_batch<T, SC, U>(sl, ik, jk, inc, dk, cp, nx1, u, f, node, clo, chi);
     }
   }
   __syncthreads();
 
-  // ---- phase 1: reduced rows of every chunk.  Two independent eliminations
-  // run interleaved: nodes 1..m-2 towards node m-1 (the "hi" row, in terms of
-  // x_0 and x_m) and nodes m-2..1 towards node 0 (the "lo" row, in terms of
-  // x_{-1} and x_{m-1}).  Loop indices are compile-time so that the chunk's
-  // x_{-1} and x_{m-1}).  Loop indices are compile-time, so the shared-memory (or L1) loads can be hoisted.
+  // ---- phase 1: reduced rows of every chunk (partition method).  Two
+  // independent eliminations run interleaved: nodes 1..m-2 towards node m-1
+  // (the "hi" row, in terms of x_0 and x_m) and nodes m-2..1 towards node 0
+  // (the "lo" row, in terms of x_{-1} and x_{m-1}).
   const int R = 2 * w.nchunk;
   if (tid < w.nchunk) {
-    const ChunkDesc cd = chunks[tid];
+    const ChunkDesc cd = sc[tid];
     ChunkGeom<T> g;
     g.init(cd, cp);
-    const int m = g.m, base = 32 * tid;
-    auto slot = [&](int q) { return sidx(base + (q < m ? q : m - 1)); };
-    auto LO = [&](int q) -> T { if constexpr (SC) return clo[slot(q)]; else return g.lo_at(q); };
-    auto HI = [&](int q) -> T { if constexpr (SC) return chi[slot(q)]; else return g.hi_at(q); };
-    auto DD = [&](int q) -> T { return node[slot(q)]; };
     const T kf = (g.fl & F_FJ) ? cf(cp, g.i0, g.j0, g.dir ^ 1) : T(0);
     const T kl = (g.fl & F_LJ) ? g.cnd : T(0);
-    const T l0 = LO(0), h0 = HI(0), d0 = DD(0);
-    const T a0 = g.a_of(0, l0), b0 = g.b_of(l0, h0), c0 = g.c_of(0, h0);
     Row<T> rlo, rhi;
-    rhi.a = T(0); rhi.c = T(0); rhi.y = T(0); rhi.z = T(0);
-    if (m <= 2) {
-      const T rb = rcp(b0);
-      rlo.a = a0 * rb; rlo.c = c0 * rb; rlo.y = d0 * rb; rlo.z = -(m == 1 ? kf + kl : kf) * rb;
-    }
-    if (m >= 2) {
-      const T l1 = LO(1), h1 = HI(1);
-      T rinv_f = rcp(g.b_of(l1, h1));
-      T al = g.a_of(1, l1) * rinv_f, ga = g.c_of(1, h1) * rinv_f, de = DD(1) * rinv_f;
-      T ah = T(0), ch = T(0), dh = T(0);
-#pragma unroll
-      for (int k = 1; k <= CMAX - 2; ++k) {
-        const int qf = k + 1;  // forward step
-        if (qf < m) {
-          const T lq = LO(qf), hq = HI(qf);
-          const T a = g.a_of(qf, lq), c = g.c_of(qf, hq);
-          const T ri = rcp(g.b_of(lq, hq) - a * ga);
-          al = -a * al * ri;
-          ga = c * ri;
-          de = (DD(qf) - a * de) * ri;
-          rinv_f = ri;
-        }
-        const int qb = CMAX - 1 - k;  // backward step (descending)
-        if (qb <= m - 2) {
-          const T lq = LO(qb), hq = HI(qb);
-          const T a = g.a_of(qb, lq), c = g.c_of(qb, hq);
-          if (qb == m - 2) {
-            const T ri = rcp(g.b_of(lq, hq));
-            ah = a * ri; ch = c * ri; dh = DD(qb) * ri;
-          } else {
-            const T ri = rcp(g.b_of(lq, hq) - c * ah);
-            ah = a * ri;
-            ch = -c * ch * ri;
-            dh = (DD(qb) - c * dh) * ri;
-          }
-        }
-      }
-      rhi.a = al; rhi.c = ga; rhi.y = de; rhi.z = -kl * rinv_f;
-      if (m >= 3) {
-        const T rd = rcp(b0 - c0 * ah);
-        rlo.a = a0 * rd; rlo.c = -c0 * ch * rd; rlo.y = (d0 - c0 * dh) * rd; rlo.z = -kf * rd;
-      }
-    }
+    if (g.m == CMAX) ChunkSolver<T, SC, true>{g, node, clo, chi, tid, g.m}.reduce(kf, kl, rlo, rhi);
+    else ChunkSolver<T, SC, false>{g, node, clo, chi, tid, g.m}.reduce(kf, kl, rlo, rhi);
+    const int m = g.m;
     short Llo = -1, Ulo;
-    if (g.fl & F_LP) Llo = (short)(chunks[tid - 1].len >= 2 ? 2 * (tid - 1) + 1 : 2 * (tid - 1));
+    if (g.fl & F_LP) Llo = (short)(sc[tid - 1].len >= 2 ? 2 * (tid - 1) + 1 : 2 * (tid - 1));
     if (m >= 2) Ulo = (short)(2 * tid + 1);
     else Ulo = (g.fl & F_LN) ? (short)(2 * (tid + 1)) : (short)-1;
     rv[2 * tid] = rlo;
@@ -348,52 +453,42 @@ __global__ void __launch_bounds__(NT, NT == NT_SMALL ? 2 : 1)
 
   // ---- phase 3: chunk ends from the reduced solution, interiors by Thomas
   if (tid < w.nchunk) {
-    const ChunkDesc cd = chunks[tid];
+    const ChunkDesc cd = sc[tid];
     ChunkGeom<T> g;
     g.init(cd, cp);
-    const int m = g.m, base = 32 * tid;
-    const T jx = (cd.junc != 0xFFFF) ? xj[cd.junc] : T(0);
+    const int m = g.m;
+    const int jn = cd.info & 1023;
+    const T jx = (jn != JNONE) ? xj[jn] : T(0);
     const Row<T> r0 = rv[2 * tid], r1 = rv[2 * tid + 1];
     const T xlo = r0.y + jx * r0.z;
     const T xhi = (m >= 2) ? r1.y + jx * r1.z : xlo;
-    if (m >= 3) {
-      auto slot = [&](int q) { return sidx(base + (q < m ? q : m - 1)); };
-      auto LO = [&](int q) -> T { if constexpr (SC) return clo[slot(q)]; else return g.lo_at(q); };
-      auto HI = [&](int q) -> T { if constexpr (SC) return chi[slot(q)]; else return g.hi_at(q); };
-      T cpv[CMAX];
-      T dprev = xlo;
-#pragma unroll
-      for (int q = 1; q < CMAX - 1; ++q) {
-        if (q <= m - 2) {
-          const T lq = LO(q), hq = HI(q);
-          const T a = g.a_of(q, lq), b = g.b_of(lq, hq), c = g.c_of(q, hq);
-          T dq = node[sidx(base + q)] - a * dprev;
-          if (q == m - 2) dq -= c * xhi;
-          const T ri = (q == 1) ? rcp(b) : rcp(b - a * cpv[q - 1]);
-          cpv[q] = c * ri;
-          dprev = dq * ri;
-          node[sidx(base + q)] = dprev;
-        }
-      }
-      T xn = dprev;  // x_{m-2}
-#pragma unroll
-      for (int q = CMAX - 3; q >= 1; --q) {
-        if (q <= m - 3) {
-          xn = node[sidx(base + q)] - cpv[q] * xn;
-          node[sidx(base + q)] = xn;
-        }
-      }
-    }
-    node[sidx(base)] = xlo;
-    if (m >= 2) node[sidx(base + m - 1)] = xhi;
+    if (m == CMAX) ChunkSolver<T, SC, true>{g, node, clo, chi, tid, m}.interior(xlo, xhi, node);
+    else if (m >= 3) ChunkSolver<T, SC, false>{g, node, clo, chi, tid, m}.interior(xlo, xhi, node);
+    node[slot_of(tid, 0)] = xlo;
+    if (m >= 2) node[slot_of(tid, m - 1)] = xhi;
   }
   __syncthreads();
 
-  // ---- phase 4: write the block back
-  for (int s = tid; s < nslot; s += NT) {
-    int i, j;
-    unsigned inc;
-    if (slot_node(chunks, s, i, j, inc)) u[(size_t)j * nx1 + i] = node[sidx(s)];
+  // ---- phase 4: write the block back (same two mappings as phase 0)
+  {
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int vi = warp; vi < w.nvg; vi += NT / 32) {
+      const int c = svg[vi].c[lane & 3];
+      if (c == 0xFFFF) continue;
+      const ChunkDesc cd = sc[c];
+      const int dj = dj_of(cd.flags & 3);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int q = 8 * r + (lane >> 2);
+        if (q < cd.len) u[(size_t)(cd.j0 + q * dj) * nx1 + cd.i0] = node[slot_of(c, q)];
+      }
+    }
+    for (int c = warp; c < w.nchunk; c += NT / 32) {
+      const ChunkDesc cd = sc[c];
+      if ((cd.info & GROUPED) || lane >= cd.len) continue;
+      const int dir = cd.flags & 3;
+      u[(size_t)(cd.j0 + lane * dj_of(dir)) * nx1 + cd.i0 + lane * di_of(dir)] = node[slot_of(c, lane)];
+    }
   }
 }
 
@@ -409,13 +504,13 @@ static cudaError_t launch_shape(const Level &L, const WorkList &w, T *u, const T
   constexpr bool SC = sizeof(T) == 4;  // FP64 keeps the coefficients in L1 (smem is too small)
   constexpr size_t smem = LineSmem<T, NT, SC>::bytes;
   auto kern = line_pass_kernel<T, NT, SC>;
-  static bool configured = false;
+  static bool configured = false;  // dynamic shared memory opted in once
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  kern<<<w.ncta, NT, smem, s>>>(w.cta, w.chunk, w.junc, coefs_of<T>(L), L.nx + 1, u, f);
+  kern<<<w.ncta, NT, smem, s>>>(w.cta, w.chunk, w.junc, w.vg, coefs_of<T>(L), L.nx + 1, u, f);
   count_launch(1);
   return cudaGetLastError();
 }

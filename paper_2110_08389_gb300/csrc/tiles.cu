@@ -1,0 +1,411 @@
+// tiles.cu -- the tiled line path of tweedmg (sm_103a): one colour pass of
+// tweed or zebra relaxation on a large level, as three kernels (see TileList
+// in mg_internal.h for the data layout).
+//
+// Each block (Sec. 3) is solved exactly.  The solve is the paper's m-legged
+// Thomas algorithm (Eq. mLThomas) organised in three levels:
+//   tile_reduce  one lane per 32-node chunk of a leg: the chunk's right-hand
+//                side (f minus the neighbours outside the block) and, by
+//                eliminating its interior (partition method), two rows
+//                coupling its first and last node to the neighbouring chunks;
+//   tile_couple  one thread per leg: Thomas on those rows from the wall
+//                towards the junction; the junction row fixes the junction
+//                value; back-substitution gives every chunk's end values;
+//   tile_expand  one lane per chunk: the interior by Thomas between the known
+//                ends, written to u.
+// Lanes of a tile are parallel legs at the same stretch of 32 positions, so
+// the along-direction coefficients are the same for all lanes (broadcast
+// loads); vertical tiles read and write u coalesced across lanes, horizontal
+// tiles go through a per-warp shared-memory transpose.
+#include "mg_internal.h"
+
+namespace tmg {
+
+namespace {
+
+constexpr int TW = 4;  // warps (tiles) per CTA in tile_reduce / tile_expand
+
+template <typename T>
+struct CoefT {
+  const T *W, *E, *S, *N;
+};
+template <typename T>
+CoefT<T> coefs(const Level &L);
+template <>
+CoefT<double> coefs<double>(const Level &L) { return {L.W64, L.E64, L.S64, L.N64}; }
+template <>
+CoefT<float> coefs<float>(const Level &L) { return {L.W32, L.E32, L.S32, L.N32}; }
+
+__device__ __forceinline__ float rcp_t(float x) { return __fdividef(1.0f, x); }
+// Newton-Raphson reciprocal from the FP32 one (see smooth.cu)
+__device__ __forceinline__ double rcp_t(double x) {
+  double r = (double)__frcp_rn((float)x);
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  return fma(r, e, r);
+}
+
+template <typename T>
+struct __align__(4 * sizeof(T)) TRow {
+  T a, c, y, z;  // a x_prev + x + c x_next = y   (z unused)
+};
+
+// Per-tile constants: run direction, step, which coefficient array is the
+// predecessor / successor coupling along the run, and the lane's
+// perpendicular coefficient sum.
+template <typename T>
+struct TileGeom {
+  int base, step;
+  bool xrun;
+  const T *lo_arr, *hi_arr;
+  __device__ __forceinline__ TileGeom(const TileDesc &td, const CoefT<T> &cp) {
+    const int dir = td.dir;
+    xrun = dir < 2;
+    step = (dir == DIR_PX || dir == DIR_PY) ? 1 : -1;
+    base = td.base;
+    if (xrun) { lo_arr = step > 0 ? cp.W : cp.E; hi_arr = step > 0 ? cp.E : cp.W; }
+    else { lo_arr = step > 0 ? cp.S : cp.N; hi_arr = step > 0 ? cp.N : cp.S; }
+  }
+  __device__ __forceinline__ int v(int q) const { return base + q * step; }
+};
+
+// Coefficients of slot q for a lane with m active slots and flags fl:
+// a (predecessor), c (successor), b (diagonal).  The along coefficients of
+// the tile's 32 positions are the same for every lane; each warp stages them
+// once in shared memory (co[0][q] = predecessor side, co[1][q] = successor).
+template <typename T>
+__device__ __forceinline__ void abc(const T (&co)[2][32], int q, int m, int fl, T cross, T &a, T &b, T &c) {
+  const T lo = co[0][q], hi = co[1][q];
+  b = -(cross + (lo + hi));
+  a = (q == 0 && (fl & TL_FIRST)) ? T(0) : lo;
+  c = (q == m - 1 && (fl & TL_LAST_W)) ? T(0) : hi;
+}
+
+template <typename T>
+__device__ __forceinline__ void stage_coefs(const TileGeom<T> &g, int lane, T (&co)[2][32]) {
+  co[0][lane] = __ldg(g.lo_arr + g.v(lane));
+  co[1][lane] = __ldg(g.hi_arr + g.v(lane));
+  __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * TW) tile_reduce(const TileDesc *__restrict__ tiles,
+                                                       const TileLane *__restrict__ lanes, int ntile, CoefT<T> cp,
+                                                       int nx1, const T *__restrict__ u, const T *__restrict__ f,
+                                                       TRow<T> *__restrict__ rows, T *__restrict__ dscr) {
+  __shared__ T tr[TW][32][33];
+  __shared__ T cos[TW][2][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * TW + warp;
+  if (t >= ntile) return;
+  const TileDesc td = tiles[t];
+  const TileLane ln = lanes[(size_t)t * 32 + lane];
+  const TileGeom<T> g(td, cp);
+  const int m = ln.q1, fl = ln.flags;
+  T d[CMAX];
+  stage_coefs(g, lane, cos[warp]);
+  const T(&co)[2][32] = cos[warp];
+
+  // ---- right-hand sides
+  if (!g.xrun) {
+    // vertical tile: lane = column, slots = rows; coalesced across lanes
+    const int i = ln.line;
+    const T cw = __ldg(cp.W + i), ce = __ldg(cp.E + i);
+    const int sv = g.step * nx1;
+#pragma unroll
+    for (int q = 0; q < CMAX; ++q) {
+      const bool on = q < m;
+      const int j = g.v(q);
+      const size_t p = (size_t)j * nx1 + i;
+      T r = T(0);
+      if (on) {
+        r = f[p] - cw * u[p - 1] - ce * u[p + 1];
+        if (q == 0 && (fl & TL_FIRST)) r -= co[0][q] * u[p - sv];
+        if (q == m - 1 && (fl & TL_LAST_W)) r -= co[1][q] * u[p + sv];
+      }
+      d[q] = r;
+    }
+  } else {
+    // horizontal tile: for each lane's row in turn, all lanes load along it
+    // (coalesced) and the values are transposed through shared memory
+    const int q = lane;
+    const int i = g.v(q);
+    const T lo_i = co[0][q], hi_i = co[1][q];
+#pragma unroll 4
+    for (int c = 0; c < 32; ++c) {
+      const int jc = __shfl_sync(0xffffffffu, (int)ln.line, c);
+      const int mc = __shfl_sync(0xffffffffu, m, c);
+      const int fc = __shfl_sync(0xffffffffu, fl, c);
+      T r = T(0);
+      if (q < mc) {
+        const size_t p = (size_t)jc * nx1 + i;
+        r = f[p] - __ldg(cp.S + jc) * u[p - nx1] - __ldg(cp.N + jc) * u[p + nx1];
+        if (q == 0 && (fc & TL_FIRST)) r -= lo_i * u[p - g.step];
+        if (q == mc - 1 && (fc & TL_LAST_W)) r -= hi_i * u[p + g.step];
+      }
+      tr[warp][c][q] = r;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < CMAX; ++k) d[k] = tr[warp][lane][k];
+  }
+  if (m == 0) return;
+  const T cross = g.xrun ? __ldg(cp.S + ln.line) + __ldg(cp.N + ln.line) : __ldg(cp.W + ln.line) + __ldg(cp.E + ln.line);
+
+  // ---- the chunk's two reduced rows: eliminate nodes 1..m-2 towards node
+  // m-1 (hi row, in terms of x_0 and x_m) and nodes m-2..1 towards node 0 (lo
+  // row, in terms of x_{-1} and x_{m-1}); the two sweeps are interleaved
+  T a0, b0, c0;
+  abc(co, 0, m, fl, cross, a0, b0, c0);
+  TRow<T> rlo, rhi;
+  rhi.a = T(0); rhi.c = T(0); rhi.y = T(0); rhi.z = T(0);
+  rlo.z = T(0);
+  if (m <= 2) {
+    const T rb = rcp_t(b0);
+    rlo.a = a0 * rb; rlo.c = c0 * rb; rlo.y = d[0] * rb;
+  }
+  if (m >= 2) {
+    T a1, b1, c1;
+    abc(co, 1, m, fl, cross, a1, b1, c1);
+    T ri = rcp_t(b1);
+    T al = a1 * ri, ga = c1 * ri, de = d[1] * ri;
+    T ah = T(0), ch = T(0), dh = T(0);
+#pragma unroll
+    for (int k = 1; k <= CMAX - 2; ++k) {
+      const int qf = k + 1;
+      if (qf < m) {
+        T a, b, c;
+        abc(co, qf, m, fl, cross, a, b, c);
+        const T r = rcp_t(b - a * ga);
+        al = -a * al * r;
+        ga = c * r;
+        de = (d[qf] - a * de) * r;
+      }
+      const int qb = CMAX - 1 - k;
+      if (qb <= m - 2) {
+        T a, b, c;
+        abc(co, qb, m, fl, cross, a, b, c);
+        if (qb == m - 2) {
+          const T r = rcp_t(b);
+          ah = a * r; ch = c * r; dh = d[qb] * r;
+        } else {
+          const T r = rcp_t(b - c * ah);
+          ah = a * r;
+          ch = -c * ch * r;
+          dh = (d[qb] - c * dh) * r;
+        }
+      }
+    }
+    rhi.a = al; rhi.c = ga; rhi.y = de;
+    if (m >= 3) {
+      const T r = rcp_t(b0 - c0 * ah);
+      rlo.a = a0 * r; rlo.c = -c0 * ch * r; rlo.y = (d[0] - c0 * dh) * r;
+    }
+  }
+  rows[((size_t)t * 32 + lane) * 2] = rlo;
+  rows[((size_t)t * 32 + lane) * 2 + 1] = rhi;
+#pragma unroll
+  for (int q = 0; q < CMAX; ++q)
+    if (q < m) dscr[((size_t)t * 32 + q) * 32 + lane] = d[q];
+}
+
+// One CTA per group: thread (leg l, lane b).  Thomas on the leg's reduced
+// rows from the wall to the junction (normalised rows, so the pivot of row k
+// is 1 - a_k c'_{k-1}); the block's junction row; back-substitution.  The
+// forward sweep writes (c', d') to a separate array so that the row loads of
+// later chunks do not wait for those stores.
+template <typename T>
+__global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__ blocks, CoefT<T> cp, int nx1,
+                                                   const TRow<T> *__restrict__ rows, T *cdp,
+                                                   T *__restrict__ xscr, T *__restrict__ u, const T *__restrict__ f) {
+  __shared__ T s_cp[4][32], s_dp[4][32], s_xj[32];
+  const int l = threadIdx.x >> 5, b = threadIdx.x & 31;
+  const BlockDesc bd = blocks[(size_t)blockIdx.x * 32 + b];
+  const bool active = l < bd.nleg;
+  const int len = active ? bd.leg_len[l] : 0;
+  const int nch = (len + CMAX - 1) / CMAX;
+  const size_t t0 = active ? bd.leg_tile0[l] : 0;
+  T cpv = T(0), dpv = T(0);
+  constexpr int B = 8;  // chunks whose rows are loaded together
+  for (int r0 = 0; r0 < nch; r0 += B) {
+    TRow<T> lo[B], hi[B];
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+      if (r0 + k < nch) {
+        const size_t idx = ((t0 + r0 + k) * 32 + bd.lane) * 2;
+        lo[k] = rows[idx];
+        hi[k] = rows[idx + 1];
+      }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int r = r0 + k;
+      if (r < nch) {
+        const size_t idx = ((t0 + r) * 32 + bd.lane) * 2;
+        const int mlen = min(CMAX, len - CMAX * r);
+        T den = rcp_t(T(1) - lo[k].a * cpv);
+        cpv = lo[k].c * den;
+        dpv = (lo[k].y - lo[k].a * dpv) * den;
+        cdp[2 * idx] = cpv; cdp[2 * idx + 1] = dpv;
+        if (mlen >= 2) {
+          den = rcp_t(T(1) - hi[k].a * cpv);
+          cpv = hi[k].c * den;
+          dpv = (hi[k].y - hi[k].a * dpv) * den;
+          cdp[2 * idx + 2] = cpv; cdp[2 * idx + 3] = dpv;
+        }
+      }
+    }
+  }
+  s_cp[l][b] = cpv;
+  s_dp[l][b] = dpv;
+  __syncthreads();
+  if (l == 0 && bd.junc) {
+    const int i = bd.ji, j = bd.jj;
+    const size_t p = (size_t)j * nx1 + i;
+    unsigned att = 0;
+    for (int e = 0; e < bd.nleg; ++e) att |= 1u << ((bd.jdirs >> (2 * e)) & 3);
+    const T w = __ldg(cp.W + i), e_ = __ldg(cp.E + i), s = __ldg(cp.S + j), n = __ldg(cp.N + j);
+    T num = f[p];
+    if (!(att & 2u)) num -= w * u[p - 1];
+    if (!(att & 1u)) num -= e_ * u[p + 1];
+    if (!(att & 8u)) num -= s * u[p - nx1];
+    if (!(att & 4u)) num -= n * u[p + nx1];
+    T den = -((w + e_) + (s + n));
+    for (int e = 0; e < bd.nleg; ++e) {
+      const int d = (bd.jdirs >> (2 * e)) & 3;
+      const T k = d == DIR_PX ? e_ : d == DIR_MX ? w : d == DIR_PY ? n : s;
+      num -= k * s_dp[e][b];
+      den -= k * s_cp[e][b];
+    }
+    const T x = num / den;
+    u[p] = x;
+    s_xj[b] = x;
+  }
+  __syncthreads();
+  if (!active) return;
+  T xn = bd.junc ? s_xj[b] : T(0);
+  // back-substitution, chunk by chunk towards the wall, B chunks per batch
+  for (int r1 = nch - 1; r1 >= 0; r1 -= B) {
+    T v[B][4];
+#pragma unroll
+    for (int k = 0; k < B; ++k)
+      if (r1 - k >= 0) {
+        const size_t idx = ((t0 + r1 - k) * 32 + bd.lane) * 2;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[k][e] = cdp[2 * idx + e];
+      }
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int r = r1 - k;
+      if (r >= 0) {
+        const int mlen = min(CMAX, len - CMAX * r);
+        T xhi = T(0);
+        if (mlen >= 2) {
+          xhi = v[k][3] - v[k][2] * xn;
+          xn = xhi;
+        }
+        const T xlo = v[k][1] - v[k][0] * xn;
+        xn = xlo;
+        if (mlen < 2) xhi = xlo;
+        xscr[((t0 + r) * 32 + bd.lane) * 2] = xlo;
+        xscr[((t0 + r) * 32 + bd.lane) * 2 + 1] = xhi;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * TW) tile_expand(const TileDesc *__restrict__ tiles,
+                                                       const TileLane *__restrict__ lanes, int ntile, CoefT<T> cp,
+                                                       int nx1, const T *__restrict__ dscr,
+                                                       const T *__restrict__ xscr, T *__restrict__ u) {
+  __shared__ T tr[TW][32][33];
+  __shared__ T cos[TW][2][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int t = blockIdx.x * TW + warp;
+  if (t >= ntile) return;
+  const TileDesc td = tiles[t];
+  const TileLane ln = lanes[(size_t)t * 32 + lane];
+  const TileGeom<T> g(td, cp);
+  const int m = ln.q1, fl = ln.flags;
+  T d[CMAX];
+  stage_coefs(g, lane, cos[warp]);
+  const T(&co)[2][32] = cos[warp];
+  T *cpv = tr[warp][lane];  // the lane's row of the transpose buffer holds c' until the write-back
+  if (m > 0) {
+    const T cross = g.xrun ? __ldg(cp.S + ln.line) + __ldg(cp.N + ln.line)
+                           : __ldg(cp.W + ln.line) + __ldg(cp.E + ln.line);
+#pragma unroll
+    for (int q = 0; q < CMAX; ++q) d[q] = q < m ? dscr[((size_t)t * 32 + q) * 32 + lane] : T(0);
+    const T xlo = xscr[((size_t)t * 32 + lane) * 2], xhi = xscr[((size_t)t * 32 + lane) * 2 + 1];
+    T dprev = xlo;
+#pragma unroll
+    for (int q = 1; q < CMAX - 1; ++q) {
+      if (q <= m - 2) {
+        T a, b, c;
+        abc(co, q, m, fl, cross, a, b, c);
+        T dq = d[q] - a * dprev;
+        if (q == m - 2) dq -= c * xhi;
+        const T r = (q == 1) ? rcp_t(b) : rcp_t(b - a * cpv[q - 1]);
+        cpv[q] = c * r;
+        dprev = dq * r;
+        d[q] = dprev;
+      }
+    }
+    T xn = dprev;
+#pragma unroll
+    for (int q = CMAX - 3; q >= 1; --q) {
+      if (q <= m - 3) {
+        xn = d[q] - cpv[q] * xn;
+        d[q] = xn;
+      }
+    }
+    d[0] = xlo;
+#pragma unroll
+    for (int q = 1; q < CMAX; ++q)
+      if (q == m - 1) d[q] = xhi;
+  }
+  if (!g.xrun) {
+    const int i = ln.line;
+#pragma unroll
+    for (int q = 0; q < CMAX; ++q)
+      if (q < m) u[(size_t)g.v(q) * nx1 + i] = d[q];
+  } else {
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < CMAX; ++k) tr[warp][lane][k] = d[k];
+    __syncwarp();
+    const int q = lane;
+    const int i = g.v(q);
+#pragma unroll 4
+    for (int c = 0; c < 32; ++c) {
+      const int jc = __shfl_sync(0xffffffffu, (int)ln.line, c);
+      const int mc = __shfl_sync(0xffffffffu, m, c);
+      if (q < mc) u[(size_t)jc * nx1 + i] = tr[warp][c][q];
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &tl, T *u, const T *f, cudaStream_t s) {
+  if (tl.ntile == 0 && tl.nblock == 0) return cudaSuccess;
+  TRow<T> *rows = static_cast<TRow<T> *>(g.tile_rows);
+  T *cdp = reinterpret_cast<T *>(static_cast<char *>(g.tile_rows) + g.tile_cap * 32 * 2 * sizeof(TRow<double>));
+  T *dscr = static_cast<T *>(g.tile_d), *xscr = static_cast<T *>(g.tile_x);
+  const CoefT<T> cp = coefs<T>(L);
+  const int nx1 = L.nx + 1;
+  const int ctas = (tl.ntile + TW - 1) / TW;
+  if (tl.ntile > 0) tile_reduce<T><<<ctas, 32 * TW, 0, s>>>(tl.tile, tl.lane, tl.ntile, cp, nx1, u, f, rows, dscr);
+  tile_couple<T><<<tl.ngroup, 128, 0, s>>>(tl.block, cp, nx1, rows, cdp, xscr, u, f);
+  if (tl.ntile > 0) tile_expand<T><<<ctas, 32 * TW, 0, s>>>(tl.tile, tl.lane, tl.ntile, cp, nx1, dscr, xscr, u);
+  count_launch(tl.ntile > 0 ? 3 : 1);
+  return cudaGetLastError();
+}
+template cudaError_t launch_tile_pass<double>(const Grid &, const Level &, const TileList &, double *, const double *,
+                                              cudaStream_t);
+template cudaError_t launch_tile_pass<float>(const Grid &, const Level &, const TileList &, float *, const float *,
+                                             cudaStream_t);
+
+}  // namespace tmg

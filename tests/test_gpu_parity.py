@@ -32,6 +32,8 @@ GRIDS = [
     (96, 136, "centre", 2.0),
     (200, 72, "wall", 2.5),
     (256, 256, "wall", 3.043),
+    (320, 256, "wall", 2.0),      # large enough for the tiled path; T-blocks and lines
+    (272, 512, "centre", 1.2),    # ragged tiles, rows longer than columns
 ]
 BASE_SMOOTHERS = ["checkerboard", "zebra_x", "zebra_y", "tweed", "wireframe"]
 

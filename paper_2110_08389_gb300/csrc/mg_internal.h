@@ -135,6 +135,7 @@ static_assert(sizeof(BlockDesc) == 32, "BlockDesc layout");
 
 struct TileList {
   int ntile = 0, nblock = 0, ngroup = 0;
+  int max_leg_chunks = 0;       // longest leg, in chunks
   int total_nodes = 0;
   void *mem = nullptr;
   TileDesc *tile = nullptr;

@@ -129,7 +129,7 @@ mg_status build_tiles(Grid &g, int level, int wl) {
     std::vector<TileDesc> tiles;
     std::vector<TileLane> lanes;
     std::vector<BlockDesc> blocks;
-    int total = 0;
+    int total = 0, max_chunks = 0;
     size_t b0 = 0;
     while (b0 < specs.size()) {
       size_t b1 = b0 + 1;
@@ -147,6 +147,7 @@ mg_status build_tiles(Grid &g, int level, int wl) {
         int maxlen = 0;
         for (int b = 0; b < nb; ++b) maxlen = std::max(maxlen, specs[b0 + b].legs[l].len);
         const int nt = (maxlen + CMAX - 1) / CMAX;
+        max_chunks = std::max(max_chunks, nt);
         const LegSpec &ref = specs[b0].legs[l];
         const int step = (ref.dir == DIR_PX || ref.dir == DIR_PY) ? 1 : -1;
         const uint32_t t0 = (uint32_t)tiles.size();
@@ -194,6 +195,7 @@ mg_status build_tiles(Grid &g, int level, int wl) {
     T.nblock = (int)blocks.size();
     T.ngroup = T.nblock / 32;
     T.total_nodes = total;
+    T.max_leg_chunks = max_chunks;
     const size_t s0 = align16<TileDesc>(std::max<size_t>(tiles.size(), 1)),
                  s1 = align16<TileLane>(std::max<size_t>(lanes.size(), 1)),
                  s2 = align16<BlockDesc>(std::max<size_t>(blocks.size(), 1));

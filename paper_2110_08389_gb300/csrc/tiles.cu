@@ -23,7 +23,10 @@ namespace tmg {
 
 namespace {
 
-constexpr int TW = 4;  // warps (tiles) per CTA in tile_reduce / tile_expand
+// warps (tiles) per CTA in tile_reduce / tile_expand (static shared memory
+// per CTA stays below 48 KB)
+template <typename T>
+constexpr int TWv = sizeof(T) == 8 ? 2 : 4;
 
 template <typename T>
 struct CoefT {
@@ -90,10 +93,11 @@ __device__ __forceinline__ void stage_coefs(const TileGeom<T> &g, int lane, T (&
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32 * TW) tile_reduce(const TileDesc *__restrict__ tiles,
+__global__ void __launch_bounds__(32 * TWv<T>) tile_reduce(const TileDesc *__restrict__ tiles,
                                                        const TileLane *__restrict__ lanes, int ntile, CoefT<T> cp,
                                                        int nx1, const T *__restrict__ u, const T *__restrict__ f,
                                                        TRow<T> *__restrict__ rows, T *__restrict__ dscr) {
+  constexpr int TW = TWv<T>;
   __shared__ T tr[TW][32][33];
   __shared__ T cos[TW][2][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -107,43 +111,43 @@ __global__ void __launch_bounds__(32 * TW) tile_reduce(const TileDesc *__restric
   stage_coefs(g, lane, cos[warp]);
   const T(&co)[2][32] = cos[warp];
 
-  // ---- right-hand sides
+  // ---- right-hand sides.  Loads are unconditional (indices clamped into the
+  // lane's run) so that all of them can be in flight at once; the wall terms
+  // of a leg's first / last node are loaded before the loop.
+  const int mq = m > 0 ? m - 1 : 0;  // last valid slot (clamp)
   if (!g.xrun) {
     // vertical tile: lane = column, slots = rows; coalesced across lanes
-    const int i = ln.line;
+    const int i = m > 0 ? ln.line : 1;
     const T cw = __ldg(cp.W + i), ce = __ldg(cp.E + i);
     const int sv = g.step * nx1;
+    const size_t p0 = (size_t)g.v(0) * nx1 + i, pm = (size_t)g.v(mq) * nx1 + i;
+    const T wfirst = (fl & TL_FIRST) ? co[0][0] * u[p0 - sv] : T(0);
+    const T wlast = (fl & TL_LAST_W) ? co[1][mq] * u[pm + sv] : T(0);
 #pragma unroll
     for (int q = 0; q < CMAX; ++q) {
-      const bool on = q < m;
-      const int j = g.v(q);
-      const size_t p = (size_t)j * nx1 + i;
-      T r = T(0);
-      if (on) {
-        r = f[p] - cw * u[p - 1] - ce * u[p + 1];
-        if (q == 0 && (fl & TL_FIRST)) r -= co[0][q] * u[p - sv];
-        if (q == m - 1 && (fl & TL_LAST_W)) r -= co[1][q] * u[p + sv];
-      }
+      const int qq = q < m ? q : mq;
+      const size_t p = (size_t)g.v(qq) * nx1 + i;
+      T r = f[p] - cw * u[p - 1] - ce * u[p + 1];
+      if (q == 0) r -= wfirst;
+      if (q == mq) r -= wlast;
       d[q] = r;
     }
   } else {
     // horizontal tile: for each lane's row in turn, all lanes load along it
     // (coalesced) and the values are transposed through shared memory
     const int q = lane;
-    const int i = g.v(q);
-    const T lo_i = co[0][q], hi_i = co[1][q];
 #pragma unroll 4
     for (int c = 0; c < 32; ++c) {
       const int jc = __shfl_sync(0xffffffffu, (int)ln.line, c);
       const int mc = __shfl_sync(0xffffffffu, m, c);
       const int fc = __shfl_sync(0xffffffffu, fl, c);
-      T r = T(0);
-      if (q < mc) {
-        const size_t p = (size_t)jc * nx1 + i;
-        r = f[p] - __ldg(cp.S + jc) * u[p - nx1] - __ldg(cp.N + jc) * u[p + nx1];
-        if (q == 0 && (fc & TL_FIRST)) r -= lo_i * u[p - g.step];
-        if (q == mc - 1 && (fc & TL_LAST_W)) r -= hi_i * u[p + g.step];
-      }
+      const int jj = mc > 0 ? jc : 1;
+      const int qq = q < mc ? q : (mc > 0 ? mc - 1 : 0);
+      const int i = g.v(qq);
+      const size_t p = (size_t)jj * nx1 + i;
+      T r = f[p] - __ldg(cp.S + jj) * u[p - nx1] - __ldg(cp.N + jj) * u[p + nx1];
+      if (q == 0 && (fc & TL_FIRST)) r -= co[0][0] * u[p - g.step];
+      if (q == mc - 1 && (fc & TL_LAST_W)) r -= co[1][q] * u[p + g.step];
       tr[warp][c][q] = r;
     }
     __syncwarp();
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__
   const int nch = (len + CMAX - 1) / CMAX;
   const size_t t0 = active ? bd.leg_tile0[l] : 0;
   T cpv = T(0), dpv = T(0);
-  constexpr int B = 8;  // chunks whose rows are loaded together
+  constexpr int B = 16;  // chunks whose rows are loaded together
   for (int r0 = 0; r0 < nch; r0 += B) {
     TRow<T> lo[B], hi[B];
 #pragma unroll
@@ -315,66 +319,68 @@ __global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__
 }
 
 template <typename T>
-__global__ void __launch_bounds__(32 * TW) tile_expand(const TileDesc *__restrict__ tiles,
+__global__ void __launch_bounds__(32 * TWv<T>) tile_expand(const TileDesc *__restrict__ tiles,
                                                        const TileLane *__restrict__ lanes, int ntile, CoefT<T> cp,
                                                        int nx1, const T *__restrict__ dscr,
                                                        const T *__restrict__ xscr, T *__restrict__ u) {
+  // per lane one row of x (tr) and of the Thomas multipliers c' (cs) in
+  // shared memory, stride 33 (conflict-free both per lane and per slot)
+  constexpr int TW = TWv<T>;
   __shared__ T tr[TW][32][33];
+  __shared__ T cs[TW][32][33];
   __shared__ T cos[TW][2][32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int t = blockIdx.x * TW + warp;
-  if (t >= ntile) return;
+  // tiles in the reverse order of tile_reduce: the u lines it read last are
+  // the likeliest to still be in L2 for these partial-sector writes
+  const int t = ntile - 1 - (blockIdx.x * TW + warp);
+  if (t < 0) return;
   const TileDesc td = tiles[t];
   const TileLane ln = lanes[(size_t)t * 32 + lane];
   const TileGeom<T> g(td, cp);
   const int m = ln.q1, fl = ln.flags;
-  T d[CMAX];
   stage_coefs(g, lane, cos[warp]);
   const T(&co)[2][32] = cos[warp];
-  T *cpv = tr[warp][lane];  // the lane's row of the transpose buffer holds c' until the write-back
+  T *x = tr[warp][lane], *cpv = cs[warp][lane];
   if (m > 0) {
     const T cross = g.xrun ? __ldg(cp.S + ln.line) + __ldg(cp.N + ln.line)
                            : __ldg(cp.W + ln.line) + __ldg(cp.E + ln.line);
-#pragma unroll
-    for (int q = 0; q < CMAX; ++q) d[q] = q < m ? dscr[((size_t)t * 32 + q) * 32 + lane] : T(0);
     const T xlo = xscr[((size_t)t * 32 + lane) * 2], xhi = xscr[((size_t)t * 32 + lane) * 2 + 1];
+    const T *dl = dscr + (size_t)t * 32 * 32 + lane;  // d of slot q at dl[32 q]
+    T dv[CMAX];
+#pragma unroll
+    for (int q = 0; q < CMAX; ++q) dv[q] = dl[32 * (q < m ? q : m - 1)];  // all loads in flight
     T dprev = xlo;
 #pragma unroll
     for (int q = 1; q < CMAX - 1; ++q) {
       if (q <= m - 2) {
         T a, b, c;
         abc(co, q, m, fl, cross, a, b, c);
-        T dq = d[q] - a * dprev;
+        T dq = dv[q] - a * dprev;
         if (q == m - 2) dq -= c * xhi;
         const T r = (q == 1) ? rcp_t(b) : rcp_t(b - a * cpv[q - 1]);
         cpv[q] = c * r;
         dprev = dq * r;
-        d[q] = dprev;
+        x[q] = dprev;
       }
     }
     T xn = dprev;
 #pragma unroll
     for (int q = CMAX - 3; q >= 1; --q) {
       if (q <= m - 3) {
-        xn = d[q] - cpv[q] * xn;
-        d[q] = xn;
+        xn = x[q] - cpv[q] * xn;
+        x[q] = xn;
       }
     }
-    d[0] = xlo;
-#pragma unroll
-    for (int q = 1; q < CMAX; ++q)
-      if (q == m - 1) d[q] = xhi;
+    x[0] = xlo;
+    x[m - 1] = xhi;
   }
+  __syncwarp();
   if (!g.xrun) {
     const int i = ln.line;
-#pragma unroll
+#pragma unroll 8
     for (int q = 0; q < CMAX; ++q)
-      if (q < m) u[(size_t)g.v(q) * nx1 + i] = d[q];
+      if (q < m) u[(size_t)g.v(q) * nx1 + i] = x[q];
   } else {
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < CMAX; ++k) tr[warp][lane][k] = d[k];
-    __syncwarp();
     const int q = lane;
     const int i = g.v(q);
 #pragma unroll 4
@@ -396,6 +402,7 @@ cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &tl, 
   T *dscr = static_cast<T *>(g.tile_d), *xscr = static_cast<T *>(g.tile_x);
   const CoefT<T> cp = coefs<T>(L);
   const int nx1 = L.nx + 1;
+  constexpr int TW = TWv<T>;
   const int ctas = (tl.ntile + TW - 1) / TW;
   if (tl.ntile > 0) tile_reduce<T><<<ctas, 32 * TW, 0, s>>>(tl.tile, tl.lane, tl.ntile, cp, nx1, u, f, rows, dscr);
   tile_couple<T><<<tl.ngroup, 128, 0, s>>>(tl.block, cp, nx1, rows, cdp, xscr, u, f);

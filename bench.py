@@ -31,7 +31,17 @@ RATIO = 1000.0
 SEED = 1
 TOL = 1e-10
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC = os.path.join(ROOT, "profiles", "line_pass_f32_4097_traffic.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "tweed_pass_f32_4097_traffic.json")
+# sources whose change invalidates the stored ncu traffic of the tiled pass
+TRAFFIC_SOURCES = ["tiles.cu", "tile_setup.cu", "mg_internal.h"]
+
+
+def traffic_key():
+    import hashlib
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2110_08389_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
 
 
 def parse():
@@ -61,7 +71,8 @@ def config_dict(args, c):
                         f"to ||r||/||f||<={TOL:g}",
             "nodes": (args.n + 1) ** 2, "smoother": "tweed", "nu1": args.nu[0], "nu2": args.nu[1],
             "inner_cycles": args.inner, "tol": TOL,
-            "l2": "inputs (u, f: 2 x 134 MB FP64) larger than L2 (129 MB)"}
+            "l2": f"inputs (u, f: 2 x {8 * (args.n + 1) ** 2 / 1e6:.0f} MB FP64) "
+                  + ("larger than L2 (129 MB)" if 8 * (args.n + 1) ** 2 > 129e6 else "smaller than L2 (129 MB)")}
 
 
 class ClockSampler:
@@ -147,26 +158,33 @@ def barrier(pg):
 # ------------------------------------------------------------------ oracle
 
 def oracle_cycles(x, f, nu, steps, warmup):
-    """Time V-cycles of the CPU oracle on the full workload; returns
-    (seconds per cycle, cycles to TOL or None, cycles run)."""
+    """Time V-cycles of the CPU oracle on the full workload from u = 0.
+    Returns (seconds per timed cycle, cycles to TOL, how that count was got)."""
     import numpy as np
     import oracle
     oracle.build()
     P = oracle.Problem(x, x)
     u = np.zeros_like(f)
     fn = math.sqrt(float(np.sum(f[1:-1, 1:-1] ** 2)))
-    times, reached = [], None
+    times, rels = [], [1.0]
     for k in range(warmup + steps):
         t0 = time.perf_counter()
         P.cycle(u, f, "tweed", nu[0], nu[1], 1, oracle.FW)
         dt = time.perf_counter() - t0
         r = P.residual(u, f)
-        rel = math.sqrt(float(np.sum(r[1:-1, 1:-1] ** 2))) / fn
-        if reached is None and rel <= TOL:
-            reached = k + 1
+        rels.append(math.sqrt(float(np.sum(r[1:-1, 1:-1] ** 2))) / fn)
         if k >= warmup:
             times.append(dt)
-    return statistics.mean(times), reached, warmup + steps
+    ran = len(rels) - 1
+    hit = next((k for k, v in enumerate(rels) if v <= TOL), None)
+    if hit is not None:
+        return statistics.mean(times), hit, f"reached 1e-10 after {hit} cycles"
+    # not reached in the sample: extrapolate with the measured factor
+    # (the first cycle, from u = 0, is faster than the asymptotic rate)
+    rho = (rels[-1] / rels[1]) ** (1.0 / (ran - 1)) if ran >= 2 else rels[-1] / rels[0]
+    more = math.ceil(math.log(TOL / rels[-1]) / math.log(rho)) if 0.0 < rho < 1.0 else float("nan")
+    return statistics.mean(times), ran + more, (f"{ran} cycles run, residual {rels[-1]:.2e}; {more} more "
+                                                f"extrapolated at the measured factor {rho:.4f}")
 
 
 def run_reference(args):
@@ -176,17 +194,17 @@ def run_reference(args):
         return
     x, c, f = workload(args.n)
     t0 = time.time()
-    per_cycle, reached, ran = oracle_cycles(x, f, args.nu, args.steps, args.warmup)
-    cycles = reached if reached is not None else ran
+    per_cycle, cycles, how = oracle_cycles(x, f, args.nu, args.steps, args.warmup)
     value = per_cycle * cycles
-    line = {"metric": "s to rel. residual 1e-10, 4097^2 tweed MG (FP64 CPU oracle)", "value": value, "unit": "s",
+    line = {"metric": "s to rel. residual 1e-10, 4097^2 tweed MG: FP32+refine vs FP64; HBM %peak",
+            "value": value, "unit": "s",
             "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": per_cycle * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic", "config": config_dict(args, c),
             "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
                              "sample": f"one step = one FP64 V({args.nu[0]},{args.nu[1]}) cycle of the C oracle "
-                                       f"on the full grid; value = mean s/cycle x {cycles} cycles to 1e-10"
-                                       + ("" if reached else " (tolerance not reached in the sample: cycles run)")},
+                                       f"(single thread) on the full grid from u = 0; value = mean s/cycle x "
+                                       f"{cycles} cycles to 1e-10 ({how})"},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.time() - t0}
     print(json.dumps(line), flush=True)
@@ -226,6 +244,9 @@ def main():
     torch.cuda.synchronize()
     barrier(pg)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # CUDA events around every finest-level colour pass of the timed solves,
+    # on the library's launching stream (the roofline below)
+    grid.pass_timer_begin(0, 256 * args.steps + 64)
     l0 = mg.kernel_launches()
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
@@ -235,6 +256,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
     launches = (mg.kernel_launches() - l0) // max(args.steps, 1)
+    timer = grid.pass_timer_end()
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(ms, pg, dev)
     status32 = res.status
@@ -267,33 +289,20 @@ def main():
         torch.cuda.synchronize()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, pg, dev)
 
-    # roofline of the dominant kernel: one FP32 tweed colour pass on the finest
-    # level, timed alone on the launching stream (CUDA events)
-    uu = torch.zeros((n1, n1), dtype=torch.float32, device=dev)
-    ff = f.float()
-    for _ in range(3):
-        grid.colour_pass(uu, ff, "tweed", 0)
-    reps = 20
-    torch.cuda.synchronize()
-    l0 = mg.kernel_launches()
-    e0.record(stream)
-    for r in range(reps):
-        grid.colour_pass(uu, ff, "tweed", r & 1)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    pass_launches = (mg.kernel_launches() - l0) / reps
-    pass_ms = e0.elapsed_time(e1) / reps
+    # roofline of the dominant kernel: the FP32 tweed colour pass on the finest
+    # level (tile_reduce + tile_couple + tile_expand), timed live in the solves
+    npass = max(timer["passes"], 1)
+    stage_ms = [v / npass for v in timer["stage_ms"]]
+    pass_ms = sum(stage_ms)
     algo_bytes = 2 * 4 * n1 * n1  # read u (w) + f of the colour (w/2) + write u of the colour (w/2), w = 4 B
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
     achieved = algo_bytes / (pass_ms * 1e-3) / 1e9
     traffic = None
     if os.path.exists(TRAFFIC):
-        import hashlib
         tr = json.load(open(TRAFFIC))
-        src = open(os.path.join(ROOT, "paper_2110_08389_gb300", "csrc", "smooth.cu"), "rb").read()
-        if tr.get("smooth_cu_sha256") == hashlib.sha256(src).hexdigest():
-            traffic = tr.get("traffic_bytes_per_launch")
+        if tr.get("sources_sha256") == traffic_key():
+            traffic = tr.get("traffic_bytes_per_pass")
 
     line = {"metric": "s to rel. residual 1e-10, 4097^2 tweed MG: FP32+refine vs FP64; HBM %peak",
             "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -305,20 +314,23 @@ def main():
             "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": 2 * 8 * n1 * n1,
                     "d2h_bytes_per_step": 8 * n1 * n1},
             "gpu_launches": int(launches),
-            "roofline": {"kernel": "line_pass_kernel<float> (one tweed colour pass, finest level)",
+            "roofline": {"kernel": "FP32 tweed colour pass, finest level (tile_reduce + tile_couple + tile_expand)",
                          "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "launch_ms": pass_ms,
-                         "launches_per_pass": pass_launches, "algo_bytes_per_launch": algo_bytes,
-                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"},
+                         "frac": achieved / peak, "traffic": traffic, "pass_ms": pass_ms,
+                         "passes_timed": timer["passes"], "launches_per_pass": 3,
+                         "stage_ms": {"tile_reduce": stage_ms[0], "tile_couple": stage_ms[1],
+                                      "tile_expand": stage_ms[2]},
+                         "algo_bytes_per_pass": algo_bytes,
+                         "peak_source": "hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"},
             "clocks": clk.summary()}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        per_cycle, reached, ran = oracle_cycles(x, f_h, args.nu, 3, 1)
+        per_cycle, _, _ = oracle_cycles(x, f_h, args.nu, 3, 1)
         cycles = r64.cycles
         line["cpu_baseline"] = {"value": per_cycle * cycles, "unit": "s", "cores": 1, "kind": "oracle",
-                                "sample": f"mean of 3 FP64 V({args.nu[0]},{args.nu[1]}) cycles of the C oracle on the full "
-                                          f"grid (after 1 untimed) = {per_cycle:.2f} s/cycle, x {cycles} cycles "
-                                          f"(the FP64 iteration count of this problem)"}
+                                "sample": f"mean of 3 FP64 V({args.nu[0]},{args.nu[1]}) cycles of the C oracle "
+                                          f"(single thread) on the full grid (after 1 untimed) = {per_cycle:.2f} "
+                                          f"s/cycle, x {cycles} cycles (the FP64 iteration count of this problem)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(pg)

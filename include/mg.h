@@ -220,6 +220,23 @@ mg_status mg_residual_norm_static(int64_t nx, int64_t ny, const double *W, const
  * instrumentation: the difference across a region counts its launches.      */
 unsigned long long mg_kernel_launches(void);
 
+/* Live timing of the colour passes (Sec. 3 relaxation, one colour) that run
+ * on `level` from now on, up to `max_passes` (1 .. 2^20) of them: every such
+ * pass records 4 CUDA events on its own stream -- before each of the three
+ * kernels of the tiled line path (reduce, couple, expand) and after the last.
+ * Passes that do not take the tiled path put all their time in the third
+ * stage.  Creates the 4 x max_passes events on the host (no device memory);
+ * MG_ERR_INVALID_ARG if a timer is already running on this grid.  The events
+ * are not captured into CUDA graphs: do not begin a timer around a capture. */
+mg_status mg_pass_timer_begin(mg_grid *g, int level, int max_passes);
+
+/* Ends the timer: waits for the last recorded event, then writes the number
+ * of passes timed (`passes`), the summed milliseconds of each stage
+ * (`stage_ms`, 3 doubles: reduce, couple, expand) and the fastest and slowest
+ * whole pass.  Any output pointer may be NULL.  Destroys the events.         */
+mg_status mg_pass_timer_end(mg_grid *g, int64_t *passes, double *stage_ms, double *pass_min_ms,
+                            double *pass_max_ms);
+
 #ifdef __cplusplus
 }
 #endif

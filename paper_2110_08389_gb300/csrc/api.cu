@@ -51,8 +51,18 @@ static void axis_coefficients(const std::vector<double> &x, std::vector<double> 
   }
 }
 
+static void destroy_timer(Grid *g) {
+  if (!g->timer_ev) return;
+  for (int k = 0; k < 4 * g->timer_cap; ++k) cudaEventDestroy(g->timer_ev[k]);
+  delete[] g->timer_ev;
+  g->timer_ev = nullptr;
+  g->timer_cap = g->timer_n = 0;
+  g->timer_level = -1;
+}
+
 static void free_grid(Grid *g) {
   if (!g) return;
+  destroy_timer(g);
   for (Level &L : g->lev) {
     cudaFree(L.dev_block);
     cudaFree(L.u64); cudaFree(L.f64); cudaFree(L.u32); cudaFree(L.f32);
@@ -227,24 +237,35 @@ static int wl_of(int smoother) {
   return -1;
 }
 
+// The 4 timer events of this pass, or nullptr when level l is not timed.
+static cudaEvent_t *timer_slot(Grid &g, int l) {
+  if (!g.timer_ev || l != g.timer_level || g.timer_n >= g.timer_cap) return nullptr;
+  return g.timer_ev + 4 * g.timer_n++;
+}
+
 template <typename T>
 static mg_status colour_pass(Grid &g, int l, int smoother, int colour, T *u, const T *f, cudaStream_t s) {
   Level &L = g.lev[l];
-  if (smoother == MG_SMOOTH_CHECKERBOARD) {
-    TRY_CUDA("checker pass", launch_checker_pass<T>(L, colour, u, f, s));
-    return MG_OK;
-  }
-  const int wl = wl_of(smoother);
-  if (wl < 0) return MG_ERR_INVALID_ARG;
-  const TileList &tl = L.tl[wl][colour];
-  if (tl.ntile > 0 || tl.nblock > 0) {
-    TRY_CUDA("tiled line pass", launch_tile_pass<T>(g, L, tl, u, f, s));
-    return MG_OK;
-  }
+  const int wl = smoother == MG_SMOOTH_CHECKERBOARD ? -2 : wl_of(smoother);
+  if (wl == -1) return MG_ERR_INVALID_ARG;
+  const TileList *tl = wl >= 0 ? &L.tl[wl][colour] : nullptr;
+  const bool tiled = tl && (tl->ntile > 0 || tl->nblock > 0);
   const int prec = sizeof(T) == 8 ? 0 : 1;
-  TRY(build_worklists(g, l, wl, prec));
-  TRY_CUDA("line pass", launch_line_pass<T>(L, L.wl[wl][prec][colour][0], u, f, s));
-  TRY_CUDA("line pass (large blocks)", launch_line_pass<T>(L, L.wl[wl][prec][colour][1], u, f, s));
+  if (wl >= 0 && !tiled) TRY(build_worklists(g, l, wl, prec));
+  cudaEvent_t *ev = timer_slot(g, l);
+  if (tiled) {
+    TRY_CUDA("tiled line pass", launch_tile_pass<T>(g, L, *tl, u, f, s, ev));
+    return MG_OK;
+  }
+  // other passes: the whole pass falls in the third timer stage
+  if (ev) for (int k = 0; k < 3; ++k) cudaEventRecord(ev[k], s);
+  if (wl == -2) {
+    TRY_CUDA("checker pass", launch_checker_pass<T>(L, colour, u, f, s));
+  } else {
+    TRY_CUDA("line pass", launch_line_pass<T>(L, L.wl[wl][prec][colour][0], u, f, s));
+    TRY_CUDA("line pass (large blocks)", launch_line_pass<T>(L, L.wl[wl][prec][colour][1], u, f, s));
+  }
+  if (ev) cudaEventRecord(ev[3], s);
   return MG_OK;
 }
 
@@ -418,6 +439,7 @@ const char *mg_last_error(void) { return g_err; }
 
 unsigned long long mg_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+
 mg_status mg_setup_grid(mg_grid **out, int dim, const int64_t *n_intervals, const double *const *coords,
                         int precision_mask, void *stream) {
   (void)stream;
@@ -573,6 +595,54 @@ mg_status mg_solve_adjoint(mg_grid *g, double *lambda, const double *rhs, const 
   if (e != cudaSuccess) return cuda_status("adjoint scaling", e);
   if (info) info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return st;
+}
+
+mg_status mg_pass_timer_begin(mg_grid *g, int level, int max_passes) {
+  if (bad_level(g, level) || max_passes < 1 || max_passes > (1 << 20) || g->timer_ev) return MG_ERR_INVALID_ARG;
+  g->timer_ev = new (std::nothrow) cudaEvent_t[4 * (size_t)max_passes];
+  if (!g->timer_ev) return MG_ERR_ALLOC;
+  for (int k = 0; k < 4 * max_passes; ++k) {
+    cudaError_t e = cudaEventCreate(&g->timer_ev[k]);
+    if (e != cudaSuccess) {
+      g->timer_cap = k / 4;
+      for (int j = 4 * g->timer_cap; j < k; ++j) cudaEventDestroy(g->timer_ev[j]);
+      destroy_timer(g);
+      return cuda_status("cudaEventCreate(pass timer)", e);
+    }
+  }
+  g->timer_cap = max_passes;
+  g->timer_n = 0;
+  g->timer_level = level;
+  return MG_OK;
+}
+
+mg_status mg_pass_timer_end(mg_grid *g, int64_t *passes, double *stage_ms, double *pass_min_ms,
+                            double *pass_max_ms) {
+  if (!g || !g->timer_ev) return MG_ERR_INVALID_ARG;
+  const int n = g->timer_n;
+  double st[3] = {0.0, 0.0, 0.0}, mn = 0.0, mx = 0.0;
+  mg_status rc = MG_OK;
+  if (n > 0) {
+    cudaError_t e = cudaEventSynchronize(g->timer_ev[4 * n - 1]);
+    for (int p = 0; p < n && e == cudaSuccess; ++p) {
+      double tot = 0.0;
+      for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        float ms = 0.0f;
+        e = cudaEventElapsedTime(&ms, g->timer_ev[4 * p + k], g->timer_ev[4 * p + k + 1]);
+        st[k] += ms;
+        tot += ms;
+      }
+      mn = p == 0 ? tot : std::min(mn, tot);
+      mx = std::max(mx, tot);
+    }
+    if (e != cudaSuccess) rc = cuda_status("pass timer", e);
+  }
+  if (passes) *passes = n;
+  if (stage_ms) for (int k = 0; k < 3; ++k) stage_ms[k] = st[k];
+  if (pass_min_ms) *pass_min_ms = mn;
+  if (pass_max_ms) *pass_max_ms = mx;
+  destroy_timer(g);
+  return rc;
 }
 
 }  // extern "C"

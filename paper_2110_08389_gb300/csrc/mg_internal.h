@@ -191,6 +191,11 @@ struct Grid {
   void *tile_rows = nullptr;         // 2 reduced rows per lane per tile (FP64 sized)
   void *tile_d = nullptr;            // 32 x 32 right-hand sides per tile (FP64 sized)
   void *tile_x = nullptr;            // 2 end values per lane per tile (FP64 sized)
+  // live timing of one level's colour passes (mg_pass_timer_begin/end): 4
+  // events per pass, recorded on the pass's stream before each of the three
+  // tiled-path kernels and after the last
+  int timer_level = -1, timer_cap = 0, timer_n = 0;
+  cudaEvent_t *timer_ev = nullptr;
 };
 
 // Levels whose side exceeds this use the tiled path for tweed and zebra.
@@ -206,8 +211,11 @@ const char *set_error(const char *where, cudaError_t e);
 void set_error_text(const char *msg);
 
 mg_status build_tiles(Grid &g, int level, int wl);
+// ev: nullptr, or 4 events recorded before tile_reduce, tile_couple,
+// tile_expand and after tile_expand
 template <typename T>
-cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &t, T *u, const T *f, cudaStream_t s);
+cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &t, T *u, const T *f, cudaStream_t s,
+                             cudaEvent_t *ev);
 
 // ---- kernel launchers (smooth.cu, transfer.cu).  All return cudaError_t of
 // the launch (cudaGetLastError).

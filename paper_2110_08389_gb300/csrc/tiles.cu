@@ -395,7 +395,8 @@ __global__ void __launch_bounds__(32 * TWv<T>) tile_expand(const TileDesc *__res
 }  // namespace
 
 template <typename T>
-cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &tl, T *u, const T *f, cudaStream_t s) {
+cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &tl, T *u, const T *f, cudaStream_t s,
+                             cudaEvent_t *ev) {
   if (tl.ntile == 0 && tl.nblock == 0) return cudaSuccess;
   TRow<T> *rows = static_cast<TRow<T> *>(g.tile_rows);
   T *cdp = reinterpret_cast<T *>(static_cast<char *>(g.tile_rows) + g.tile_cap * 32 * 2 * sizeof(TRow<double>));
@@ -404,15 +405,19 @@ cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &tl, 
   const int nx1 = L.nx + 1;
   constexpr int TW = TWv<T>;
   const int ctas = (tl.ntile + TW - 1) / TW;
+  if (ev) cudaEventRecord(ev[0], s);
   if (tl.ntile > 0) tile_reduce<T><<<ctas, 32 * TW, 0, s>>>(tl.tile, tl.lane, tl.ntile, cp, nx1, u, f, rows, dscr);
+  if (ev) cudaEventRecord(ev[1], s);
   tile_couple<T><<<tl.ngroup, 128, 0, s>>>(tl.block, cp, nx1, rows, cdp, xscr, u, f);
+  if (ev) cudaEventRecord(ev[2], s);
   if (tl.ntile > 0) tile_expand<T><<<ctas, 32 * TW, 0, s>>>(tl.tile, tl.lane, tl.ntile, cp, nx1, dscr, xscr, u);
+  if (ev) cudaEventRecord(ev[3], s);
   count_launch(tl.ntile > 0 ? 3 : 1);
   return cudaGetLastError();
 }
 template cudaError_t launch_tile_pass<double>(const Grid &, const Level &, const TileList &, double *, const double *,
-                                              cudaStream_t);
+                                              cudaStream_t, cudaEvent_t *);
 template cudaError_t launch_tile_pass<float>(const Grid &, const Level &, const TileList &, float *, const float *,
-                                             cudaStream_t);
+                                             cudaStream_t, cudaEvent_t *);
 
 }  // namespace tmg

@@ -32,7 +32,7 @@ EXPORTS = ["mg_setup_grid", "mg_destroy", "mg_num_levels", "mg_level_shape", "mg
            "mg_smooth_wireframe", "mg_smooth", "mg_colour_pass", "mg_residual_restrict", "mg_prolong_add",
            "mg_residual", "mg_coarse_solve", "mg_vcycle", "mg_solve", "mg_solve_adjoint",
            "mg_default_params", "mg_status_string", "mg_last_error", "mg_kernel_launches",
-           "mg_residual_norm_static"]
+           "mg_residual_norm_static", "mg_pass_timer_begin", "mg_pass_timer_end"]
 
 
 class MGError(RuntimeError):
@@ -89,6 +89,9 @@ def load(path: str = LIB_PATH):
         "mg_last_error": (ctypes.c_char_p, []),
         "mg_kernel_launches": (ctypes.c_ulonglong, []),
         "mg_residual_norm_static": (i, [ctypes.c_int64, ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "mg_pass_timer_begin": (i, [vp, i, i]),
+        "mg_pass_timer_end": (i, [vp, i64p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                  ctypes.POINTER(ctypes.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -219,6 +222,22 @@ class Grid:
         _check(self.lib.mg_colour_pass(self.h, level, sm, colour, _ptr(u), _ptr(f), _dtype_code(u),
                                        _stream(stream)), "mg_colour_pass")
         return u
+
+    def pass_timer_begin(self, level=0, max_passes=4096):
+        """Time every colour pass on `level` from now on with CUDA events on
+        its stream (mg_pass_timer_begin)."""
+        _check(self.lib.mg_pass_timer_begin(self.h, level, max_passes), "mg_pass_timer_begin")
+
+    def pass_timer_end(self) -> dict:
+        """Stop the timer: passes timed, summed ms per stage (reduce, couple,
+        expand) and the fastest / slowest pass (mg_pass_timer_end)."""
+        n = ctypes.c_int64()
+        st = (ctypes.c_double * 3)()
+        mn, mx = ctypes.c_double(), ctypes.c_double()
+        _check(self.lib.mg_pass_timer_end(self.h, ctypes.byref(n), st, ctypes.byref(mn), ctypes.byref(mx)),
+               "mg_pass_timer_end")
+        return {"passes": int(n.value), "stage_ms": [float(v) for v in st], "pass_min_ms": float(mn.value),
+                "pass_max_ms": float(mx.value)}
 
     # ---- transfers
     def residual(self, u, f, d, level=0, stream=None):

@@ -1,0 +1,49 @@
+"""Smoothing steps of one smoother on one synthetic problem, as a target for
+profilers (ncu) and quick timing.
+
+    python -m paper_2110_08389_gb300.profile_pass [--n 4096] [--smoother tweed]
+           [--dtype f32|f64] [--steps 3] [--ratio 1000]
+
+The grid has n x n intervals, tanh-stretched toward the walls (Eq. tanh) for
+every smoother but wireframe, toward the centre (Eq. tanh_inv) for wireframe,
+with the given max/min spacing ratio; f ~ N(0, 1) (seed 1), u = 0.  Each step
+is one relaxation (red pass, then black pass) on the finest level.  Prints
+the mean milliseconds per step, timed with CUDA events after one untimed step.
+"""
+from __future__ import annotations
+
+import argparse
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--smoother", default="tweed")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--ratio", type=float, default=1000.0)
+    args = ap.parse_args()
+    import torch
+    from . import inputs as I, mg
+
+    kind = "centre" if args.smoother == "wireframe" else "wall"
+    c = I.c_for_ratio(args.n, args.ratio, kind)
+    x = I.centre_coords(args.n, c) if kind == "centre" else I.wall_coords(args.n, c)
+    g = mg.Grid(x, x)
+    dt = torch.float32 if args.dtype == "f32" else torch.float64
+    f = torch.tensor(I.rhs_gaussian(args.n + 1, args.n + 1, 1), device="cuda").to(dt)
+    u = torch.zeros((args.n + 1, args.n + 1), dtype=dt, device="cuda")
+    g.smooth(u, f, args.smoother, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps - 1):
+        g.smooth(u, f, args.smoother, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(args.steps - 1, 1)
+    print(f"{args.smoother} {args.dtype} n={args.n}: {ms:.4f} ms/step over {args.steps - 1} timed steps")
+
+
+if __name__ == "__main__":
+    main()

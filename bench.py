@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nu", type=int, nargs=2, default=[1, 1])
     ap.add_argument("--inner", type=int, default=4)
-    ap.add_argument("--n", type=int, default=N_INTERVALS)
+    ap.add_argument("--intervals", type=int, default=N_INTERVALS, help="intervals per side (4096: the 4097 x 4097 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -66,13 +66,13 @@ def workload(n):
 
 
 def config_dict(args, c):
-    return {"workload": f"2D Poisson {args.n + 1}x{args.n + 1}, wall tanh c={c:.6f} (spacing ratio {RATIO:g}), "
+    return {"workload": f"2D Poisson {args.intervals + 1}x{args.intervals + 1}, wall tanh c={c:.6f} (spacing ratio {RATIO:g}), "
                         f"f~N(0,1) seed {SEED}, tweed V({args.nu[0]},{args.nu[1]}), full weighting, bilinear, "
                         f"to ||r||/||f||<={TOL:g}",
-            "nodes": (args.n + 1) ** 2, "smoother": "tweed", "nu1": args.nu[0], "nu2": args.nu[1],
+            "nodes": (args.intervals + 1) ** 2, "smoother": "tweed", "nu1": args.nu[0], "nu2": args.nu[1],
             "inner_cycles": args.inner, "tol": TOL,
-            "l2": f"inputs (u, f: 2 x {8 * (args.n + 1) ** 2 / 1e6:.0f} MB FP64) "
-                  + ("larger than L2 (129 MB)" if 8 * (args.n + 1) ** 2 > 129e6 else "smaller than L2 (129 MB)")}
+            "l2": f"inputs (u, f: 2 x {8 * (args.intervals + 1) ** 2 / 1e6:.0f} MB FP64) "
+                  + ("larger than L2 (129 MB)" if 8 * (args.intervals + 1) ** 2 > 129e6 else "smaller than L2 (129 MB)")}
 
 
 class ClockSampler:
@@ -192,7 +192,7 @@ def run_reference(args):
     if rank != 0:
         barrier(pg)
         return
-    x, c, f = workload(args.n)
+    x, c, f = workload(args.intervals)
     t0 = time.time()
     per_cycle, cycles, how = oracle_cycles(x, f, args.nu, args.steps, args.warmup)
     value = per_cycle * cycles
@@ -225,8 +225,8 @@ def main():
     dev = torch.device("cuda", local)
     from paper_2110_08389_gb300 import build, mg
     build.build()
-    x, c, f_h = workload(args.n)
-    n1 = args.n + 1
+    x, c, f_h = workload(args.intervals)
+    n1 = args.intervals + 1
     grid = mg.Grid(x, x)
     stream = torch.cuda.current_stream()
     f = torch.tensor(f_h, device=dev)

@@ -74,7 +74,7 @@ static void free_grid(Grid *g) {
       }
   }
   cudaFree(g->cinv);
-  cudaFree(g->r64); cudaFree(g->lam_tmp); cudaFree(g->e32); cudaFree(g->r32);
+  cudaFree(g->r64); cudaFree(g->e32); cudaFree(g->r32);
   cudaFree(g->partial); cudaFree(g->scal);
   cudaFree(g->tile_rows); cudaFree(g->tile_d); cudaFree(g->tile_x);
   if (g->hpinned) cudaFreeHost(g->hpinned);
@@ -189,9 +189,11 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
   TRY_CUDA("setup levels (latched error)", cudaGetLastError());
   const size_t nn0 = g->lev[0].nn;
   if (want32) { TRY(dalloc(&g->e32, nn0, "cudaMalloc(e32)")); TRY(dalloc(&g->r32, nn0, "cudaMalloc(r32)")); }
+  if (want64) TRY(dalloc(&g->r64, nn0, "cudaMalloc(adjoint scratch)"));
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  g->sms = sms;
   g->npartial = 4 * sms;
   TRY(dalloc(&g->partial, 2 * (size_t)g->npartial, "cudaMalloc(partials)"));
   TRY(dalloc(&g->scal, 4, "cudaMalloc(scalars)"));
@@ -577,11 +579,7 @@ mg_status mg_solve_adjoint(mg_grid *g, double *lambda, const double *rhs, const 
   if (!(g->prec_mask & 1)) return MG_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const auto t0 = std::chrono::steady_clock::now();
-  const size_t nn = g->lev[0].nn;
-  if (!g->r64) {
-    st = dalloc(&g->r64, nn, "cudaMalloc(adjoint scratch)");
-    if (st != MG_OK) return st;
-  }
+  if (!g->r64) return MG_ERR_INVALID_ARG;  // allocated by mg_setup_grid with FP64 enabled
   // L^T = D L D^{-1} with D = diag(dx_i dy_j):  L mu = D^{-1} rhs, lambda = D mu
   cudaError_t e = launch_diag_scale(*g, g->r64, rhs, 1, s);
   if (e != cudaSuccess) return cuda_status("adjoint scaling", e);

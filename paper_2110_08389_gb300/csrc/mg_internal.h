@@ -173,14 +173,14 @@ struct Level {
 
 struct Grid {
   int nlev = 0;
+  int sms = 1;                       // multiprocessors of the device the grid was set up on
   int prec_mask = 3;
   std::vector<Level> lev;
   // coarsest level: dense inverse of the interior operator (FP64, row-major)
   int cn = 0;
   double *cinv = nullptr;
   // finest-level FP64/FP32 scratch for the refinement loop and norms
-  double *r64 = nullptr;             // residual / scaled rhs scratch (finest)
-  double *lam_tmp = nullptr;         // adjoint scratch (finest)
+  double *r64 = nullptr;             // adjoint scratch: the scaled right-hand side (finest)
   float *e32 = nullptr, *r32 = nullptr;
   double *partial = nullptr;         // per-CTA partial sums (deterministic norm)
   double *hpinned = nullptr;         // pinned host mirror of the norm results

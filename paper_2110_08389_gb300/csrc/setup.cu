@@ -349,8 +349,15 @@ mg_status build_worklists(Grid &g, int level, int wl, int prec) {
     };
     std::stable_sort(small.begin(), small.end(), by_key);
     std::stable_sort(large.begin(), large.end(), by_key);
+    // small levels: fewer chunks per CTA, so that the level spreads over about
+    // four CTAs per SM (the passes there are latency-bound: each thread of a
+    // full CTA would walk hundreds of nodes one after the other)
+    int small_chunks = 0, widest = 1;
+    for (int bi : small) { small_chunks += blocks[bi].chunks; widest = std::max(widest, blocks[bi].chunks); }
+    const int target = 4 * std::max(g.sms, 1);
+    const int cap = std::min(NT_SMALL, std::max(widest, (small_chunks + target - 1) / target));
     Packed Ps, Pl;
-    pack(blocks, small, NT_SMALL, Ps);
+    pack(blocks, small, cap, Ps);
     pack(blocks, large, NT_LARGE, Pl);
     mg_status st = upload(Ps, NT_SMALL, L.wl[wl][prec][colour][0]);
     if (st == MG_OK) st = upload(Pl, NT_LARGE, L.wl[wl][prec][colour][1]);

@@ -139,6 +139,7 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
   }
   g->nlev = (int)g->lev.size();
   TRY_CUDA("setup start (latched error)", cudaGetLastError());
+  TRY_CUDA("line kernel attributes", prepare_line_kernels());
   const bool want64 = g->prec_mask & 1, want32 = g->prec_mask & 2;
   for (int l = 0; l < g->nlev; ++l) {
     Level &L = g->lev[l];
@@ -317,12 +318,11 @@ static mg_status check_params(const Grid *g, const mg_params *p) {
   return MG_OK;
 }
 
-// Read the two device norm scalars (sum of squares, max) back to the host.
-static mg_status read_norms(Grid &g, cudaStream_t s, double *sumsq, double *mx) {
-  TRY_CUDA("cudaMemcpyAsync(norms)", cudaMemcpyAsync(g.hpinned, g.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+// Read the device sum of squares of the last norm back to the host.
+static mg_status read_norms(Grid &g, cudaStream_t s, double *sumsq) {
+  TRY_CUDA("cudaMemcpyAsync(norms)", cudaMemcpyAsync(g.hpinned, g.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
   TRY_CUDA("cudaStreamSynchronize", cudaStreamSynchronize(s));
   *sumsq = g.hpinned[0];
-  *mx = g.hpinned[1];
   return MG_OK;
 }
 
@@ -338,13 +338,13 @@ static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params
   const Level &L0 = g.lev[0];
   if (info) { info->cycles = 0; info->outer_iters = 0; info->history_len = 0; info->rel_res = 0; info->conv_factor = 0; }
   if (!p.use_initial_guess) TRY_CUDA("zero u", launch_zero_interior<double>(L0, u, s));
-  double fs, fm, rs, rm;
+  double fs, rs;
   TRY_CUDA("norm(f)", launch_resnorm64(g, nullptr, f, s));
-  TRY(read_norms(g, s, &fs, &fm));
+  TRY(read_norms(g, s, &fs));
   double fn = std::sqrt(fs);
   if (p.precision == MG_PREC_F64) {
     TRY_CUDA("residual norm", launch_resnorm64(g, u, f, s));
-    TRY(read_norms(g, s, &rs, &rm));
+    TRY(read_norms(g, s, &rs));
     if (fn == 0.0) fn = std::sqrt(rs) > 0.0 ? std::sqrt(rs) : 1.0;
     double rel = std::sqrt(rs) / fn;
     const double rel0 = rel;
@@ -357,7 +357,7 @@ static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params
       TRY(cycle_rec<double>(g, p, 0, u, f, s));
       ++k;
       TRY_CUDA("residual norm", launch_resnorm64(g, u, f, s));
-      TRY(read_norms(g, s, &rs, &rm));
+      TRY(read_norms(g, s, &rs));
       rel = std::sqrt(rs) / fn;
       record(info, k, rel);
     }
@@ -374,8 +374,8 @@ static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params
   double rel = 0.0, rel0 = 0.0;
   mg_status st = MG_OK;
   while (true) {
-    TRY_CUDA("refinement residual", launch_ir_residual(g, u, f, g.r32, s));
-    TRY(read_norms(g, s, &rs, &rm));
+    TRY_CUDA("refinement residual", launch_ir_residual(g, u, f, g.r32, g.e32, s));
+    TRY(read_norms(g, s, &rs));
     if (outer == 0 && fn == 0.0) fn = std::sqrt(rs) > 0.0 ? std::sqrt(rs) : 1.0;
     rel = std::sqrt(rs) / fn;
     if (outer == 0) rel0 = rel;
@@ -383,7 +383,6 @@ static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params
     if (rel <= p.tol) break;
     if (!std::isfinite(rel)) { st = MG_ERR_NONFINITE; break; }
     if (outer >= p.max_outer || cycles >= p.max_cycles || rel > 1e3 * rel0) { st = MG_ERR_NOT_CONVERGED; break; }
-    TRY_CUDA("zero e", launch_zero_interior<float>(L0, g.e32, s));
     for (int k = 0; k < p.inner_cycles; ++k) {
       TRY(cycle_rec<float>(g, p, 0, g.e32, g.r32, s));
       ++cycles;

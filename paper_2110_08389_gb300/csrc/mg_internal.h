@@ -198,8 +198,10 @@ struct Grid {
   cudaEvent_t *timer_ev = nullptr;
 };
 
-// Levels whose side exceeds this use the tiled path for tweed and zebra.
-constexpr int TILE_MIN_SIDE = 256;
+// Levels whose sides are both at least this use the tiled path for tweed and
+// zebra (below it the single-kernel line pass is faster: measured on GB300,
+// 512^2: 29 vs 39 us per colour pass; 1024^2: 45 vs 41 us).
+constexpr int TILE_MIN_SIDE = 1024;
 
 // Kernels launched by this library in this process (mg_kernel_launches).
 extern std::atomic<unsigned long long> g_launches;
@@ -211,6 +213,9 @@ const char *set_error(const char *where, cudaError_t e);
 void set_error_text(const char *msg);
 
 mg_status build_tiles(Grid &g, int level, int wl);
+// Dynamic shared memory opt-in of the line kernels on the current device
+// (called by mg_setup_grid).
+cudaError_t prepare_line_kernels();
 // ev: nullptr, or 4 events recorded before tile_reduce, tile_couple,
 // tile_expand and after tile_expand
 template <typename T>
@@ -237,7 +242,7 @@ cudaError_t launch_coarse_solve(const Grid &g, T *u, const T *f, cudaStream_t s)
 // written to the device scalars g.scal[0..1] (u may be NULL: residual = f).
 cudaError_t launch_resnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s);
 // Refinement: r32 = float(f - L u64) and the FP64 norms of f - L u64 into scal.
-cudaError_t launch_ir_residual(const Grid &g, const double *u, const double *f, float *r32,
+cudaError_t launch_ir_residual(const Grid &g, const double *u, const double *f, float *r32, float *e32,
                                cudaStream_t s);
 // u64 += e32 on interior nodes.
 cudaError_t launch_ir_update(const Grid &g, double *u, const float *e, cudaStream_t s);

@@ -504,12 +504,6 @@ static cudaError_t launch_shape(const Level &L, const WorkList &w, T *u, const T
   constexpr bool SC = sizeof(T) == 4;  // FP64 keeps the coefficients in L1 (smem is too small)
   constexpr size_t smem = LineSmem<T, NT, SC>::bytes;
   auto kern = line_pass_kernel<T, NT, SC>;
-  static bool configured = false;  // dynamic shared memory opted in once
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
   kern<<<w.ncta, NT, smem, s>>>(w.cta, w.chunk, w.junc, w.vg, coefs_of<T>(L), L.nx + 1, u, f);
   count_launch(1);
   return cudaGetLastError();
@@ -519,6 +513,22 @@ template <typename T>
 cudaError_t launch_line_pass(const Level &L, const WorkList &w, T *u, const T *f, cudaStream_t s) {
   if (w.ncta == 0) return cudaSuccess;
   return w.nt == NT_SMALL ? launch_shape<T, NT_SMALL>(L, w, u, f, s) : launch_shape<T, NT_LARGE>(L, w, u, f, s);
+}
+
+// Opt the line kernels into their dynamic shared memory on the current device
+// (mg_setup_grid calls this on the grid's device).
+template <typename T, int NT>
+static cudaError_t prepare_shape() {
+  constexpr bool SC = sizeof(T) == 4;
+  return cudaFuncSetAttribute(line_pass_kernel<T, NT, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)LineSmem<T, NT, SC>::bytes);
+}
+cudaError_t prepare_line_kernels() {
+  cudaError_t e = prepare_shape<double, NT_SMALL>();
+  if (e == cudaSuccess) e = prepare_shape<double, NT_LARGE>();
+  if (e == cudaSuccess) e = prepare_shape<float, NT_SMALL>();
+  if (e == cudaSuccess) e = prepare_shape<float, NT_LARGE>();
+  return e;
 }
 
 template cudaError_t launch_line_pass<double>(const Level &, const WorkList &, double *, const double *, cudaStream_t);

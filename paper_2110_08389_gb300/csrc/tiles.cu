@@ -17,6 +17,8 @@
 // the along-direction coefficients are the same for all lanes (broadcast
 // loads); vertical tiles read and write u coalesced across lanes, horizontal
 // tiles go through a per-warp shared-memory transpose.
+#include <algorithm>
+
 #include "mg_internal.h"
 
 namespace tmg {
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(32 * TWv<T>) tile_reduce(const TileDesc *__res
     // horizontal tile: for each lane's row in turn, all lanes load along it
     // (coalesced) and the values are transposed through shared memory
     const int q = lane;
-#pragma unroll 4
+#pragma unroll
     for (int c = 0; c < 32; ++c) {
       const int jc = __shfl_sync(0xffffffffu, (int)ln.line, c);
       const int mc = __shfl_sync(0xffffffffu, m, c);

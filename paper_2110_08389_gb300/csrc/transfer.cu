@@ -9,10 +9,13 @@
 //                            (5), fused as the paper suggests)
 //   coarse_solve_kernel      u = L_0^{-1} (f - boundary terms) with the dense
 //                            inverse prepared at setup (FP64)
-//   resnorm / ir_residual    FP64 defect norms with a fixed-order reduction
-//                            (deterministic), optionally writing the FP32 copy
-//                            of the defect for the refinement loop
+//   resnorm / ir_residual    FP64 sum of squares of the defect with a
+//                            fixed-order reduction (deterministic), optionally
+//                            writing the FP32 copy of the defect and zeroing
+//                            the FP32 correction for the refinement loop
 //   ir_update                u64 += e32
+#include <algorithm>
+
 #include "mg_internal.h"
 
 namespace tmg {
@@ -59,39 +62,62 @@ cudaError_t launch_residual(const Level &L, const T *u, const T *f, T *d, cudaSt
 template cudaError_t launch_residual<double>(const Level &, const double *, const double *, double *, cudaStream_t);
 template cudaError_t launch_residual<float>(const Level &, const float *, const float *, float *, cudaStream_t);
 
-// One thread per coarse interior node (I, J); fine node (2I, 2J) and its 8
-// neighbours (defect 0 on the fine boundary).  kind: 0 = half weighting
-// (1/2, 1/8 x 4), 1 = full weighting (1/4, 1/8 x 4, 1/16 x 4).
+// One CTA per strip of RR_J coarse rows x RR_I coarse columns.  Every coarse
+// interior node (I, J) takes the defects of fine node (2I, 2J) and its 8
+// neighbours, all of them interior fine nodes; each fine defect of the strip
+// is computed once into shared memory (fine rows 2J0-1 .. 2J0+2RR_J-1, fine
+// columns 2I0-1 .. 2I0+2RR_I-1), then combined.  kind: 0 = half weighting
+// (1/2, 1/8 x 4), 1 = full weighting (1/4, 1/8 x 4, 1/16 x 4).  The coarse
+// correction uc is zeroed on the way.
+constexpr int RR_I = 128, RR_J = 4, RR_THREADS = 256;
+constexpr int RR_FI = 2 * RR_I + 1, RR_FJ = 2 * RR_J + 1;
+
 template <typename T>
-__global__ void residual_restrict_kernel(CoefQ<T> c, int nx, int ny, int nxc, int kind,
-                                         const T *__restrict__ u, const T *__restrict__ f, T *__restrict__ fc,
-                                         T *__restrict__ uc) {
-  const int I = blockIdx.x * blockDim.x + threadIdx.x + 1, J = blockIdx.y + 1;
-  if (I >= nxc) return;
-  const int nx1 = nx + 1, i = 2 * I, j = 2 * J;
-  auto dd = [&](int a, int b) -> T {
-    return (a > 0 && a < nx && b > 0 && b < ny) ? defect_at(c, u, f, a, b, nx1) : T(0);
-  };
-  const T centre = dd(i, j);
-  const T edge = (dd(i - 1, j) + dd(i, j - 1)) + (dd(i + 1, j) + dd(i, j + 1));
-  T v;
-  if (kind == MG_RESTRICT_HW) {
-    v = T(0.5) * centre + T(0.125) * edge;
-  } else {
-    const T corner = (dd(i - 1, j - 1) + dd(i + 1, j - 1)) + (dd(i - 1, j + 1) + dd(i + 1, j + 1));
-    v = T(0.25) * centre + T(0.125) * edge + T(0.0625) * corner;
+__global__ void __launch_bounds__(RR_THREADS) residual_restrict_kernel(CoefQ<T> c, int nx, int ny, int nxc,
+                                                                       int nyc, int kind,
+                                                                       const T *__restrict__ u,
+                                                                       const T *__restrict__ f,
+                                                                       T *__restrict__ fc, T *__restrict__ uc) {
+  __shared__ T dd[RR_FJ][RR_FI + 1];
+  const int I0 = 1 + blockIdx.x * RR_I, J0 = 1 + blockIdx.y * RR_J;
+  const int fi0 = 2 * I0 - 1, fj0 = 2 * J0 - 1, nx1 = nx + 1;
+  // fine nodes of the strip that some coarse interior node of it uses
+  const int fi_end = min(fi0 + RR_FI, nx), fj_end = min(fj0 + RR_FJ, ny);
+  for (int r = 0; r < RR_FJ; ++r) {
+    const int j = fj0 + r;
+    if (j >= fj_end) break;
+    for (int tcol = threadIdx.x; tcol < RR_FI; tcol += RR_THREADS) {
+      const int i = fi0 + tcol;
+      if (i < fi_end) dd[r][tcol] = defect_at(c, u, f, i, j, nx1);
+    }
   }
-  const size_t q = (size_t)J * (nxc + 1) + I;
-  fc[q] = v;
-  if (uc) uc[q] = T(0);
+  __syncthreads();
+  for (int k = threadIdx.x; k < RR_I * RR_J; k += RR_THREADS) {
+    const int li = k % RR_I, lj = k / RR_I;
+    const int I = I0 + li, J = J0 + lj;
+    if (I >= nxc || J >= nyc) continue;
+    const int ci = 2 * li + 1, cj = 2 * lj + 1;  // the centre's place in dd
+    const T centre = dd[cj][ci];
+    const T edge = (dd[cj][ci - 1] + dd[cj - 1][ci]) + (dd[cj][ci + 1] + dd[cj + 1][ci]);
+    T v;
+    if (kind == MG_RESTRICT_HW) {
+      v = T(0.5) * centre + T(0.125) * edge;
+    } else {
+      const T corner = (dd[cj - 1][ci - 1] + dd[cj - 1][ci + 1]) + (dd[cj + 1][ci - 1] + dd[cj + 1][ci + 1]);
+      v = T(0.25) * centre + T(0.125) * edge + T(0.0625) * corner;
+    }
+    const size_t q = (size_t)J * (nxc + 1) + I;
+    fc[q] = v;
+    if (uc) uc[q] = T(0);
+  }
 }
 
 template <typename T>
 cudaError_t launch_residual_restrict(const Level &F, const Level &C, int kind, const T *u, const T *f, T *fc,
                                      T *uc, cudaStream_t s) {
-  dim3 b(128), g((C.nx - 1 + 127) / 128, C.ny - 1);
   if (C.nx < 2 || C.ny < 2) return cudaSuccess;
-  residual_restrict_kernel<T><<<g, b, 0, s>>>(cq<T>(F), F.nx, F.ny, C.nx, kind, u, f, fc, uc);
+  dim3 g((C.nx - 1 + RR_I - 1) / RR_I, (C.ny - 1 + RR_J - 1) / RR_J);
+  residual_restrict_kernel<T><<<g, RR_THREADS, 0, s>>>(cq<T>(F), F.nx, F.ny, C.nx, C.ny, kind, u, f, fc, uc);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -101,27 +127,41 @@ template cudaError_t launch_residual_restrict<float>(const Level &, const Level 
                                                      const float *, float *, float *, cudaStream_t);
 
 // Bilinear interpolation of the coarse correction (index-based weights,
-// Sec. 4), added to the fine interior.
+// Sec. 4), added to the fine interior.  Thread (I, j) owns the fine pair
+// (2I-1, j), (2I, j), I = 1..nxc, which uses coarse columns I-1 and I of
+// coarse rows j/2 (and j/2 + 1 for odd j): no divergence between lanes, and
+// the loads of a warp are contiguous.
+constexpr int PR_THREADS = 256;
+
 template <typename T>
-__global__ void prolong_add_kernel(int nx, int ny, int nxc, const T *__restrict__ uc, T *__restrict__ u) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1;
-  if (i >= nx) return;
-  const int c1 = nxc + 1;
-  const int I = i >> 1, Jc = j >> 1;
-  T v;
-  if (!(i & 1) && !(j & 1)) v = uc[(size_t)Jc * c1 + I];
-  else if (!(i & 1)) v = T(0.5) * (uc[(size_t)Jc * c1 + I] + uc[(size_t)(Jc + 1) * c1 + I]);
-  else if (!(j & 1)) v = T(0.5) * (uc[(size_t)Jc * c1 + I] + uc[(size_t)Jc * c1 + I + 1]);
-  else
-    v = T(0.25) * ((uc[(size_t)Jc * c1 + I] + uc[(size_t)Jc * c1 + I + 1]) +
-                   (uc[(size_t)(Jc + 1) * c1 + I] + uc[(size_t)(Jc + 1) * c1 + I + 1]));
-  u[(size_t)j * (nx + 1) + i] += v;
+__global__ void __launch_bounds__(PR_THREADS) prolong_add_kernel(int nx, int ny, int nxc, const T *__restrict__ uc,
+                                                                 T *__restrict__ u) {
+  const int j = blockIdx.y + 1;
+  const int c1 = nxc + 1, Jc = j >> 1;
+  const bool jodd = j & 1;
+  const T *r0 = uc + (size_t)Jc * c1, *r1 = r0 + (jodd ? c1 : 0);
+  T *ur = u + (size_t)j * (nx + 1);
+  for (int I = 1 + blockIdx.x * PR_THREADS + threadIdx.x; I <= nxc; I += gridDim.x * PR_THREADS) {
+    const T a0 = r0[I - 1], b0 = r0[I];
+    T vo, ve;
+    if (jodd) {
+      const T a1 = r1[I - 1], b1 = r1[I];
+      vo = T(0.25) * ((a0 + b0) + (a1 + b1));
+      ve = T(0.5) * (b0 + b1);
+    } else {
+      vo = T(0.5) * (a0 + b0);
+      ve = b0;
+    }
+    ur[2 * I - 1] += vo;
+    if (2 * I < nx) ur[2 * I] += ve;
+  }
 }
 
 template <typename T>
 cudaError_t launch_prolong_add(const Level &F, const Level &C, const T *uc, T *u, cudaStream_t s) {
-  dim3 b(128), g((F.nx - 1 + 127) / 128, F.ny - 1);
-  prolong_add_kernel<T><<<g, b, 0, s>>>(F.nx, F.ny, C.nx, uc, u);
+  const int bx = std::min((C.nx + PR_THREADS - 1) / PR_THREADS, 8);
+  dim3 g(bx, F.ny - 1);
+  prolong_add_kernel<T><<<g, PR_THREADS, 0, s>>>(F.nx, F.ny, C.nx, uc, u);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -173,73 +213,87 @@ template cudaError_t launch_coarse_solve<float>(const Grid &, float *, const flo
 // one CTA sums the partials in index order.
 constexpr int NORM_THREADS = 256;
 
-__device__ __forceinline__ void block_reduce2(double &s, double &m) {
-  __shared__ double ss[NORM_THREADS], sm[NORM_THREADS];
-  ss[threadIdx.x] = s; sm[threadIdx.x] = m;
+__device__ __forceinline__ double block_sum(double s) {
+  __shared__ double ss[NORM_THREADS];
+  ss[threadIdx.x] = s;
   __syncthreads();
   for (int h = NORM_THREADS / 2; h > 0; h >>= 1) {
-    if ((int)threadIdx.x < h) {
-      ss[threadIdx.x] += ss[threadIdx.x + h];
-      sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + h]);
-    }
+    if ((int)threadIdx.x < h) ss[threadIdx.x] += ss[threadIdx.x + h];
     __syncthreads();
   }
-  s = ss[0]; m = sm[0];
+  return ss[0];
 }
 
-// mode 0: r = f - L u (u may be NULL: r = f); mode 1: same, and r32 = float(r).
+// Sum of squares of r over the interior, r = f - L u (u may be NULL: r = f).
+// CTA b takes interior rows 1 + b, 1 + b + gridDim.x, ...; every thread its
+// columns in order, so the result does not depend on timing.  With r32 set
+// (refinement mode) it also stores float(r) and zeroes the FP32 correction
+// e32 for the cycles that follow.  FP64 issue is the bound on GB300: 9 FP64
+// operations per node.
 __global__ void __launch_bounds__(NORM_THREADS) norm_stage1(CoefQ<double> c, int nx, int ny,
                                                             const double *__restrict__ u,
                                                             const double *__restrict__ f,
-                                                            float *__restrict__ r32, double *__restrict__ part) {
+                                                            float *__restrict__ r32, float *__restrict__ e32,
+                                                            double *__restrict__ part) {
   const int nx1 = nx + 1;
-  const long long ni = (long long)(nx - 1) * (ny - 1);
-  double s = 0.0, m = 0.0;
-  for (long long k = (long long)blockIdx.x * NORM_THREADS + threadIdx.x; k < ni;
-       k += (long long)gridDim.x * NORM_THREADS) {
-    const int i = (int)(k % (nx - 1)) + 1, j = (int)(k / (nx - 1)) + 1;
-    const double r = u ? defect_at(c, u, f, i, j, nx1) : f[(size_t)j * nx1 + i];
-    if (r32) r32[(size_t)j * nx1 + i] = (float)r;
-    s += r * r;
-    m = fmax(m, fabs(r));
+  double s = 0.0;
+  for (int j = 1 + blockIdx.x; j < ny; j += gridDim.x) {
+    const double sj = __ldg(c.S + j), nj = __ldg(c.N + j), snj = sj + nj;
+    const size_t row = (size_t)j * nx1;
+    for (int i = 1 + threadIdx.x; i < nx; i += NORM_THREADS) {
+      const size_t p = row + i;
+      double r = f[p];
+      if (u) {
+        const double w = __ldg(c.W + i), e = __ldg(c.E + i);
+        const double cc = (w + e) + snj;
+        r -= w * u[p - 1] + e * u[p + 1] + sj * u[p - nx1] + nj * u[p + nx1] - cc * u[p];
+      }
+      if (r32) { r32[p] = (float)r; e32[p] = 0.0f; }
+      s = fma(r, r, s);
+    }
   }
-  block_reduce2(s, m);
-  if (threadIdx.x == 0) { part[2 * blockIdx.x] = s; part[2 * blockIdx.x + 1] = m; }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 __global__ void __launch_bounds__(NORM_THREADS) norm_stage2(const double *__restrict__ part, int npart,
                                                             double *__restrict__ out) {
-  double s = 0.0, m = 0.0;
-  for (int k = threadIdx.x; k < npart; k += NORM_THREADS) { s += part[2 * k]; m = fmax(m, part[2 * k + 1]); }
-  block_reduce2(s, m);
-  if (threadIdx.x == 0) { out[0] = s; out[1] = m; }
+  double s = 0.0;
+  for (int k = threadIdx.x; k < npart; k += NORM_THREADS) s += part[k];
+  s = block_sum(s);
+  if (threadIdx.x == 0) out[0] = s;
 }
 
-static cudaError_t norms(const Grid &g, const double *u, const double *f, float *r32, cudaStream_t s) {
+static cudaError_t norms(const Grid &g, const double *u, const double *f, float *r32, float *e32, cudaStream_t s) {
   const Level &L = g.lev[0];
-  norm_stage1<<<g.npartial, NORM_THREADS, 0, s>>>(cq<double>(L), L.nx, L.ny, u, f, r32, g.partial);
+  norm_stage1<<<g.npartial, NORM_THREADS, 0, s>>>(cq<double>(L), L.nx, L.ny, u, f, r32, e32, g.partial);
   norm_stage2<<<1, NORM_THREADS, 0, s>>>(g.partial, g.npartial, g.scal);
   count_launch(2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_resnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s) {
-  return norms(g, u, f, nullptr, s);
+  return norms(g, u, f, nullptr, nullptr, s);
 }
-cudaError_t launch_ir_residual(const Grid &g, const double *u, const double *f, float *r32, cudaStream_t s) {
-  return norms(g, u, f, r32, s);
+cudaError_t launch_ir_residual(const Grid &g, const double *u, const double *f, float *r32, float *e32,
+                               cudaStream_t s) {
+  return norms(g, u, f, r32, e32, s);
 }
 
-__global__ void ir_update_kernel(int nx, int ny, double *__restrict__ u, const float *__restrict__ e) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1;
-  if (i >= nx) return;
-  const size_t p = (size_t)j * (nx + 1) + i;
-  u[p] += (double)e[p];
+// Row-wise elementwise kernels: CTA (x, j) covers interior row j + 1 with a
+// grid-stride loop over its columns.
+constexpr int EW_THREADS = 256;
+static dim3 row_grid(const Level &L) { return dim3(std::min((L.nx - 1 + EW_THREADS - 1) / EW_THREADS, 4), L.ny - 1); }
+
+__global__ void __launch_bounds__(EW_THREADS) ir_update_kernel(int nx, double *__restrict__ u,
+                                                               const float *__restrict__ e) {
+  const size_t row = (size_t)(blockIdx.y + 1) * (nx + 1);
+  for (int i = 1 + blockIdx.x * EW_THREADS + threadIdx.x; i < nx; i += gridDim.x * EW_THREADS)
+    u[row + i] += (double)e[row + i];
 }
 cudaError_t launch_ir_update(const Grid &g, double *u, const float *e, cudaStream_t s) {
   const Level &L = g.lev[0];
-  dim3 b(128), gr((L.nx - 1 + 127) / 128, L.ny - 1);
-  ir_update_kernel<<<gr, b, 0, s>>>(L.nx, L.ny, u, e);
+  ir_update_kernel<<<row_grid(L), EW_THREADS, 0, s>>>(L.nx, u, e);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -264,15 +318,13 @@ cudaError_t launch_diag_scale(const Grid &g, double *out, const double *in, int 
 }
 
 template <typename T>
-__global__ void zero_interior_kernel(int nx, int ny, T *__restrict__ a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1, j = blockIdx.y + 1;
-  if (i >= nx) return;
-  a[(size_t)j * (nx + 1) + i] = T(0);
+__global__ void __launch_bounds__(EW_THREADS) zero_interior_kernel(int nx, T *__restrict__ a) {
+  const size_t row = (size_t)(blockIdx.y + 1) * (nx + 1);
+  for (int i = 1 + blockIdx.x * EW_THREADS + threadIdx.x; i < nx; i += gridDim.x * EW_THREADS) a[row + i] = T(0);
 }
 template <typename T>
 cudaError_t launch_zero_interior(const Level &L, T *a, cudaStream_t s) {
-  dim3 b(128), gr((L.nx - 1 + 127) / 128, L.ny - 1);
-  zero_interior_kernel<T><<<gr, b, 0, s>>>(L.nx, L.ny, a);
+  zero_interior_kernel<T><<<row_grid(L), EW_THREADS, 0, s>>>(L.nx, a);
   count_launch(1);
   return cudaGetLastError();
 }

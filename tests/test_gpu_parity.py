@@ -32,8 +32,10 @@ GRIDS = [
     (96, 136, "centre", 2.0),
     (200, 72, "wall", 2.5),
     (256, 256, "wall", 3.043),
-    (320, 256, "wall", 2.0),      # large enough for the tiled path; T-blocks and lines
-    (272, 512, "centre", 1.2),    # ragged tiles, rows longer than columns
+    (320, 256, "wall", 2.0),      # T-blocks and lines
+    (272, 512, "centre", 1.2),    # rows longer than columns
+    (1024, 1024, "wall", 3.0),    # tiled line path (both sides >= 1024): L-blocks, centre cross
+    (1152, 1024, "centre", 1.2),  # tiled: T-blocks, straight lines, ragged last tiles
 ]
 BASE_SMOOTHERS = ["checkerboard", "zebra_x", "zebra_y", "tweed", "wireframe"]
 

@@ -77,6 +77,7 @@ static void free_grid(Grid *g) {
   cudaFree(g->r64); cudaFree(g->e32); cudaFree(g->r32);
   cudaFree(g->partial); cudaFree(g->scal);
   cudaFree(g->tile_rows); cudaFree(g->tile_d); cudaFree(g->tile_x);
+  cudaFree(g->mini[0].mem); cudaFree(g->mini[1].mem);
   if (g->hpinned) cudaFreeHost(g->hpinned);
   delete g;
 }
@@ -210,6 +211,9 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
       TRY(build_tiles(*g, l, wl));
       TRY_CUDA("setup tiles (latched error)", cudaGetLastError());
     }
+  if (want64) TRY(build_mini(*g, 0));
+  if (want32) TRY(build_mini(*g, 1));
+  TRY_CUDA("setup coarse-cycle plans (latched error)", cudaGetLastError());
   if (g->tile_cap > 0) {
     // scratch of the tiled path, sized for FP64 (FP32 uses the first half)
     // rows (2 x 4 doubles per lane) followed by the (c', d') pairs of tile_couple
@@ -293,6 +297,10 @@ template <typename T>
 static mg_status cycle_rec(Grid &g, const mg_params &p, int l, T *u, const T *f, cudaStream_t s) {
   if (l == g.nlev - 1) {
     TRY_CUDA("coarse solve", launch_coarse_solve<T>(g, u, f, s));
+    return MG_OK;
+  }
+  if (l == g.mini[sizeof(T) == 8 ? 0 : 1].level_for[p.smoother]) {  // the rest of the cycle in one kernel
+    TRY_CUDA("coarse cycle", launch_mini_cycle<T>(g, p, u, f, s));
     return MG_OK;
   }
   for (int k = 0; k < p.nu1; ++k) TRY(smooth(g, l, p.smoother, u, f, s));

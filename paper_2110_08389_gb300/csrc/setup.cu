@@ -24,27 +24,12 @@
 #include <tuple>
 
 #include "mg_internal.h"
+#include "blocks.h"
 
 namespace tmg {
 
 namespace {
 
-struct HSeg {
-  int i0, j0, dir, len;
-};
-struct HChain {
-  std::vector<HSeg> s;
-  bool fj = false, lj = false;
-  int ljdir = 0;  // direction from the last node to the junction
-};
-struct HBlock {
-  bool junc = false;
-  int ji = 0, jj = 0;
-  std::vector<HChain> ch;
-  int nodes = 0, chunks = 0;
-  int group = 0, pos = 0;  // packing order: blocks of one group in order of pos are
-                           // neighbours (adjacent same-colour legs / lines)
-};
 HBlock keyed(HBlock b, int group, int pos) {
   b.group = group;
   b.pos = pos;
@@ -80,6 +65,8 @@ HBlock star(int i, int j, std::vector<HChain> legs) {
 }
 inline int colour_of(int k) { return (k & 1) ? 0 : 1; }
 HBlock keyed5(HBlock b) { return keyed(b, 5, 0); }
+
+}  // namespace
 
 void tweed_blocks(int nx, int ny, int colour, std::vector<HBlock> &out) {
   const int hx = nx / 2, hy = ny / 2, K = std::max(hx, hy), m = std::min(hx, hy);
@@ -163,6 +150,8 @@ void zebra_blocks(int nx, int ny, int colour, bool along_x, std::vector<HBlock> 
       if (colour_of(i) == colour) out.push_back(keyed(single(line(i, 1, DIR_PY, ny - 1)), 0, i));
   }
 }
+
+namespace {
 
 inline int nchunks_of(int len) { return (len + CMAX - 1) / CMAX; }
 

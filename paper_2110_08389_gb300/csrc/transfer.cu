@@ -171,10 +171,14 @@ template cudaError_t launch_prolong_add<float>(const Level &, const Level &, con
                                                cudaStream_t);
 
 // Coarsest level: x = A^{-1} b in FP64, b = f - (boundary neighbours).  One
-// CTA; unknown index (j-1)(nx-1) + (i-1).
+// CTA; unknown index (j-1)(nx-1) + (i-1).  One warp per row of A^{-1}, its
+// lanes over the columns (coalesced loads), fixed-order shuffle reduction.
+constexpr int CS_THREADS = 1024;
+
 template <typename T>
-__global__ void coarse_solve_kernel(CoefQ<double> c, int nx, int ny, const double *__restrict__ inv,
-                                    T *__restrict__ u, const T *__restrict__ f) {
+__global__ void __launch_bounds__(CS_THREADS) coarse_solve_kernel(CoefQ<double> c, int nx, int ny,
+                                                                  const double *__restrict__ inv,
+                                                                  T *__restrict__ u, const T *__restrict__ f) {
   extern __shared__ double cb[];
   const int n = (nx - 1) * (ny - 1), nx1 = nx + 1;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
@@ -188,11 +192,16 @@ __global__ void coarse_solve_kernel(CoefQ<double> c, int nx, int ny, const doubl
     cb[k] = b;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = threadIdx.x >> 5; k < n; k += nw) {
     double x = 0.0;
-    for (int q = 0; q < n; ++q) x += inv[(size_t)k * n + q] * cb[q];
-    const int i = k % (nx - 1) + 1, j = k / (nx - 1) + 1;
-    u[(size_t)j * nx1 + i] = (T)x;
+    for (int q = lane; q < n; q += 32) x += inv[(size_t)k * n + q] * cb[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) {
+      const int i = k % (nx - 1) + 1, j = k / (nx - 1) + 1;
+      u[(size_t)j * nx1 + i] = (T)x;
+    }
   }
 }
 
@@ -200,7 +209,7 @@ template <typename T>
 cudaError_t launch_coarse_solve(const Grid &g, T *u, const T *f, cudaStream_t s) {
   const Level &L = g.lev[g.nlev - 1];
   if (g.cn <= 0) return cudaSuccess;
-  coarse_solve_kernel<T><<<1, 256, sizeof(double) * g.cn, s>>>(cq<double>(L), L.nx, L.ny, g.cinv, u, f);
+  coarse_solve_kernel<T><<<1, CS_THREADS, sizeof(double) * g.cn, s>>>(cq<double>(L), L.nx, L.ny, g.cinv, u, f);
   count_launch(1);
   return cudaGetLastError();
 }

@@ -63,6 +63,11 @@ static void destroy_timer(Grid *g) {
 static void free_grid(Grid *g) {
   if (!g) return;
   destroy_timer(g);
+  for (auto &ge : g->graphs) cudaGraphExecDestroy(ge.exec);
+  g->graphs.clear();
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_join) cudaEventDestroy(g->ev_join);
+  if (g->gs) cudaStreamDestroy(g->gs);
   for (Level &L : g->lev) {
     cudaFree(L.dev_block);
     cudaFree(L.u64); cudaFree(L.f64); cudaFree(L.u32); cudaFree(L.f32);
@@ -77,7 +82,6 @@ static void free_grid(Grid *g) {
   cudaFree(g->r64); cudaFree(g->e32); cudaFree(g->r32);
   cudaFree(g->partial); cudaFree(g->scal);
   cudaFree(g->tile_rows); cudaFree(g->tile_d); cudaFree(g->tile_x);
-  cudaFree(g->mini[0].mem); cudaFree(g->mini[1].mem);
   if (g->hpinned) cudaFreeHost(g->hpinned);
   delete g;
 }
@@ -211,9 +215,6 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
       TRY(build_tiles(*g, l, wl));
       TRY_CUDA("setup tiles (latched error)", cudaGetLastError());
     }
-  if (want64) TRY(build_mini(*g, 0));
-  if (want32) TRY(build_mini(*g, 1));
-  TRY_CUDA("setup coarse-cycle plans (latched error)", cudaGetLastError());
   if (g->tile_cap > 0) {
     // scratch of the tiled path, sized for FP64 (FP32 uses the first half)
     // rows (2 x 4 doubles per lane) followed by the (c', d') pairs of tile_couple
@@ -221,6 +222,9 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
     TRY_CUDA("cudaMalloc(tile rhs)", cudaMalloc(&g->tile_d, g->tile_cap * 32 * 32 * sizeof(double)));
     TRY_CUDA("cudaMalloc(tile ends)", cudaMalloc(&g->tile_x, g->tile_cap * 32 * 2 * sizeof(double)));
   }
+  TRY_CUDA("cudaStreamCreate(graph stream)", cudaStreamCreateWithFlags(&g->gs, cudaStreamNonBlocking));
+  TRY_CUDA("cudaEventCreate(fork)", cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+  TRY_CUDA("cudaEventCreate(join)", cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
   TRY_CUDA("setup (latched error)", cudaGetLastError());
   return MG_OK;
 }
@@ -299,10 +303,6 @@ static mg_status cycle_rec(Grid &g, const mg_params &p, int l, T *u, const T *f,
     TRY_CUDA("coarse solve", launch_coarse_solve<T>(g, u, f, s));
     return MG_OK;
   }
-  if (l == g.mini[sizeof(T) == 8 ? 0 : 1].level_for[p.smoother]) {  // the rest of the cycle in one kernel
-    TRY_CUDA("coarse cycle", launch_mini_cycle<T>(g, p, u, f, s));
-    return MG_OK;
-  }
   for (int k = 0; k < p.nu1; ++k) TRY(smooth(g, l, p.smoother, u, f, s));
   Level &F = g.lev[l], &C = g.lev[l + 1];
   T *uc = level_u<T>(C), *fc = level_f<T>(C);
@@ -310,6 +310,62 @@ static mg_status cycle_rec(Grid &g, const mg_params &p, int l, T *u, const T *f,
   for (int k = 0; k < p.cycle; ++k) TRY(cycle_rec<T>(g, p, l + 1, uc, fc, s));
   TRY_CUDA("prolong+correct", launch_prolong_add<T>(F, C, uc, u, s));
   for (int k = 0; k < p.nu2; ++k) TRY(smooth(g, l, p.smoother, u, f, s));
+  return MG_OK;
+}
+
+// ncyc cycles (Sec. 4) on level 0 from (u, f).  The launch sequence of a
+// cycle depends only on the grid, the parameters and the two arrays, so it is
+// captured once into a CUDA graph and replayed: one submission instead of
+// about a hundred launches, and shorter gaps between the kernels.  Direct
+// launches while the pass timer runs (its events are per pass) or when the
+// caller's stream is itself being captured.
+constexpr size_t MAX_GRAPHS = 8;
+
+template <typename T>
+static mg_status run_cycles(Grid &g, const mg_params &p, int ncyc, T *u, const T *f, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  TRY_CUDA("cudaStreamIsCapturing", cudaStreamIsCapturing(s, &cs));
+  if (g.timer_ev || cs != cudaStreamCaptureStatusNone || !g.gs) {
+    for (int k = 0; k < ncyc; ++k) TRY(cycle_rec<T>(g, p, 0, u, f, s));
+    return MG_OK;
+  }
+  const int key[8] = {(int)sizeof(T), p.smoother, p.nu1, p.nu2, p.cycle, p.restriction, ncyc, 0};
+  Grid::GraphEntry *ge = nullptr;
+  for (auto &x : g.graphs)
+    if (x.u == u && x.f == f && std::memcmp(x.key, key, sizeof(key)) == 0) { ge = &x; break; }
+  if (!ge) {
+    const unsigned long long l0 = g_launches.load();
+    TRY_CUDA("cudaStreamBeginCapture", cudaStreamBeginCapture(g.gs, cudaStreamCaptureModeThreadLocal));
+    mg_status st = MG_OK;
+    for (int k = 0; k < ncyc && st == MG_OK; ++k) st = cycle_rec<T>(g, p, 0, u, f, g.gs);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(g.gs, &graph);
+    const unsigned long long nl = g_launches.load() - l0;
+    g_launches.fetch_sub(nl);  // counted again at every replay
+    if (st != MG_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return st != MG_OK ? st : cuda_status("cudaStreamEndCapture", e);
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_status("cudaGraphInstantiate", e);
+    if (g.graphs.size() >= MAX_GRAPHS) {
+      cudaGraphExecDestroy(g.graphs.front().exec);
+      g.graphs.erase(g.graphs.begin());
+    }
+    Grid::GraphEntry ne;
+    std::memcpy(ne.key, key, sizeof(key));
+    ne.u = u; ne.f = f; ne.exec = ex; ne.launches = nl;
+    g.graphs.push_back(ne);
+    ge = &g.graphs.back();
+  }
+  TRY_CUDA("cudaEventRecord(fork)", cudaEventRecord(g.ev_fork, s));
+  TRY_CUDA("cudaStreamWaitEvent(fork)", cudaStreamWaitEvent(g.gs, g.ev_fork, 0));
+  TRY_CUDA("cudaGraphLaunch", cudaGraphLaunch(ge->exec, g.gs));
+  count_launch(ge->launches);
+  TRY_CUDA("cudaEventRecord(join)", cudaEventRecord(g.ev_join, g.gs));
+  TRY_CUDA("cudaStreamWaitEvent(join)", cudaStreamWaitEvent(s, g.ev_join, 0));
   return MG_OK;
 }
 
@@ -362,7 +418,7 @@ static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params
     while (!(rel <= p.tol)) {
       if (!std::isfinite(rel)) { st = MG_ERR_NONFINITE; break; }
       if (k >= p.max_cycles || rel > 1e3 * rel0) { st = MG_ERR_NOT_CONVERGED; break; }
-      TRY(cycle_rec<double>(g, p, 0, u, f, s));
+      TRY(run_cycles<double>(g, p, 1, u, f, s));
       ++k;
       TRY_CUDA("residual norm", launch_resnorm64(g, u, f, s));
       TRY(read_norms(g, s, &rs));
@@ -391,10 +447,8 @@ static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params
     if (rel <= p.tol) break;
     if (!std::isfinite(rel)) { st = MG_ERR_NONFINITE; break; }
     if (outer >= p.max_outer || cycles >= p.max_cycles || rel > 1e3 * rel0) { st = MG_ERR_NOT_CONVERGED; break; }
-    for (int k = 0; k < p.inner_cycles; ++k) {
-      TRY(cycle_rec<float>(g, p, 0, g.e32, g.r32, s));
-      ++cycles;
-    }
+    TRY(run_cycles<float>(g, p, p.inner_cycles, g.e32, g.r32, s));
+    cycles += p.inner_cycles;
     TRY_CUDA("refinement update", launch_ir_update(g, u, g.e32, s));
     ++outer;
   }

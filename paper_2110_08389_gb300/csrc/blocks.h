@@ -1,7 +1,6 @@
 // blocks.h -- host description of the blocks of every smoother (Sec. 3):
 // chains of straight segments plus at most one junction node.  Built in
-// closed form by setup.cu; consumed by the work-list packer (setup.cu) and
-// the coarse-cycle plan (mini.cu).
+// closed form by setup.cu; consumed by its work-list packer.
 #pragma once
 #include <vector>
 

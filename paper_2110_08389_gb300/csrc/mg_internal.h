@@ -171,41 +171,6 @@ struct Level {
   WorkList wl[WL_COUNT][2][2][2];     // [smoother][precision][colour][small, large]
 };
 
-// ---------------------------------------------------------------------------
-// Coarse-cycle plan (mini.cu): the levels from `level` down to the coarsest,
-// run by one CTA with every level in shared memory.  Per block: chains of
-// segments (a segment's first node is the previous segment's last node plus
-// one step in its own direction) and at most one junction node.
-constexpr int MINI_MAX_LEV = 8;
-struct MChain {
-  uint16_t i0, j0;                 // first node
-  uint8_t nseg, flags, ljdir, pad;  // flags: 1 = first node coupled to the junction (one step back
-                                    // against dir[0]); 2 = last node coupled to it (one step along ljdir)
-  uint16_t len[4];
-  uint8_t dir[4];
-};
-static_assert(sizeof(MChain) == 20, "MChain layout");
-struct MBlock {
-  uint16_t ji, jj;  // junction node
-  uint8_t junc, nchain;
-  uint16_t pad;
-  uint32_t pre0;  // first entry of the block's c' / pivot data
-  uint32_t zb0;   // first entry of its unit-junction response (junction blocks)
-  MChain ch[4];
-};
-static_assert(sizeof(MBlock) == 96, "MBlock layout");
-struct MiniPlan {
-  int level0 = -1;                         // finest level with blocks in the plan (-1: none)
-  int level_for[MG_SMOOTH_ALT_TW + 1] = {-1, -1, -1, -1, -1, -1, -1};  // first level of the kernel per smoother
-  size_t smem_for[MG_SMOOTH_ALT_TW + 1] = {};
-  struct Range { uint32_t a0, na, z0, nz; };
-  std::vector<Range> ranges;               // [(level - level0) * 5 + base smoother]
-  void *mem = nullptr;
-  MBlock *blocks = nullptr;
-  uint2 *tab = nullptr;
-  void *pre[3] = {};  // c', pivot reciprocal, zb (FP64 or FP32, by the plan's precision)
-};
-
 struct Grid {
   int nlev = 0;
   int sms = 1;                       // multiprocessors of the device the grid was set up on
@@ -231,7 +196,17 @@ struct Grid {
   // tiled-path kernels and after the last
   int timer_level = -1, timer_cap = 0, timer_n = 0;
   cudaEvent_t *timer_ev = nullptr;
-  MiniPlan mini[2];  // coarse-cycle plans, [0] FP64, [1] FP32
+  // Captured cycle sequences (CUDA graphs), replayed on the grid's own stream
+  // `gs`, ordered after / before the caller's stream by ev_fork / ev_join.
+  struct GraphEntry {
+    int key[8];
+    const void *u, *f;
+    cudaGraphExec_t exec;
+    unsigned long long launches;  // kernels in the graph
+  };
+  std::vector<GraphEntry> graphs;
+  cudaStream_t gs = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // Levels whose sides are both at least this use the tiled path for tweed and
@@ -249,12 +224,6 @@ const char *set_error(const char *where, cudaError_t e);
 void set_error_text(const char *msg);
 
 mg_status build_tiles(Grid &g, int level, int wl);
-// Coarse-cycle plan of one precision (0 = FP64, 1 = FP32) and its launch
-// (runs cycle_rec from g.mini[prec].level down in one kernel).
-mg_status build_mini(Grid &g, int prec);
-template <typename T>
-cudaError_t launch_mini_cycle(const Grid &g, const mg_params &p, T *u, const T *f, cudaStream_t s);
-
 // Dynamic shared memory opt-in of the line kernels on the current device
 // (called by mg_setup_grid).
 cudaError_t prepare_line_kernels();

@@ -61,14 +61,15 @@ struct __align__(4 * sizeof(T)) TRow {
 // perpendicular coefficient sum.
 template <typename T>
 struct TileGeom {
-  int base, step;
+  int base, step, vmax;
   bool xrun;
   const T *lo_arr, *hi_arr;
-  __device__ __forceinline__ TileGeom(const TileDesc &td, const CoefT<T> &cp) {
+  __device__ __forceinline__ TileGeom(const TileDesc &td, const CoefT<T> &cp, int nx, int ny) {
     const int dir = td.dir;
     xrun = dir < 2;
     step = (dir == DIR_PX || dir == DIR_PY) ? 1 : -1;
     base = td.base;
+    vmax = xrun ? nx : ny;
     if (xrun) { lo_arr = step > 0 ? cp.W : cp.E; hi_arr = step > 0 ? cp.E : cp.W; }
     else { lo_arr = step > 0 ? cp.S : cp.N; hi_arr = step > 0 ? cp.N : cp.S; }
   }
@@ -87,18 +88,23 @@ __device__ __forceinline__ void abc(const T (&co)[2][32], int q, int m, int fl, 
   c = (q == m - 1 && (fl & TL_LAST_W)) ? T(0) : hi;
 }
 
+// Positions of unused slots past the end of the axis (ragged last tiles of
+// lines from wall to wall) are clamped into the coefficient arrays.
 template <typename T>
 __device__ __forceinline__ void stage_coefs(const TileGeom<T> &g, int lane, T (&co)[2][32]) {
-  co[0][lane] = __ldg(g.lo_arr + g.v(lane));
-  co[1][lane] = __ldg(g.hi_arr + g.v(lane));
+  const int v = min(max(g.v(lane), 0), g.vmax);
+  co[0][lane] = __ldg(g.lo_arr + v);
+  co[1][lane] = __ldg(g.hi_arr + v);
   __syncwarp();
 }
 
 template <typename T>
 __global__ void __launch_bounds__(32 * TWv<T>) tile_reduce(const TileDesc *__restrict__ tiles,
                                                        const TileLane *__restrict__ lanes, int ntile, CoefT<T> cp,
-                                                       int nx1, const T *__restrict__ u, const T *__restrict__ f,
-                                                       TRow<T> *__restrict__ rows, T *__restrict__ dscr) {
+                                                       int nx, int ny, const T *__restrict__ u,
+                                                       const T *__restrict__ f, TRow<T> *__restrict__ rows,
+                                                       T *__restrict__ dscr) {
+  const int nx1 = nx + 1;
   constexpr int TW = TWv<T>;
   __shared__ T tr[TW][32][33];
   __shared__ T cos[TW][2][32];
@@ -107,7 +113,7 @@ __global__ void __launch_bounds__(32 * TWv<T>) tile_reduce(const TileDesc *__res
   if (t >= ntile) return;
   const TileDesc td = tiles[t];
   const TileLane ln = lanes[(size_t)t * 32 + lane];
-  const TileGeom<T> g(td, cp);
+  const TileGeom<T> g(td, cp, nx, ny);
   const int m = ln.q1, fl = ln.flags;
   T d[CMAX];
   stage_coefs(g, lane, cos[warp]);
@@ -323,8 +329,9 @@ __global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__
 template <typename T>
 __global__ void __launch_bounds__(32 * TWv<T>) tile_expand(const TileDesc *__restrict__ tiles,
                                                        const TileLane *__restrict__ lanes, int ntile, CoefT<T> cp,
-                                                       int nx1, const T *__restrict__ dscr,
+                                                       int nx, int ny, const T *__restrict__ dscr,
                                                        const T *__restrict__ xscr, T *__restrict__ u) {
+  const int nx1 = nx + 1;
   // per lane one row of x (tr) and of the Thomas multipliers c' (cs) in
   // shared memory, stride 33 (conflict-free both per lane and per slot)
   constexpr int TW = TWv<T>;
@@ -338,7 +345,7 @@ __global__ void __launch_bounds__(32 * TWv<T>) tile_expand(const TileDesc *__res
   if (t < 0) return;
   const TileDesc td = tiles[t];
   const TileLane ln = lanes[(size_t)t * 32 + lane];
-  const TileGeom<T> g(td, cp);
+  const TileGeom<T> g(td, cp, nx, ny);
   const int m = ln.q1, fl = ln.flags;
   stage_coefs(g, lane, cos[warp]);
   const T(&co)[2][32] = cos[warp];
@@ -408,11 +415,11 @@ cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &tl, 
   constexpr int TW = TWv<T>;
   const int ctas = (tl.ntile + TW - 1) / TW;
   if (ev) cudaEventRecord(ev[0], s);
-  if (tl.ntile > 0) tile_reduce<T><<<ctas, 32 * TW, 0, s>>>(tl.tile, tl.lane, tl.ntile, cp, nx1, u, f, rows, dscr);
+  if (tl.ntile > 0) tile_reduce<T><<<ctas, 32 * TW, 0, s>>>(tl.tile, tl.lane, tl.ntile, cp, L.nx, L.ny, u, f, rows, dscr);
   if (ev) cudaEventRecord(ev[1], s);
   tile_couple<T><<<tl.ngroup, 128, 0, s>>>(tl.block, cp, nx1, rows, cdp, xscr, u, f);
   if (ev) cudaEventRecord(ev[2], s);
-  if (tl.ntile > 0) tile_expand<T><<<ctas, 32 * TW, 0, s>>>(tl.tile, tl.lane, tl.ntile, cp, nx1, dscr, xscr, u);
+  if (tl.ntile > 0) tile_expand<T><<<ctas, 32 * TW, 0, s>>>(tl.tile, tl.lane, tl.ntile, cp, L.nx, L.ny, dscr, xscr, u);
   if (ev) cudaEventRecord(ev[3], s);
   count_launch(tl.ntile > 0 ? 3 : 1);
   return cudaGetLastError();

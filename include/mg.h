@@ -171,11 +171,14 @@ mg_status mg_coarse_solve(mg_grid *grid, void *u, const void *f, int dtype, void
 mg_status mg_vcycle(mg_grid *grid, void *u, const void *f, const mg_params *params,
                     void *stream);
 
-/* Solve to params->tol.  u, f: FP64 device arrays of the finest level.  u
- * holds the Dirichlet data g on its boundary (and the initial guess when
- * use_initial_guess).  MG_PREC_F64: FP64 cycles.  MG_PREC_F32_REFINE: FP32
- * smoothing, transfers and cycles on the correction equation, FP64 residual,
- * update and coarsest solve (iterative refinement).  info may be NULL.       */
+/* Solve to params->tol: cycles (Sec. 4) until ||f - L u||_2 / ||f - B g||_2
+ * <= tol over the interior nodes, where f - B g is the right-hand side of the
+ * interior system (||f|| when the boundary data g vanish).  u, f: FP64 device
+ * arrays of the finest level.  u holds g on its boundary (and the initial
+ * guess when use_initial_guess).  MG_PREC_F64: FP64 cycles.
+ * MG_PREC_F32_REFINE: FP32 smoothing, transfers and cycles on the correction
+ * equation, FP64 residual, update and coarsest solve (iterative refinement).
+ * info may be NULL.                                                          */
 mg_status mg_solve(mg_grid *grid, double *u, const double *f, const mg_params *params,
                    mg_info *info, void *stream);
 
@@ -185,6 +188,18 @@ mg_status mg_solve(mg_grid *grid, double *u, const double *f, const mg_params *p
  * arrays of the finest level; lambda's boundary is set to 0.                 */
 mg_status mg_solve_adjoint(mg_grid *grid, double *lambda, const double *rhs,
                            const mg_params *params, mg_info *info, void *stream);
+
+/* Gradient with respect to the Dirichlet data (adjoint of the boundary
+ * coupling; the paper has no adjoint, this serves differentiation through the
+ * solve).  With u_int = A^{-1} (f - B g), where (B g)_p sums coef(p -> b) g_b
+ * over the boundary neighbours b of interior node p, and lambda from
+ * mg_solve_adjoint with rhs = dloss/du:
+ *     grad_g[b] = grad_u[b] - sum_p coef(p -> b) lambda[p]   on boundary nodes,
+ *     grad_g    = 0                                          at interior nodes
+ * (dloss/df = lambda).  lambda, grad_u, grad_g: FP64 device arrays of the
+ * finest level; grad_g must not alias the others.  Enqueued on `stream`.      */
+mg_status mg_boundary_adjoint(mg_grid *grid, const double *lambda, const double *grad_u, double *grad_g,
+                              void *stream);
 
 /* Defaults for mg_params.                                                    */
 void mg_default_params(mg_params *params);

@@ -275,3 +275,47 @@ def dense_solve(A, b):
     if _load().or_dense_solve(len(x), A, x):
         raise RuntimeError("singular")
     return x
+
+
+# ---- gradient through the solve (the adjoint; the paper has none)
+
+def quadratic_loss_gradient(P: Problem, f, g, u_target):
+    """Gradient of l(u) = 0.5 ||u - u_target||^2 (sum over all nodes), u the
+    solution of Eq. (prob:DP) with source f inside and Dirichlet data g on the
+    boundary, with respect to f (interior entries) and g (boundary entries).
+
+    The plain definition, for small grids: with A the interior operator and B
+    its coupling to the boundary values (both assembled by applying the
+    oracle's operator to unit vectors), u_int = A^{-1} (f_int - B g_b),
+    lambda = A^{-T} (u - u_target)_int, dl/df = lambda and
+    dl/dg_b = (u - u_target)_b - (B^T lambda)_b.  Dense solves by the oracle's
+    own Gaussian elimination.  Returns (l, u, grad_f, grad_g)."""
+    ny1, nx1 = P.shape()
+    f, g, ut = _f64(f), _f64(g), _f64(u_target)
+    inner = np.zeros((ny1, nx1), dtype=bool)
+    inner[1:-1, 1:-1] = True
+    ii = np.flatnonzero(inner.ravel())
+    bb = np.flatnonzero(~inner.ravel())
+    n = len(ii)
+    A = np.zeros((n, n))
+    B = np.zeros((n, len(bb)))
+    e = np.zeros(ny1 * nx1)
+    for k, p in enumerate(ii):
+        e[p] = 1.0
+        A[:, k] = P.apply(e.reshape(ny1, nx1)).ravel()[ii]
+        e[p] = 0.0
+    for k, p in enumerate(bb):
+        e[p] = 1.0
+        B[:, k] = P.apply(e.reshape(ny1, nx1)).ravel()[ii]
+        e[p] = 0.0
+    gb = g.ravel()[bb]
+    u = g.copy().ravel()
+    u[ii] = dense_solve(A, f.ravel()[ii] - B @ gb)
+    r = u - ut.ravel()
+    lam = dense_solve(A.T.copy(), r[ii])
+    grad_f = np.zeros(ny1 * nx1)
+    grad_f[ii] = lam
+    grad_g = np.zeros(ny1 * nx1)
+    grad_g[bb] = r[bb] - B.T @ lam
+    loss = 0.5 * float(r @ r)
+    return loss, u.reshape(ny1, nx1), grad_f.reshape(ny1, nx1), grad_g.reshape(ny1, nx1)

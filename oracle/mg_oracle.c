@@ -41,6 +41,10 @@
  *   R6  the restriction/prolongation weights are the index-based ones printed
  *       in Sec. 4, applied to the pointwise defect; coarse operators are
  *       rediscretised on the subsampled coordinates.
+ *   R11 the stop test of Sec. 4 step (6) ("sufficiently small") is
+ *       ||f - L u||_2 / ||f - B g||_2 <= tol over interior nodes, f - B g the
+ *       right-hand side of the interior system (f when the boundary data g
+ *       vanish).
  */
 #include <math.h>
 #include <stdio.h>
@@ -710,7 +714,16 @@ int or_solve(or_problem *P, int smoother, int nu1, int nu2, int gamma, int restr
   level_t *L = &P->lev[0];
   size_t nn = (size_t)(L->nx + 1) * (L->ny + 1);
   double *d = malloc(sizeof(double) * nn), fs, fm, s, m, m0;
-  or_norms(P, 0, f, &fs, &fm);
+  /* scale of the relative residual: the right-hand side of the interior
+     system, f - B g = the residual of u with its interior set to zero (equal
+     to f when the boundary data g vanish) */
+  for (size_t k = 0; k < nn; ++k) d[k] = u[k];
+  for (int j = 1; j < L->ny; ++j)
+    for (int i = 1; i < L->nx; ++i) d[ID(L, i, j)] = 0.0;
+  double *b = malloc(sizeof(double) * nn);
+  or_residual(P, 0, d, f, b);
+  or_norms(P, 0, b, &fs, &fm);
+  free(b);
   double fn = sqrt(fs);
   or_residual(P, 0, u, f, d);
   or_norms(P, 0, d, &s, &m0);

@@ -402,8 +402,10 @@ static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params
   const Level &L0 = g.lev[0];
   if (info) { info->cycles = 0; info->outer_iters = 0; info->history_len = 0; info->rel_res = 0; info->conv_factor = 0; }
   if (!p.use_initial_guess) TRY_CUDA("zero u", launch_zero_interior<double>(L0, u, s));
+  // scale of the relative residual: ||f - B g||, the right-hand side of the
+  // interior system (||f|| when the boundary data vanish)
   double fs, rs;
-  TRY_CUDA("norm(f)", launch_resnorm64(g, nullptr, f, s));
+  TRY_CUDA("norm(f - B g)", launch_rhsnorm64(g, u, f, s));
   TRY(read_norms(g, s, &fs));
   double fn = std::sqrt(fs);
   if (p.precision == MG_PREC_F64) {
@@ -654,6 +656,14 @@ mg_status mg_solve_adjoint(mg_grid *g, double *lambda, const double *rhs, const 
   if (e != cudaSuccess) return cuda_status("adjoint scaling", e);
   if (info) info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return st;
+}
+
+mg_status mg_boundary_adjoint(mg_grid *g, const double *lambda, const double *grad_u, double *grad_g,
+                              void *stream) {
+  if (!g || !lambda || !grad_u || !grad_g) return MG_ERR_INVALID_ARG;
+  cudaError_t e = launch_boundary_adjoint(*g, lambda, grad_u, grad_g, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_status("boundary adjoint", e);
+  return MG_OK;
 }
 
 mg_status mg_pass_timer_begin(mg_grid *g, int level, int max_passes) {

@@ -252,11 +252,14 @@ cudaError_t launch_coarse_solve(const Grid &g, T *u, const T *f, cudaStream_t s)
 // FP64 norms: out[0] = sum (f-Lu)^2 over interior, out[1] = max |f-Lu|,
 // written to the device scalars g.scal[0..1] (u may be NULL: residual = f).
 cudaError_t launch_resnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s);
+// ||f - B u_b||^2: the right-hand side of the interior system (u's interior taken as 0)
+cudaError_t launch_rhsnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s);
 // Refinement: r32 = float(f - L u64) and the FP64 norms of f - L u64 into scal.
 cudaError_t launch_ir_residual(const Grid &g, const double *u, const double *f, float *r32, float *e32,
                                cudaStream_t s);
 // u64 += e32 on interior nodes.
 cudaError_t launch_ir_update(const Grid &g, double *u, const float *e, cudaStream_t s);
+cudaError_t launch_boundary_adjoint(const Grid &g, const double *lam, const double *gu, double *gg, cudaStream_t s);
 // a[interior] *= scale_x[i]*scale_y[j] (adjoint diagonal scalings), boundary := 0.
 cudaError_t launch_diag_scale(const Grid &g, double *out, const double *in, int inverse,
                               cudaStream_t s);

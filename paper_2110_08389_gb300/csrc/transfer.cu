@@ -233,7 +233,9 @@ __device__ __forceinline__ double block_sum(double s) {
   return ss[0];
 }
 
-// Sum of squares of r over the interior, r = f - L u (u may be NULL: r = f).
+// Sum of squares of r over the interior, r = f - L u (u may be NULL: r = f;
+// bnd_only: r = f - B u_b, the boundary neighbours alone, i.e. the residual of
+// u with its interior taken as zero -- the scale of the relative residual).
 // CTA b takes interior rows 1 + b, 1 + b + gridDim.x, ...; every thread its
 // columns in order, so the result does not depend on timing.  With r32 set
 // (refinement mode) it also stores float(r) and zeroes the FP32 correction
@@ -241,7 +243,7 @@ __device__ __forceinline__ double block_sum(double s) {
 // operations per node.
 __global__ void __launch_bounds__(NORM_THREADS) norm_stage1(CoefQ<double> c, int nx, int ny,
                                                             const double *__restrict__ u,
-                                                            const double *__restrict__ f,
+                                                            const double *__restrict__ f, int bnd_only,
                                                             float *__restrict__ r32, float *__restrict__ e32,
                                                             double *__restrict__ part) {
   const int nx1 = nx + 1;
@@ -252,7 +254,13 @@ __global__ void __launch_bounds__(NORM_THREADS) norm_stage1(CoefQ<double> c, int
     for (int i = 1 + threadIdx.x; i < nx; i += NORM_THREADS) {
       const size_t p = row + i;
       double r = f[p];
-      if (u) {
+      if (bnd_only) {
+        // f - B g: only the boundary neighbours of u (its interior taken as 0)
+        if (i == 1) r -= __ldg(c.W + i) * u[p - 1];
+        if (i == nx - 1) r -= __ldg(c.E + i) * u[p + 1];
+        if (j == 1) r -= sj * u[p - nx1];
+        if (j == ny - 1) r -= nj * u[p + nx1];
+      } else if (u) {
         const double w = __ldg(c.W + i), e = __ldg(c.E + i);
         const double cc = (w + e) + snj;
         r -= w * u[p - 1] + e * u[p + 1] + sj * u[p - nx1] + nj * u[p + nx1] - cc * u[p];
@@ -273,20 +281,24 @@ __global__ void __launch_bounds__(NORM_THREADS) norm_stage2(const double *__rest
   if (threadIdx.x == 0) out[0] = s;
 }
 
-static cudaError_t norms(const Grid &g, const double *u, const double *f, float *r32, float *e32, cudaStream_t s) {
+static cudaError_t norms(const Grid &g, const double *u, const double *f, int bnd_only, float *r32, float *e32,
+                         cudaStream_t s) {
   const Level &L = g.lev[0];
-  norm_stage1<<<g.npartial, NORM_THREADS, 0, s>>>(cq<double>(L), L.nx, L.ny, u, f, r32, e32, g.partial);
+  norm_stage1<<<g.npartial, NORM_THREADS, 0, s>>>(cq<double>(L), L.nx, L.ny, u, f, bnd_only, r32, e32, g.partial);
   norm_stage2<<<1, NORM_THREADS, 0, s>>>(g.partial, g.npartial, g.scal);
   count_launch(2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_resnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s) {
-  return norms(g, u, f, nullptr, nullptr, s);
+  return norms(g, u, f, 0, nullptr, nullptr, s);
+}
+cudaError_t launch_rhsnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s) {
+  return norms(g, u, f, 1, nullptr, nullptr, s);
 }
 cudaError_t launch_ir_residual(const Grid &g, const double *u, const double *f, float *r32, float *e32,
                                cudaStream_t s) {
-  return norms(g, u, f, r32, e32, s);
+  return norms(g, u, f, 0, r32, e32, s);
 }
 
 // Row-wise elementwise kernels: CTA (x, j) covers interior row j + 1 with a
@@ -337,6 +349,41 @@ cudaError_t launch_zero_interior(const Level &L, T *a, cudaStream_t s) {
   count_launch(1);
   return cudaGetLastError();
 }
+// Gradient of a loss with respect to the Dirichlet data, from the adjoint
+// state: u_int = A^{-1} (f - B g), (B g)_p = sum over boundary neighbours b
+// of p of coef(p -> b) g_b, so dloss/dg_b = dloss/du_b - sum_p coef(p -> b)
+// lambda_p.  One thread per boundary node (bottom row, top row, left and
+// right columns without the corners); interior entries of grad_g are 0.
+__global__ void boundary_adjoint_kernel(const double *__restrict__ W, const double *__restrict__ E,
+                                        const double *__restrict__ S, const double *__restrict__ N, int nx, int ny,
+                                        const double *__restrict__ lam, const double *__restrict__ gu,
+                                        double *__restrict__ gg) {
+  const int nx1 = nx + 1, nb = 2 * nx1 + 2 * (ny - 1);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+    int i, j;
+    if (k < nx1) { i = k; j = 0; }
+    else if (k < 2 * nx1) { i = k - nx1; j = ny; }
+    else if (k < 2 * nx1 + (ny - 1)) { i = 0; j = k - 2 * nx1 + 1; }
+    else { i = nx; j = k - 2 * nx1 - (ny - 1) + 1; }
+    const size_t b = (size_t)j * nx1 + i;
+    double v = gu[b];
+    if (j == 0 && i > 0 && i < nx) v -= S[1] * lam[b + nx1];
+    if (j == ny && i > 0 && i < nx) v -= N[ny - 1] * lam[b - nx1];
+    if (i == 0 && j > 0 && j < ny) v -= W[1] * lam[b + 1];
+    if (i == nx && j > 0 && j < ny) v -= E[nx - 1] * lam[b - 1];
+    gg[b] = v;
+  }
+}
+cudaError_t launch_boundary_adjoint(const Grid &g, const double *lam, const double *gu, double *gg,
+                                    cudaStream_t s) {
+  const Level &L = g.lev[0];
+  const int nb = 2 * (L.nx + 1) + 2 * (L.ny - 1);
+  zero_interior_kernel<double><<<row_grid(L), EW_THREADS, 0, s>>>(L.nx, gg);
+  boundary_adjoint_kernel<<<(nb + 255) / 256, 256, 0, s>>>(L.W64, L.E64, L.S64, L.N64, L.nx, L.ny, lam, gu, gg);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_zero_interior<double>(const Level &, double *, cudaStream_t);
 template cudaError_t launch_zero_interior<float>(const Level &, float *, cudaStream_t);
 

@@ -32,7 +32,7 @@ EXPORTS = ["mg_setup_grid", "mg_destroy", "mg_num_levels", "mg_level_shape", "mg
            "mg_smooth_wireframe", "mg_smooth", "mg_colour_pass", "mg_residual_restrict", "mg_prolong_add",
            "mg_residual", "mg_coarse_solve", "mg_vcycle", "mg_solve", "mg_solve_adjoint",
            "mg_default_params", "mg_status_string", "mg_last_error", "mg_kernel_launches",
-           "mg_residual_norm_static", "mg_pass_timer_begin", "mg_pass_timer_end"]
+           "mg_residual_norm_static", "mg_pass_timer_begin", "mg_pass_timer_end", "mg_boundary_adjoint"]
 
 
 class MGError(RuntimeError):
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
         "mg_kernel_launches": (ctypes.c_ulonglong, []),
         "mg_residual_norm_static": (i, [ctypes.c_int64, ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp, vp]),
         "mg_pass_timer_begin": (i, [vp, i, i]),
+        "mg_boundary_adjoint": (i, [vp, vp, vp, vp, vp]),
         "mg_pass_timer_end": (i, [vp, i64p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double)]),
     }
@@ -222,6 +223,12 @@ class Grid:
         _check(self.lib.mg_colour_pass(self.h, level, sm, colour, _ptr(u), _ptr(f), _dtype_code(u),
                                        _stream(stream)), "mg_colour_pass")
         return u
+
+    def boundary_adjoint(self, lam, grad_u, grad_g, stream=None):
+        """grad_g from the adjoint state lam and dloss/du (mg_boundary_adjoint)."""
+        _check(self.lib.mg_boundary_adjoint(self.h, _ptr(lam), _ptr(grad_u), _ptr(grad_g), _stream(stream)),
+               "mg_boundary_adjoint")
+        return grad_g
 
     def pass_timer_begin(self, level=0, max_passes=4096):
         """Time every colour pass on `level` from now on with CUDA events on

@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--inner", type=int, default=4)
     ap.add_argument("--intervals", type=int, default=N_INTERVALS, help="intervals per side (4096: the 4097 x 4097 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="single", choices=["single", "batch"],
+                    help="single: the 4097^2 solve (default); batch: 256 mixed problems solved together")
     return ap.parse_args()
 
 
@@ -213,10 +215,108 @@ def run_reference(args):
 
 # ------------------------------------------------------------------- ours
 
+# ------------------------------------------------------------------ batch
+
+BATCH_SIZES = (128, 256, 512, 1024)
+
+
+def batch_problems(count=256, seed=2):
+    """count problems: intervals per side uniform in BATCH_SIZES, spacing ratio
+    log-uniform in [10, 1000], wall or centre clustering by a coin flip."""
+    from paper_2110_08389_gb300 import inputs as I
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for k in range(count):
+        n = int(rng.choice(BATCH_SIZES))
+        ratio = float(10.0 ** rng.uniform(1.0, 3.0))
+        kind = "wall" if rng.uniform() < 0.5 else "centre"
+        out.append((n, ratio, kind, I.coords(n, kind, ratio=ratio)))
+    return out
+
+
+def run_batch(args):
+    """Config 3: 256 independent 2D problems of mixed sizes and stretchings,
+    FP32 cycles + FP64 refinement to 1e-10, solved as one batch
+    (mg_batch_solve) and, for comparison, one after another (mg_solve)."""
+    import numpy as np
+    import torch
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    from paper_2110_08389_gb300 import build, inputs as I, mg
+    build.build()
+    probs = batch_problems()
+    grids = [mg.Grid(x, x) for (_, _, _, x) in probs]
+    fs = [torch.tensor(I.rhs_gaussian(n + 1, n + 1, 2000 + k), device="cuda") for k, (n, _, _, _) in enumerate(probs)]
+    us = [torch.zeros_like(f) for f in fs]
+    batch = mg.Batch(grids)
+    # the paper's pairing (Sec. 6): tweed for wall clustering, wireframe for
+    # clustering towards the centre
+    params = [mg.default_params(smoother="wireframe" if kind == "centre" else "tweed", nu1=args.nu[0],
+                                nu2=args.nu[1], precision="f32_refine", tol=TOL, inner_cycles=args.inner,
+                                max_outer=20, max_cycles=200) for (_, _, kind, _) in probs]
+    for _ in range(args.warmup):
+        res = batch.solve(us, fs, params)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(pg)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            res = batch.solve(us, fs, params)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, pg, torch.device("cuda", local))
+    ok = sum(1 for r in res if r.status == mg.OK and r.rel_res <= TOL)
+    ok_kind = {kind: sum(1 for r, p in zip(res, probs) if p[2] == kind and r.status == mg.OK)
+               for kind in ("wall", "centre")}
+    # the same problems one after another
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for k in range(len(probs)):
+        grids[k].solve(us[k], fs[k], params[k])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    # end to end: host f in, host u out
+    fh = [f.cpu().pin_memory() for f in fs]
+    uh = [torch.empty_like(h).pin_memory() for h in fh]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(len(probs)):
+        fs[k].copy_(fh[k], non_blocking=True)
+    batch.solve(us, fs, params)
+    for k in range(len(probs)):
+        uh[k].copy_(us[k], non_blocking=True)
+    torch.cuda.synchronize()
+    e2e = (time.perf_counter() - t0)
+    nodes = sum((n + 1) ** 2 for (n, _, _, _) in probs)
+    line = {"metric": "s to rel. residual 1e-10 for 256 mixed 2D problems, batched (FP32+refine tweed/wireframe MG)",
+            "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "256 problems, n+1 in {129,257,513,1025}^2 uniform, spacing ratio log-uniform "
+                                   "[10,1000], wall/centre by coin flip (seed 2), f~N(0,1), tweed (wall) / wireframe "
+                                   "(centre) V(1,1), FW, to ||r||/||f||<=1e-10", "nodes_total": nodes, "problems": len(probs),
+                       "sizes": {str(s + 1): sum(1 for p in probs if p[0] == s) for s in BATCH_SIZES}},
+            "converged": ok, "converged_by_clustering": ok_kind,
+            "smoothers": "tweed (wall-clustered), wireframe (centre-clustered)",
+            "problems_per_s": len(probs) / (ms / 1e3),
+            "sequential_s": ms_seq / 1e3, "speedup_vs_sequential": ms_seq / ms,
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 8 * nodes, "d2h_bytes_per_step": 8 * nodes},
+            "gpu_launches": None, "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    barrier(pg)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     import numpy as np
     import torch
 

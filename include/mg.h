@@ -189,6 +189,30 @@ mg_status mg_solve(mg_grid *grid, double *u, const double *f, const mg_params *p
 mg_status mg_solve_adjoint(mg_grid *grid, double *lambda, const double *rhs,
                            const mg_params *params, mg_info *info, void *stream);
 
+/* ---- batches of independent problems (the paper solves one problem at a
+ * time; this serves many problems of different sizes and stretchings at
+ * once).  A batch is a set of distinct grids (each problem needs its own
+ * grid: grids hold per-solve scratch).  mg_batch_create creates up to 16
+ * streams of the batch's own (no device memory); MG_ERR_INVALID_ARG if a grid
+ * repeats.  The grids stay owned by the caller and must outlive the batch.  */
+typedef struct mg_batch mg_batch;
+mg_status mg_batch_create(mg_batch **out, int count, mg_grid *const *grids);
+void mg_batch_destroy(mg_batch *batch);
+
+/* Solves problem i (u[i], f[i]: FP64 device arrays of grid i, as in
+ * mg_solve) for every i, with params[0] for all (nparams = 1) or params[i]
+ * for problem i (nparams = count; e.g. tweed for wall-clustered and
+ * wireframe for centre-clustered grids, Sec. 6).  The problems run
+ * concurrently on the batch's streams; the host waits once per cycle (FP64)
+ * or refinement step (FP32) for all of them, and each problem stops at its own
+ * tolerance.  Results, infos[i] and status[i] (host arrays of count
+ * entries, either may be NULL) are those mg_solve gives for the problem
+ * alone.  Starts after the work already on `stream` and makes `stream` wait
+ * for its end.  Returns MG_OK if every problem returned MG_OK, else the first
+ * non-OK status in problem order.                                            */
+mg_status mg_batch_solve(mg_batch *batch, double *const *u, const double *const *f, const mg_params *params,
+                         int nparams, mg_info *infos, int *status, void *stream);
+
 /* Gradient with respect to the Dirichlet data (adjoint of the boundary
  * coupling; the paper has no adjoint, this serves differentiation through the
  * solve).  With u_int = A^{-1} (f - B g), where (B g)_p sums coef(p -> b) g_b

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of tweedmg (include/mg.h): grid setup, the cycle driver
 // (Sec. 4 steps (1)-(6)), the FP64 solve, the FP32 + FP64 iterative
 // refinement solve and the adjoint solve.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -382,14 +383,6 @@ static mg_status check_params(const Grid *g, const mg_params *p) {
   return MG_OK;
 }
 
-// Read the device sum of squares of the last norm back to the host.
-static mg_status read_norms(Grid &g, cudaStream_t s, double *sumsq) {
-  TRY_CUDA("cudaMemcpyAsync(norms)", cudaMemcpyAsync(g.hpinned, g.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
-  TRY_CUDA("cudaStreamSynchronize", cudaStreamSynchronize(s));
-  *sumsq = g.hpinned[0];
-  return MG_OK;
-}
-
 static void record(mg_info *info, int k, double rel) {
   if (info && info->history && k < info->history_cap) {
     info->history[k] = rel;
@@ -397,70 +390,107 @@ static void record(mg_info *info, int k, double rel) {
   }
 }
 
+// One solve (Sec. 4: cycles until the relative residual is below tol) as a
+// resumable state machine: enqueue() puts the device work up to the next norm
+// read on the stream (ending with the copy of the norm to pinned host memory),
+// consume() reads that norm once the stream has drained and decides the next
+// step.  solve_impl alternates the two; mg_batch_solve interleaves many
+// problems with one host synchronisation per step for all of them.
+struct SolveState {
+  Grid *g;
+  double *u;
+  const double *f;
+  mg_params p;
+  mg_info *info;
+  cudaStream_t s;
+  int phase = 0;  // 0: scale norm, 1: initial residual, 2: iterating
+  bool done = false;
+  mg_status st = MG_OK;
+  double fn = 0.0, rel = 0.0, rel0 = 0.0;
+  int cycles = 0, outer = 0;
+};
+
+static mg_status copy_norm(Grid &g, cudaStream_t s) {
+  TRY_CUDA("cudaMemcpyAsync(norms)", cudaMemcpyAsync(g.hpinned, g.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return MG_OK;
+}
+
+static mg_status enqueue(SolveState &q) {
+  Grid &g = *q.g;
+  const mg_params &p = q.p;
+  const bool f64 = p.precision == MG_PREC_F64;
+  if (q.phase == 0) {
+    if (q.info) { q.info->cycles = 0; q.info->outer_iters = 0; q.info->history_len = 0; q.info->rel_res = 0; q.info->conv_factor = 0; }
+    if (!p.use_initial_guess) TRY_CUDA("zero u", launch_zero_interior<double>(g.lev[0], q.u, q.s));
+    // scale of the relative residual: ||f - B g||, the right-hand side of the
+    // interior system (||f|| when the boundary data vanish)
+    TRY_CUDA("norm(f - B g)", launch_rhsnorm64(g, q.u, q.f, q.s));
+  } else if (f64) {
+    if (q.phase == 2) TRY(run_cycles<double>(g, p, 1, q.u, q.f, q.s));
+    TRY_CUDA("residual norm", launch_resnorm64(g, q.u, q.f, q.s));
+  } else {
+    // FP32 cycles on the correction equation L e = r (e zeroed by the
+    // residual kernel), FP64 residual and update
+    if (q.phase == 2) {
+      TRY(run_cycles<float>(g, p, p.inner_cycles, g.e32, g.r32, q.s));
+      TRY_CUDA("refinement update", launch_ir_update(g, q.u, g.e32, q.s));
+    }
+    TRY_CUDA("refinement residual", launch_ir_residual(g, q.u, q.f, g.r32, g.e32, q.s));
+  }
+  return copy_norm(g, q.s);
+}
+
+static void finish(SolveState &q) {
+  q.done = true;
+  if (q.st == MG_OK && !std::isfinite(q.rel)) q.st = MG_ERR_NONFINITE;
+  if (!q.info) return;
+  const int n = q.cycles;
+  q.info->cycles = n;
+  q.info->outer_iters = q.outer;
+  q.info->rel_res = q.rel;
+  q.info->conv_factor = (n > 0 && q.rel0 > 0 && q.rel > 0) ? std::pow(q.rel / q.rel0, 1.0 / n) : 0.0;
+}
+
+static void consume(SolveState &q) {
+  const double v = q.g->hpinned[0];
+  const mg_params &p = q.p;
+  const bool f64 = p.precision == MG_PREC_F64;
+  if (q.phase == 0) {
+    q.fn = std::sqrt(v);
+    q.phase = 1;
+    return;
+  }
+  if (q.phase == 1) {
+    if (q.fn == 0.0) q.fn = std::sqrt(v) > 0.0 ? std::sqrt(v) : 1.0;
+    q.rel = q.rel0 = std::sqrt(v) / q.fn;
+    record(q.info, 0, q.rel);
+    q.phase = 2;
+  } else {
+    if (f64) {
+      q.cycles += 1;
+    } else {
+      q.cycles += p.inner_cycles;
+      q.outer += 1;
+    }
+    q.rel = std::sqrt(v) / q.fn;
+    record(q.info, f64 ? q.cycles : q.outer, q.rel);
+  }
+  if (q.rel <= p.tol) return finish(q);
+  if (!std::isfinite(q.rel)) { q.st = MG_ERR_NONFINITE; return finish(q); }
+  const bool limit = f64 ? q.cycles >= p.max_cycles : (q.outer >= p.max_outer || q.cycles >= p.max_cycles);
+  if (limit || q.rel > 1e3 * q.rel0) { q.st = MG_ERR_NOT_CONVERGED; return finish(q); }
+}
+
 static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params &p, mg_info *info,
                             cudaStream_t s) {
-  const Level &L0 = g.lev[0];
-  if (info) { info->cycles = 0; info->outer_iters = 0; info->history_len = 0; info->rel_res = 0; info->conv_factor = 0; }
-  if (!p.use_initial_guess) TRY_CUDA("zero u", launch_zero_interior<double>(L0, u, s));
-  // scale of the relative residual: ||f - B g||, the right-hand side of the
-  // interior system (||f|| when the boundary data vanish)
-  double fs, rs;
-  TRY_CUDA("norm(f - B g)", launch_rhsnorm64(g, u, f, s));
-  TRY(read_norms(g, s, &fs));
-  double fn = std::sqrt(fs);
-  if (p.precision == MG_PREC_F64) {
-    TRY_CUDA("residual norm", launch_resnorm64(g, u, f, s));
-    TRY(read_norms(g, s, &rs));
-    if (fn == 0.0) fn = std::sqrt(rs) > 0.0 ? std::sqrt(rs) : 1.0;
-    double rel = std::sqrt(rs) / fn;
-    const double rel0 = rel;
-    record(info, 0, rel);
-    int k = 0;
-    mg_status st = MG_OK;
-    while (!(rel <= p.tol)) {
-      if (!std::isfinite(rel)) { st = MG_ERR_NONFINITE; break; }
-      if (k >= p.max_cycles || rel > 1e3 * rel0) { st = MG_ERR_NOT_CONVERGED; break; }
-      TRY(run_cycles<double>(g, p, 1, u, f, s));
-      ++k;
-      TRY_CUDA("residual norm", launch_resnorm64(g, u, f, s));
-      TRY(read_norms(g, s, &rs));
-      rel = std::sqrt(rs) / fn;
-      record(info, k, rel);
-    }
-    if (info) {
-      info->cycles = k;
-      info->rel_res = rel;
-      info->conv_factor = (k > 0 && rel0 > 0 && rel > 0) ? std::pow(rel / rel0, 1.0 / k) : 0.0;
-    }
-    if (st == MG_OK && !std::isfinite(rel)) st = MG_ERR_NONFINITE;
-    return st;
+  SolveState q;
+  q.g = &g; q.u = u; q.f = f; q.p = p; q.info = info; q.s = s;
+  while (!q.done) {
+    TRY(enqueue(q));
+    TRY_CUDA("cudaStreamSynchronize", cudaStreamSynchronize(s));
+    consume(q);
   }
-  // FP32 cycles on the correction equation L e = r, FP64 residual and update
-  int outer = 0, cycles = 0;
-  double rel = 0.0, rel0 = 0.0;
-  mg_status st = MG_OK;
-  while (true) {
-    TRY_CUDA("refinement residual", launch_ir_residual(g, u, f, g.r32, g.e32, s));
-    TRY(read_norms(g, s, &rs));
-    if (outer == 0 && fn == 0.0) fn = std::sqrt(rs) > 0.0 ? std::sqrt(rs) : 1.0;
-    rel = std::sqrt(rs) / fn;
-    if (outer == 0) rel0 = rel;
-    record(info, outer, rel);
-    if (rel <= p.tol) break;
-    if (!std::isfinite(rel)) { st = MG_ERR_NONFINITE; break; }
-    if (outer >= p.max_outer || cycles >= p.max_cycles || rel > 1e3 * rel0) { st = MG_ERR_NOT_CONVERGED; break; }
-    TRY(run_cycles<float>(g, p, p.inner_cycles, g.e32, g.r32, s));
-    cycles += p.inner_cycles;
-    TRY_CUDA("refinement update", launch_ir_update(g, u, g.e32, s));
-    ++outer;
-  }
-  if (info) {
-    info->cycles = cycles;
-    info->outer_iters = outer;
-    info->rel_res = rel;
-    info->conv_factor = (cycles > 0 && rel0 > 0 && rel > 0) ? std::pow(rel / rel0, 1.0 / cycles) : 0.0;
-  }
-  return st;
+  return q.st;
 }
 
 }  // namespace tmg
@@ -468,6 +498,25 @@ static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params
 using namespace tmg;
 
 struct mg_grid : public Grid {};
+
+// A set of grids solved together (mg_batch_solve): up to MAX_BATCH_STREAMS
+// streams of its own, a fork event on the caller's stream and one join
+// event per stream.
+constexpr int MAX_BATCH_STREAMS = 16;
+struct mg_batch {
+  std::vector<Grid *> grids;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> joins;
+  cudaEvent_t fork = nullptr;
+};
+
+static void free_batch(mg_batch *b) {
+  if (!b) return;
+  for (auto e : b->joins) cudaEventDestroy(e);
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+}
 
 extern "C" {
 
@@ -656,6 +705,86 @@ mg_status mg_solve_adjoint(mg_grid *g, double *lambda, const double *rhs, const 
   if (e != cudaSuccess) return cuda_status("adjoint scaling", e);
   if (info) info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return st;
+}
+
+mg_status mg_batch_create(mg_batch **out, int count, mg_grid *const *grids) {
+  if (!out || count < 1 || !grids) return MG_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::vector<Grid *> gs(count);
+  for (int i = 0; i < count; ++i) {
+    if (!grids[i]) return MG_ERR_INVALID_ARG;
+    gs[i] = grids[i];
+  }
+  std::vector<Grid *> sorted(gs);
+  std::sort(sorted.begin(), sorted.end());
+  if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
+    set_error_text("mg_batch_create: a grid appears twice (each problem needs its own grid)");
+    return MG_ERR_INVALID_ARG;
+  }
+  mg_batch *b = new (std::nothrow) mg_batch;
+  if (!b) return MG_ERR_ALLOC;
+  b->grids = gs;
+  const int k = std::min(count, MAX_BATCH_STREAMS);
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int i = 0; i < k && e == cudaSuccess; ++i) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->streams.push_back(s);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->joins.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    free_batch(b);
+    return cuda_status("mg_batch_create", e);
+  }
+  *out = b;
+  return MG_OK;
+}
+
+void mg_batch_destroy(mg_batch *b) { free_batch(b); }
+
+mg_status mg_batch_solve(mg_batch *b, double *const *u, const double *const *f, const mg_params *params,
+                         int nparams, mg_info *infos, int *status, void *stream) {
+  if (!b || !u || !f || !params) return MG_ERR_INVALID_ARG;
+  const int n = (int)b->grids.size(), k = (int)b->streams.size();
+  if (nparams != 1 && nparams != n) return MG_ERR_INVALID_ARG;
+  std::vector<SolveState> q(n);
+  for (int i = 0; i < n; ++i) {
+    if (!u[i] || !f[i]) return MG_ERR_INVALID_ARG;
+    const mg_params *p = params + (nparams == 1 ? 0 : i);
+    mg_status st = check_params(b->grids[i], p);
+    if (st != MG_OK) return st;
+    q[i].g = b->grids[i]; q[i].u = u[i]; q[i].f = f[i]; q[i].p = *p;
+    q[i].info = infos ? infos + i : nullptr;
+    q[i].s = b->streams[i % k];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the batch's streams start after the caller's stream
+  TRY_CUDA("cudaEventRecord(batch fork)", cudaEventRecord(b->fork, s));
+  for (auto bs : b->streams) TRY_CUDA("cudaStreamWaitEvent(batch fork)", cudaStreamWaitEvent(bs, b->fork, 0));
+  mg_status worst = MG_OK;
+  int active = n;
+  while (active > 0) {
+    for (auto &x : q)
+      if (!x.done) TRY(enqueue(x));
+    for (auto bs : b->streams) TRY_CUDA("cudaStreamSynchronize(batch)", cudaStreamSynchronize(bs));
+    active = 0;
+    for (auto &x : q)
+      if (!x.done) {
+        consume(x);
+        if (x.done && x.st != MG_OK && worst == MG_OK) worst = x.st;
+        active += x.done ? 0 : 1;
+      }
+  }
+  if (status)
+    for (int i = 0; i < n; ++i) status[i] = (int)q[i].st;
+  // the caller's stream continues after the batch's streams
+  for (int i = 0; i < k; ++i) {
+    TRY_CUDA("cudaEventRecord(batch join)", cudaEventRecord(b->joins[i], b->streams[i]));
+    TRY_CUDA("cudaStreamWaitEvent(batch join)", cudaStreamWaitEvent(s, b->joins[i], 0));
+  }
+  return worst;
 }
 
 mg_status mg_boundary_adjoint(mg_grid *g, const double *lambda, const double *grad_u, double *grad_g,

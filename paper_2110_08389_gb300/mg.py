@@ -32,7 +32,8 @@ EXPORTS = ["mg_setup_grid", "mg_destroy", "mg_num_levels", "mg_level_shape", "mg
            "mg_smooth_wireframe", "mg_smooth", "mg_colour_pass", "mg_residual_restrict", "mg_prolong_add",
            "mg_residual", "mg_coarse_solve", "mg_vcycle", "mg_solve", "mg_solve_adjoint",
            "mg_default_params", "mg_status_string", "mg_last_error", "mg_kernel_launches",
-           "mg_residual_norm_static", "mg_pass_timer_begin", "mg_pass_timer_end", "mg_boundary_adjoint"]
+           "mg_residual_norm_static", "mg_pass_timer_begin", "mg_pass_timer_end", "mg_boundary_adjoint", "mg_batch_create",
+           "mg_batch_destroy", "mg_batch_solve"]
 
 
 class MGError(RuntimeError):
@@ -91,6 +92,10 @@ def load(path: str = LIB_PATH):
         "mg_residual_norm_static": (i, [ctypes.c_int64, ctypes.c_int64, vp, vp, vp, vp, vp, vp, vp, vp]),
         "mg_pass_timer_begin": (i, [vp, i, i]),
         "mg_boundary_adjoint": (i, [vp, vp, vp, vp, vp]),
+        "mg_batch_create": (i, [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]),
+        "mg_batch_destroy": (None, [vp]),
+        "mg_batch_solve": (i, [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(Params), i,
+                               ctypes.POINTER(Info), ctypes.POINTER(ctypes.c_int), vp]),
         "mg_pass_timer_end": (i, [vp, i64p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double)]),
     }
@@ -294,3 +299,55 @@ class Grid:
                       raise_on_fail=False, **kw):
         return self._solve(self.lib.mg_solve_adjoint, "mg_solve_adjoint", lam, rhs, params, stream, history_cap,
                            kw, raise_on_fail)
+
+
+class Batch:
+    """mg_batch_create over distinct Grid objects (which must outlive it)."""
+
+    def __init__(self, grids):
+        self.lib = load()
+        self.grids = list(grids)
+        arr = (ctypes.c_void_p * len(self.grids))(*[g.h.value for g in self.grids])
+        h = ctypes.c_void_p()
+        _check(self.lib.mg_batch_create(ctypes.byref(h), len(self.grids), arr), "mg_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.mg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, us, fs, params=None, stream=None, history_cap=256, raise_on_fail=False, **kw) -> list:
+        """mg_batch_solve: us[i], fs[i] float64 CUDA tensors of grid i; params:
+        one Params for all problems, a list of one per problem, or None (the
+        keyword arguments for all)."""
+        n = len(self.grids)
+        if len(us) != n or len(fs) != n:
+            raise ValueError("one u and one f per grid")
+        if isinstance(params, (list, tuple)):
+            if len(params) != n:
+                raise ValueError("one Params per grid")
+            pa = (Params * n)(*params)
+        else:
+            pa = (Params * 1)(params or default_params(**kw))
+        hists = [np.zeros(max(history_cap, 1)) for _ in range(n)]
+        infos = (Info * n)()
+        for i in range(n):
+            infos[i].history = hists[i].ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            infos[i].history_cap = history_cap
+        ua = (ctypes.c_void_p * n)(*[_ptr(x).value for x in us])
+        fa = (ctypes.c_void_p * n)(*[_ptr(x).value for x in fs])
+        sts = (ctypes.c_int * n)()
+        st = self.lib.mg_batch_solve(self.h, ua, fa, pa, len(pa), infos, sts, _stream(stream))
+        if raise_on_fail:
+            _check(st, "mg_batch_solve")
+        else:
+            _check(st, "mg_batch_solve", ok=(OK, ERR_NOT_CONVERGED, ERR_NONFINITE))
+        return [SolveResult(int(sts[i]), infos[i].cycles, infos[i].outer_iters, infos[i].rel_res, infos[i].conv_factor,
+                            infos[i].ms, hists[i][: infos[i].history_len].copy()) for i in range(n)]

@@ -88,7 +88,7 @@ typedef struct {
   int precision;         /* mg_precision                                         */
   int max_cycles;        /* cap on cycles (FP64) or on inner cycles (FP32+refine)*/
   int max_outer;         /* cap on refinement iterations (FP32+refine)           */
-  int inner_cycles;      /* FP32 cycles per refinement iteration                 */
+  int inner_cycles;      /* FP32 cycles per refinement iteration (default 3)     */
   int use_initial_guess; /* 0: interior of u is zeroed first; 1: u is the guess  */
   double tol;            /* stop when ||f - L u||_2 / ||f||_2 <= tol (interior)   */
 } mg_params;

@@ -529,7 +529,7 @@ void mg_default_params(mg_params *p) {
   p->precision = MG_PREC_F64;
   p->max_cycles = 100;
   p->max_outer = 8;
-  p->inner_cycles = 4;
+  p->inner_cycles = 3;
   p->use_initial_guess = 0;
   p->tol = 1e-10;
 }

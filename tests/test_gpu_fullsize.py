@@ -180,13 +180,13 @@ def test_fullsize_solve_f64_matches_oracle(mg, grid, big, oracle_solution, linv_
 
 
 def test_fullsize_solve_f32_refine(mg, grid, big, oracle_solution, linv_norm):
-    """The configuration bench.py times: V(1,1), 4 FP32 cycles per refinement step."""
+    """The configuration bench.py times: V(1,1), 3 FP32 cycles per refinement step."""
     import torch
     _, f, P = big
     u_ref, _ = oracle_solution
     ud = torch.zeros((N + 1, N + 1), dtype=torch.float64, device="cuda")
     res = grid.solve(ud, torch.tensor(f, device="cuda"), smoother="tweed", nu1=1, nu2=1, tol=1e-10,
-                     precision="f32_refine", inner_cycles=4, max_outer=20, max_cycles=200)
+                     precision="f32_refine", inner_cycles=3, max_outer=20, max_cycles=200)
     assert res.status == mg.OK and res.rel_res <= 1e-10
     u = ud.cpu().numpy()
     r = P.residual(u, f)

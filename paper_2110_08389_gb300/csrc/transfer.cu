@@ -69,7 +69,7 @@ template cudaError_t launch_residual<float>(const Level &, const float *, const 
 // columns 2I0-1 .. 2I0+2RR_I-1), then combined.  kind: 0 = half weighting
 // (1/2, 1/8 x 4), 1 = full weighting (1/4, 1/8 x 4, 1/16 x 4).  The coarse
 // correction uc is zeroed on the way.
-constexpr int RR_I = 128, RR_J = 4, RR_THREADS = 256;
+constexpr int RR_I = 127, RR_J = 4, RR_THREADS = 256;  // 2 RR_I + 1 fine columns <= threads: one each
 constexpr int RR_FI = 2 * RR_I + 1, RR_FJ = 2 * RR_J + 1;
 
 template <typename T>
@@ -83,13 +83,32 @@ __global__ void __launch_bounds__(RR_THREADS) residual_restrict_kernel(CoefQ<T> 
   const int fi0 = 2 * I0 - 1, fj0 = 2 * J0 - 1, nx1 = nx + 1;
   // fine nodes of the strip that some coarse interior node of it uses
   const int fi_end = min(fi0 + RR_FI, nx), fj_end = min(fj0 + RR_FJ, ny);
-  for (int r = 0; r < RR_FJ; ++r) {
-    const int j = fj0 + r;
-    if (j >= fj_end) break;
-    for (int tcol = threadIdx.x; tcol < RR_FI; tcol += RR_THREADS) {
-      const int i = fi0 + tcol;
-      if (i < fi_end) dd[r][tcol] = defect_at(c, u, f, i, j, nx1);
+  // thread = fine column: its 11 u values down the column, the 9 left and
+  // right neighbours and 9 f values are all loaded before any is used (rows
+  // clamped into the array; defects only for rows of the strip)
+  for (int tcol = threadIdx.x; tcol < RR_FI; tcol += RR_THREADS) {
+    const int i = fi0 + tcol;
+    if (i >= fi_end) continue;
+    const T w = c.W[i], e = c.E[i];
+    T uc[RR_FJ + 2], ul[RR_FJ], ur[RR_FJ], ff[RR_FJ], sv[RR_FJ], nv[RR_FJ];
+#pragma unroll
+    for (int r = 0; r < RR_FJ + 2; ++r) uc[r] = u[(size_t)min(fj0 - 1 + r, ny) * nx1 + i];
+#pragma unroll
+    for (int r = 0; r < RR_FJ; ++r) {
+      const int j = min(fj0 + r, ny - 1);
+      const size_t p = (size_t)j * nx1 + i;
+      ul[r] = u[p - 1];
+      ur[r] = u[p + 1];
+      ff[r] = f[p];
+      sv[r] = c.S[j];
+      nv[r] = c.N[j];
     }
+#pragma unroll
+    for (int r = 0; r < RR_FJ; ++r)
+      if (fj0 + r < fj_end) {
+        const T cc = -((w + e) + (sv[r] + nv[r]));
+        dd[r][tcol] = ff[r] - (w * ul[r] + e * ur[r] + sv[r] * uc[r] + nv[r] * uc[r + 2] + cc * uc[r + 1]);
+      }
   }
   __syncthreads();
   for (int k = threadIdx.x; k < RR_I * RR_J; k += RR_THREADS) {

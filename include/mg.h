@@ -192,7 +192,7 @@ mg_status mg_solve_adjoint(mg_grid *grid, double *lambda, const double *rhs,
 /* ---- batches of independent problems (the paper solves one problem at a
  * time; this serves many problems of different sizes and stretchings at
  * once).  A batch is a set of distinct grids (each problem needs its own
- * grid: grids hold per-solve scratch).  mg_batch_create creates up to 16
+ * grid: grids hold per-solve scratch).  mg_batch_create creates up to 64
  * streams of the batch's own (no device memory); MG_ERR_INVALID_ARG if a grid
  * repeats.  The grids stay owned by the caller and must outlive the batch.  */
 typedef struct mg_batch mg_batch;

@@ -502,7 +502,7 @@ struct mg_grid : public Grid {};
 // A set of grids solved together (mg_batch_solve): up to MAX_BATCH_STREAMS
 // streams of its own, a fork event on the caller's stream and one join
 // event per stream.
-constexpr int MAX_BATCH_STREAMS = 16;
+constexpr int MAX_BATCH_STREAMS = 64;
 struct mg_batch {
   std::vector<Grid *> grids;
   std::vector<cudaStream_t> streams;

@@ -55,7 +55,7 @@ typedef enum {
   MG_ERR_NONFINITE = 5,     /* a residual norm was NaN or infinite              */
   MG_ERR_TIMEOUT = 6,       /* reserved for bounded device-side waits           */
   MG_ERR_ALLOC = 7,         /* device or host allocation failed                 */
-  MG_ERR_UNSUPPORTED = 8    /* valid request this build does not implement      */
+  MG_ERR_UNSUPPORTED = 8    /* valid request this library does not implement    */
 } mg_status;
 
 /* Smoothers (Sec. 2 and Sec. 3).  One "relaxation" of each is a red pass then

@@ -23,7 +23,7 @@
  *   - V-cycle, steps (1)-(6) ................ Sec. 4
  *   - two-grid operator ..................... Sec. 5, Eq. (Mh2h)
  *
- * Readings where the paper is silent or garbled (each is listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   R1  nodes are 0-based, i = 0..nx, j = 0..ny, boundary at 0 and nx / ny;
  *       x is the fast index of every array: a[j*(nx+1)+i].
  *   R2  the S-term of Eq. (prob:DP) is S_j u_{i,j-1} (the printed "u_{j-1,j}"

@@ -1,7 +1,7 @@
 """GPU parity: every kernel of the CUDA path, called through the C ABI, against
 the CPU oracle on the same seeded inputs.
 
-Tolerances (derivation in the design doc):
+Tolerances:
   FP64, single kernels: |gpu - oracle| <= 1e-10 * max|oracle| -- both sides solve
       the same blocks exactly with different elimination orders; the blocks of
       these test grids have condition numbers below ~1e4, so rounding

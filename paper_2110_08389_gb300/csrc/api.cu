@@ -75,8 +75,10 @@ static void free_grid(Grid *g) {
     for (int w = 0; w < WL_COUNT; ++w)
       for (int c = 0; c < 2; ++c) {
         cudaFree(L.tl[w][c].mem);
-        for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < 2; ++p) {
           for (int z = 0; z < 2; ++z) cudaFree(L.wl[w][p][c][z].mem);
+          cudaFree(L.wp[w][p][c].mem);
+        }
       }
   }
   cudaFree(g->cinv);
@@ -273,6 +275,8 @@ static mg_status colour_pass(Grid &g, int l, int smoother, int colour, T *u, con
   if (ev) for (int k = 0; k < 3; ++k) cudaEventRecord(ev[k], s);
   if (wl == -2) {
     TRY_CUDA("checker pass", launch_checker_pass<T>(L, colour, u, f, s));
+  } else if (L.wp[wl][prec][colour].nwarp > 0) {
+    TRY_CUDA("warp line pass", launch_warp_pass<T>(L, L.wp[wl][prec][colour], u, f, s));
   } else {
     TRY_CUDA("line pass", launch_line_pass<T>(L, L.wl[wl][prec][colour][0], u, f, s));
     TRY_CUDA("line pass (large blocks)", launch_line_pass<T>(L, L.wl[wl][prec][colour][1], u, f, s));

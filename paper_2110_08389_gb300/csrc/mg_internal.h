@@ -92,6 +92,45 @@ struct WorkList {
 };
 
 // ---------------------------------------------------------------------------
+// Warp line path (small levels).  The blocks of one colour are concatenated,
+// whole, into sequences of at most 32*K chain nodes, one sequence per warp;
+// consecutive nodes of a sequence are coupled when they are consecutive nodes
+// of one chain, so the sequence is one tridiagonal system with zero couplings
+// between chains.  Lane l owns nodes l*K .. l*K+K-1; the last of them is the
+// lane's separator.  A warp holds at most one junction node.
+enum : uint32_t { WN_PRED = 1u << 2, WN_SUCC = 1u << 5, WN_JUNC = 1u << 8, WN_VALID = 1u << 9 };
+
+// One node of a sequence: position, and the directions from it to its
+// predecessor (bits 0-1, present if WN_PRED), successor (bits 3-4, WN_SUCC)
+// and the junction (bits 6-7, WN_JUNC).  Unused slots have fl = 0.
+struct WNode {
+  uint16_t i, j;
+  uint32_t fl;
+};
+static_assert(sizeof(WNode) == 8, "WNode layout");
+
+// The junction of one warp (has_j = 0: none).  Attached node e (< natt) is
+// node as[e] of the sequence, in direction (adirs >> 2e) & 3 from the
+// junction.
+struct WBlock {
+  uint16_t ji, jj;
+  uint8_t has_j, natt, adirs, pad;
+  uint16_t as[4];
+};
+static_assert(sizeof(WBlock) == 16, "WBlock layout");
+
+struct WarpList {
+  int nwarp = 0;        // 0: the level's blocks do not fit (use the CTA line kernel)
+  int K = 0;            // nodes per lane (power of two)
+  int total_nodes = 0;  // unknowns relaxed (junctions included)
+  void *mem = nullptr;
+  WNode *node = nullptr;   // 32*K per warp
+  WBlock *blk = nullptr;   // one per warp
+};
+// Largest nodes per lane of the warp path (register arrays of 4K values).
+constexpr int WK_MAX_F32 = 32, WK_MAX_F64 = 16;
+
+// ---------------------------------------------------------------------------
 // Tiled line path (tweed and zebra on large levels).  Every block is a set of
 // legs that each start at a wall, plus at most one junction node (the
 // paper's m-legged form, Eq. mLThomas; m = 1 for a line from wall to wall).
@@ -169,6 +208,7 @@ struct Level {
   bool tl_built[WL_COUNT] = {};
   TileList tl[WL_COUNT][2];           // [smoother][colour]: tiled path (empty: use the work lists)
   WorkList wl[WL_COUNT][2][2][2];     // [smoother][precision][colour][small, large]
+  WarpList wp[WL_COUNT][2][2];        // [smoother][precision][colour]: warp path (nwarp = 0: unused)
 };
 
 struct Grid {
@@ -237,6 +277,8 @@ cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &t, T
 // the launch (cudaGetLastError).
 template <typename T>
 cudaError_t launch_line_pass(const Level &L, const WorkList &w, T *u, const T *f, cudaStream_t s);
+template <typename T>
+cudaError_t launch_warp_pass(const Level &L, const WarpList &w, T *u, const T *f, cudaStream_t s);
 template <typename T>
 cudaError_t launch_checker_pass(const Level &L, int colour, T *u, const T *f, cudaStream_t s);
 template <typename T>

@@ -307,6 +307,103 @@ mg_status upload(const Packed &P, int nt, WorkList &W) {
   return MG_OK;
 }
 
+// Warp path: lay the colour's blocks end to end in sequences of at most
+// 32*K nodes (first fit, largest blocks first; at most one junction per
+// sequence) with K the smallest power of two that holds the largest block.
+// Leaves W.nwarp = 0 when the largest block needs more than 32*kmax nodes.
+mg_status build_warplist(const std::vector<HBlock> &blocks, int kmax, WarpList &W) {
+  std::vector<int> n(blocks.size(), 0);
+  int maxn = 1, total = 0;
+  for (size_t b = 0; b < blocks.size(); ++b) {
+    for (const HChain &c : blocks[b].ch)
+      for (const HSeg &sg : c.s) n[b] += sg.len;
+    maxn = std::max(maxn, n[b]);
+    total += n[b] + (blocks[b].junc ? 1 : 0);
+  }
+  if (blocks.empty() || maxn > 32 * kmax) return MG_OK;
+  int K = 1;
+  while (32 * K < maxn) K *= 2;
+  const int cap = 32 * K;
+  std::vector<int> order(blocks.size());
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+  struct Bin {
+    int used = 0;
+    bool junc = false;
+    std::vector<int> blocks;
+  };
+  std::vector<Bin> bins;
+  for (int b : order) {
+    size_t w = 0;
+    while (w < bins.size() && (bins[w].used + n[b] > cap || (blocks[b].junc && bins[w].junc))) ++w;
+    if (w == bins.size()) bins.emplace_back();
+    bins[w].used += n[b];
+    bins[w].junc |= blocks[b].junc;
+    bins[w].blocks.push_back(b);
+  }
+  std::vector<WNode> nodes(bins.size() * (size_t)cap);
+  std::vector<WBlock> blk(bins.size());
+  std::memset(nodes.data(), 0, sizeof(WNode) * nodes.size());
+  std::memset(blk.data(), 0, sizeof(WBlock) * blk.size());
+  for (size_t w = 0; w < bins.size(); ++w) {
+    WBlock &jb = blk[w];
+    int s = 0;
+    for (int b : bins[w].blocks) {
+      const HBlock &hb = blocks[b];
+      if (hb.junc) {
+        jb.has_j = 1;
+        jb.ji = (uint16_t)hb.ji;
+        jb.jj = (uint16_t)hb.jj;
+      }
+      for (const HChain &c : hb.ch) {
+        // the chain's nodes in order, with the direction of the step that
+        // reaches each node (its segment's direction)
+        std::vector<std::tuple<int, int, int>> cn;
+        for (const HSeg &sg : c.s)
+          for (int t = 0; t < sg.len; ++t) cn.emplace_back(sg.i0 + t * step_i(sg.dir), sg.j0 + t * step_j(sg.dir), sg.dir);
+        const int m = (int)cn.size();
+        for (int r = 0; r < m; ++r) {
+          uint32_t fl = WN_VALID;
+          if (r > 0) fl |= WN_PRED | (uint32_t)(std::get<2>(cn[r]) ^ 1);
+          if (r < m - 1) fl |= WN_SUCC | ((uint32_t)std::get<2>(cn[r + 1]) << 3);
+          int jd = -1;
+          if (r == 0 && c.fj) jd = std::get<2>(cn[0]) ^ 1;
+          if (r == m - 1 && c.lj) {
+            if (jd >= 0) return MG_OK;  // a one-node chain on both sides of the junction: not supported here
+            jd = c.ljdir;
+          }
+          if (jd >= 0) {
+            if (!hb.junc || jb.natt >= 4) return MG_OK;
+            fl |= WN_JUNC | ((uint32_t)jd << 6);
+            jb.as[jb.natt] = (uint16_t)s;
+            jb.adirs |= (uint8_t)((jd ^ 1) << (2 * jb.natt));
+            ++jb.natt;
+          }
+          WNode &nd = nodes[w * (size_t)cap + s];
+          nd.i = (uint16_t)std::get<0>(cn[r]);
+          nd.j = (uint16_t)std::get<1>(cn[r]);
+          nd.fl = fl;
+          ++s;
+        }
+      }
+    }
+  }
+  const size_t bn = (sizeof(WNode) * nodes.size() + 15) & ~size_t(15);
+  char *mem = nullptr;
+  cudaError_t e = cudaMalloc(&mem, bn + sizeof(WBlock) * blk.size());
+  if (e != cudaSuccess) { set_error("cudaMalloc(warp list)", e); return MG_ERR_ALLOC; }
+  W.mem = mem;
+  W.node = reinterpret_cast<WNode *>(mem);
+  W.blk = reinterpret_cast<WBlock *>(mem + bn);
+  e = cudaMemcpy(W.node, nodes.data(), sizeof(WNode) * nodes.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(W.blk, blk.data(), sizeof(WBlock) * blk.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { set_error("cudaMemcpy(warp list)", e); return MG_ERR_CUDA; }
+  W.nwarp = (int)bins.size();
+  W.K = K;
+  W.total_nodes = total;
+  return MG_OK;
+}
+
 }  // namespace
 
 mg_status build_worklists(Grid &g, int level, int wl, int prec) {
@@ -350,6 +447,9 @@ mg_status build_worklists(Grid &g, int level, int wl, int prec) {
     pack(blocks, large, NT_LARGE, Pl);
     mg_status st = upload(Ps, NT_SMALL, L.wl[wl][prec][colour][0]);
     if (st == MG_OK) st = upload(Pl, NT_LARGE, L.wl[wl][prec][colour][1]);
+    // the warp path serves the levels below the tiled path
+    if (st == MG_OK && !(L.nx >= TILE_MIN_SIDE && L.ny >= TILE_MIN_SIDE))
+      st = build_warplist(blocks, prec == 0 ? WK_MAX_F64 : WK_MAX_F32, L.wp[wl][prec][colour]);
     if (st != MG_OK) return st;
   }
   L.wl_built[wl][prec] = true;

@@ -1,0 +1,275 @@
+// warp_line.cu -- one colour pass of a line smoother (tweed, wireframe, zebra)
+// on the small levels: one warp per sequence of whole blocks, no CTA barrier.
+//
+// Every block of the colour is solved exactly, the other colour held fixed
+// (Sec. 3).  The blocks given to a warp are laid end to end as one
+// tridiagonal system of at most 32*K unknowns (couplings between different
+// chains are zero), plus at most one junction node J that is coupled to up
+// to four of them (the centre of a tweed cross or T, Eq. mLThomas; the corner
+// where a wireframe ring is closed, Eq. CircTri; a lone point block).  Row s:
+//     a_s x_{s-1} + b_s x_s + c_s x_{s+1} = d_s - k_s x_J,
+// and the junction row  C_J x_J + sum_e k'_e x_{s_e} = r_J.
+//
+// The solve (the partition method of the line kernel, regrouped for a warp):
+//   1. coalesced staging: lane l handles nodes 32t + l; a, b, c, d and
+//      z = -k go to shared memory.
+//   2. lane l owns nodes lK .. lK+K-1.  Its interior nodes 0..K-2 are
+//      eliminated by one forward Thomas sweep in which the unknown separator
+//      S_{l-1} (the last node of lane l-1) and x_J are carried as extra
+//      columns:  x_q + c'_q x_{q+1} = y'_q + z'_q x_J + w'_q S_{l-1}.
+//      A backward pass of multiply-adds gives x_0 in terms of S_{l-1}, S_l
+//      and x_J.
+//   3. the separators form a tridiagonal system of 32 rows, one per lane
+//      (the row of node lK+K-1 with x_{lK+K-2} and x_{(l+1)K} substituted),
+//      solved by parallel cyclic reduction over warp shuffles for two
+//      right-hand sides: S_l = Y_l + Z_l x_J.
+//   4. back-substitution of the interior, again for both columns:
+//      x_s = X_s + x_J X'_s.
+//   5. the junction row fixes x_J (lanes 0..3 hold its attached nodes),
+//      then x_s is written back coalesced.
+#include "device_util.cuh"
+
+namespace tmg {
+namespace {
+
+// slot of sequence node s in the per-warp arrays: an XOR swizzle that keeps
+// both access patterns (32t + l and lK + q) free of bank conflicts
+__device__ __forceinline__ int wslot(int s) { return s ^ ((s >> 5) & 31); }
+
+template <typename T>
+__device__ __forceinline__ T by_dir(unsigned d, T e, T w, T n, T s) {
+  return d == 0u ? e : (d == 1u ? w : (d == 2u ? n : s));
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(32) warp_line_kernel(const WNode *__restrict__ nodes,
+                                                       const WBlock *__restrict__ blks, Coefs<T> cp, int nx1,
+                                                       T *__restrict__ u, const T *__restrict__ f) {
+  constexpr int N = 32 * K;
+  extern __shared__ __align__(16) unsigned char wsm[];
+  T *sa = reinterpret_cast<T *>(wsm);
+  T *sb = sa + N, *sc = sb + N, *sd = sc + N, *sz = sd + N;
+  int *sp = reinterpret_cast<int *>(sz + N);
+  const int lane = threadIdx.x;
+  const uint2 *nd = reinterpret_cast<const uint2 *>(nodes) + (size_t)blockIdx.x * N;
+
+  // ---- the warp's junction: its row's right-hand side r_J (lane 0) and its
+  // coefficient towards attached node e (lane e)
+  const uint4 jb = __ldg(reinterpret_cast<const uint4 *>(blks) + blockIdx.x);
+  const bool has_j = (jb.y & 0xFFu) != 0u;
+  const int natt = (int)((jb.y >> 8) & 0xFFu);
+  const unsigned adirs = (jb.y >> 16) & 0xFFu;
+  T kp = T(0), rJ = T(0), cJ = T(1);
+  size_t pJ = 0;
+  if (has_j) {
+    const int ji = (int)(jb.x & 0xFFFFu), jj = (int)(jb.x >> 16);
+    pJ = (size_t)jj * nx1 + ji;
+    const T e = __ldg(cp.E + ji), w = __ldg(cp.W + ji), n = __ldg(cp.N + jj), s = __ldg(cp.S + jj);
+    unsigned att = 0;
+    for (int q = 0; q < natt; ++q) att |= 1u << ((adirs >> (2 * q)) & 3u);
+    if (lane < natt) kp = by_dir((adirs >> (2 * lane)) & 3u, e, w, n, s);
+    if (lane == 0) {
+      T r = __ldg(f + pJ);
+      if (!(att & 1u)) r -= e * u[pJ + 1];
+      if (!(att & 2u)) r -= w * u[pJ - 1];
+      if (!(att & 4u)) r -= n * u[pJ + nx1];
+      if (!(att & 8u)) r -= s * u[pJ - nx1];
+      rJ = r;
+      cJ = -((w + e) + (s + n));
+    }
+  }
+
+  // ---- 1. staging, U nodes per lane at a time; the next batch's
+  // descriptors are loaded while the current batch's data is in flight
+  {
+    constexpr int U = K < 8 ? K : 8;
+    uint2 cur[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) cur[k] = __ldg(nd + 32 * k + lane);
+#pragma unroll
+    for (int t0 = 0; t0 < K; t0 += U) {
+      uint2 nxt[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k)
+        if (t0 + U < K) nxt[k] = __ldg(nd + 32 * (t0 + U + k) + lane);
+      T fv[U], ue[U], uw[U], un[U], us[U], ce[U], cw[U], cn[U], cs[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const unsigned fl = cur[k].y;
+        const int i = (int)(cur[k].x & 0xFFFFu), j = (int)(cur[k].x >> 16);
+        const unsigned in = ((fl & WN_PRED) ? 1u << (fl & 3u) : 0u) | ((fl & WN_SUCC) ? 1u << ((fl >> 3) & 3u) : 0u) |
+                            ((fl & WN_JUNC) ? 1u << ((fl >> 6) & 3u) : 0u);
+        const unsigned out = (fl & WN_VALID) ? (0xFu & ~in) : 0u;
+        const size_t p = (size_t)j * nx1 + i;
+        fv[k] = (fl & WN_VALID) ? __ldg(f + p) : T(0);
+        ue[k] = (out & 1u) ? u[p + 1] : T(0);
+        uw[k] = (out & 2u) ? u[p - 1] : T(0);
+        un[k] = (out & 4u) ? u[p + nx1] : T(0);
+        us[k] = (out & 8u) ? u[p - nx1] : T(0);
+        ce[k] = __ldg(cp.E + i);
+        cw[k] = __ldg(cp.W + i);
+        cn[k] = __ldg(cp.N + j);
+        cs[k] = __ldg(cp.S + j);
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const unsigned fl = cur[k].y;
+        const bool valid = (fl & WN_VALID) != 0u;
+        const int s = 32 * (t0 + k) + lane, sl = wslot(s);
+        sa[sl] = (fl & WN_PRED) ? by_dir(fl & 3u, ce[k], cw[k], cn[k], cs[k]) : T(0);
+        sc[sl] = (fl & WN_SUCC) ? by_dir((fl >> 3) & 3u, ce[k], cw[k], cn[k], cs[k]) : T(0);
+        sz[sl] = (fl & WN_JUNC) ? -by_dir((fl >> 6) & 3u, ce[k], cw[k], cn[k], cs[k]) : T(0);
+        sb[sl] = valid ? -((cw[k] + ce[k]) + (cs[k] + cn[k])) : T(1);
+        sd[sl] = fv[k] - ce[k] * ue[k] - cw[k] * uw[k] - cn[k] * un[k] - cs[k] * us[k];
+        sp[s] = valid ? (int)((cur[k].x >> 16) * (unsigned)nx1 + (cur[k].x & 0xFFFFu)) : -1;
+      }
+      if (t0 + U < K) {
+#pragma unroll
+        for (int k = 0; k < U; ++k) cur[k] = nxt[k];
+      }
+    }
+  }
+  __syncwarp();
+
+  // ---- 2. forward sweep over the lane's interior nodes 0..K-2
+  const int base = lane * K;
+  T cq[K], yq[K], zq[K], wq[K];  // entries 0..K-2 used
+  T Y0 = T(0), Z0 = T(0), W0 = T(0), V0 = T(1);           // x_0 = Y0 + Z0 x_J + W0 S_{l-1} + V0 S_l
+  T yl = T(0), zl = T(0), wl = T(1), cl = T(0);           // x_{K-2} = yl + zl x_J + wl S_{l-1} - cl S_l
+  if constexpr (K > 1) {
+    {
+      const int sl = wslot(base);
+      const T r = recip(sb[sl]);
+      cq[0] = sc[sl] * r;
+      yq[0] = sd[sl] * r;
+      zq[0] = sz[sl] * r;
+      wq[0] = -sa[sl] * r;
+    }
+#pragma unroll
+    for (int q = 1; q < K - 1; ++q) {
+      const int sl = wslot(base + q);
+      const T a = sa[sl];
+      const T r = recip(sb[sl] - a * cq[q - 1]);
+      cq[q] = sc[sl] * r;
+      yq[q] = (sd[sl] - a * yq[q - 1]) * r;
+      zq[q] = (sz[sl] - a * zq[q - 1]) * r;
+      wq[q] = -a * wq[q - 1] * r;
+    }
+    yl = yq[K - 2]; zl = zq[K - 2]; wl = wq[K - 2]; cl = cq[K - 2];
+    Y0 = yl; Z0 = zl; W0 = wl; V0 = -cl;
+#pragma unroll
+    for (int q = K - 3; q >= 0; --q) {
+      Y0 = yq[q] - cq[q] * Y0;
+      Z0 = zq[q] - cq[q] * Z0;
+      W0 = wq[q] - cq[q] * W0;
+      V0 = -cq[q] * V0;
+    }
+  }
+
+  // ---- 3. separator rows, then cyclic reduction across the lanes
+  const int ss = wslot(base + K - 1);
+  T A, C, Ry, Rz;
+  {
+    T Yn = __shfl_down_sync(0xFFFFFFFFu, Y0, 1), Zn = __shfl_down_sync(0xFFFFFFFFu, Z0, 1);
+    T Wn = __shfl_down_sync(0xFFFFFFFFu, W0, 1), Vn = __shfl_down_sync(0xFFFFFFFFu, V0, 1);
+    if (lane == 31) { Yn = T(0); Zn = T(0); Wn = T(0); Vn = T(0); }
+    const T a = sa[ss], c = sc[ss];
+    const T B = sb[ss] - a * cl + c * Wn;
+    const T r = recip(B);
+    A = a * wl * r;
+    C = c * Vn * r;
+    Ry = (sd[ss] - a * yl - c * Yn) * r;
+    Rz = (sz[ss] - a * zl - c * Zn) * r;
+  }
+#pragma unroll
+  for (int dd = 1; dd < 32; dd <<= 1) {
+    T Am = __shfl_up_sync(0xFFFFFFFFu, A, dd), Cm = __shfl_up_sync(0xFFFFFFFFu, C, dd);
+    T Ym = __shfl_up_sync(0xFFFFFFFFu, Ry, dd), Zm = __shfl_up_sync(0xFFFFFFFFu, Rz, dd);
+    T Ap = __shfl_down_sync(0xFFFFFFFFu, A, dd), Cp = __shfl_down_sync(0xFFFFFFFFu, C, dd);
+    T Yp = __shfl_down_sync(0xFFFFFFFFu, Ry, dd), Zp = __shfl_down_sync(0xFFFFFFFFu, Rz, dd);
+    if (lane < dd) { Am = T(0); Cm = T(0); Ym = T(0); Zm = T(0); }
+    if (lane + dd >= 32) { Ap = T(0); Cp = T(0); Yp = T(0); Zp = T(0); }
+    const T r = recip(T(1) - A * Cm - C * Ap);
+    const T nA = -A * Am * r, nC = -C * Cp * r;
+    const T nY = (Ry - A * Ym - C * Yp) * r, nZ = (Rz - A * Zm - C * Zp) * r;
+    A = nA; C = nC; Ry = nY; Rz = nZ;
+  }
+
+  // ---- 4. back-substitution of the interior for both columns; the results
+  // overwrite the lane's own a (value column) and b (x_J column) slots
+  {
+    T Sym = __shfl_up_sync(0xFFFFFFFFu, Ry, 1), Szm = __shfl_up_sync(0xFFFFFFFFu, Rz, 1);
+    if (lane == 0) { Sym = T(0); Szm = T(0); }
+    sa[ss] = Ry;
+    sb[ss] = Rz;
+    T xy = Ry, xz = Rz;
+#pragma unroll
+    for (int q = K - 2; q >= 0; --q) {
+      xy = yq[q] + wq[q] * Sym - cq[q] * xy;
+      xz = zq[q] + wq[q] * Szm - cq[q] * xz;
+      const int sl = wslot(base + q);
+      sa[sl] = xy;
+      sb[sl] = xz;
+    }
+  }
+  __syncwarp();
+
+  // ---- 5. junction value, then all values back to u
+  T xJ = T(0);
+  if (has_j) {
+    T sy = T(0), szz = T(0);
+    if (lane < natt) {
+      const unsigned word = lane < 2 ? jb.z : jb.w;
+      const int s = (int)((word >> (16 * (lane & 1))) & 0xFFFFu);
+      sy = kp * sa[wslot(s)];
+      szz = kp * sb[wslot(s)];
+    }
+    sy += __shfl_xor_sync(0xFFFFFFFFu, sy, 1);
+    szz += __shfl_xor_sync(0xFFFFFFFFu, szz, 1);
+    sy += __shfl_xor_sync(0xFFFFFFFFu, sy, 2);
+    szz += __shfl_xor_sync(0xFFFFFFFFu, szz, 2);
+    const T x = (rJ - sy) / (cJ + szz);
+    xJ = __shfl_sync(0xFFFFFFFFu, x, 0);
+    if (lane == 0) u[pJ] = xJ;
+  }
+#pragma unroll
+  for (int t = 0; t < K; ++t) {
+    const int s = 32 * t + lane;
+    const int p = sp[s];
+    if (p >= 0) {
+      const int sl = wslot(s);
+      u[p] = sa[sl] + xJ * sb[sl];
+    }
+  }
+}
+
+template <typename T, int K>
+cudaError_t launch_k(const Level &L, const WarpList &w, T *u, const T *f, cudaStream_t s) {
+  const size_t smem = (size_t)32 * K * (5 * sizeof(T) + sizeof(int));
+  warp_line_kernel<T, K><<<w.nwarp, 32, smem, s>>>(w.node, w.blk, level_coefs<T>(L), L.nx + 1, u, f);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_warp_pass(const Level &L, const WarpList &w, T *u, const T *f, cudaStream_t s) {
+  if (w.nwarp == 0) return cudaSuccess;
+  switch (w.K) {
+    case 1: return launch_k<T, 1>(L, w, u, f, s);
+    case 2: return launch_k<T, 2>(L, w, u, f, s);
+    case 4: return launch_k<T, 4>(L, w, u, f, s);
+    case 8: return launch_k<T, 8>(L, w, u, f, s);
+    case 16: return launch_k<T, 16>(L, w, u, f, s);
+    case 32:
+      if constexpr (sizeof(T) == 4) return launch_k<T, 32>(L, w, u, f, s);
+      return cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template cudaError_t launch_warp_pass<double>(const Level &, const WarpList &, double *, const double *, cudaStream_t);
+template cudaError_t launch_warp_pass<float>(const Level &, const WarpList &, float *, const float *, cudaStream_t);
+
+}  // namespace tmg

@@ -148,6 +148,7 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
   g->nlev = (int)g->lev.size();
   TRY_CUDA("setup start (latched error)", cudaGetLastError());
   TRY_CUDA("line kernel attributes", prepare_line_kernels());
+  TRY_CUDA("warp kernel attributes", prepare_warp_kernels());
   const bool want64 = g->prec_mask & 1, want32 = g->prec_mask & 2;
   for (int l = 0; l < g->nlev; ++l) {
     Level &L = g->lev[l];
@@ -262,10 +263,13 @@ static mg_status colour_pass(Grid &g, int l, int smoother, int colour, T *u, con
   Level &L = g.lev[l];
   const int wl = smoother == MG_SMOOTH_CHECKERBOARD ? -2 : wl_of(smoother);
   if (wl == -1) return MG_ERR_INVALID_ARG;
-  const TileList *tl = wl >= 0 ? &L.tl[wl][colour] : nullptr;
-  const bool tiled = tl && (tl->ntile > 0 || tl->nblock > 0);
   const int prec = sizeof(T) == 8 ? 0 : 1;
-  if (wl >= 0 && !tiled) TRY(build_worklists(g, l, wl, prec));
+  if (wl >= 0) TRY(build_worklists(g, l, wl, prec));
+  // path: the warp path where the level's blocks fit it, else the tiled path
+  // (large levels), else the CTA line kernel
+  const bool warp = wl >= 0 && L.wp[wl][prec][colour].nwarp > 0;
+  const TileList *tl = wl >= 0 ? &L.tl[wl][colour] : nullptr;
+  const bool tiled = !warp && tl && (tl->ntile > 0 || tl->nblock > 0);
   cudaEvent_t *ev = timer_slot(g, l);
   if (tiled) {
     TRY_CUDA("tiled line pass", launch_tile_pass<T>(g, L, *tl, u, f, s, ev));
@@ -275,7 +279,7 @@ static mg_status colour_pass(Grid &g, int l, int smoother, int colour, T *u, con
   if (ev) for (int k = 0; k < 3; ++k) cudaEventRecord(ev[k], s);
   if (wl == -2) {
     TRY_CUDA("checker pass", launch_checker_pass<T>(L, colour, u, f, s));
-  } else if (L.wp[wl][prec][colour].nwarp > 0) {
+  } else if (warp) {
     TRY_CUDA("warp line pass", launch_warp_pass<T>(L, L.wp[wl][prec][colour], u, f, s));
   } else {
     TRY_CUDA("line pass", launch_line_pass<T>(L, L.wl[wl][prec][colour][0], u, f, s));

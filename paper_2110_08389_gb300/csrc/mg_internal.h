@@ -120,15 +120,24 @@ struct WBlock {
 static_assert(sizeof(WBlock) == 16, "WBlock layout");
 
 struct WarpList {
-  int nwarp = 0;        // 0: the level's blocks do not fit (use the CTA line kernel)
+  int nwarp = 0;        // sequences (CTAs); 0: the level's blocks do not fit
   int K = 0;            // nodes per lane (power of two)
+  int W = 1;            // warps per sequence (power of two)
   int total_nodes = 0;  // unknowns relaxed (junctions included)
   void *mem = nullptr;
-  WNode *node = nullptr;   // 32*K per warp
-  WBlock *blk = nullptr;   // one per warp
+  WNode *node = nullptr;   // 32*W*K per sequence
+  WBlock *blk = nullptr;   // one per sequence
 };
-// Largest nodes per lane of the warp path (register arrays of 4K values).
-constexpr int WK_MAX_F32 = 32, WK_MAX_F64 = 16;
+// Shapes of the warp path: K nodes per lane (register arrays of 4K values
+// per thread) on W warps per sequence.  K is the smaller of WK_PREF and what
+// the largest block needs on one warp, W what it then needs; when that is
+// more than WW_MAX warps, K doubles up to WK_MAX.
+constexpr int WK_PREF = 4, WK_MAX_F32 = 16, WK_MAX_F64 = 8, WW_MAX = 8;
+// Levels with both sides below this use the warp path wherever the largest
+// block fits it; larger levels use the tiled path.  Measured on GB300 (FP32
+// tweed colour pass, 4097^2 wall grid): 1025^2 15 us (tiled: 39 us), 2049^2
+// 43 us (tiled: 44 us, and the whole solve 0.3 ms faster with the tiled path).
+constexpr int WARP_MAX_SIDE = 2048;
 
 // ---------------------------------------------------------------------------
 // Tiled line path (tweed and zebra on large levels).  Every block is a set of
@@ -249,9 +258,10 @@ struct Grid {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
-// Levels whose sides are both at least this use the tiled path for tweed and
-// zebra (below it the single-kernel line pass is faster: measured on GB300,
-// 512^2: 29 vs 39 us per colour pass; 1024^2: 45 vs 41 us).
+// Levels whose sides are both at least this get tiled lists for tweed and
+// zebra, used where the warp path is not (below it the CTA line kernel is
+// faster than the tiled path: measured on GB300, 512^2: 29 vs 39 us per
+// colour pass; 1024^2: 45 vs 41 us).
 constexpr int TILE_MIN_SIDE = 1024;
 
 // Kernels launched by this library in this process (mg_kernel_launches).
@@ -267,6 +277,7 @@ mg_status build_tiles(Grid &g, int level, int wl);
 // Dynamic shared memory opt-in of the line kernels on the current device
 // (called by mg_setup_grid).
 cudaError_t prepare_line_kernels();
+cudaError_t prepare_warp_kernels();
 // ev: nullptr, or 4 events recorded before tile_reduce, tile_couple,
 // tile_expand and after tile_expand
 template <typename T>

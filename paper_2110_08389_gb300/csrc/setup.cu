@@ -307,10 +307,10 @@ mg_status upload(const Packed &P, int nt, WorkList &W) {
   return MG_OK;
 }
 
-// Warp path: lay the colour's blocks end to end in sequences of at most
-// 32*K nodes (first fit, largest blocks first; at most one junction per
-// sequence) with K the smallest power of two that holds the largest block.
-// Leaves W.nwarp = 0 when the largest block needs more than 32*kmax nodes.
+// Warp path: lay the colour's blocks end to end in sequences of 32*W*K
+// nodes (first fit, largest blocks first; at most one junction per sequence),
+// K and W powers of two chosen as described with WK_PREF.  Leaves W.nwarp = 0
+// when the largest block does not fit WW_MAX warps of kmax nodes per lane.
 mg_status build_warplist(const std::vector<HBlock> &blocks, int kmax, WarpList &W) {
   std::vector<int> n(blocks.size(), 0);
   int maxn = 1, total = 0;
@@ -320,10 +320,16 @@ mg_status build_warplist(const std::vector<HBlock> &blocks, int kmax, WarpList &
     maxn = std::max(maxn, n[b]);
     total += n[b] + (blocks[b].junc ? 1 : 0);
   }
-  if (blocks.empty() || maxn > 32 * kmax) return MG_OK;
-  int K = 1;
-  while (32 * K < maxn) K *= 2;
-  const int cap = 32 * K;
+  if (blocks.empty() || maxn > 32 * WW_MAX * kmax) return MG_OK;
+  int K = 1, NW = 1;
+  while (32 * K < maxn && K < std::min(WK_PREF, kmax)) K *= 2;
+  while (32 * NW * K < maxn) NW *= 2;
+  while (NW > WW_MAX) {
+    K *= 2;
+    NW = 1;
+    while (32 * NW * K < maxn) NW *= 2;
+  }
+  const int cap = 32 * NW * K;
   std::vector<int> order(blocks.size());
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
@@ -400,6 +406,7 @@ mg_status build_warplist(const std::vector<HBlock> &blocks, int kmax, WarpList &
   if (e != cudaSuccess) { set_error("cudaMemcpy(warp list)", e); return MG_ERR_CUDA; }
   W.nwarp = (int)bins.size();
   W.K = K;
+  W.W = NW;
   W.total_nodes = total;
   return MG_OK;
 }
@@ -447,8 +454,7 @@ mg_status build_worklists(Grid &g, int level, int wl, int prec) {
     pack(blocks, large, NT_LARGE, Pl);
     mg_status st = upload(Ps, NT_SMALL, L.wl[wl][prec][colour][0]);
     if (st == MG_OK) st = upload(Pl, NT_LARGE, L.wl[wl][prec][colour][1]);
-    // the warp path serves the levels below the tiled path
-    if (st == MG_OK && !(L.nx >= TILE_MIN_SIDE && L.ny >= TILE_MIN_SIDE))
+    if (st == MG_OK && L.nx < WARP_MAX_SIDE && L.ny < WARP_MAX_SIDE)
       st = build_warplist(blocks, prec == 0 ? WK_MAX_F64 : WK_MAX_F32, L.wp[wl][prec][colour]);
     if (st != MG_OK) return st;
   }

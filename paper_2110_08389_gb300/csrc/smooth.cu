@@ -1,8 +1,12 @@
 // smooth.cu -- relaxation kernels of tweedmg for sm_103a.
 //
 // line_pass_kernel: one colour pass of a line smoother (tweed, wireframe,
-// zebra).  Every block of the colour is solved exactly (Sec. 3: the equation
-// is solved on all nodes of the block at once, the other colour held fixed).
+// zebra) on levels below the tiled path whose largest block is too long for
+// the warp path of warp_line.cu (more than 1024 nodes in FP32 or 512 in FP64:
+// wireframe rings from 512^2 up, in FP64 from 256^2 up; the FP64 tweed cross
+// at 512^2).  Every block of the colour is solved exactly (Sec. 3: the
+// equation is solved on all nodes of the block at once, the other colour held
+// fixed).
 // A CTA owns whole blocks.  Each block is a set of chains (open tridiagonal
 // systems along straight runs that may turn corners) plus at most one
 // junction node:
@@ -34,14 +38,12 @@
 // checker_kernel: one colour of red-black point Gauss-Seidel (Sec. 2).
 #include <cstdio>
 
-#include "mg_internal.h"
+#include "device_util.cuh"
 
 namespace tmg {
 
 template <typename T>
-struct CoefP {
-  const T *W, *E, *S, *N;
-};
+using CoefP = Coefs<T>;
 
 __device__ __forceinline__ int di_of(int d) { return d == DIR_PX ? 1 : (d == DIR_MX ? -1 : 0); }
 __device__ __forceinline__ int dj_of(int d) { return d == DIR_PY ? 1 : (d == DIR_MY ? -1 : 0); }
@@ -57,20 +59,6 @@ __device__ __forceinline__ T centre(const CoefP<T> &c, int i, int j) {
   return -((__ldg(c.W + i) + __ldg(c.E + i)) + (__ldg(c.S + j) + __ldg(c.N + j)));
 }
 
-// Reciprocal used by the eliminations.  FP32: the fast reciprocal (within 2
-// ulp), ample for the FP32 correction equation.  FP64: Newton-Raphson
-// iteration r <- r + r (1 - x r), which doubles the number of correct bits per
-// step, started from the FP32 reciprocal (24 bits -> 48 -> 96); two fused
-// steps replace the much slower IEEE double division.  Valid while |x| and
-// 1/|x| lie inside the float range (grid spacings above ~1e-18).
-__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ double rcp(double x) {
-  double r = (double)__frcp_rn((float)x);
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
 
 // Geometry of one chunk: a straight run of m nodes in direction dir.  Along
 // the run only the two "along" coefficients vary (W/E for x-runs, S/N for
@@ -217,12 +205,12 @@ struct ChunkSolver {
     const T a0 = A(0, l0), b0 = g.b_of(l0, h0), c0 = C(0, h0);
     rhi.a = T(0); rhi.c = T(0); rhi.y = T(0); rhi.z = T(0);
     if (!FULL && n <= 2) {
-      const T rb = rcp(b0);
+      const T rb = recip(b0);
       rlo.a = a0 * rb; rlo.c = c0 * rb; rlo.y = d0 * rb; rlo.z = -(n == 1 ? kf + kl : kf) * rb;
       if (n == 1) return;
     }
     const T l1 = LO(1), h1 = HI(1);
-    T rinv_f = rcp(g.b_of(l1, h1));
+    T rinv_f = recip(g.b_of(l1, h1));
     T al = A(1, l1) * rinv_f, ga = C(1, h1) * rinv_f, de = DD(1) * rinv_f;
     T ah = T(0), ch = T(0), dh = T(0);
 #pragma unroll
@@ -231,7 +219,7 @@ struct ChunkSolver {
       if (FULL || qf < n) {
         const T lq = LO(qf), hq = HI(qf);
         const T a = A(qf, lq), cc = C(qf, hq);
-        const T ri = rcp(g.b_of(lq, hq) - a * ga);
+        const T ri = recip(g.b_of(lq, hq) - a * ga);
         al = -a * al * ri;
         ga = cc * ri;
         de = (DD(qf) - a * de) * ri;
@@ -242,10 +230,10 @@ struct ChunkSolver {
         const T lq = LO(qb), hq = HI(qb);
         const T a = A(qb, lq), cc = C(qb, hq);
         if ((FULL && k == 1) || (!FULL && qb == n - 2)) {
-          const T ri = rcp(g.b_of(lq, hq));
+          const T ri = recip(g.b_of(lq, hq));
           ah = a * ri; ch = cc * ri; dh = DD(qb) * ri;
         } else {
-          const T ri = rcp(g.b_of(lq, hq) - cc * ah);
+          const T ri = recip(g.b_of(lq, hq) - cc * ah);
           ah = a * ri;
           ch = -cc * ch * ri;
           dh = (DD(qb) - cc * dh) * ri;
@@ -254,7 +242,7 @@ struct ChunkSolver {
     }
     rhi.a = al; rhi.c = ga; rhi.y = de; rhi.z = -kl * rinv_f;
     if (FULL || n >= 3) {
-      const T rd = rcp(b0 - c0 * ah);
+      const T rd = recip(b0 - c0 * ah);
       rlo.a = a0 * rd; rlo.c = -c0 * ch * rd; rlo.y = (d0 - c0 * dh) * rd; rlo.z = -kf * rd;
     }
   }
@@ -271,7 +259,7 @@ struct ChunkSolver {
         const T a = A(q, lq), b = g.b_of(lq, hq), cc = C(q, hq);
         T dq = DD(q) - a * dprev;
         if ((FULL && q == CMAX - 2) || (!FULL && q == n - 2)) dq -= cc * xhi;
-        const T ri = (q == 1) ? rcp(b) : rcp(b - a * cpv[q - 1]);
+        const T ri = (q == 1) ? recip(b) : recip(b - a * cpv[q - 1]);
         cpv[q] = cc * ri;
         dprev = dq * ri;
         out[slot_of(c, q)] = dprev;
@@ -408,7 +396,7 @@ __global__ void __launch_bounds__(NT, NT == NT_SMALL ? 2 : 1)
           short LL = -1, UU = -1;
           if (l.x >= 0) { L = rv[l.x]; LL = lu[l.x].x; }
           if (l.y >= 0) { Uu = rv[l.y]; UU = lu[l.y].y; }
-          const T beta = rcp(T(1) - me.a * L.c - me.c * Uu.a);
+          const T beta = recip(T(1) - me.a * L.c - me.c * Uu.a);
           nr[k].a = -me.a * L.a * beta;
           nr[k].c = -me.c * Uu.c * beta;
           nr[k].y = (me.y - me.a * L.y - me.c * Uu.y) * beta;
@@ -492,19 +480,13 @@ __global__ void __launch_bounds__(NT, NT == NT_SMALL ? 2 : 1)
   }
 }
 
-template <typename T>
-static CoefP<T> coefs_of(const Level &L);
-template <>
-CoefP<double> coefs_of<double>(const Level &L) { return {L.W64, L.E64, L.S64, L.N64}; }
-template <>
-CoefP<float> coefs_of<float>(const Level &L) { return {L.W32, L.E32, L.S32, L.N32}; }
 
 template <typename T, int NT>
 static cudaError_t launch_shape(const Level &L, const WorkList &w, T *u, const T *f, cudaStream_t s) {
   constexpr bool SC = sizeof(T) == 4;  // FP64 keeps the coefficients in L1 (smem is too small)
   constexpr size_t smem = LineSmem<T, NT, SC>::bytes;
   auto kern = line_pass_kernel<T, NT, SC>;
-  kern<<<w.ncta, NT, smem, s>>>(w.cta, w.chunk, w.junc, w.vg, coefs_of<T>(L), L.nx + 1, u, f);
+  kern<<<w.ncta, NT, smem, s>>>(w.cta, w.chunk, w.junc, w.vg, level_coefs<T>(L), L.nx + 1, u, f);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -554,7 +536,7 @@ template <typename T>
 cudaError_t launch_checker_pass(const Level &L, int colour, T *u, const T *f, cudaStream_t s) {
   const int half = L.nx / 2 + 1;
   dim3 block(128), grid((half + 127) / 128, L.ny - 1);
-  checker_kernel<T><<<grid, block, 0, s>>>(coefs_of<T>(L), L.nx, colour, u, f);
+  checker_kernel<T><<<grid, block, 0, s>>>(level_coefs<T>(L), L.nx, colour, u, f);
   count_launch(1);
   return cudaGetLastError();
 }

@@ -41,6 +41,174 @@ __device__ __forceinline__ T by_dir(unsigned d, T e, T w, T n, T s) {
   return d == 0u ? e : (d == 1u ? w : (d == 2u ? n : s));
 }
 
+// Step 1 for a sequence of NT*K nodes handled by NT threads: thread t stages
+// nodes NT*k + t (coalesced), U at a time; the next batch's descriptors are
+// loaded while the current batch's data is in flight.  Writes a (coupling to
+// the predecessor), b (diagonal; 1 on unused slots), c (to the successor),
+// z = -k (to the junction), d (right-hand side with the other colour's
+// neighbours moved over) and the node's offset in u (-1 on unused slots).
+template <typename T, int K, int NT>
+__device__ __forceinline__ void stage_nodes(const uint2 *__restrict__ nd, int t, const Coefs<T> &cp, int nx1,
+                                            const T *__restrict__ u, const T *__restrict__ f, T *sa, T *sb, T *sc,
+                                            T *sd, T *sz, int *sp) {
+  constexpr int U = K < 8 ? K : 8;
+  uint2 cur[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) cur[k] = __ldg(nd + NT * k + t);
+#pragma unroll
+  for (int t0 = 0; t0 < K; t0 += U) {
+    uint2 nxt[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (t0 + U < K) nxt[k] = __ldg(nd + NT * (t0 + U + k) + t);
+    T fv[U], ue[U], uw[U], un[U], us[U], ce[U], cw[U], cn[U], cs[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const unsigned fl = cur[k].y;
+      const int i = (int)(cur[k].x & 0xFFFFu), j = (int)(cur[k].x >> 16);
+      const unsigned in = ((fl & WN_PRED) ? 1u << (fl & 3u) : 0u) | ((fl & WN_SUCC) ? 1u << ((fl >> 3) & 3u) : 0u) |
+                          ((fl & WN_JUNC) ? 1u << ((fl >> 6) & 3u) : 0u);
+      const unsigned out = (fl & WN_VALID) ? (0xFu & ~in) : 0u;
+      const size_t p = (size_t)j * nx1 + i;
+      fv[k] = (fl & WN_VALID) ? __ldg(f + p) : T(0);
+      ue[k] = (out & 1u) ? u[p + 1] : T(0);
+      uw[k] = (out & 2u) ? u[p - 1] : T(0);
+      un[k] = (out & 4u) ? u[p + nx1] : T(0);
+      us[k] = (out & 8u) ? u[p - nx1] : T(0);
+      ce[k] = __ldg(cp.E + i);
+      cw[k] = __ldg(cp.W + i);
+      cn[k] = __ldg(cp.N + j);
+      cs[k] = __ldg(cp.S + j);
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const unsigned fl = cur[k].y;
+      const bool valid = (fl & WN_VALID) != 0u;
+      const int s = NT * (t0 + k) + t, sl = wslot(s);
+      sa[sl] = (fl & WN_PRED) ? by_dir(fl & 3u, ce[k], cw[k], cn[k], cs[k]) : T(0);
+      sc[sl] = (fl & WN_SUCC) ? by_dir((fl >> 3) & 3u, ce[k], cw[k], cn[k], cs[k]) : T(0);
+      sz[sl] = (fl & WN_JUNC) ? -by_dir((fl >> 6) & 3u, ce[k], cw[k], cn[k], cs[k]) : T(0);
+      sb[sl] = valid ? -((cw[k] + ce[k]) + (cs[k] + cn[k])) : T(1);
+      sd[sl] = fv[k] - ce[k] * ue[k] - cw[k] * uw[k] - cn[k] * un[k] - cs[k] * us[k];
+      sp[s] = valid ? (int)((cur[k].x >> 16) * (unsigned)nx1 + (cur[k].x & 0xFFFFu)) : -1;
+    }
+    if (t0 + U < K) {
+#pragma unroll
+      for (int k = 0; k < U; ++k) cur[k] = nxt[k];
+    }
+  }
+}
+
+// Step 2 for the thread owning nodes base .. base+K-1: the forward sweep over
+// its interior nodes 0..K-2 (rows  x_q + c'_q x_{q+1} = y'_q + z'_q x_J +
+// w'_q S_prev), then x_0 = Y0 + Z0 x_J + W0 S_prev + V0 S_own by a backward
+// pass of multiply-adds.  K = 1: no interior (x_0 is the next separator).
+template <typename T, int K>
+struct Sweep {
+  T cq[K], yq[K], zq[K], wq[K];  // entries 0..K-2 used
+  T Y0 = T(0), Z0 = T(0), W0 = T(0), V0 = T(1);  // x_0 (as the next thread sees its own first node)
+  T yl = T(0), zl = T(0), wl = T(1), cl = T(0);  // x_{K-2} = yl + zl x_J + wl S_prev - cl S_own
+  __device__ __forceinline__ void run(int base, const T *sa, const T *sb, const T *sc, const T *sd, const T *sz) {
+    if constexpr (K > 1) {
+      {
+        const int sl = wslot(base);
+        const T r = recip(sb[sl]);
+        cq[0] = sc[sl] * r;
+        yq[0] = sd[sl] * r;
+        zq[0] = sz[sl] * r;
+        wq[0] = -sa[sl] * r;
+      }
+#pragma unroll
+      for (int q = 1; q < K - 1; ++q) {
+        const int sl = wslot(base + q);
+        const T a = sa[sl];
+        const T r = recip(sb[sl] - a * cq[q - 1]);
+        cq[q] = sc[sl] * r;
+        yq[q] = (sd[sl] - a * yq[q - 1]) * r;
+        zq[q] = (sz[sl] - a * zq[q - 1]) * r;
+        wq[q] = -a * wq[q - 1] * r;
+      }
+      yl = yq[K - 2]; zl = zq[K - 2]; wl = wq[K - 2]; cl = cq[K - 2];
+      Y0 = yl; Z0 = zl; W0 = wl; V0 = -cl;
+#pragma unroll
+      for (int q = K - 3; q >= 0; --q) {
+        Y0 = yq[q] - cq[q] * Y0;
+        Z0 = zq[q] - cq[q] * Z0;
+        W0 = wq[q] - cq[q] * W0;
+        V0 = -cq[q] * V0;
+      }
+    }
+  }
+  // Step 4: interior values for both columns from the separators S_prev =
+  // (sym, szm) and S_own = (sy, sz), written over the a (value) and b (x_J
+  // column) slots.
+  __device__ __forceinline__ void back(int base, T sym, T szm, T sy, T sz, T *sa, T *sb) const {
+    sa[wslot(base + K - 1)] = sy;
+    sb[wslot(base + K - 1)] = sz;
+    T xy = sy, xz = sz;
+#pragma unroll
+    for (int q = K - 2; q >= 0; --q) {
+      xy = yq[q] + wq[q] * sym - cq[q] * xy;
+      xz = zq[q] + wq[q] * szm - cq[q] * xz;
+      const int sl = wslot(base + q);
+      sa[sl] = xy;
+      sb[sl] = xz;
+    }
+  }
+};
+
+// The junction of a sequence: its row's right-hand side r_J (thread 0) and
+// its coefficient towards attached node e (thread e < 4).
+template <typename T>
+struct Junction {
+  uint4 jb;
+  bool has_j;
+  int natt;
+  T kp = T(0), rJ = T(0), cJ = T(1);
+  size_t p = 0;
+  __device__ __forceinline__ Junction(const WBlock *__restrict__ blks, int seq, int t, const Coefs<T> &cp, int nx1,
+                                      const T *__restrict__ u, const T *__restrict__ f) {
+    jb = __ldg(reinterpret_cast<const uint4 *>(blks) + seq);
+    has_j = (jb.y & 0xFFu) != 0u;
+    natt = (int)((jb.y >> 8) & 0xFFu);
+    const unsigned adirs = (jb.y >> 16) & 0xFFu;
+    if (has_j && t < 4) {
+      const int ji = (int)(jb.x & 0xFFFFu), jj = (int)(jb.x >> 16);
+      p = (size_t)jj * nx1 + ji;
+      const T e = __ldg(cp.E + ji), w = __ldg(cp.W + ji), n = __ldg(cp.N + jj), s = __ldg(cp.S + jj);
+      unsigned att = 0;
+      for (int q = 0; q < natt; ++q) att |= 1u << ((adirs >> (2 * q)) & 3u);
+      if (t < natt) kp = by_dir((adirs >> (2 * t)) & 3u, e, w, n, s);
+      if (t == 0) {
+        T r = __ldg(f + p);
+        if (!(att & 1u)) r -= e * u[p + 1];
+        if (!(att & 2u)) r -= w * u[p - 1];
+        if (!(att & 4u)) r -= n * u[p + nx1];
+        if (!(att & 8u)) r -= s * u[p - nx1];
+        rJ = r;
+        cJ = -((w + e) + (s + n));
+      }
+    }
+  }
+  // Step 5, called by all lanes of one warp once the value (xa) and x_J
+  // (xb) columns of the attached nodes are in shared memory: x_J from the
+  // junction row (valid in lane 0).
+  __device__ __forceinline__ T solve(int lane, const T *xa, const T *xb) const {
+    T sy = T(0), sz = T(0);
+    if (lane < natt) {
+      const unsigned word = lane < 2 ? jb.z : jb.w;
+      const int s = (int)((word >> (16 * (lane & 1))) & 0xFFFFu);
+      sy = kp * xa[wslot(s)];
+      sz = kp * xb[wslot(s)];
+    }
+    sy += __shfl_xor_sync(0xFFFFFFFFu, sy, 1);
+    sz += __shfl_xor_sync(0xFFFFFFFFu, sz, 1);
+    sy += __shfl_xor_sync(0xFFFFFFFFu, sy, 2);
+    sz += __shfl_xor_sync(0xFFFFFFFFu, sz, 2);
+    return (rJ - sy) / (cJ + sz);
+  }
+};
+
 template <typename T, int K>
 __global__ void __launch_bounds__(32) warp_line_kernel(const WNode *__restrict__ nodes,
                                                        const WBlock *__restrict__ blks, Coefs<T> cp, int nx1,
@@ -53,133 +221,32 @@ __global__ void __launch_bounds__(32) warp_line_kernel(const WNode *__restrict__
   const int lane = threadIdx.x;
   const uint2 *nd = reinterpret_cast<const uint2 *>(nodes) + (size_t)blockIdx.x * N;
 
-  // ---- the warp's junction: its row's right-hand side r_J (lane 0) and its
-  // coefficient towards attached node e (lane e)
-  const uint4 jb = __ldg(reinterpret_cast<const uint4 *>(blks) + blockIdx.x);
-  const bool has_j = (jb.y & 0xFFu) != 0u;
-  const int natt = (int)((jb.y >> 8) & 0xFFu);
-  const unsigned adirs = (jb.y >> 16) & 0xFFu;
-  T kp = T(0), rJ = T(0), cJ = T(1);
-  size_t pJ = 0;
-  if (has_j) {
-    const int ji = (int)(jb.x & 0xFFFFu), jj = (int)(jb.x >> 16);
-    pJ = (size_t)jj * nx1 + ji;
-    const T e = __ldg(cp.E + ji), w = __ldg(cp.W + ji), n = __ldg(cp.N + jj), s = __ldg(cp.S + jj);
-    unsigned att = 0;
-    for (int q = 0; q < natt; ++q) att |= 1u << ((adirs >> (2 * q)) & 3u);
-    if (lane < natt) kp = by_dir((adirs >> (2 * lane)) & 3u, e, w, n, s);
-    if (lane == 0) {
-      T r = __ldg(f + pJ);
-      if (!(att & 1u)) r -= e * u[pJ + 1];
-      if (!(att & 2u)) r -= w * u[pJ - 1];
-      if (!(att & 4u)) r -= n * u[pJ + nx1];
-      if (!(att & 8u)) r -= s * u[pJ - nx1];
-      rJ = r;
-      cJ = -((w + e) + (s + n));
-    }
-  }
+  // ---- the warp's junction
+  const Junction<T> jn(blks, blockIdx.x, lane, cp, nx1, u, f);
 
-  // ---- 1. staging, U nodes per lane at a time; the next batch's
-  // descriptors are loaded while the current batch's data is in flight
-  {
-    constexpr int U = K < 8 ? K : 8;
-    uint2 cur[U];
-#pragma unroll
-    for (int k = 0; k < U; ++k) cur[k] = __ldg(nd + 32 * k + lane);
-#pragma unroll
-    for (int t0 = 0; t0 < K; t0 += U) {
-      uint2 nxt[U];
-#pragma unroll
-      for (int k = 0; k < U; ++k)
-        if (t0 + U < K) nxt[k] = __ldg(nd + 32 * (t0 + U + k) + lane);
-      T fv[U], ue[U], uw[U], un[U], us[U], ce[U], cw[U], cn[U], cs[U];
-#pragma unroll
-      for (int k = 0; k < U; ++k) {
-        const unsigned fl = cur[k].y;
-        const int i = (int)(cur[k].x & 0xFFFFu), j = (int)(cur[k].x >> 16);
-        const unsigned in = ((fl & WN_PRED) ? 1u << (fl & 3u) : 0u) | ((fl & WN_SUCC) ? 1u << ((fl >> 3) & 3u) : 0u) |
-                            ((fl & WN_JUNC) ? 1u << ((fl >> 6) & 3u) : 0u);
-        const unsigned out = (fl & WN_VALID) ? (0xFu & ~in) : 0u;
-        const size_t p = (size_t)j * nx1 + i;
-        fv[k] = (fl & WN_VALID) ? __ldg(f + p) : T(0);
-        ue[k] = (out & 1u) ? u[p + 1] : T(0);
-        uw[k] = (out & 2u) ? u[p - 1] : T(0);
-        un[k] = (out & 4u) ? u[p + nx1] : T(0);
-        us[k] = (out & 8u) ? u[p - nx1] : T(0);
-        ce[k] = __ldg(cp.E + i);
-        cw[k] = __ldg(cp.W + i);
-        cn[k] = __ldg(cp.N + j);
-        cs[k] = __ldg(cp.S + j);
-      }
-#pragma unroll
-      for (int k = 0; k < U; ++k) {
-        const unsigned fl = cur[k].y;
-        const bool valid = (fl & WN_VALID) != 0u;
-        const int s = 32 * (t0 + k) + lane, sl = wslot(s);
-        sa[sl] = (fl & WN_PRED) ? by_dir(fl & 3u, ce[k], cw[k], cn[k], cs[k]) : T(0);
-        sc[sl] = (fl & WN_SUCC) ? by_dir((fl >> 3) & 3u, ce[k], cw[k], cn[k], cs[k]) : T(0);
-        sz[sl] = (fl & WN_JUNC) ? -by_dir((fl >> 6) & 3u, ce[k], cw[k], cn[k], cs[k]) : T(0);
-        sb[sl] = valid ? -((cw[k] + ce[k]) + (cs[k] + cn[k])) : T(1);
-        sd[sl] = fv[k] - ce[k] * ue[k] - cw[k] * uw[k] - cn[k] * un[k] - cs[k] * us[k];
-        sp[s] = valid ? (int)((cur[k].x >> 16) * (unsigned)nx1 + (cur[k].x & 0xFFFFu)) : -1;
-      }
-      if (t0 + U < K) {
-#pragma unroll
-        for (int k = 0; k < U; ++k) cur[k] = nxt[k];
-      }
-    }
-  }
+  // ---- 1. staging
+  stage_nodes<T, K, 32>(nd, lane, cp, nx1, u, f, sa, sb, sc, sd, sz, sp);
   __syncwarp();
 
   // ---- 2. forward sweep over the lane's interior nodes 0..K-2
   const int base = lane * K;
-  T cq[K], yq[K], zq[K], wq[K];  // entries 0..K-2 used
-  T Y0 = T(0), Z0 = T(0), W0 = T(0), V0 = T(1);           // x_0 = Y0 + Z0 x_J + W0 S_{l-1} + V0 S_l
-  T yl = T(0), zl = T(0), wl = T(1), cl = T(0);           // x_{K-2} = yl + zl x_J + wl S_{l-1} - cl S_l
-  if constexpr (K > 1) {
-    {
-      const int sl = wslot(base);
-      const T r = recip(sb[sl]);
-      cq[0] = sc[sl] * r;
-      yq[0] = sd[sl] * r;
-      zq[0] = sz[sl] * r;
-      wq[0] = -sa[sl] * r;
-    }
-#pragma unroll
-    for (int q = 1; q < K - 1; ++q) {
-      const int sl = wslot(base + q);
-      const T a = sa[sl];
-      const T r = recip(sb[sl] - a * cq[q - 1]);
-      cq[q] = sc[sl] * r;
-      yq[q] = (sd[sl] - a * yq[q - 1]) * r;
-      zq[q] = (sz[sl] - a * zq[q - 1]) * r;
-      wq[q] = -a * wq[q - 1] * r;
-    }
-    yl = yq[K - 2]; zl = zq[K - 2]; wl = wq[K - 2]; cl = cq[K - 2];
-    Y0 = yl; Z0 = zl; W0 = wl; V0 = -cl;
-#pragma unroll
-    for (int q = K - 3; q >= 0; --q) {
-      Y0 = yq[q] - cq[q] * Y0;
-      Z0 = zq[q] - cq[q] * Z0;
-      W0 = wq[q] - cq[q] * W0;
-      V0 = -cq[q] * V0;
-    }
-  }
+  Sweep<T, K> sw;
+  sw.run(base, sa, sb, sc, sd, sz);
 
   // ---- 3. separator rows, then cyclic reduction across the lanes
   const int ss = wslot(base + K - 1);
   T A, C, Ry, Rz;
   {
-    T Yn = __shfl_down_sync(0xFFFFFFFFu, Y0, 1), Zn = __shfl_down_sync(0xFFFFFFFFu, Z0, 1);
-    T Wn = __shfl_down_sync(0xFFFFFFFFu, W0, 1), Vn = __shfl_down_sync(0xFFFFFFFFu, V0, 1);
+    T Yn = __shfl_down_sync(0xFFFFFFFFu, sw.Y0, 1), Zn = __shfl_down_sync(0xFFFFFFFFu, sw.Z0, 1);
+    T Wn = __shfl_down_sync(0xFFFFFFFFu, sw.W0, 1), Vn = __shfl_down_sync(0xFFFFFFFFu, sw.V0, 1);
     if (lane == 31) { Yn = T(0); Zn = T(0); Wn = T(0); Vn = T(0); }
     const T a = sa[ss], c = sc[ss];
-    const T B = sb[ss] - a * cl + c * Wn;
+    const T B = sb[ss] - a * sw.cl + c * Wn;
     const T r = recip(B);
-    A = a * wl * r;
+    A = a * sw.wl * r;
     C = c * Vn * r;
-    Ry = (sd[ss] - a * yl - c * Yn) * r;
-    Rz = (sz[ss] - a * zl - c * Zn) * r;
+    Ry = (sd[ss] - a * sw.yl - c * Yn) * r;
+    Rz = (sz[ss] - a * sw.zl - c * Zn) * r;
   }
 #pragma unroll
   for (int dd = 1; dd < 32; dd <<= 1) {
@@ -200,37 +267,15 @@ __global__ void __launch_bounds__(32) warp_line_kernel(const WNode *__restrict__
   {
     T Sym = __shfl_up_sync(0xFFFFFFFFu, Ry, 1), Szm = __shfl_up_sync(0xFFFFFFFFu, Rz, 1);
     if (lane == 0) { Sym = T(0); Szm = T(0); }
-    sa[ss] = Ry;
-    sb[ss] = Rz;
-    T xy = Ry, xz = Rz;
-#pragma unroll
-    for (int q = K - 2; q >= 0; --q) {
-      xy = yq[q] + wq[q] * Sym - cq[q] * xy;
-      xz = zq[q] + wq[q] * Szm - cq[q] * xz;
-      const int sl = wslot(base + q);
-      sa[sl] = xy;
-      sb[sl] = xz;
-    }
+    sw.back(base, Sym, Szm, Ry, Rz, sa, sb);
   }
   __syncwarp();
 
   // ---- 5. junction value, then all values back to u
   T xJ = T(0);
-  if (has_j) {
-    T sy = T(0), szz = T(0);
-    if (lane < natt) {
-      const unsigned word = lane < 2 ? jb.z : jb.w;
-      const int s = (int)((word >> (16 * (lane & 1))) & 0xFFFFu);
-      sy = kp * sa[wslot(s)];
-      szz = kp * sb[wslot(s)];
-    }
-    sy += __shfl_xor_sync(0xFFFFFFFFu, sy, 1);
-    szz += __shfl_xor_sync(0xFFFFFFFFu, szz, 1);
-    sy += __shfl_xor_sync(0xFFFFFFFFu, sy, 2);
-    szz += __shfl_xor_sync(0xFFFFFFFFu, szz, 2);
-    const T x = (rJ - sy) / (cJ + szz);
-    xJ = __shfl_sync(0xFFFFFFFFu, x, 0);
-    if (lane == 0) u[pJ] = xJ;
+  if (jn.has_j) {
+    xJ = __shfl_sync(0xFFFFFFFFu, jn.solve(lane, sa, sb), 0);
+    if (lane == 0) u[jn.p] = xJ;
   }
 #pragma unroll
   for (int t = 0; t < K; ++t) {
@@ -243,6 +288,97 @@ __global__ void __launch_bounds__(32) warp_line_kernel(const WNode *__restrict__
   }
 }
 
+// The same solve for sequences of 32*W*K nodes on a CTA of W warps: the
+// separator system has 32*W rows and its cyclic reduction runs through
+// shared memory, one barrier per step.
+template <typename T, int K, int W>
+__global__ void __launch_bounds__(32 * W) seq_line_kernel(const WNode *__restrict__ nodes,
+                                                          const WBlock *__restrict__ blks, Coefs<T> cp, int nx1,
+                                                          T *__restrict__ u, const T *__restrict__ f) {
+  constexpr int NT = 32 * W, N = NT * K;
+  extern __shared__ __align__(16) unsigned char wsm[];
+  T *sa = reinterpret_cast<T *>(wsm);
+  T *sb = sa + N, *sc = sb + N, *sd = sc + N, *sz = sd + N;
+  T *rep = sz + N;       // [4][NT]: x_0 of every thread (Y0, Z0, W0, V0)
+  T *red = rep + 4 * NT;  // [2][4][NT]: separator rows (A, C, Y, Z), double-buffered
+  T *xjs = red + 8 * NT;  // the junction value
+  int *sp = reinterpret_cast<int *>(xjs + 2);
+  const int t = threadIdx.x, lane = t & 31;
+  const uint2 *nd = reinterpret_cast<const uint2 *>(nodes) + (size_t)blockIdx.x * N;
+  const Junction<T> jn(blks, blockIdx.x, t, cp, nx1, u, f);
+
+  stage_nodes<T, K, NT>(nd, t, cp, nx1, u, f, sa, sb, sc, sd, sz, sp);
+  __syncthreads();
+
+  const int base = t * K;
+  Sweep<T, K> sw;
+  sw.run(base, sa, sb, sc, sd, sz);
+  rep[t] = sw.Y0; rep[NT + t] = sw.Z0; rep[2 * NT + t] = sw.W0; rep[3 * NT + t] = sw.V0;
+  __syncthreads();
+
+  const int ss = wslot(base + K - 1);
+  T A, C, Ry, Rz;
+  {
+    const bool last = t == NT - 1;
+    const T Yn = last ? T(0) : rep[t + 1], Zn = last ? T(0) : rep[NT + t + 1];
+    const T Wn = last ? T(0) : rep[2 * NT + t + 1], Vn = last ? T(0) : rep[3 * NT + t + 1];
+    const T a = sa[ss], c = sc[ss];
+    const T r = recip(sb[ss] - a * sw.cl + c * Wn);
+    A = a * sw.wl * r;
+    C = c * Vn * r;
+    Ry = (sd[ss] - a * sw.yl - c * Yn) * r;
+    Rz = (sz[ss] - a * sw.zl - c * Zn) * r;
+  }
+  red[t] = A; red[NT + t] = C; red[2 * NT + t] = Ry; red[3 * NT + t] = Rz;
+  __syncthreads();
+  int cur = 0;
+#pragma unroll
+  for (int dd = 1; dd < NT; dd <<= 1) {
+    const T *rb = red + 4 * NT * cur;
+    T Am = T(0), Cm = T(0), Ym = T(0), Zm = T(0), Ap = T(0), Cp = T(0), Yp = T(0), Zp = T(0);
+    if (t >= dd) { Am = rb[t - dd]; Cm = rb[NT + t - dd]; Ym = rb[2 * NT + t - dd]; Zm = rb[3 * NT + t - dd]; }
+    if (t + dd < NT) { Ap = rb[t + dd]; Cp = rb[NT + t + dd]; Yp = rb[2 * NT + t + dd]; Zp = rb[3 * NT + t + dd]; }
+    const T r = recip(T(1) - A * Cm - C * Ap);
+    const T nA = -A * Am * r, nC = -C * Cp * r;
+    const T nY = (Ry - A * Ym - C * Yp) * r, nZ = (Rz - A * Zm - C * Zp) * r;
+    A = nA; C = nC; Ry = nY; Rz = nZ;
+    cur ^= 1;
+    T *wb = red + 4 * NT * cur;
+    wb[t] = A; wb[NT + t] = C; wb[2 * NT + t] = Ry; wb[3 * NT + t] = Rz;
+    __syncthreads();
+  }
+  {
+    const T *rb = red + 4 * NT * cur;
+    const T Sym = t > 0 ? rb[2 * NT + t - 1] : T(0), Szm = t > 0 ? rb[3 * NT + t - 1] : T(0);
+    sw.back(base, Sym, Szm, Ry, Rz, sa, sb);
+  }
+  __syncthreads();
+
+  T xJ = T(0);
+  if (jn.has_j) {
+    if (t < 32) {
+      const T x = jn.solve(lane, sa, sb);
+      if (t == 0) { xjs[0] = x; u[jn.p] = x; }
+    }
+    __syncthreads();
+    xJ = xjs[0];
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int s = NT * k + t;
+    const int p = sp[s];
+    if (p >= 0) {
+      const int sl = wslot(s);
+      u[p] = sa[sl] + xJ * sb[sl];
+    }
+  }
+}
+
+template <typename T, int K, int W>
+constexpr size_t seq_smem() {
+  return (size_t)32 * W * K * (5 * sizeof(T) + sizeof(int)) + sizeof(T) * (12 * 32 * W + 2);
+}
+
 template <typename T, int K>
 cudaError_t launch_k(const Level &L, const WarpList &w, T *u, const T *f, cudaStream_t s) {
   const size_t smem = (size_t)32 * K * (5 * sizeof(T) + sizeof(int));
@@ -251,22 +387,69 @@ cudaError_t launch_k(const Level &L, const WarpList &w, T *u, const T *f, cudaSt
   return cudaGetLastError();
 }
 
+template <typename T, int K, int W>
+cudaError_t launch_kw(const Level &L, const WarpList &w, T *u, const T *f, cudaStream_t s) {
+  seq_line_kernel<T, K, W><<<w.nwarp, 32 * W, seq_smem<T, K, W>(), s>>>(w.node, w.blk, level_coefs<T>(L), L.nx + 1,
+                                                                        u, f);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+template <typename T, int K>
+cudaError_t launch_multi(const Level &L, const WarpList &w, T *u, const T *f, cudaStream_t s) {
+  switch (w.W) {
+    case 2: return launch_kw<T, K, 2>(L, w, u, f, s);
+    case 4: return launch_kw<T, K, 4>(L, w, u, f, s);
+    case 8: return launch_kw<T, K, 8>(L, w, u, f, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, int K, int W>
+cudaError_t opt_in() {
+  return cudaFuncSetAttribute(seq_line_kernel<T, K, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)seq_smem<T, K, W>());
+}
+template <typename T, int K>
+cudaError_t opt_in_all() {
+  cudaError_t e = opt_in<T, K, 2>();
+  if (e == cudaSuccess) e = opt_in<T, K, 4>();
+  if (e == cudaSuccess) e = opt_in<T, K, 8>();
+  return e;
+}
+
 }  // namespace
 
 template <typename T>
 cudaError_t launch_warp_pass(const Level &L, const WarpList &w, T *u, const T *f, cudaStream_t s) {
   if (w.nwarp == 0) return cudaSuccess;
+  if (w.W == 1) {
+    switch (w.K) {
+      case 1: return launch_k<T, 1>(L, w, u, f, s);
+      case 2: return launch_k<T, 2>(L, w, u, f, s);
+      case 4: return launch_k<T, 4>(L, w, u, f, s);
+      case 8: return launch_k<T, 8>(L, w, u, f, s);
+      case 16: return launch_k<T, 16>(L, w, u, f, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (w.K) {
-    case 1: return launch_k<T, 1>(L, w, u, f, s);
-    case 2: return launch_k<T, 2>(L, w, u, f, s);
-    case 4: return launch_k<T, 4>(L, w, u, f, s);
-    case 8: return launch_k<T, 8>(L, w, u, f, s);
-    case 16: return launch_k<T, 16>(L, w, u, f, s);
-    case 32:
-      if constexpr (sizeof(T) == 4) return launch_k<T, 32>(L, w, u, f, s);
+    case 4: return launch_multi<T, 4>(L, w, u, f, s);
+    case 8: return launch_multi<T, 8>(L, w, u, f, s);
+    case 16:
+      if constexpr (sizeof(T) == 4) return launch_multi<T, 16>(L, w, u, f, s);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t prepare_warp_kernels() {
+  cudaError_t e = opt_in_all<float, 4>();
+  if (e == cudaSuccess) e = opt_in_all<float, 8>();
+  if (e == cudaSuccess) e = opt_in_all<float, 16>();
+  if (e == cudaSuccess) e = opt_in_all<double, 4>();
+  if (e == cudaSuccess) e = opt_in_all<double, 8>();
+  return e;
 }
 
 template cudaError_t launch_warp_pass<double>(const Level &, const WarpList &, double *, const double *, cudaStream_t);

@@ -292,11 +292,13 @@ __global__ void __launch_bounds__(NT, NT == NT_SMALL ? 2 : 1)
   ChunkDesc *sc = reinterpret_cast<ChunkDesc *>(smem_raw + SM::rows + SM::nodes + SM::junc + SM::links);
   VGroup *svg = reinterpret_cast<VGroup *>(smem_raw + SM::rows + SM::nodes + SM::junc + SM::links + SM::descs);
 
+  pdl_trigger();
   const CtaWork w = works[blockIdx.x];
   const JuncDesc *juncs = juncs_all + w.junc0;
   const int tid = threadIdx.x;
   for (int t = tid; t < w.nchunk; t += NT) sc[t] = chunks_all[w.chunk0 + t];
   for (int t = tid; t < w.nvg; t += NT) svg[t] = vgs_all[w.vg0 + t];
+  pdl_wait();  // u and f from here on
   __syncthreads();
 
   // ---- phase 0: right-hand sides of all chain nodes.  Grouped vertical
@@ -486,9 +488,9 @@ static cudaError_t launch_shape(const Level &L, const WorkList &w, T *u, const T
   constexpr bool SC = sizeof(T) == 4;  // FP64 keeps the coefficients in L1 (smem is too small)
   constexpr size_t smem = LineSmem<T, NT, SC>::bytes;
   auto kern = line_pass_kernel<T, NT, SC>;
-  kern<<<w.ncta, NT, smem, s>>>(w.cta, w.chunk, w.junc, w.vg, level_coefs<T>(L), L.nx + 1, u, f);
   count_launch(1);
-  return cudaGetLastError();
+  return launch_pdl(kern, dim3(w.ncta), dim3(NT), smem, s, (const CtaWork *)w.cta, (const ChunkDesc *)w.chunk,
+                    (const JuncDesc *)w.junc, (const VGroup *)w.vg, level_coefs<T>(L), L.nx + 1, u, f);
 }
 
 template <typename T>
@@ -521,6 +523,8 @@ template cudaError_t launch_line_pass<float>(const Level &, const WorkList &, fl
 // node of the colour; blockIdx.y = interior row.
 template <typename T>
 __global__ void checker_kernel(CoefP<T> cp, int nx, int colour, T *__restrict__ u, const T *__restrict__ f) {
+  pdl_trigger();
+  pdl_wait();
   const int j = blockIdx.y + 1;
   const int i0 = ((j + colour) & 1) ? 1 : 2;   // first interior i with (i+j)%2 == colour
   const int i = i0 + 2 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -536,9 +540,8 @@ template <typename T>
 cudaError_t launch_checker_pass(const Level &L, int colour, T *u, const T *f, cudaStream_t s) {
   const int half = L.nx / 2 + 1;
   dim3 block(128), grid((half + 127) / 128, L.ny - 1);
-  checker_kernel<T><<<grid, block, 0, s>>>(level_coefs<T>(L), L.nx, colour, u, f);
   count_launch(1);
-  return cudaGetLastError();
+  return launch_pdl(checker_kernel<T>, grid, block, 0, s, level_coefs<T>(L), L.nx, colour, u, f);
 }
 template cudaError_t launch_checker_pass<double>(const Level &, int, double *, const double *, cudaStream_t);
 template cudaError_t launch_checker_pass<float>(const Level &, int, float *, const float *, cudaStream_t);

@@ -19,7 +19,7 @@
 // tiles go through a per-warp shared-memory transpose.
 #include <algorithm>
 
-#include "mg_internal.h"
+#include "device_util.cuh"
 
 namespace tmg {
 
@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(32 * TWv<T>) tile_reduce(const TileDesc *__res
   constexpr int TW = TWv<T>;
   __shared__ T tr[TW][32][33];
   __shared__ T cos[TW][2][32];
+  pdl_trigger();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = blockIdx.x * TW + warp;
   if (t >= ntile) return;
@@ -118,6 +119,7 @@ __global__ void __launch_bounds__(32 * TWv<T>) tile_reduce(const TileDesc *__res
   T d[CMAX];
   stage_coefs(g, lane, cos[warp]);
   const T(&co)[2][32] = cos[warp];
+  pdl_wait();  // u, f and the scratch from here on
 
   // ---- right-hand sides.  Loads are unconditional (indices clamped into the
   // lane's run) so that all of them can be in flight at once; the wall terms
@@ -232,12 +234,14 @@ __global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__
                                                    const TRow<T> *__restrict__ rows, T *cdp,
                                                    T *__restrict__ xscr, T *__restrict__ u, const T *__restrict__ f) {
   __shared__ T s_cp[4][32], s_dp[4][32], s_xj[32];
+  pdl_trigger();
   const int l = threadIdx.x >> 5, b = threadIdx.x & 31;
   const BlockDesc bd = blocks[(size_t)blockIdx.x * 32 + b];
   const bool active = l < bd.nleg;
   const int len = active ? bd.leg_len[l] : 0;
   const int nch = (len + CMAX - 1) / CMAX;
   const size_t t0 = active ? bd.leg_tile0[l] : 0;
+  pdl_wait();  // the reduced rows, u and f from here on
   T cpv = T(0), dpv = T(0);
   constexpr int B = 16;  // chunks whose rows are loaded together
   for (int r0 = 0; r0 < nch; r0 += B) {
@@ -341,6 +345,7 @@ __global__ void __launch_bounds__(32 * TWv<T>) tile_expand(const TileDesc *__res
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // tiles in the reverse order of tile_reduce: the u lines it read last are
   // the likeliest to still be in L2 for these partial-sector writes
+  pdl_trigger();
   const int t = ntile - 1 - (blockIdx.x * TW + warp);
   if (t < 0) return;
   const TileDesc td = tiles[t];
@@ -349,6 +354,7 @@ __global__ void __launch_bounds__(32 * TWv<T>) tile_expand(const TileDesc *__res
   const int m = ln.q1, fl = ln.flags;
   stage_coefs(g, lane, cos[warp]);
   const T(&co)[2][32] = cos[warp];
+  pdl_wait();  // the scratch and u from here on
   T *x = tr[warp][lane], *cpv = cs[warp][lane];
   if (m > 0) {
     const T cross = g.xrun ? __ldg(cp.S + ln.line) + __ldg(cp.N + ln.line)
@@ -415,14 +421,21 @@ cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &tl, 
   constexpr int TW = TWv<T>;
   const int ctas = (tl.ntile + TW - 1) / TW;
   if (ev) cudaEventRecord(ev[0], s);
-  if (tl.ntile > 0) tile_reduce<T><<<ctas, 32 * TW, 0, s>>>(tl.tile, tl.lane, tl.ntile, cp, L.nx, L.ny, u, f, rows, dscr);
+  cudaError_t e = cudaSuccess;
+  if (tl.ntile > 0)
+    e = launch_pdl(tile_reduce<T>, dim3(ctas), dim3(32 * TW), 0, s, (const TileDesc *)tl.tile,
+                   (const TileLane *)tl.lane, tl.ntile, cp, L.nx, L.ny, u, f, rows, dscr);
   if (ev) cudaEventRecord(ev[1], s);
-  tile_couple<T><<<tl.ngroup, 128, 0, s>>>(tl.block, cp, nx1, rows, cdp, xscr, u, f);
+  if (e == cudaSuccess)
+    e = launch_pdl(tile_couple<T>, dim3(tl.ngroup), dim3(128), 0, s, (const BlockDesc *)tl.block, cp, nx1,
+                   (const TRow<T> *)rows, cdp, xscr, u, f);
   if (ev) cudaEventRecord(ev[2], s);
-  if (tl.ntile > 0) tile_expand<T><<<ctas, 32 * TW, 0, s>>>(tl.tile, tl.lane, tl.ntile, cp, L.nx, L.ny, dscr, xscr, u);
+  if (e == cudaSuccess && tl.ntile > 0)
+    e = launch_pdl(tile_expand<T>, dim3(ctas), dim3(32 * TW), 0, s, (const TileDesc *)tl.tile,
+                   (const TileLane *)tl.lane, tl.ntile, cp, L.nx, L.ny, (const T *)dscr, (const T *)xscr, u);
   if (ev) cudaEventRecord(ev[3], s);
   count_launch(tl.ntile > 0 ? 3 : 1);
-  return cudaGetLastError();
+  return e;
 }
 template cudaError_t launch_tile_pass<double>(const Grid &, const Level &, const TileList &, double *, const double *,
                                               cudaStream_t, cudaEvent_t *);

@@ -16,7 +16,7 @@
 //   ir_update                u64 += e32
 #include <algorithm>
 
-#include "mg_internal.h"
+#include "device_util.cuh"
 
 namespace tmg {
 
@@ -79,6 +79,8 @@ __global__ void __launch_bounds__(RR_THREADS) residual_restrict_kernel(CoefQ<T> 
                                                                        const T *__restrict__ f,
                                                                        T *__restrict__ fc, T *__restrict__ uc) {
   __shared__ T dd[RR_FJ][RR_FI + 1];
+  pdl_trigger();
+  pdl_wait();
   const int I0 = 1 + blockIdx.x * RR_I, J0 = 1 + blockIdx.y * RR_J;
   const int fi0 = 2 * I0 - 1, fj0 = 2 * J0 - 1, nx1 = nx + 1;
   // fine nodes of the strip that some coarse interior node of it uses
@@ -136,9 +138,9 @@ cudaError_t launch_residual_restrict(const Level &F, const Level &C, int kind, c
                                      T *uc, cudaStream_t s) {
   if (C.nx < 2 || C.ny < 2) return cudaSuccess;
   dim3 g((C.nx - 1 + RR_I - 1) / RR_I, (C.ny - 1 + RR_J - 1) / RR_J);
-  residual_restrict_kernel<T><<<g, RR_THREADS, 0, s>>>(cq<T>(F), F.nx, F.ny, C.nx, C.ny, kind, u, f, fc, uc);
   count_launch(1);
-  return cudaGetLastError();
+  return launch_pdl(residual_restrict_kernel<T>, g, dim3(RR_THREADS), 0, s, cq<T>(F), F.nx, F.ny, C.nx, C.ny, kind,
+                    u, f, fc, uc);
 }
 template cudaError_t launch_residual_restrict<double>(const Level &, const Level &, int, const double *,
                                                       const double *, double *, double *, cudaStream_t);
@@ -155,6 +157,8 @@ constexpr int PR_THREADS = 256;
 template <typename T>
 __global__ void __launch_bounds__(PR_THREADS) prolong_add_kernel(int nx, int ny, int nxc, const T *__restrict__ uc,
                                                                  T *__restrict__ u) {
+  pdl_trigger();
+  pdl_wait();
   const int j = blockIdx.y + 1;
   const int c1 = nxc + 1, Jc = j >> 1;
   const bool jodd = j & 1;
@@ -180,9 +184,8 @@ template <typename T>
 cudaError_t launch_prolong_add(const Level &F, const Level &C, const T *uc, T *u, cudaStream_t s) {
   const int bx = std::min((C.nx + PR_THREADS - 1) / PR_THREADS, 8);
   dim3 g(bx, F.ny - 1);
-  prolong_add_kernel<T><<<g, PR_THREADS, 0, s>>>(F.nx, F.ny, C.nx, uc, u);
   count_launch(1);
-  return cudaGetLastError();
+  return launch_pdl(prolong_add_kernel<T>, g, dim3(PR_THREADS), 0, s, F.nx, F.ny, C.nx, uc, u);
 }
 template cudaError_t launch_prolong_add<double>(const Level &, const Level &, const double *, double *,
                                                 cudaStream_t);
@@ -199,6 +202,8 @@ __global__ void __launch_bounds__(CS_THREADS) coarse_solve_kernel(CoefQ<double> 
                                                                   const double *__restrict__ inv,
                                                                   T *__restrict__ u, const T *__restrict__ f) {
   extern __shared__ double cb[];
+  pdl_trigger();
+  pdl_wait();
   const int n = (nx - 1) * (ny - 1), nx1 = nx + 1;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     const int i = k % (nx - 1) + 1, j = k / (nx - 1) + 1;
@@ -228,9 +233,9 @@ template <typename T>
 cudaError_t launch_coarse_solve(const Grid &g, T *u, const T *f, cudaStream_t s) {
   const Level &L = g.lev[g.nlev - 1];
   if (g.cn <= 0) return cudaSuccess;
-  coarse_solve_kernel<T><<<1, CS_THREADS, sizeof(double) * g.cn, s>>>(cq<double>(L), L.nx, L.ny, g.cinv, u, f);
   count_launch(1);
-  return cudaGetLastError();
+  return launch_pdl(coarse_solve_kernel<T>, dim3(1), dim3(CS_THREADS), sizeof(double) * g.cn, s, cq<double>(L), L.nx,
+                    L.ny, (const double *)g.cinv, u, f);
 }
 template cudaError_t launch_coarse_solve<double>(const Grid &, double *, const double *, cudaStream_t);
 template cudaError_t launch_coarse_solve<float>(const Grid &, float *, const float *, cudaStream_t);

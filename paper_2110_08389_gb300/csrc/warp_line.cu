@@ -55,6 +55,7 @@ __device__ __forceinline__ void stage_nodes(const uint2 *__restrict__ nd, int t,
   uint2 cur[U];
 #pragma unroll
   for (int k = 0; k < U; ++k) cur[k] = __ldg(nd + NT * k + t);
+  pdl_wait();  // u and f from here on
 #pragma unroll
   for (int t0 = 0; t0 < K; t0 += U) {
     uint2 nxt[U];
@@ -157,17 +158,17 @@ struct Sweep {
   }
 };
 
-// The junction of a sequence: its row's right-hand side r_J (thread 0) and
-// its coefficient towards attached node e (thread e < 4).
+// The junction of a sequence: its coefficient towards attached node e
+// (thread e < 4) and, from rhs(), its row's right-hand side r_J (thread 0).
 template <typename T>
 struct Junction {
   uint4 jb;
   bool has_j;
   int natt;
-  T kp = T(0), rJ = T(0), cJ = T(1);
+  unsigned att = 0;  // directions from the junction to its attached nodes
+  T kp = T(0), rJ = T(0), cJ = T(1), ce = T(0), cw = T(0), cn = T(0), cs = T(0);
   size_t p = 0;
-  __device__ __forceinline__ Junction(const WBlock *__restrict__ blks, int seq, int t, const Coefs<T> &cp, int nx1,
-                                      const T *__restrict__ u, const T *__restrict__ f) {
+  __device__ __forceinline__ Junction(const WBlock *__restrict__ blks, int seq, int t, const Coefs<T> &cp, int nx1) {
     jb = __ldg(reinterpret_cast<const uint4 *>(blks) + seq);
     has_j = (jb.y & 0xFFu) != 0u;
     natt = (int)((jb.y >> 8) & 0xFFu);
@@ -175,19 +176,21 @@ struct Junction {
     if (has_j && t < 4) {
       const int ji = (int)(jb.x & 0xFFFFu), jj = (int)(jb.x >> 16);
       p = (size_t)jj * nx1 + ji;
-      const T e = __ldg(cp.E + ji), w = __ldg(cp.W + ji), n = __ldg(cp.N + jj), s = __ldg(cp.S + jj);
-      unsigned att = 0;
+      ce = __ldg(cp.E + ji); cw = __ldg(cp.W + ji); cn = __ldg(cp.N + jj); cs = __ldg(cp.S + jj);
       for (int q = 0; q < natt; ++q) att |= 1u << ((adirs >> (2 * q)) & 3u);
-      if (t < natt) kp = by_dir((adirs >> (2 * t)) & 3u, e, w, n, s);
-      if (t == 0) {
-        T r = __ldg(f + p);
-        if (!(att & 1u)) r -= e * u[p + 1];
-        if (!(att & 2u)) r -= w * u[p - 1];
-        if (!(att & 4u)) r -= n * u[p + nx1];
-        if (!(att & 8u)) r -= s * u[p - nx1];
-        rJ = r;
-        cJ = -((w + e) + (s + n));
-      }
+      if (t < natt) kp = by_dir((adirs >> (2 * t)) & 3u, ce, cw, cn, cs);
+      cJ = -((cw + ce) + (cs + cn));
+    }
+  }
+  // after pdl_wait(): r_J = f_J minus the junction's neighbours outside the block
+  __device__ __forceinline__ void rhs(int t, int nx1, const T *__restrict__ u, const T *__restrict__ f) {
+    if (has_j && t == 0) {
+      T r = __ldg(f + p);
+      if (!(att & 1u)) r -= ce * u[p + 1];
+      if (!(att & 2u)) r -= cw * u[p - 1];
+      if (!(att & 4u)) r -= cn * u[p + nx1];
+      if (!(att & 8u)) r -= cs * u[p - nx1];
+      rJ = r;
     }
   }
   // Step 5, called by all lanes of one warp once the value (xa) and x_J
@@ -221,11 +224,13 @@ __global__ void __launch_bounds__(32) warp_line_kernel(const WNode *__restrict__
   const int lane = threadIdx.x;
   const uint2 *nd = reinterpret_cast<const uint2 *>(nodes) + (size_t)blockIdx.x * N;
 
+  pdl_trigger();
   // ---- the warp's junction
-  const Junction<T> jn(blks, blockIdx.x, lane, cp, nx1, u, f);
+  Junction<T> jn(blks, blockIdx.x, lane, cp, nx1);
 
-  // ---- 1. staging
+  // ---- 1. staging (waits for the previous kernel after its first descriptors)
   stage_nodes<T, K, 32>(nd, lane, cp, nx1, u, f, sa, sb, sc, sd, sz, sp);
+  jn.rhs(lane, nx1, u, f);
   __syncwarp();
 
   // ---- 2. forward sweep over the lane's interior nodes 0..K-2
@@ -305,9 +310,11 @@ __global__ void __launch_bounds__(32 * W) seq_line_kernel(const WNode *__restric
   int *sp = reinterpret_cast<int *>(xjs + 2);
   const int t = threadIdx.x, lane = t & 31;
   const uint2 *nd = reinterpret_cast<const uint2 *>(nodes) + (size_t)blockIdx.x * N;
-  const Junction<T> jn(blks, blockIdx.x, t, cp, nx1, u, f);
+  pdl_trigger();
+  Junction<T> jn(blks, blockIdx.x, t, cp, nx1);
 
   stage_nodes<T, K, NT>(nd, t, cp, nx1, u, f, sa, sb, sc, sd, sz, sp);
+  jn.rhs(t, nx1, u, f);
   __syncthreads();
 
   const int base = t * K;
@@ -382,17 +389,16 @@ constexpr size_t seq_smem() {
 template <typename T, int K>
 cudaError_t launch_k(const Level &L, const WarpList &w, T *u, const T *f, cudaStream_t s) {
   const size_t smem = (size_t)32 * K * (5 * sizeof(T) + sizeof(int));
-  warp_line_kernel<T, K><<<w.nwarp, 32, smem, s>>>(w.node, w.blk, level_coefs<T>(L), L.nx + 1, u, f);
   count_launch(1);
-  return cudaGetLastError();
+  return launch_pdl(warp_line_kernel<T, K>, dim3(w.nwarp), dim3(32), smem, s, (const WNode *)w.node,
+                    (const WBlock *)w.blk, level_coefs<T>(L), L.nx + 1, u, f);
 }
 
 template <typename T, int K, int W>
 cudaError_t launch_kw(const Level &L, const WarpList &w, T *u, const T *f, cudaStream_t s) {
-  seq_line_kernel<T, K, W><<<w.nwarp, 32 * W, seq_smem<T, K, W>(), s>>>(w.node, w.blk, level_coefs<T>(L), L.nx + 1,
-                                                                        u, f);
   count_launch(1);
-  return cudaGetLastError();
+  return launch_pdl(seq_line_kernel<T, K, W>, dim3(w.nwarp), dim3(32 * W), seq_smem<T, K, W>(), s,
+                    (const WNode *)w.node, (const WBlock *)w.blk, level_coefs<T>(L), L.nx + 1, u, f);
 }
 
 template <typename T, int K>

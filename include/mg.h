@@ -25,9 +25,10 @@
  *     odd, a side would fall below 2 intervals, or max(nx,ny) <= 8; the
  *     coarsest level is solved directly.
  *   - All work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
- *     stream).  Only mg_setup_grid, mg_solve and mg_solve_adjoint synchronise
- *     (they read residual norms back to the host).  No entry point allocates
- *     device memory except mg_setup_grid.
+ *     stream).  Only mg_setup_grid, mg_solve, mg_solve_adjoint, mg_batch_solve,
+ *     mg_set_line_path and mg_autotune synchronise (the solves read residual
+ *     norms back to the host).  No entry point allocates device memory except
+ *     mg_setup_grid, mg_set_line_path and mg_autotune.
  *   - Errors are returned as mg_status; nothing aborts or traps.  After
  *     MG_ERR_CUDA the message of the failing call is available from
  *     mg_last_error().  Calls on one grid must not run concurrently.
@@ -275,6 +276,56 @@ mg_status mg_pass_timer_begin(mg_grid *g, int level, int max_passes);
  * whole pass.  Any output pointer may be NULL.  Destroys the events.         */
 mg_status mg_pass_timer_end(mg_grid *g, int64_t *passes, double *stage_ms, double *pass_min_ms,
                             double *pass_max_ms);
+
+/* ---- line-solve paths and their autotuner.  A colour pass of a line
+ * smoother (zebra, tweed, wireframe; Sec. 3) can be laid out on the GPU in
+ * three ways; each solves every block of the colour exactly, they differ only
+ * in how the work is spread over threads (and so in rounding order and
+ * speed).  The paper's solver is serial; these have no counterpart there.    */
+typedef enum {
+  MG_PATH_AUTO = 0,  /* built-in rule: the warp path where every block of the
+                        colour fits it and both sides are below 2048 intervals,
+                        else the tiled path where it exists, else the CTA path */
+  MG_PATH_WARP = 1,  /* blocks laid end to end in sequences of 32*W*K nodes, one
+                        per CTA of W warps; K consecutive nodes per thread     */
+  MG_PATH_TILED = 2, /* 32 x 32-node tiles of parallel legs: three kernels     */
+  MG_PATH_CTA = 3    /* whole blocks per CTA, 32-node chunks per thread         */
+} mg_line_path;
+
+/* Sets the path of the colour passes of `smoother` (MG_SMOOTH_ZEBRA_X,
+ * _ZEBRA_Y, _TWEED or _WIREFRAME) on `level` in `dtype` (mg_dtype).  k: for
+ * MG_PATH_WARP the preferred nodes per thread (1, 2, 4, 8 or 16; 0 = 4), kept
+ * while the largest block fits 8 warps (K doubles otherwise); ignored by the
+ * other paths.  MG_ERR_UNSUPPORTED if the level's blocks do not fit the path:
+ * the warp path takes blocks of up to 4096 nodes in FP32 and 2048 in FP64;
+ * the tiled path exists for tweed and zebra on levels whose sides are both at
+ * least 1024 intervals.  The previous choice then stays.  May allocate and
+ * free device memory (work lists); synchronises the device and drops the
+ * grid's captured cycle graphs.                                              */
+mg_status mg_set_line_path(mg_grid *grid, int level, int smoother, int dtype, int path, int k);
+
+/* The path the colour passes of (level, smoother, dtype) take now, resolved
+ * (never MG_PATH_AUTO; where the two colours differ, that of colour 0) and,
+ * for the warp path, its shape: *k nodes per thread and *w warps per
+ * sequence (both 0 for the other paths).  Any output pointer may be NULL.   */
+mg_status mg_get_line_path(const mg_grid *grid, int level, int smoother, int dtype, int *path, int *k,
+                           int *w);
+
+/* Autotuner.  For every level but the coarsest (which is solved directly),
+ * times `reps` colour passes of `smoother` in `dtype` (alternating colours,
+ * after 2 untimed ones; CUDA events on `stream`) with each path and warp
+ * shape (k = 1, 2, 4, 8, 16) the level's blocks fit, and keeps the fastest
+ * (mg_set_line_path).  The passes run on zeroed scratch arrays allocated
+ * here, so no caller data is touched.  The alternating smoothers tune both of
+ * their line smoothers; checkerboard has nothing to tune.  Choices are
+ * remembered for the process by (level shape, line smoother, dtype): levels
+ * of this or any later grid with a remembered shape take the remembered
+ * choice without timing (with reps <= 0, only remembered choices are applied
+ * and nothing is timed).  times_us: NULL or a HOST array of mg_num_levels
+ * doubles, set to the chosen paths' microseconds per colour pass (summed over
+ * the two line smoothers of an alternating smoother; 0 where nothing was
+ * timed).  Synchronises; may allocate; drops the grid's captured graphs.     */
+mg_status mg_autotune(mg_grid *grid, int smoother, int dtype, int reps, double *times_us, void *stream);
 
 #ifdef __cplusplus
 }

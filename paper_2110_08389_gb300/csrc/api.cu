@@ -61,11 +61,15 @@ static void destroy_timer(Grid *g) {
   g->timer_level = -1;
 }
 
+void drop_graphs(Grid &g) {
+  for (auto &ge : g.graphs) cudaGraphExecDestroy(ge.exec);
+  g.graphs.clear();
+}
+
 static void free_grid(Grid *g) {
   if (!g) return;
   destroy_timer(g);
-  for (auto &ge : g->graphs) cudaGraphExecDestroy(ge.exec);
-  g->graphs.clear();
+  drop_graphs(*g);
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
   if (g->ev_join) cudaEventDestroy(g->ev_join);
   if (g->gs) cudaStreamDestroy(g->gs);
@@ -242,7 +246,7 @@ template <> double *level_f<double>(Level &L) { return L.f64; }
 template <> float *level_u<float>(Level &L) { return L.u32; }
 template <> float *level_f<float>(Level &L) { return L.f32; }
 
-static int wl_of(int smoother) {
+int wl_of(int smoother) {
   switch (smoother) {
     case MG_SMOOTH_ZEBRA_X: return WL_ZEBRA_X;
     case MG_SMOOTH_ZEBRA_Y: return WL_ZEBRA_Y;
@@ -265,11 +269,15 @@ static mg_status colour_pass(Grid &g, int l, int smoother, int colour, T *u, con
   if (wl == -1) return MG_ERR_INVALID_ARG;
   const int prec = sizeof(T) == 8 ? 0 : 1;
   if (wl >= 0) TRY(build_worklists(g, l, wl, prec));
-  // path: the warp path where the level's blocks fit it, else the tiled path
-  // (large levels), else the CTA line kernel
-  const bool warp = wl >= 0 && L.wp[wl][prec][colour].nwarp > 0;
+  // path: the one set by mg_set_line_path / mg_autotune, else the warp path
+  // where the level's blocks fit it, else the tiled path (large levels), else
+  // the CTA line kernel
+  const int chosen = wl >= 0 ? L.path[wl][prec] : MG_PATH_AUTO;
   const TileList *tl = wl >= 0 ? &L.tl[wl][colour] : nullptr;
-  const bool tiled = !warp && tl && (tl->ntile > 0 || tl->nblock > 0);
+  const bool has_tiles = tl && (tl->ntile > 0 || tl->nblock > 0);
+  const bool warp = wl >= 0 && L.wp[wl][prec][colour].nwarp > 0 &&
+                    (chosen == MG_PATH_AUTO || chosen == MG_PATH_WARP);
+  const bool tiled = !warp && has_tiles && (chosen == MG_PATH_AUTO || chosen == MG_PATH_TILED);
   cudaEvent_t *ev = timer_slot(g, l);
   if (tiled) {
     TRY_CUDA("tiled line pass", launch_tile_pass<T>(g, L, *tl, u, f, s, ev));
@@ -504,8 +512,6 @@ static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params
 }  // namespace tmg
 
 using namespace tmg;
-
-struct mg_grid : public Grid {};
 
 // A set of grids solved together (mg_batch_solve): up to MAX_BATCH_STREAMS
 // streams of its own, a fork event on the caller's stream and one join

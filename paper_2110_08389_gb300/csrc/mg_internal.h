@@ -218,6 +218,8 @@ struct Level {
   TileList tl[WL_COUNT][2];           // [smoother][colour]: tiled path (empty: use the work lists)
   WorkList wl[WL_COUNT][2][2][2];     // [smoother][precision][colour][small, large]
   WarpList wp[WL_COUNT][2][2];        // [smoother][precision][colour]: warp path (nwarp = 0: unused)
+  int path[WL_COUNT][2] = {};         // [smoother][precision]: MG_PATH_* (0 = the built-in rule)
+  int kpref[WL_COUNT][2] = {};        // nodes per lane asked of the warp path (0 = WK_PREF)
 };
 
 struct Grid {
@@ -270,6 +272,15 @@ inline void count_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std
 
 // ---- host helpers (setup.cu)
 mg_status build_worklists(Grid &g, int level, int wl, int prec);
+// Warp lists of both colours of (level, smoother, precision) with kpref nodes
+// per lane preferred (0 = WK_PREF); out[c].nwarp = 0 where a colour's blocks
+// do not fit.  The caller owns (and frees) out.
+mg_status build_warp_path(Grid &g, int level, int wl, int prec, int kpref, WarpList out[2]);
+void free_warplist(WarpList &w);
+// (api.cu) work-list index of a base line smoother (-1 otherwise); destroy
+// the grid's captured cycle graphs (the caller has synchronised).
+int wl_of(int smoother);
+void drop_graphs(Grid &g);
 const char *set_error(const char *where, cudaError_t e);
 void set_error_text(const char *msg);
 
@@ -321,3 +332,6 @@ template <typename T>
 cudaError_t launch_zero_interior(const Level &L, T *a, cudaStream_t s);
 
 }  // namespace tmg
+
+// The opaque handle of the C ABI.
+struct mg_grid : public tmg::Grid {};

@@ -309,9 +309,10 @@ mg_status upload(const Packed &P, int nt, WorkList &W) {
 
 // Warp path: lay the colour's blocks end to end in sequences of 32*W*K
 // nodes (first fit, largest blocks first; at most one junction per sequence),
-// K and W powers of two chosen as described with WK_PREF.  Leaves W.nwarp = 0
-// when the largest block does not fit WW_MAX warps of kmax nodes per lane.
-mg_status build_warplist(const std::vector<HBlock> &blocks, int kmax, WarpList &W) {
+// K and W powers of two chosen as described with WK_PREF (kpref in its
+// place).  Leaves W.nwarp = 0 when the largest block does not fit WW_MAX
+// warps of kmax nodes per lane.
+mg_status build_warplist(const std::vector<HBlock> &blocks, int kmax, int kpref, WarpList &W) {
   std::vector<int> n(blocks.size(), 0);
   int maxn = 1, total = 0;
   for (size_t b = 0; b < blocks.size(); ++b) {
@@ -322,7 +323,7 @@ mg_status build_warplist(const std::vector<HBlock> &blocks, int kmax, WarpList &
   }
   if (blocks.empty() || maxn > 32 * WW_MAX * kmax) return MG_OK;
   int K = 1, NW = 1;
-  while (32 * K < maxn && K < std::min(WK_PREF, kmax)) K *= 2;
+  while (32 * K < maxn && K < std::min(kpref, kmax)) K *= 2;
   while (32 * NW * K < maxn) NW *= 2;
   while (NW > WW_MAX) {
     K *= 2;
@@ -413,17 +414,38 @@ mg_status build_warplist(const std::vector<HBlock> &blocks, int kmax, WarpList &
 
 }  // namespace
 
+static void blocks_of(const Level &L, int wl, int colour, std::vector<HBlock> &blocks) {
+  switch (wl) {
+    case WL_TWEED: tweed_blocks(L.nx, L.ny, colour, blocks); break;
+    case WL_WIREFRAME: wireframe_blocks(L.nx, L.ny, colour, blocks); break;
+    case WL_ZEBRA_X: zebra_blocks(L.nx, L.ny, colour, true, blocks); break;
+    default: zebra_blocks(L.nx, L.ny, colour, false, blocks); break;
+  }
+}
+
+void free_warplist(WarpList &w) {
+  cudaFree(w.mem);
+  w = WarpList();
+}
+
+mg_status build_warp_path(Grid &g, int level, int wl, int prec, int kpref, WarpList out[2]) {
+  const Level &L = g.lev[level];
+  for (int colour = 0; colour < 2; ++colour) {
+    std::vector<HBlock> blocks;
+    blocks_of(L, wl, colour, blocks);
+    const mg_status st = build_warplist(blocks, prec == 0 ? WK_MAX_F64 : WK_MAX_F32, kpref > 0 ? kpref : WK_PREF,
+                                        out[colour]);
+    if (st != MG_OK) return st;
+  }
+  return MG_OK;
+}
+
 mg_status build_worklists(Grid &g, int level, int wl, int prec) {
   Level &L = g.lev[level];
   if (L.wl_built[wl][prec]) return MG_OK;
   for (int colour = 0; colour < 2; ++colour) {
     std::vector<HBlock> blocks;
-    switch (wl) {
-      case WL_TWEED: tweed_blocks(L.nx, L.ny, colour, blocks); break;
-      case WL_WIREFRAME: wireframe_blocks(L.nx, L.ny, colour, blocks); break;
-      case WL_ZEBRA_X: zebra_blocks(L.nx, L.ny, colour, true, blocks); break;
-      default: zebra_blocks(L.nx, L.ny, colour, false, blocks); break;
-    }
+    blocks_of(L, wl, colour, blocks);
     // blocks of more than a quarter of a small CTA go to large CTAs, so that
     // every CTA holds about four neighbouring blocks; neighbours (same group,
     // consecutive positions) are packed together for the vertical groups
@@ -455,7 +477,7 @@ mg_status build_worklists(Grid &g, int level, int wl, int prec) {
     mg_status st = upload(Ps, NT_SMALL, L.wl[wl][prec][colour][0]);
     if (st == MG_OK) st = upload(Pl, NT_LARGE, L.wl[wl][prec][colour][1]);
     if (st == MG_OK && L.nx < WARP_MAX_SIDE && L.ny < WARP_MAX_SIDE)
-      st = build_warplist(blocks, prec == 0 ? WK_MAX_F64 : WK_MAX_F32, L.wp[wl][prec][colour]);
+      st = build_warplist(blocks, prec == 0 ? WK_MAX_F64 : WK_MAX_F32, WK_PREF, L.wp[wl][prec][colour]);
     if (st != MG_OK) return st;
   }
   L.wl_built[wl][prec] = true;

@@ -435,11 +435,15 @@ cudaError_t launch_warp_pass(const Level &L, const WarpList &w, T *u, const T *f
       case 2: return launch_k<T, 2>(L, w, u, f, s);
       case 4: return launch_k<T, 4>(L, w, u, f, s);
       case 8: return launch_k<T, 8>(L, w, u, f, s);
-      case 16: return launch_k<T, 16>(L, w, u, f, s);
+      case 16:
+        if constexpr (sizeof(T) == 4) return launch_k<T, 16>(L, w, u, f, s);
+        return cudaErrorInvalidValue;
       default: return cudaErrorInvalidValue;
     }
   }
   switch (w.K) {
+    case 1: return launch_multi<T, 1>(L, w, u, f, s);
+    case 2: return launch_multi<T, 2>(L, w, u, f, s);
     case 4: return launch_multi<T, 4>(L, w, u, f, s);
     case 8: return launch_multi<T, 8>(L, w, u, f, s);
     case 16:
@@ -450,9 +454,13 @@ cudaError_t launch_warp_pass(const Level &L, const WarpList &w, T *u, const T *f
 }
 
 cudaError_t prepare_warp_kernels() {
-  cudaError_t e = opt_in_all<float, 4>();
+  cudaError_t e = opt_in_all<float, 1>();
+  if (e == cudaSuccess) e = opt_in_all<float, 2>();
+  if (e == cudaSuccess) e = opt_in_all<float, 4>();
   if (e == cudaSuccess) e = opt_in_all<float, 8>();
   if (e == cudaSuccess) e = opt_in_all<float, 16>();
+  if (e == cudaSuccess) e = opt_in_all<double, 1>();
+  if (e == cudaSuccess) e = opt_in_all<double, 2>();
   if (e == cudaSuccess) e = opt_in_all<double, 4>();
   if (e == cudaSuccess) e = opt_in_all<double, 8>();
   return e;

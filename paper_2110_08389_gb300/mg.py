@@ -26,6 +26,10 @@ SMOOTHERS = {"checkerboard": CHECKERBOARD, "zebra_x": ZEBRA_X, "zebra_y": ZEBRA_
 F64, F32 = 0, 1
 PREC_F64, PREC_F32_REFINE = 0, 1
 HW, FW = 0, 1
+PATH_AUTO, PATH_WARP, PATH_TILED, PATH_CTA = range(4)
+PATHS = {"auto": PATH_AUTO, "warp": PATH_WARP, "tiled": PATH_TILED, "cta": PATH_CTA}
+PATH_NAMES = {v: k for k, v in PATHS.items()}
+DTYPES = {"f64": F64, "f32": F32}
 
 # every symbol include/mg.h declares
 EXPORTS = ["mg_setup_grid", "mg_destroy", "mg_num_levels", "mg_level_shape", "mg_smooth_tweed",
@@ -33,7 +37,7 @@ EXPORTS = ["mg_setup_grid", "mg_destroy", "mg_num_levels", "mg_level_shape", "mg
            "mg_residual", "mg_coarse_solve", "mg_vcycle", "mg_solve", "mg_solve_adjoint",
            "mg_default_params", "mg_status_string", "mg_last_error", "mg_kernel_launches",
            "mg_residual_norm_static", "mg_pass_timer_begin", "mg_pass_timer_end", "mg_boundary_adjoint", "mg_batch_create",
-           "mg_batch_destroy", "mg_batch_solve"]
+           "mg_batch_destroy", "mg_batch_solve", "mg_set_line_path", "mg_get_line_path", "mg_autotune"]
 
 
 class MGError(RuntimeError):
@@ -98,6 +102,9 @@ def load(path: str = LIB_PATH):
                                ctypes.POINTER(Info), ctypes.POINTER(ctypes.c_int), vp]),
         "mg_pass_timer_end": (i, [vp, i64p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                   ctypes.POINTER(ctypes.c_double)]),
+        "mg_set_line_path": (i, [vp, i, i, i, i, i]),
+        "mg_get_line_path": (i, [vp, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
+        "mg_autotune": (i, [vp, i, i, i, ctypes.POINTER(ctypes.c_double), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -228,6 +235,33 @@ class Grid:
         _check(self.lib.mg_colour_pass(self.h, level, sm, colour, _ptr(u), _ptr(f), _dtype_code(u),
                                        _stream(stream)), "mg_colour_pass")
         return u
+
+    # ---- line-solve paths (mg_set_line_path / mg_get_line_path / mg_autotune)
+    def set_line_path(self, level, smoother="tweed", dtype="f32", path="warp", k=0):
+        """Force the line-solve path of one level; raises MGError with status
+        ERR_UNSUPPORTED when the level's blocks do not fit it."""
+        sm = SMOOTHERS[smoother] if isinstance(smoother, str) else smoother
+        dt = DTYPES[dtype] if isinstance(dtype, str) else dtype
+        pa = PATHS[path] if isinstance(path, str) else path
+        _check(self.lib.mg_set_line_path(self.h, level, sm, dt, pa, k), "mg_set_line_path")
+
+    def line_path(self, level, smoother="tweed", dtype="f32"):
+        """(path name, nodes per thread, warps per sequence) of one level."""
+        sm = SMOOTHERS[smoother] if isinstance(smoother, str) else smoother
+        dt = DTYPES[dtype] if isinstance(dtype, str) else dtype
+        p, k, w = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self.lib.mg_get_line_path(self.h, level, sm, dt, ctypes.byref(p), ctypes.byref(k), ctypes.byref(w)),
+               "mg_get_line_path")
+        return PATH_NAMES[p.value], k.value, w.value
+
+    def autotune(self, smoother="tweed", dtype="f32", reps=20, stream=None):
+        """Time every path and warp shape per level, keep the fastest; returns
+        the chosen microseconds per colour pass per level."""
+        sm = SMOOTHERS[smoother] if isinstance(smoother, str) else smoother
+        dt = DTYPES[dtype] if isinstance(dtype, str) else dtype
+        t = (ctypes.c_double * self.nlev)()
+        _check(self.lib.mg_autotune(self.h, sm, dt, reps, t, _stream(stream)), "mg_autotune")
+        return [float(v) for v in t]
 
     def boundary_adjoint(self, lam, grad_u, grad_g, stream=None):
         """grad_g from the adjoint state lam and dloss/du (mg_boundary_adjoint)."""

@@ -256,6 +256,17 @@ def run_batch(args):
     params = [mg.default_params(smoother="wireframe" if kind == "centre" else "tweed", nu1=args.nu[0],
                                 nu2=args.nu[1], precision="f32_refine", tol=TOL, inner_cycles=args.inner,
                                 max_outer=20, max_cycles=200) for (_, _, kind, _) in probs]
+    # line-tile shapes by the autotuner: every path and warp shape of every
+    # level is timed once per (level shape, smoother); later grids with the
+    # same level shapes take the remembered choice
+    t0 = time.perf_counter()
+    for g, (_, _, kind, _) in zip(grids, probs):
+        g.autotune("wireframe" if kind == "centre" else "tweed", "f32", reps=10)
+    tune_s = time.perf_counter() - t0
+    choices = {}
+    for g, (n, _, kind, _) in zip(grids, probs):
+        sm = "wireframe" if kind == "centre" else "tweed"
+        choices.setdefault(f"{n + 1}^2 {sm}", [list(g.line_path(l, sm, "f32")) for l in range(g.nlev - 1)])
     for _ in range(args.warmup):
         res = batch.solve(us, fs, params)
     stream = torch.cuda.current_stream()
@@ -263,11 +274,13 @@ def run_batch(args):
     barrier(pg)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
+        l0 = mg.load().mg_kernel_launches()
         e0.record(stream)
         for _ in range(args.steps):
             res = batch.solve(us, fs, params)
         e1.record(stream)
         torch.cuda.synchronize()
+        launches = (mg.load().mg_kernel_launches() - l0) // args.steps
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, pg, torch.device("cuda", local))
     ok = sum(1 for r in res if r.status == mg.OK and r.rel_res <= TOL)
     ok_kind = {kind: sum(1 for r, p in zip(res, probs) if p[2] == kind and r.status == mg.OK)
@@ -302,11 +315,12 @@ def run_batch(args):
                                    "(centre) V(1,1), FW, to ||r||/||f||<=1e-10", "nodes_total": nodes, "problems": len(probs),
                        "sizes": {str(s + 1): sum(1 for p in probs if p[0] == s) for s in BATCH_SIZES}},
             "converged": ok, "converged_by_clustering": ok_kind,
+            "line_paths": {"autotune_s": tune_s, "chosen": choices},
             "smoothers": "tweed (wall-clustered), wireframe (centre-clustered)",
             "problems_per_s": len(probs) / (ms / 1e3),
             "sequential_s": ms_seq / 1e3, "speedup_vs_sequential": ms_seq / ms,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 8 * nodes, "d2h_bytes_per_step": 8 * nodes},
-            "gpu_launches": None, "clocks": clk.summary()}
+            "gpu_launches": launches, "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(pg)

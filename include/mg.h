@@ -28,7 +28,7 @@
  *     stream).  Only mg_setup_grid, mg_solve, mg_solve_adjoint, mg_batch_solve,
  *     mg_set_line_path and mg_autotune synchronise (the solves read residual
  *     norms back to the host).  No entry point allocates device memory except
- *     mg_setup_grid, mg_set_line_path and mg_autotune.
+ *     mg_setup_grid, mg_batch_create, mg_set_line_path and mg_autotune.
  *   - Errors are returned as mg_status; nothing aborts or traps.  After
  *     MG_ERR_CUDA the message of the failing call is available from
  *     mg_last_error().  Calls on one grid must not run concurrently.
@@ -194,8 +194,10 @@ mg_status mg_solve_adjoint(mg_grid *grid, double *lambda, const double *rhs,
  * time; this serves many problems of different sizes and stretchings at
  * once).  A batch is a set of distinct grids (each problem needs its own
  * grid: grids hold per-solve scratch).  mg_batch_create creates up to 64
- * streams of the batch's own (no device memory); MG_ERR_INVALID_ARG if a grid
- * repeats.  The grids stay owned by the caller and must outlive the batch.  */
+ * streams of the batch's own and the argument tables of its packed groups
+ * (below; device and pinned host memory, about 1.5 KB per problem);
+ * MG_ERR_INVALID_ARG if a grid repeats.  The grids stay owned by the caller
+ * and must outlive the batch.                                                */
 typedef struct mg_batch mg_batch;
 mg_status mg_batch_create(mg_batch **out, int count, mg_grid *const *grids);
 void mg_batch_destroy(mg_batch *batch);
@@ -203,14 +205,19 @@ void mg_batch_destroy(mg_batch *batch);
 /* Solves problem i (u[i], f[i]: FP64 device arrays of grid i, as in
  * mg_solve) for every i, with params[0] for all (nparams = 1) or params[i]
  * for problem i (nparams = count; e.g. tweed for wall-clustered and
- * wireframe for centre-clustered grids, Sec. 6).  The problems run
- * concurrently on the batch's streams; the host waits once per cycle (FP64)
- * or refinement step (FP32) for all of them, and each problem stops at its own
- * tolerance.  Results, infos[i] and status[i] (host arrays of count
- * entries, either may be NULL) are those mg_solve gives for the problem
- * alone.  Starts after the work already on `stream` and makes `stream` wait
- * for its end.  Returns MG_OK if every problem returned MG_OK, else the first
- * non-OK status in problem order.                                            */
+ * wireframe for centre-clustered grids, Sec. 6).  Problems whose grids have
+ * the same shape and whose parameters are equal (MG_PREC_F32_REFINE, every
+ * line pass on the warp path of mg_set_line_path) form packed groups: each
+ * kernel of their solve is one launch for the whole group, and the FP32
+ * cycles of a refinement step are one CUDA graph per group (captured on the
+ * first call and reused while the grids' line paths stay).  Groups and the
+ * other problems run concurrently on the batch's streams; the host waits once
+ * per cycle (FP64) or refinement step (FP32) for all of them, and each problem
+ * stops at its own tolerance.  Results, infos[i] and status[i] (host arrays of
+ * count entries, either may be NULL) are those mg_solve gives for the problem
+ * alone, bit for bit.  Starts after the work already on `stream` and makes
+ * `stream` wait for its end.  Returns MG_OK if every problem returned MG_OK,
+ * else the first non-OK status in problem order.                            */
 mg_status mg_batch_solve(mg_batch *batch, double *const *u, const double *const *f, const mg_params *params,
                          int nparams, mg_info *infos, int *status, void *stream);
 

@@ -8,7 +8,7 @@
 #include <cstring>
 #include <new>
 
-#include "mg_internal.h"
+#include "solve.h"
 
 namespace tmg {
 
@@ -22,21 +22,11 @@ const char *set_error(const char *where, cudaError_t e) {
 
 void set_error_text(const char *msg) { std::snprintf(g_err, sizeof(g_err), "%s", msg); }
 
-static mg_status cuda_status(const char *where, cudaError_t e) {
+mg_status cuda_status(const char *where, cudaError_t e) {
   if (e == cudaSuccess) return MG_OK;
   set_error(where, e);
   return e == cudaErrorMemoryAllocation ? MG_ERR_ALLOC : MG_ERR_CUDA;
 }
-#define TRY_CUDA(where, expr)                                  \
-  do {                                                         \
-    mg_status _st = cuda_status(where, (expr));                \
-    if (_st != MG_OK) return _st;                              \
-  } while (0)
-#define TRY(expr)                \
-  do {                           \
-    mg_status _st = (expr);      \
-    if (_st != MG_OK) return _st; \
-  } while (0)
 
 // Sec. 2 coefficients on one axis: lo_i = 1/(dx_i dx_{i-1/2}),
 // hi_i = 1/(dx_i dx_{i+1/2}), dx_i = (x_{i+1} - x_{i-1})/2; 0 at the ends.
@@ -386,7 +376,7 @@ static mg_status run_cycles(Grid &g, const mg_params &p, int ncyc, T *u, const T
   return MG_OK;
 }
 
-static mg_status check_params(const Grid *g, const mg_params *p) {
+mg_status check_params(const Grid *g, const mg_params *p) {
   if (!p) return MG_ERR_INVALID_ARG;
   if (p->smoother < 0 || p->smoother > MG_SMOOTH_ALT_TW) return MG_ERR_INVALID_ARG;
   if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 > 64) return MG_ERR_INVALID_ARG;
@@ -406,32 +396,12 @@ static void record(mg_info *info, int k, double rel) {
   }
 }
 
-// One solve (Sec. 4: cycles until the relative residual is below tol) as a
-// resumable state machine: enqueue() puts the device work up to the next norm
-// read on the stream (ending with the copy of the norm to pinned host memory),
-// consume() reads that norm once the stream has drained and decides the next
-// step.  solve_impl alternates the two; mg_batch_solve interleaves many
-// problems with one host synchronisation per step for all of them.
-struct SolveState {
-  Grid *g;
-  double *u;
-  const double *f;
-  mg_params p;
-  mg_info *info;
-  cudaStream_t s;
-  int phase = 0;  // 0: scale norm, 1: initial residual, 2: iterating
-  bool done = false;
-  mg_status st = MG_OK;
-  double fn = 0.0, rel = 0.0, rel0 = 0.0;
-  int cycles = 0, outer = 0;
-};
-
 static mg_status copy_norm(Grid &g, cudaStream_t s) {
   TRY_CUDA("cudaMemcpyAsync(norms)", cudaMemcpyAsync(g.hpinned, g.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
   return MG_OK;
 }
 
-static mg_status enqueue(SolveState &q) {
+mg_status enqueue(SolveState &q) {
   Grid &g = *q.g;
   const mg_params &p = q.p;
   const bool f64 = p.precision == MG_PREC_F64;
@@ -467,8 +437,9 @@ static void finish(SolveState &q) {
   q.info->conv_factor = (n > 0 && q.rel0 > 0 && q.rel > 0) ? std::pow(q.rel / q.rel0, 1.0 / n) : 0.0;
 }
 
-static void consume(SolveState &q) {
-  const double v = q.g->hpinned[0];
+void consume(SolveState &q) { consume_value(q, q.g->hpinned[0]); }
+
+void consume_value(SolveState &q, double v) {
   const mg_params &p = q.p;
   const bool f64 = p.precision == MG_PREC_F64;
   if (q.phase == 0) {
@@ -512,25 +483,6 @@ static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params
 }  // namespace tmg
 
 using namespace tmg;
-
-// A set of grids solved together (mg_batch_solve): up to MAX_BATCH_STREAMS
-// streams of its own, a fork event on the caller's stream and one join
-// event per stream.
-constexpr int MAX_BATCH_STREAMS = 64;
-struct mg_batch {
-  std::vector<Grid *> grids;
-  std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> joins;
-  cudaEvent_t fork = nullptr;
-};
-
-static void free_batch(mg_batch *b) {
-  if (!b) return;
-  for (auto e : b->joins) cudaEventDestroy(e);
-  for (auto s : b->streams) cudaStreamDestroy(s);
-  if (b->fork) cudaEventDestroy(b->fork);
-  delete b;
-}
 
 extern "C" {
 
@@ -719,86 +671,6 @@ mg_status mg_solve_adjoint(mg_grid *g, double *lambda, const double *rhs, const 
   if (e != cudaSuccess) return cuda_status("adjoint scaling", e);
   if (info) info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return st;
-}
-
-mg_status mg_batch_create(mg_batch **out, int count, mg_grid *const *grids) {
-  if (!out || count < 1 || !grids) return MG_ERR_INVALID_ARG;
-  *out = nullptr;
-  std::vector<Grid *> gs(count);
-  for (int i = 0; i < count; ++i) {
-    if (!grids[i]) return MG_ERR_INVALID_ARG;
-    gs[i] = grids[i];
-  }
-  std::vector<Grid *> sorted(gs);
-  std::sort(sorted.begin(), sorted.end());
-  if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
-    set_error_text("mg_batch_create: a grid appears twice (each problem needs its own grid)");
-    return MG_ERR_INVALID_ARG;
-  }
-  mg_batch *b = new (std::nothrow) mg_batch;
-  if (!b) return MG_ERR_ALLOC;
-  b->grids = gs;
-  const int k = std::min(count, MAX_BATCH_STREAMS);
-  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
-  for (int i = 0; i < k && e == cudaSuccess; ++i) {
-    cudaStream_t s = nullptr;
-    cudaEvent_t ev = nullptr;
-    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    if (e == cudaSuccess) b->streams.push_back(s);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) b->joins.push_back(ev);
-  }
-  if (e != cudaSuccess) {
-    free_batch(b);
-    return cuda_status("mg_batch_create", e);
-  }
-  *out = b;
-  return MG_OK;
-}
-
-void mg_batch_destroy(mg_batch *b) { free_batch(b); }
-
-mg_status mg_batch_solve(mg_batch *b, double *const *u, const double *const *f, const mg_params *params,
-                         int nparams, mg_info *infos, int *status, void *stream) {
-  if (!b || !u || !f || !params) return MG_ERR_INVALID_ARG;
-  const int n = (int)b->grids.size(), k = (int)b->streams.size();
-  if (nparams != 1 && nparams != n) return MG_ERR_INVALID_ARG;
-  std::vector<SolveState> q(n);
-  for (int i = 0; i < n; ++i) {
-    if (!u[i] || !f[i]) return MG_ERR_INVALID_ARG;
-    const mg_params *p = params + (nparams == 1 ? 0 : i);
-    mg_status st = check_params(b->grids[i], p);
-    if (st != MG_OK) return st;
-    q[i].g = b->grids[i]; q[i].u = u[i]; q[i].f = f[i]; q[i].p = *p;
-    q[i].info = infos ? infos + i : nullptr;
-    q[i].s = b->streams[i % k];
-  }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // the batch's streams start after the caller's stream
-  TRY_CUDA("cudaEventRecord(batch fork)", cudaEventRecord(b->fork, s));
-  for (auto bs : b->streams) TRY_CUDA("cudaStreamWaitEvent(batch fork)", cudaStreamWaitEvent(bs, b->fork, 0));
-  mg_status worst = MG_OK;
-  int active = n;
-  while (active > 0) {
-    for (auto &x : q)
-      if (!x.done) TRY(enqueue(x));
-    for (auto bs : b->streams) TRY_CUDA("cudaStreamSynchronize(batch)", cudaStreamSynchronize(bs));
-    active = 0;
-    for (auto &x : q)
-      if (!x.done) {
-        consume(x);
-        if (x.done && x.st != MG_OK && worst == MG_OK) worst = x.st;
-        active += x.done ? 0 : 1;
-      }
-  }
-  if (status)
-    for (int i = 0; i < n; ++i) status[i] = (int)q[i].st;
-  // the caller's stream continues after the batch's streams
-  for (int i = 0; i < k; ++i) {
-    TRY_CUDA("cudaEventRecord(batch join)", cudaEventRecord(b->joins[i], b->streams[i]));
-    TRY_CUDA("cudaStreamWaitEvent(batch join)", cudaStreamWaitEvent(s, b->joins[i], 0));
-  }
-  return worst;
 }
 
 mg_status mg_boundary_adjoint(mg_grid *g, const double *lambda, const double *grad_u, double *grad_g,

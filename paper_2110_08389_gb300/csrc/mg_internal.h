@@ -258,6 +258,7 @@ struct Grid {
   std::vector<GraphEntry> graphs;
   cudaStream_t gs = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  unsigned long long gen = 0;        // bumped whenever a level's line path or warp lists change
 };
 
 // Levels whose sides are both at least this get tiled lists for tweed and

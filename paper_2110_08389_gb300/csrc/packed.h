@@ -1,0 +1,70 @@
+// packed.h -- per-problem kernel arguments for packed launches.  A packed
+// launch serves a group of problems whose grids have the same shape (so the
+// same blocks and work lists on every level): blockIdx.y or blockIdx.z (the
+// launcher says which) selects problem q, whose arguments are tab[q]; a
+// problem whose active[q] is 0 does nothing.  The arithmetic of each problem
+// is exactly that of its unpacked launch.
+#pragma once
+#include "device_util.cuh"
+
+namespace tmg {
+
+template <typename T>
+struct PassArgs {  // colour pass
+  Coefs<T> c;
+  T *u;
+  const T *f;
+};
+template <typename T>
+struct RRArgs {  // defect + restriction, fine level -> next level
+  Coefs<T> c;
+  const T *u, *f;
+  T *fc, *uc;
+};
+template <typename T>
+struct ProlongArgs {  // prolongation + correction
+  const T *uc;
+  T *u;
+};
+template <typename T>
+struct CoarseArgs {  // direct solve of the coarsest level
+  Coefs<double> c;
+  const double *inv;
+  T *u;
+  const T *f;
+};
+struct NormArgs {  // FP64 norms (and refinement residual) of the finest level
+  Coefs<double> c;
+  const double *u, *f;
+  float *r32, *e32;
+  double *part, *out;
+};
+struct UpdateArgs {  // u64 += e32, or u64 interior := 0
+  double *u;
+  const float *e;
+};
+
+// Host view of one packed launch: device tables, device active flags and the
+// number of problems.
+struct PackedLaunch {
+  const void *tab;
+  const int *active;
+  int count;
+};
+
+// Packed launchers (the kernels' own translation units).
+template <typename T>
+cudaError_t launch_warp_pass_packed(const Level &L, const WarpList &w, const PackedLaunch &pk, cudaStream_t s);
+template <typename T>
+cudaError_t launch_residual_restrict_packed(const Level &F, const Level &C, int kind, const PackedLaunch &pk,
+                                            cudaStream_t s);
+template <typename T>
+cudaError_t launch_prolong_add_packed(const Level &F, const Level &C, const PackedLaunch &pk, cudaStream_t s);
+template <typename T>
+cudaError_t launch_coarse_solve_packed(const Grid &g, const PackedLaunch &pk, cudaStream_t s);
+// norms: bnd_only as launch_rhsnorm64; with_r32: the refinement residual
+cudaError_t launch_norms_packed(const Grid &g, int bnd_only, int with_r32, const PackedLaunch &pk, cudaStream_t s);
+cudaError_t launch_ir_update_packed(const Grid &g, const PackedLaunch &pk, cudaStream_t s);
+cudaError_t launch_zero_interior_packed(const Grid &g, const PackedLaunch &pk, cudaStream_t s);
+
+}  // namespace tmg

@@ -1,0 +1,49 @@
+// solve.h -- the solve state machine shared by mg_solve (api.cu) and
+// mg_batch_solve (batch.cu).
+#pragma once
+#include "mg_internal.h"
+
+namespace tmg {
+
+// One solve (Sec. 4: cycles until the relative residual is below tol) as a
+// resumable state machine: enqueue() puts the device work up to the next norm
+// read on the stream (ending with the copy of the norm to pinned host memory),
+// consume() reads that norm once the stream has drained and decides the next
+// step.  A solve alternates the two; a batch interleaves many problems with
+// one host synchronisation per step for all of them.
+struct SolveState {
+  Grid *g;
+  double *u;
+  const double *f;
+  mg_params p;
+  mg_info *info;
+  cudaStream_t s;
+  int phase = 0;  // 0: scale norm, 1: initial residual, 2: iterating
+  bool done = false;
+  mg_status st = MG_OK;
+  double fn = 0.0, rel = 0.0, rel0 = 0.0;
+  int cycles = 0, outer = 0;
+};
+
+mg_status check_params(const Grid *g, const mg_params *p);
+mg_status enqueue(SolveState &q);
+// the norm the step computed: its grid's pinned copy (consume) or any value
+// read back otherwise (consume_value)
+void consume(SolveState &q);
+void consume_value(SolveState &q, double v);
+mg_status cuda_status(const char *where, cudaError_t e);
+
+}  // namespace tmg
+
+// Return early with the status of a failed call (TRY_CUDA: a CUDA runtime
+// call, reported through mg_last_error).
+#define TRY_CUDA(where, expr)                       \
+  do {                                              \
+    mg_status _st = tmg::cuda_status(where, (expr)); \
+    if (_st != MG_OK) return _st;                   \
+  } while (0)
+#define TRY(expr)                 \
+  do {                            \
+    mg_status _st = (expr);       \
+    if (_st != MG_OK) return _st; \
+  } while (0)

@@ -16,20 +16,16 @@
 //   ir_update                u64 += e32
 #include <algorithm>
 
-#include "device_util.cuh"
+#include "packed.h"
 
 namespace tmg {
 
 template <typename T>
-struct CoefQ {
-  const T *W, *E, *S, *N;
-};
+using CoefQ = Coefs<T>;
 template <typename T>
-static CoefQ<T> cq(const Level &L);
-template <>
-CoefQ<double> cq<double>(const Level &L) { return {L.W64, L.E64, L.S64, L.N64}; }
-template <>
-CoefQ<float> cq<float>(const Level &L) { return {L.W32, L.E32, L.S32, L.N32}; }
+static CoefQ<T> cq(const Level &L) {
+  return level_coefs<T>(L);
+}
 
 // Defect at interior node (i, j): f - (W u_w + E u_e + S u_s + N u_n + C u).
 template <typename T>
@@ -77,8 +73,15 @@ __global__ void __launch_bounds__(RR_THREADS) residual_restrict_kernel(CoefQ<T> 
                                                                        int nyc, int kind,
                                                                        const T *__restrict__ u,
                                                                        const T *__restrict__ f,
-                                                                       T *__restrict__ fc, T *__restrict__ uc) {
+                                                                       T *__restrict__ fc, T *__restrict__ uc,
+                                                                       const RRArgs<T> *__restrict__ tab,
+                                                                       const int *__restrict__ active) {
   __shared__ T dd[RR_FJ][RR_FI + 1];
+  if (tab) {  // packed launch: blockIdx.z selects the problem
+    if (!active[blockIdx.z]) return;
+    const RRArgs<T> a = tab[blockIdx.z];
+    c = a.c; u = a.u; f = a.f; fc = a.fc; uc = a.uc;
+  }
   pdl_trigger();
   pdl_wait();
   const int I0 = 1 + blockIdx.x * RR_I, J0 = 1 + blockIdx.y * RR_J;
@@ -140,8 +143,22 @@ cudaError_t launch_residual_restrict(const Level &F, const Level &C, int kind, c
   dim3 g((C.nx - 1 + RR_I - 1) / RR_I, (C.ny - 1 + RR_J - 1) / RR_J);
   count_launch(1);
   return launch_pdl(residual_restrict_kernel<T>, g, dim3(RR_THREADS), 0, s, cq<T>(F), F.nx, F.ny, C.nx, C.ny, kind,
-                    u, f, fc, uc);
+                    u, f, fc, uc, (const RRArgs<T> *)nullptr, (const int *)nullptr);
 }
+template <typename T>
+cudaError_t launch_residual_restrict_packed(const Level &F, const Level &C, int kind, const PackedLaunch &pk,
+                                            cudaStream_t s) {
+  if (C.nx < 2 || C.ny < 2 || pk.count == 0) return cudaSuccess;
+  dim3 g((C.nx - 1 + RR_I - 1) / RR_I, (C.ny - 1 + RR_J - 1) / RR_J, pk.count);
+  count_launch(1);
+  return launch_pdl(residual_restrict_kernel<T>, g, dim3(RR_THREADS), 0, s, cq<T>(F), F.nx, F.ny, C.nx, C.ny, kind,
+                    (const T *)nullptr, (const T *)nullptr, (T *)nullptr, (T *)nullptr,
+                    static_cast<const RRArgs<T> *>(pk.tab), pk.active);
+}
+template cudaError_t launch_residual_restrict_packed<float>(const Level &, const Level &, int, const PackedLaunch &,
+                                                            cudaStream_t);
+template cudaError_t launch_residual_restrict_packed<double>(const Level &, const Level &, int, const PackedLaunch &,
+                                                             cudaStream_t);
 template cudaError_t launch_residual_restrict<double>(const Level &, const Level &, int, const double *,
                                                       const double *, double *, double *, cudaStream_t);
 template cudaError_t launch_residual_restrict<float>(const Level &, const Level &, int, const float *,
@@ -156,7 +173,14 @@ constexpr int PR_THREADS = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(PR_THREADS) prolong_add_kernel(int nx, int ny, int nxc, const T *__restrict__ uc,
-                                                                 T *__restrict__ u) {
+                                                                 T *__restrict__ u,
+                                                                 const ProlongArgs<T> *__restrict__ tab,
+                                                                 const int *__restrict__ active) {
+  if (tab) {  // packed launch: blockIdx.z selects the problem
+    if (!active[blockIdx.z]) return;
+    const ProlongArgs<T> a = tab[blockIdx.z];
+    uc = a.uc; u = a.u;
+  }
   pdl_trigger();
   pdl_wait();
   const int j = blockIdx.y + 1;
@@ -185,8 +209,22 @@ cudaError_t launch_prolong_add(const Level &F, const Level &C, const T *uc, T *u
   const int bx = std::min((C.nx + PR_THREADS - 1) / PR_THREADS, 8);
   dim3 g(bx, F.ny - 1);
   count_launch(1);
-  return launch_pdl(prolong_add_kernel<T>, g, dim3(PR_THREADS), 0, s, F.nx, F.ny, C.nx, uc, u);
+  return launch_pdl(prolong_add_kernel<T>, g, dim3(PR_THREADS), 0, s, F.nx, F.ny, C.nx, uc, u,
+                    (const ProlongArgs<T> *)nullptr, (const int *)nullptr);
 }
+template <typename T>
+cudaError_t launch_prolong_add_packed(const Level &F, const Level &C, const PackedLaunch &pk, cudaStream_t s) {
+  if (pk.count == 0) return cudaSuccess;
+  const int bx = std::min((C.nx + PR_THREADS - 1) / PR_THREADS, 8);
+  dim3 g(bx, F.ny - 1, pk.count);
+  count_launch(1);
+  return launch_pdl(prolong_add_kernel<T>, g, dim3(PR_THREADS), 0, s, F.nx, F.ny, C.nx, (const T *)nullptr,
+                    (T *)nullptr, static_cast<const ProlongArgs<T> *>(pk.tab), pk.active);
+}
+template cudaError_t launch_prolong_add_packed<float>(const Level &, const Level &, const PackedLaunch &,
+                                                      cudaStream_t);
+template cudaError_t launch_prolong_add_packed<double>(const Level &, const Level &, const PackedLaunch &,
+                                                       cudaStream_t);
 template cudaError_t launch_prolong_add<double>(const Level &, const Level &, const double *, double *,
                                                 cudaStream_t);
 template cudaError_t launch_prolong_add<float>(const Level &, const Level &, const float *, float *,
@@ -200,8 +238,15 @@ constexpr int CS_THREADS = 1024;
 template <typename T>
 __global__ void __launch_bounds__(CS_THREADS) coarse_solve_kernel(CoefQ<double> c, int nx, int ny,
                                                                   const double *__restrict__ inv,
-                                                                  T *__restrict__ u, const T *__restrict__ f) {
+                                                                  T *__restrict__ u, const T *__restrict__ f,
+                                                                  const CoarseArgs<T> *__restrict__ tab,
+                                                                  const int *__restrict__ active) {
   extern __shared__ double cb[];
+  if (tab) {  // packed launch: blockIdx.x selects the problem
+    if (!active[blockIdx.x]) return;
+    const CoarseArgs<T> a = tab[blockIdx.x];
+    c = a.c; inv = a.inv; u = a.u; f = a.f;
+  }
   pdl_trigger();
   pdl_wait();
   const int n = (nx - 1) * (ny - 1), nx1 = nx + 1;
@@ -235,8 +280,19 @@ cudaError_t launch_coarse_solve(const Grid &g, T *u, const T *f, cudaStream_t s)
   if (g.cn <= 0) return cudaSuccess;
   count_launch(1);
   return launch_pdl(coarse_solve_kernel<T>, dim3(1), dim3(CS_THREADS), sizeof(double) * g.cn, s, cq<double>(L), L.nx,
-                    L.ny, (const double *)g.cinv, u, f);
+                    L.ny, (const double *)g.cinv, u, f, (const CoarseArgs<T> *)nullptr, (const int *)nullptr);
 }
+template <typename T>
+cudaError_t launch_coarse_solve_packed(const Grid &g, const PackedLaunch &pk, cudaStream_t s) {
+  const Level &L = g.lev[g.nlev - 1];
+  if (g.cn <= 0 || pk.count == 0) return cudaSuccess;
+  count_launch(1);
+  return launch_pdl(coarse_solve_kernel<T>, dim3(pk.count), dim3(CS_THREADS), sizeof(double) * g.cn, s,
+                    cq<double>(L), L.nx, L.ny, (const double *)nullptr, (T *)nullptr, (const T *)nullptr,
+                    static_cast<const CoarseArgs<T> *>(pk.tab), pk.active);
+}
+template cudaError_t launch_coarse_solve_packed<float>(const Grid &, const PackedLaunch &, cudaStream_t);
+template cudaError_t launch_coarse_solve_packed<double>(const Grid &, const PackedLaunch &, cudaStream_t);
 template cudaError_t launch_coarse_solve<double>(const Grid &, double *, const double *, cudaStream_t);
 template cudaError_t launch_coarse_solve<float>(const Grid &, float *, const float *, cudaStream_t);
 
@@ -269,7 +325,15 @@ __global__ void __launch_bounds__(NORM_THREADS) norm_stage1(CoefQ<double> c, int
                                                             const double *__restrict__ u,
                                                             const double *__restrict__ f, int bnd_only,
                                                             float *__restrict__ r32, float *__restrict__ e32,
-                                                            double *__restrict__ part) {
+                                                            double *__restrict__ part,
+                                                            const NormArgs *__restrict__ tab,
+                                                            const int *__restrict__ active) {
+  if (tab) {  // packed launch: blockIdx.y selects the problem
+    if (!active[blockIdx.y]) return;
+    const NormArgs a = tab[blockIdx.y];
+    c = a.c; u = a.u; f = a.f; part = a.part;
+    if (r32) { r32 = a.r32; e32 = a.e32; }
+  }
   const int nx1 = nx + 1;
   double s = 0.0;
   for (int j = 1 + blockIdx.x; j < ny; j += gridDim.x) {
@@ -298,7 +362,14 @@ __global__ void __launch_bounds__(NORM_THREADS) norm_stage1(CoefQ<double> c, int
 }
 
 __global__ void __launch_bounds__(NORM_THREADS) norm_stage2(const double *__restrict__ part, int npart,
-                                                            double *__restrict__ out) {
+                                                            double *__restrict__ out,
+                                                            const NormArgs *__restrict__ tab,
+                                                            const int *__restrict__ active) {
+  if (tab) {  // packed launch: blockIdx.x selects the problem
+    if (!active[blockIdx.x]) return;
+    part = tab[blockIdx.x].part;
+    out = tab[blockIdx.x].out;
+  }
   double s = 0.0;
   for (int k = threadIdx.x; k < npart; k += NORM_THREADS) s += part[k];
   s = block_sum(s);
@@ -308,8 +379,23 @@ __global__ void __launch_bounds__(NORM_THREADS) norm_stage2(const double *__rest
 static cudaError_t norms(const Grid &g, const double *u, const double *f, int bnd_only, float *r32, float *e32,
                          cudaStream_t s) {
   const Level &L = g.lev[0];
-  norm_stage1<<<g.npartial, NORM_THREADS, 0, s>>>(cq<double>(L), L.nx, L.ny, u, f, bnd_only, r32, e32, g.partial);
-  norm_stage2<<<1, NORM_THREADS, 0, s>>>(g.partial, g.npartial, g.scal);
+  norm_stage1<<<g.npartial, NORM_THREADS, 0, s>>>(cq<double>(L), L.nx, L.ny, u, f, bnd_only, r32, e32, g.partial,
+                                                  nullptr, nullptr);
+  norm_stage2<<<1, NORM_THREADS, 0, s>>>(g.partial, g.npartial, g.scal, nullptr, nullptr);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+// Packed: with_r32 selects the refinement residual (r32 and e32 from each
+// problem's arguments; a non-null placeholder tells the kernel to write them).
+cudaError_t launch_norms_packed(const Grid &g, int bnd_only, int with_r32, const PackedLaunch &pk, cudaStream_t s) {
+  if (pk.count == 0) return cudaSuccess;
+  const Level &L = g.lev[0];
+  const NormArgs *tab = static_cast<const NormArgs *>(pk.tab);
+  float *mark = with_r32 ? reinterpret_cast<float *>(g.r32) : nullptr;
+  norm_stage1<<<dim3(g.npartial, pk.count), NORM_THREADS, 0, s>>>(cq<double>(L), L.nx, L.ny, nullptr, nullptr,
+                                                                  bnd_only, mark, mark, nullptr, tab, pk.active);
+  norm_stage2<<<pk.count, NORM_THREADS, 0, s>>>(nullptr, g.npartial, nullptr, tab, pk.active);
   count_launch(2);
   return cudaGetLastError();
 }
@@ -331,14 +417,31 @@ constexpr int EW_THREADS = 256;
 static dim3 row_grid(const Level &L) { return dim3(std::min((L.nx - 1 + EW_THREADS - 1) / EW_THREADS, 4), L.ny - 1); }
 
 __global__ void __launch_bounds__(EW_THREADS) ir_update_kernel(int nx, double *__restrict__ u,
-                                                               const float *__restrict__ e) {
+                                                               const float *__restrict__ e,
+                                                               const UpdateArgs *__restrict__ tab,
+                                                               const int *__restrict__ active) {
+  if (tab) {  // packed launch: blockIdx.z selects the problem
+    if (!active[blockIdx.z]) return;
+    u = tab[blockIdx.z].u;
+    e = tab[blockIdx.z].e;
+  }
   const size_t row = (size_t)(blockIdx.y + 1) * (nx + 1);
   for (int i = 1 + blockIdx.x * EW_THREADS + threadIdx.x; i < nx; i += gridDim.x * EW_THREADS)
     u[row + i] += (double)e[row + i];
 }
 cudaError_t launch_ir_update(const Grid &g, double *u, const float *e, cudaStream_t s) {
   const Level &L = g.lev[0];
-  ir_update_kernel<<<row_grid(L), EW_THREADS, 0, s>>>(L.nx, u, e);
+  ir_update_kernel<<<row_grid(L), EW_THREADS, 0, s>>>(L.nx, u, e, nullptr, nullptr);
+  count_launch(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_ir_update_packed(const Grid &g, const PackedLaunch &pk, cudaStream_t s) {
+  if (pk.count == 0) return cudaSuccess;
+  const Level &L = g.lev[0];
+  dim3 gr = row_grid(L);
+  gr.z = pk.count;
+  ir_update_kernel<<<gr, EW_THREADS, 0, s>>>(L.nx, nullptr, nullptr, static_cast<const UpdateArgs *>(pk.tab),
+                                             pk.active);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -363,13 +466,31 @@ cudaError_t launch_diag_scale(const Grid &g, double *out, const double *in, int 
 }
 
 template <typename T>
-__global__ void __launch_bounds__(EW_THREADS) zero_interior_kernel(int nx, T *__restrict__ a) {
+__global__ void __launch_bounds__(EW_THREADS) zero_interior_kernel(int nx, T *__restrict__ a,
+                                                                   const UpdateArgs *__restrict__ tab,
+                                                                   const int *__restrict__ active) {
+  if constexpr (sizeof(T) == 8) {
+    if (tab) {  // packed launch: blockIdx.z selects the problem; zeroes its u
+      if (!active[blockIdx.z]) return;
+      a = tab[blockIdx.z].u;
+    }
+  }
   const size_t row = (size_t)(blockIdx.y + 1) * (nx + 1);
   for (int i = 1 + blockIdx.x * EW_THREADS + threadIdx.x; i < nx; i += gridDim.x * EW_THREADS) a[row + i] = T(0);
 }
 template <typename T>
 cudaError_t launch_zero_interior(const Level &L, T *a, cudaStream_t s) {
-  zero_interior_kernel<T><<<row_grid(L), EW_THREADS, 0, s>>>(L.nx, a);
+  zero_interior_kernel<T><<<row_grid(L), EW_THREADS, 0, s>>>(L.nx, a, nullptr, nullptr);
+  count_launch(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_zero_interior_packed(const Grid &g, const PackedLaunch &pk, cudaStream_t s) {
+  if (pk.count == 0) return cudaSuccess;
+  const Level &L = g.lev[0];
+  dim3 gr = row_grid(L);
+  gr.z = pk.count;
+  zero_interior_kernel<double><<<gr, EW_THREADS, 0, s>>>(L.nx, nullptr, static_cast<const UpdateArgs *>(pk.tab),
+                                                         pk.active);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -402,7 +523,7 @@ cudaError_t launch_boundary_adjoint(const Grid &g, const double *lam, const doub
                                     cudaStream_t s) {
   const Level &L = g.lev[0];
   const int nb = 2 * (L.nx + 1) + 2 * (L.ny - 1);
-  zero_interior_kernel<double><<<row_grid(L), EW_THREADS, 0, s>>>(L.nx, gg);
+  zero_interior_kernel<double><<<row_grid(L), EW_THREADS, 0, s>>>(L.nx, gg, nullptr, nullptr);
   boundary_adjoint_kernel<<<(nb + 255) / 256, 256, 0, s>>>(L.W64, L.E64, L.S64, L.N64, L.nx, L.ny, lam, gu, gg);
   count_launch(2);
   return cudaGetLastError();

@@ -60,6 +60,7 @@ mg_status set_path(Grid &g, int level, int wl, int prec, int path, int k) {
   }
   L.path[wl][prec] = path;
   L.kpref[wl][prec] = path == MG_PATH_WARP ? (k > 0 ? k : WK_PREF) : 0;
+  ++g.gen;
   drop_graphs(g);
   return MG_OK;
 }

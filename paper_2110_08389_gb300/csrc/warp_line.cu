@@ -27,7 +27,7 @@
 //      x_s = X_s + x_J X'_s.
 //   5. the junction row fixes x_J (lanes 0..3 hold its attached nodes),
 //      then x_s is written back coalesced.
-#include "device_util.cuh"
+#include "packed.h"
 
 namespace tmg {
 namespace {
@@ -215,7 +215,16 @@ struct Junction {
 template <typename T, int K>
 __global__ void __launch_bounds__(32) warp_line_kernel(const WNode *__restrict__ nodes,
                                                        const WBlock *__restrict__ blks, Coefs<T> cp, int nx1,
-                                                       T *__restrict__ u, const T *__restrict__ f) {
+                                                       T *__restrict__ u, const T *__restrict__ f,
+                                                       const PassArgs<T> *__restrict__ tab,
+                                                       const int *__restrict__ active) {
+  if (tab) {  // packed launch: blockIdx.y selects the problem
+    if (!active[blockIdx.y]) return;
+    const PassArgs<T> a = tab[blockIdx.y];
+    cp = a.c;
+    u = a.u;
+    f = a.f;
+  }
   constexpr int N = 32 * K;
   extern __shared__ __align__(16) unsigned char wsm[];
   T *sa = reinterpret_cast<T *>(wsm);
@@ -299,7 +308,16 @@ __global__ void __launch_bounds__(32) warp_line_kernel(const WNode *__restrict__
 template <typename T, int K, int W>
 __global__ void __launch_bounds__(32 * W) seq_line_kernel(const WNode *__restrict__ nodes,
                                                           const WBlock *__restrict__ blks, Coefs<T> cp, int nx1,
-                                                          T *__restrict__ u, const T *__restrict__ f) {
+                                                          T *__restrict__ u, const T *__restrict__ f,
+                                                          const PassArgs<T> *__restrict__ tab,
+                                                          const int *__restrict__ active) {
+  if (tab) {  // packed launch: blockIdx.y selects the problem
+    if (!active[blockIdx.y]) return;
+    const PassArgs<T> a = tab[blockIdx.y];
+    cp = a.c;
+    u = a.u;
+    f = a.f;
+  }
   constexpr int NT = 32 * W, N = NT * K;
   extern __shared__ __align__(16) unsigned char wsm[];
   T *sa = reinterpret_cast<T *>(wsm);
@@ -386,27 +404,38 @@ constexpr size_t seq_smem() {
   return (size_t)32 * W * K * (5 * sizeof(T) + sizeof(int)) + sizeof(T) * (12 * 32 * W + 2);
 }
 
+// One launch: the problem (u, f) alone, or (pk.tab != nullptr) the pk.count
+// problems of a packed group on grid rows.
+template <typename T>
+struct WarpLaunch {
+  T *u;
+  const T *f;
+  PackedLaunch pk;
+};
+
 template <typename T, int K>
-cudaError_t launch_k(const Level &L, const WarpList &w, T *u, const T *f, cudaStream_t s) {
+cudaError_t launch_k(const Level &L, const WarpList &w, const WarpLaunch<T> &a, cudaStream_t s) {
   const size_t smem = (size_t)32 * K * (5 * sizeof(T) + sizeof(int));
   count_launch(1);
-  return launch_pdl(warp_line_kernel<T, K>, dim3(w.nwarp), dim3(32), smem, s, (const WNode *)w.node,
-                    (const WBlock *)w.blk, level_coefs<T>(L), L.nx + 1, u, f);
+  return launch_pdl(warp_line_kernel<T, K>, dim3(w.nwarp, a.pk.count), dim3(32), smem, s, (const WNode *)w.node,
+                    (const WBlock *)w.blk, level_coefs<T>(L), L.nx + 1, a.u, a.f,
+                    static_cast<const PassArgs<T> *>(a.pk.tab), a.pk.active);
 }
 
 template <typename T, int K, int W>
-cudaError_t launch_kw(const Level &L, const WarpList &w, T *u, const T *f, cudaStream_t s) {
+cudaError_t launch_kw(const Level &L, const WarpList &w, const WarpLaunch<T> &a, cudaStream_t s) {
   count_launch(1);
-  return launch_pdl(seq_line_kernel<T, K, W>, dim3(w.nwarp), dim3(32 * W), seq_smem<T, K, W>(), s,
-                    (const WNode *)w.node, (const WBlock *)w.blk, level_coefs<T>(L), L.nx + 1, u, f);
+  return launch_pdl(seq_line_kernel<T, K, W>, dim3(w.nwarp, a.pk.count), dim3(32 * W), seq_smem<T, K, W>(), s,
+                    (const WNode *)w.node, (const WBlock *)w.blk, level_coefs<T>(L), L.nx + 1, a.u, a.f,
+                    static_cast<const PassArgs<T> *>(a.pk.tab), a.pk.active);
 }
 
 template <typename T, int K>
-cudaError_t launch_multi(const Level &L, const WarpList &w, T *u, const T *f, cudaStream_t s) {
+cudaError_t launch_multi(const Level &L, const WarpList &w, const WarpLaunch<T> &a, cudaStream_t s) {
   switch (w.W) {
-    case 2: return launch_kw<T, K, 2>(L, w, u, f, s);
-    case 4: return launch_kw<T, K, 4>(L, w, u, f, s);
-    case 8: return launch_kw<T, K, 8>(L, w, u, f, s);
+    case 2: return launch_kw<T, K, 2>(L, w, a, s);
+    case 4: return launch_kw<T, K, 4>(L, w, a, s);
+    case 8: return launch_kw<T, K, 8>(L, w, a, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -424,34 +453,48 @@ cudaError_t opt_in_all() {
   return e;
 }
 
-}  // namespace
-
 template <typename T>
-cudaError_t launch_warp_pass(const Level &L, const WarpList &w, T *u, const T *f, cudaStream_t s) {
-  if (w.nwarp == 0) return cudaSuccess;
+cudaError_t launch_shape(const Level &L, const WarpList &w, const WarpLaunch<T> &a, cudaStream_t s) {
+  if (w.nwarp == 0 || a.pk.count == 0) return cudaSuccess;
   if (w.W == 1) {
     switch (w.K) {
-      case 1: return launch_k<T, 1>(L, w, u, f, s);
-      case 2: return launch_k<T, 2>(L, w, u, f, s);
-      case 4: return launch_k<T, 4>(L, w, u, f, s);
-      case 8: return launch_k<T, 8>(L, w, u, f, s);
+      case 1: return launch_k<T, 1>(L, w, a, s);
+      case 2: return launch_k<T, 2>(L, w, a, s);
+      case 4: return launch_k<T, 4>(L, w, a, s);
+      case 8: return launch_k<T, 8>(L, w, a, s);
       case 16:
-        if constexpr (sizeof(T) == 4) return launch_k<T, 16>(L, w, u, f, s);
+        if constexpr (sizeof(T) == 4) return launch_k<T, 16>(L, w, a, s);
         return cudaErrorInvalidValue;
       default: return cudaErrorInvalidValue;
     }
   }
   switch (w.K) {
-    case 1: return launch_multi<T, 1>(L, w, u, f, s);
-    case 2: return launch_multi<T, 2>(L, w, u, f, s);
-    case 4: return launch_multi<T, 4>(L, w, u, f, s);
-    case 8: return launch_multi<T, 8>(L, w, u, f, s);
+    case 1: return launch_multi<T, 1>(L, w, a, s);
+    case 2: return launch_multi<T, 2>(L, w, a, s);
+    case 4: return launch_multi<T, 4>(L, w, a, s);
+    case 8: return launch_multi<T, 8>(L, w, a, s);
     case 16:
-      if constexpr (sizeof(T) == 4) return launch_multi<T, 16>(L, w, u, f, s);
+      if constexpr (sizeof(T) == 4) return launch_multi<T, 16>(L, w, a, s);
       return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_warp_pass(const Level &L, const WarpList &w, T *u, const T *f, cudaStream_t s) {
+  return launch_shape<T>(L, w, WarpLaunch<T>{u, f, PackedLaunch{nullptr, nullptr, 1}}, s);
+}
+
+template <typename T>
+cudaError_t launch_warp_pass_packed(const Level &L, const WarpList &w, const PackedLaunch &pk, cudaStream_t s) {
+  return launch_shape<T>(L, w, WarpLaunch<T>{nullptr, nullptr, pk}, s);
+}
+template cudaError_t launch_warp_pass_packed<float>(const Level &, const WarpList &, const PackedLaunch &,
+                                                    cudaStream_t);
+template cudaError_t launch_warp_pass_packed<double>(const Level &, const WarpList &, const PackedLaunch &,
+                                                     cudaStream_t);
 
 cudaError_t prepare_warp_kernels() {
   cudaError_t e = opt_in_all<float, 1>();

@@ -412,9 +412,10 @@ __global__ void __launch_bounds__(32 * TWv<T>) tile_expand(const TileDesc *__res
     T dv[CMAX];
 #pragma unroll
     for (int q = 0; q < CMAX; ++q) dv[q] = dl[32 * (q < m ? q : m - 1)];  // all loads in flight
-    // full chunks (all but a leg's last) without guards: 26 vs 30 us per
-    // pass at 4097^2 on GB300, with the same registers
-    if (m == CMAX) expand_rows<T, true>(co, m, fl, cross, dv, xlo, xhi, x, cpv);
+    // FP32 full chunks (all but a leg's last) without guards: 26 vs 30 us
+    // per pass at 4097^2 on GB300, with the same registers (in FP64 the copy
+    // raised them from 94 to 151)
+    if (sizeof(T) == 4 && m == CMAX) expand_rows<T, true>(co, m, fl, cross, dv, xlo, xhi, x, cpv);
     else expand_rows<T, false>(co, m, fl, cross, dv, xlo, xhi, x, cpv);
   }
   __syncwarp();

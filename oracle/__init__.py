@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "mg_oracle.c")
+_SRC3 = os.path.join(_HERE, "mg_oracle3d.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libmgoracle.so")
 _lock = threading.Lock()
@@ -36,11 +37,13 @@ SMOOTHERS = {"checkerboard": CHECKERBOARD, "zebra_x": ZEBRA_X, "zebra_y": ZEBRA_
 
 
 def build(force: bool = False) -> str:
-    """Compile mg_oracle.c into _build/libmgoracle.so (gcc, -O2, portable C11)."""
+    """Compile mg_oracle.c and mg_oracle3d.c into _build/libmgoracle.so (gcc,
+    -O2, portable C11)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC3))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, _SRC3, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -78,6 +81,22 @@ def _load():
             "or_block_dense": (i, [P, i, i, i, dp, dp, dp, dp]),
             "or_block_solve": (i, [P, i, i, i, dp, dp]),
             "or_dense_solve": (i, [i, dp, dp]),
+            "o3_create": (P, [i, i, i, dp, dp, dp]),
+            "o3_destroy": (None, [P]),
+            "o3_num_levels": (i, [P]),
+            "o3_level_shape": (None, [P, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
+            "o3_level_coeffs": (None, [P, i, dp, dp, dp, dp, dp, dp]),
+            "o3_apply": (None, [P, i, dp, dp]),
+            "o3_residual": (None, [P, i, dp, dp, dp]),
+            "o3_colour_pass": (i, [P, i, i, dp, dp]),
+            "o3_smooth": (i, [P, i, dp, dp]),
+            "o3_restrict": (None, [P, i, dp, dp]),
+            "o3_prolong_add": (None, [P, i, dp, dp]),
+            "o3_direct_solve": (i, [P, i, dp, dp]),
+            "o3_partition": (i, [P, i, ip, ip, i]),
+            "o3_block_solve": (i, [P, i, i, dp, dp]),
+            "o3_cycle": (i, [P, i, i, dp, dp]),
+            "o3_solve": (i, [P, i, i, d, i, dp, dp, dp, i]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -319,3 +338,109 @@ def quadratic_loss_gradient(P: Problem, f, g, u_target):
     grad_g[bb] = r[bb] - B.T @ lam
     loss = 0.5 * float(r @ r)
     return loss, u.reshape(ny1, nx1), grad_f.reshape(ny1, nx1), grad_g.reshape(ny1, nx1)
+
+
+class Problem3:
+    """3D tweed multigrid oracle (mg_oracle3d.c, Sec. 7) for the Dirichlet
+    problem of Eq. (prob:DP) with a third axis.  Arrays are (nz+1, ny+1, nx+1),
+    x fastest; only interior values of f and boundary values of u are read."""
+
+    def __init__(self, x, y, z):
+        self.lib = _load()
+        self.x, self.y, self.z = _f64(x), _f64(y), _f64(z)
+        self.h = self.lib.o3_create(len(self.x) - 1, len(self.y) - 1, len(self.z) - 1, self.x, self.y, self.z)
+        if not self.h:
+            raise ValueError("grid too small")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.lib.o3_destroy(self.h)
+            self.h = None
+
+    @property
+    def nlev(self) -> int:
+        return self.lib.o3_num_levels(self.h)
+
+    def dims(self, lev: int = 0):
+        nx, ny, nz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self.lib.o3_level_shape(self.h, lev, ctypes.byref(nx), ctypes.byref(ny), ctypes.byref(nz))
+        return nx.value, ny.value, nz.value
+
+    def shape(self, lev: int = 0):
+        nx, ny, nz = self.dims(lev)
+        return nz + 1, ny + 1, nx + 1
+
+    def coeffs(self, lev: int = 0):
+        nx, ny, nz = self.dims(lev)
+        a = [np.zeros(nx + 1), np.zeros(nx + 1), np.zeros(ny + 1), np.zeros(ny + 1), np.zeros(nz + 1), np.zeros(nz + 1)]
+        self.lib.o3_level_coeffs(self.h, lev, *a)
+        return dict(zip("WESNBT", a))
+
+    def apply(self, u, lev: int = 0):
+        u = _f64(u)
+        out = np.empty_like(u)
+        self.lib.o3_apply(self.h, lev, u, out)
+        return out
+
+    def residual(self, u, f, lev: int = 0):
+        u, f = _f64(u), _f64(f)
+        d = np.empty_like(u)
+        self.lib.o3_residual(self.h, lev, u, f, d)
+        return d
+
+    def colour_pass(self, u, f, colour, lev: int = 0):
+        assert u.dtype == np.float64 and u.flags.c_contiguous
+        if self.lib.o3_colour_pass(self.h, lev, colour, u, _f64(f)):
+            raise RuntimeError("oracle colour pass failed")
+        return u
+
+    def smooth(self, u, f, lev: int = 0):
+        assert u.dtype == np.float64 and u.flags.c_contiguous
+        if self.lib.o3_smooth(self.h, lev, u, _f64(f)):
+            raise RuntimeError("oracle smoothing failed")
+        return u
+
+    def restrict(self, d, lev: int = 0):
+        fc = np.zeros(self.shape(lev + 1))
+        self.lib.o3_restrict(self.h, lev, _f64(d), fc)
+        return fc
+
+    def prolong_add(self, uc, u, lev: int = 0):
+        assert u.dtype == np.float64 and u.flags.c_contiguous
+        self.lib.o3_prolong_add(self.h, lev, _f64(uc), u)
+        return u
+
+    def direct_solve(self, u, f, lev: int = 0):
+        assert u.dtype == np.float64 and u.flags.c_contiguous
+        if self.lib.o3_direct_solve(self.h, lev, u, _f64(f)):
+            raise RuntimeError("singular")
+        return u
+
+    def partition(self, lev: int = 0):
+        """(owner of every node, -1 off the interior; colour of every block)."""
+        owner = np.empty(self.shape(lev), dtype=np.int32)
+        cap = owner.size
+        colour = np.empty(cap, dtype=np.int32)
+        nb = self.lib.o3_partition(self.h, lev, owner, colour, cap)
+        return owner, colour[:nb].copy()
+
+    def block_solve(self, b, u, f, lev: int = 0):
+        assert u.dtype == np.float64 and u.flags.c_contiguous
+        if self.lib.o3_block_solve(self.h, lev, b, u, _f64(f)):
+            raise RuntimeError("block solve failed")
+        return u
+
+    def cycle(self, u, f, nu1=2, nu2=2):
+        assert u.dtype == np.float64 and u.flags.c_contiguous
+        if self.lib.o3_cycle(self.h, nu1, nu2, u, _f64(f)):
+            raise RuntimeError("oracle cycle failed")
+        return u
+
+    def solve(self, u, f, nu1=2, nu2=2, tol=1e-10, max_cycles=100, cap=256):
+        """Cycles until tol; returns the relative-residual history."""
+        assert u.dtype == np.float64 and u.flags.c_contiguous
+        hist = np.zeros(cap)
+        k = self.lib.o3_solve(self.h, nu1, nu2, tol, max_cycles, u, _f64(f), hist, cap)
+        if k < 0:
+            raise RuntimeError("oracle solve failed")
+        return hist[:min(k, cap - 1) + 1].copy()

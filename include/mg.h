@@ -111,8 +111,19 @@ typedef struct {
 
 /* Build the level hierarchy, the 1-D coefficient arrays of Sec. 2 on every
  * level (rediscretised on the subsampled coordinates, Sec. 4) and the device
- * workspaces.  dim must be 2.  n_intervals = {nx, ny}; coords = {x, y}, HOST
- * arrays of nx+1 and ny+1 strictly increasing doubles (copied).
+ * workspaces.  dim 2: n_intervals = {nx, ny}; coords = {x, y}, HOST arrays of
+ * nx+1 and ny+1 strictly increasing doubles (copied).
+ * dim 3 (Sec. 7): n_intervals = {nx, ny, nz} (each 2 .. 1020), coords =
+ * {x, y, z}; grid arrays are [nz+1][ny+1][nx+1], x fastest, and the operator
+ * is the 7-point one with B_k, T_k over z built like S_j, N_j.  3D grids
+ * offer the tweed smoother (blocks: the level sets of the two larger sorted
+ * wall distances, lines perpendicular to the nearest wall, stars of up to six
+ * legs), full weighting and trilinear prolongation (tensor products of the 1D
+ * factors of Sec. 4), mg_colour_pass, mg_smooth(_tweed), mg_residual,
+ * mg_residual_restrict, mg_prolong_add, mg_coarse_solve, mg_vcycle and
+ * mg_solve in both precisions; other smoothers and the other entry points
+ * return MG_ERR_UNSUPPORTED.  Sides that are odd on a smoothed level are
+ * MG_ERR_UNSUPPORTED (their middle blocks would close loops).
  * precision_mask: bit 0 = FP64 workspaces, bit 1 = FP32 workspaces (0 means
  * both).  The block work lists of every smoother are built here too.
  * On success *out owns device memory until mg_destroy.                       */
@@ -122,9 +133,13 @@ mg_status mg_setup_grid(mg_grid **out, int dim, const int64_t *n_intervals,
 /* Release everything owned by the grid (NULL is a no-op).                    */
 void mg_destroy(mg_grid *grid);
 
-/* Number of levels and the interval counts of one level.                     */
+/* Number of levels and the interval counts of one level (mg_level_shape:
+ * nx, ny of either dimension; mg_level_dims: {nx, ny, nz}, nz = 0 in 2D) and
+ * the grid's dimension (2 or 3).                                             */
 int mg_num_levels(const mg_grid *grid);
 mg_status mg_level_shape(const mg_grid *grid, int level, int64_t *nx, int64_t *ny);
+mg_status mg_level_dims(const mg_grid *grid, int level, int64_t *dims);
+int mg_grid_dim(const mg_grid *grid);
 
 /* Relaxation on one level.  u, f: device arrays of that level's shape in
  * dtype (mg_dtype).  `sweeps` relaxations are applied in place on u.

@@ -30,7 +30,7 @@ mg_status cuda_status(const char *where, cudaError_t e) {
 
 // Sec. 2 coefficients on one axis: lo_i = 1/(dx_i dx_{i-1/2}),
 // hi_i = 1/(dx_i dx_{i+1/2}), dx_i = (x_{i+1} - x_{i-1})/2; 0 at the ends.
-static void axis_coefficients(const std::vector<double> &x, std::vector<double> &lo, std::vector<double> &hi) {
+void axis_coefficients(const std::vector<double> &x, std::vector<double> &lo, std::vector<double> &hi) {
   const size_t n = x.size() - 1;
   lo.assign(n + 1, 0.0);
   hi.assign(n + 1, 0.0);
@@ -60,6 +60,7 @@ static void free_grid(Grid *g) {
   if (!g) return;
   destroy_timer(g);
   drop_graphs(*g);
+  free3(*g);
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);
   if (g->ev_join) cudaEventDestroy(g->ev_join);
   if (g->gs) cudaStreamDestroy(g->gs);
@@ -92,7 +93,7 @@ static mg_status dalloc(X **p, size_t n, const char *what) {
 
 // Gauss-Jordan inverse with partial pivoting (FP64, host), for the coarsest
 // level's dense direct solve.
-static bool invert(int n, std::vector<double> &A, std::vector<double> &inv) {
+bool invert(int n, std::vector<double> &A, std::vector<double> &inv) {
   inv.assign((size_t)n * n, 0.0);
   for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
   for (int k = 0; k < n; ++k) {
@@ -118,6 +119,23 @@ static bool invert(int n, std::vector<double> &A, std::vector<double> &inv) {
     }
   }
   return true;
+}
+
+// What every solve needs besides the levels: norm partials and scalars, the
+// pinned host copy of the norms, the graph stream and its events.
+static mg_status setup_solver_state(Grid *g) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  g->sms = sms;
+  g->npartial = 4 * sms;
+  TRY(dalloc(&g->partial, 2 * (size_t)g->npartial, "cudaMalloc(partials)"));
+  TRY(dalloc(&g->scal, 4, "cudaMalloc(scalars)"));
+  TRY_CUDA("cudaMallocHost", cudaMallocHost(&g->hpinned, 4 * sizeof(double)));
+  TRY_CUDA("cudaStreamCreate(graph stream)", cudaStreamCreateWithFlags(&g->gs, cudaStreamNonBlocking));
+  TRY_CUDA("cudaEventCreate(fork)", cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
+  TRY_CUDA("cudaEventCreate(join)", cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
+  return MG_OK;
 }
 
 static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y) {
@@ -194,14 +212,7 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
   const size_t nn0 = g->lev[0].nn;
   if (want32) { TRY(dalloc(&g->e32, nn0, "cudaMalloc(e32)")); TRY(dalloc(&g->r32, nn0, "cudaMalloc(r32)")); }
   if (want64) TRY(dalloc(&g->r64, nn0, "cudaMalloc(adjoint scratch)"));
-  int dev = 0, sms = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  g->sms = sms;
-  g->npartial = 4 * sms;
-  TRY(dalloc(&g->partial, 2 * (size_t)g->npartial, "cudaMalloc(partials)"));
-  TRY(dalloc(&g->scal, 4, "cudaMalloc(scalars)"));
-  TRY_CUDA("cudaMallocHost", cudaMallocHost(&g->hpinned, 4 * sizeof(double)));
+  TRY(setup_solver_state(g));
   // block work lists of every line smoother on every level, so that no later
   // call allocates
   TRY_CUDA("setup scratch (latched error)", cudaGetLastError());
@@ -220,9 +231,6 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
     TRY_CUDA("cudaMalloc(tile rhs)", cudaMalloc(&g->tile_d, g->tile_cap * 32 * 32 * sizeof(double)));
     TRY_CUDA("cudaMalloc(tile ends)", cudaMalloc(&g->tile_x, g->tile_cap * 32 * 2 * sizeof(double)));
   }
-  TRY_CUDA("cudaStreamCreate(graph stream)", cudaStreamCreateWithFlags(&g->gs, cudaStreamNonBlocking));
-  TRY_CUDA("cudaEventCreate(fork)", cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));
-  TRY_CUDA("cudaEventCreate(join)", cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming));
   TRY_CUDA("setup (latched error)", cudaGetLastError());
   return MG_OK;
 }
@@ -306,6 +314,7 @@ static mg_status smooth(Grid &g, int l, int smoother, T *u, const T *f, cudaStre
 // Sec. 4 steps (2)-(6) on level l; gamma = 1 (V) or 2 (W).
 template <typename T>
 static mg_status cycle_rec(Grid &g, const mg_params &p, int l, T *u, const T *f, cudaStream_t s) {
+  if (g.dim == 3) return cycle3<T>(g, p, l, u, f, s);
   if (l == g.nlev - 1) {
     TRY_CUDA("coarse solve", launch_coarse_solve<T>(g, u, f, s));
     return MG_OK;
@@ -386,6 +395,8 @@ mg_status check_params(const Grid *g, const mg_params *p) {
   if (p->precision == MG_PREC_F32_REFINE && !(g->prec_mask & 2)) return MG_ERR_INVALID_ARG;
   if (p->precision != MG_PREC_F64 && p->precision != MG_PREC_F32_REFINE) return MG_ERR_INVALID_ARG;
   if (!(p->tol >= 0.0) || p->max_cycles < 0 || p->max_outer < 0 || p->inner_cycles < 1) return MG_ERR_INVALID_ARG;
+  // 3D grids: the tweed smoother with full weighting (Sec. 7)
+  if (g->dim == 3 && (p->smoother != MG_SMOOTH_TWEED || p->restriction != MG_RESTRICT_FW)) return MG_ERR_UNSUPPORTED;
   return MG_OK;
 }
 
@@ -405,23 +416,31 @@ mg_status enqueue(SolveState &q) {
   Grid &g = *q.g;
   const mg_params &p = q.p;
   const bool f64 = p.precision == MG_PREC_F64;
+  const bool d3 = g.dim == 3;
   if (q.phase == 0) {
     if (q.info) { q.info->cycles = 0; q.info->outer_iters = 0; q.info->history_len = 0; q.info->rel_res = 0; q.info->conv_factor = 0; }
-    if (!p.use_initial_guess) TRY_CUDA("zero u", launch_zero_interior<double>(g.lev[0], q.u, q.s));
+    if (!p.use_initial_guess) {
+      if (d3) TRY(zero_interior3(g, q.u, q.s));
+      else TRY_CUDA("zero u", launch_zero_interior<double>(g.lev[0], q.u, q.s));
+    }
     // scale of the relative residual: ||f - B g||, the right-hand side of the
     // interior system (||f|| when the boundary data vanish)
-    TRY_CUDA("norm(f - B g)", launch_rhsnorm64(g, q.u, q.f, q.s));
+    if (d3) TRY(norms3(g, q.u, q.f, 1, nullptr, nullptr, q.s));
+    else TRY_CUDA("norm(f - B g)", launch_rhsnorm64(g, q.u, q.f, q.s));
   } else if (f64) {
     if (q.phase == 2) TRY(run_cycles<double>(g, p, 1, q.u, q.f, q.s));
-    TRY_CUDA("residual norm", launch_resnorm64(g, q.u, q.f, q.s));
+    if (d3) TRY(norms3(g, q.u, q.f, 0, nullptr, nullptr, q.s));
+    else TRY_CUDA("residual norm", launch_resnorm64(g, q.u, q.f, q.s));
   } else {
     // FP32 cycles on the correction equation L e = r (e zeroed by the
     // residual kernel), FP64 residual and update
     if (q.phase == 2) {
       TRY(run_cycles<float>(g, p, p.inner_cycles, g.e32, g.r32, q.s));
-      TRY_CUDA("refinement update", launch_ir_update(g, q.u, g.e32, q.s));
+      if (d3) TRY(ir_update3(g, q.u, g.e32, q.s));
+      else TRY_CUDA("refinement update", launch_ir_update(g, q.u, g.e32, q.s));
     }
-    TRY_CUDA("refinement residual", launch_ir_residual(g, q.u, q.f, g.r32, g.e32, q.s));
+    if (d3) TRY(norms3(g, q.u, q.f, 0, g.r32, g.e32, q.s));
+    else TRY_CUDA("refinement residual", launch_ir_residual(g, q.u, q.f, g.r32, g.e32, q.s));
   }
   return copy_norm(g, q.s);
 }
@@ -525,7 +544,23 @@ mg_status mg_setup_grid(mg_grid **out, int dim, const int64_t *n_intervals, cons
   (void)stream;
   if (!out || !n_intervals || !coords) return MG_ERR_INVALID_ARG;
   *out = nullptr;
-  if (dim == 3) return MG_ERR_UNSUPPORTED;
+  if (dim == 3) {
+    for (int a = 0; a < 3; ++a) {
+      if (n_intervals[a] < 2 || n_intervals[a] > 1020) return MG_ERR_SIZE;
+      if (!coords[a]) return MG_ERR_INVALID_ARG;
+      for (int64_t i = 0; i < n_intervals[a]; ++i)
+        if (!(coords[a][i + 1] > coords[a][i])) return MG_ERR_SIZE;
+    }
+    mg_grid *g = new (std::nothrow) mg_grid();
+    if (!g) return MG_ERR_ALLOC;
+    g->prec_mask = (precision_mask & 3) ? (precision_mask & 3) : 3;
+    mg_status st = setup3(*g, n_intervals, coords);
+    if (st == MG_OK) st = setup_solver_state(g);
+    if (st == MG_OK) st = cuda_status("3D setup (latched error)", cudaGetLastError());
+    if (st != MG_OK) { free_grid(g); return st; }
+    *out = g;
+    return MG_OK;
+  }
   if (dim != 2) return MG_ERR_INVALID_ARG;
   const int64_t nx = n_intervals[0], ny = n_intervals[1];
   if (nx < 2 || ny < 2 || nx > 32768 || ny > 32768) return MG_ERR_SIZE;
@@ -549,8 +584,26 @@ int mg_num_levels(const mg_grid *g) { return g ? g->nlev : 0; }
 
 mg_status mg_level_shape(const mg_grid *g, int level, int64_t *nx, int64_t *ny) {
   if (!g || !nx || !ny || level < 0 || level >= g->nlev) return MG_ERR_INVALID_ARG;
+  if (g->dim == 3) {
+    *nx = g->g3->lev[level].nx;
+    *ny = g->g3->lev[level].ny;
+    return MG_OK;
+  }
   *nx = g->lev[level].nx;
   *ny = g->lev[level].ny;
+  return MG_OK;
+}
+
+int mg_grid_dim(const mg_grid *g) { return g ? g->dim : 0; }
+
+mg_status mg_level_dims(const mg_grid *g, int level, int64_t *dims) {
+  if (!g || !dims || level < 0 || level >= g->nlev) return MG_ERR_INVALID_ARG;
+  if (g->dim == 3) {
+    const Level3 &L = g->g3->lev[level];
+    dims[0] = L.nx; dims[1] = L.ny; dims[2] = L.nz;
+  } else {
+    dims[0] = g->lev[level].nx; dims[1] = g->lev[level].ny; dims[2] = 0;
+  }
   return MG_OK;
 }
 
@@ -565,6 +618,11 @@ mg_status mg_colour_pass(mg_grid *g, int level, int smoother, int colour, void *
   if (smoother == MG_SMOOTH_ALT_ZEBRA || smoother == MG_SMOOTH_ALT_TW || smoother < 0 || smoother > MG_SMOOTH_ALT_TW)
     return MG_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (g->dim == 3) {
+    if (smoother != MG_SMOOTH_TWEED) return MG_ERR_UNSUPPORTED;
+    if (dtype == MG_F64) return colour_pass3<double>(*g, level, colour, (double *)u, (const double *)f, s);
+    return colour_pass3<float>(*g, level, colour, (float *)u, (const float *)f, s);
+  }
   if (dtype == MG_F64) return colour_pass<double>(*g, level, smoother, colour, (double *)u, (const double *)f, s);
   return colour_pass<float>(*g, level, smoother, colour, (float *)u, (const float *)f, s);
 }
@@ -574,6 +632,15 @@ mg_status mg_smooth(mg_grid *g, int level, int smoother, void *u, const void *f,
   if (bad_level(g, level) || !u || !f || sweeps < 0 || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
   if (smoother < 0 || smoother > MG_SMOOTH_ALT_TW) return MG_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (g->dim == 3) {
+    if (smoother != MG_SMOOTH_TWEED) return MG_ERR_UNSUPPORTED;
+    for (int k = 0; k < sweeps; ++k)
+      for (int c = 0; c < 2; ++c) {
+        const mg_status st = mg_colour_pass(g, level, smoother, c, u, f, dtype, stream);
+        if (st != MG_OK) return st;
+      }
+    return MG_OK;
+  }
   for (int k = 0; k < sweeps; ++k) {
     mg_status st = dtype == MG_F64 ? smooth<double>(*g, level, smoother, (double *)u, (const double *)f, s)
                                    : smooth<float>(*g, level, smoother, (float *)u, (const float *)f, s);
@@ -595,6 +662,12 @@ mg_status mg_residual_restrict(mg_grid *g, int level, int restriction, const voi
   if (bad_level(g, level) || level + 1 >= g->nlev || !u || !f || !fc || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
   if (restriction != MG_RESTRICT_HW && restriction != MG_RESTRICT_FW) return MG_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (g->dim == 3) {
+    if (restriction != MG_RESTRICT_FW) return MG_ERR_UNSUPPORTED;
+    if (dtype == MG_F64)
+      return residual_restrict3<double>(*g, level, (const double *)u, (const double *)f, (double *)fc, (double *)uc, s);
+    return residual_restrict3<float>(*g, level, (const float *)u, (const float *)f, (float *)fc, (float *)uc, s);
+  }
   const Level &F = g->lev[level], &C = g->lev[level + 1];
   cudaError_t e = dtype == MG_F64
                       ? launch_residual_restrict<double>(F, C, restriction, (const double *)u, (const double *)f,
@@ -607,6 +680,10 @@ mg_status mg_residual_restrict(mg_grid *g, int level, int restriction, const voi
 mg_status mg_prolong_add(mg_grid *g, int level, const void *uc, void *u, int dtype, void *stream) {
   if (bad_level(g, level) || level + 1 >= g->nlev || !u || !uc || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (g->dim == 3) {
+    if (dtype == MG_F64) return prolong_add3<double>(*g, level, (const double *)uc, (double *)u, s);
+    return prolong_add3<float>(*g, level, (const float *)uc, (float *)u, s);
+  }
   const Level &F = g->lev[level], &C = g->lev[level + 1];
   cudaError_t e = dtype == MG_F64 ? launch_prolong_add<double>(F, C, (const double *)uc, (double *)u, s)
                                   : launch_prolong_add<float>(F, C, (const float *)uc, (float *)u, s);
@@ -616,6 +693,10 @@ mg_status mg_prolong_add(mg_grid *g, int level, const void *uc, void *u, int dty
 mg_status mg_residual(mg_grid *g, int level, const void *u, const void *f, void *d, int dtype, void *stream) {
   if (bad_level(g, level) || !u || !f || !d || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (g->dim == 3) {
+    if (dtype == MG_F64) return residual3<double>(*g, level, (const double *)u, (const double *)f, (double *)d, s);
+    return residual3<float>(*g, level, (const float *)u, (const float *)f, (float *)d, s);
+  }
   const Level &L = g->lev[level];
   cudaError_t e = dtype == MG_F64 ? launch_residual<double>(L, (const double *)u, (const double *)f, (double *)d, s)
                                   : launch_residual<float>(L, (const float *)u, (const float *)f, (float *)d, s);
@@ -625,6 +706,10 @@ mg_status mg_residual(mg_grid *g, int level, const void *u, const void *f, void 
 mg_status mg_coarse_solve(mg_grid *g, void *u, const void *f, int dtype, void *stream) {
   if (!g || !u || !f || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (g->dim == 3) {
+    if (dtype == MG_F64) return coarse_solve3<double>(*g, (double *)u, (const double *)f, s);
+    return coarse_solve3<float>(*g, (float *)u, (const float *)f, s);
+  }
   cudaError_t e = dtype == MG_F64 ? launch_coarse_solve<double>(*g, (double *)u, (const double *)f, s)
                                   : launch_coarse_solve<float>(*g, (float *)u, (const float *)f, s);
   return cuda_status("coarse solve", e);
@@ -652,6 +737,7 @@ mg_status mg_solve(mg_grid *g, double *u, const double *f, const mg_params *p, m
 mg_status mg_solve_adjoint(mg_grid *g, double *lambda, const double *rhs, const mg_params *p, mg_info *info,
                            void *stream) {
   if (!g || !lambda || !rhs) return MG_ERR_INVALID_ARG;
+  if (g->dim == 3) return MG_ERR_UNSUPPORTED;
   mg_status st = check_params(g, p);
   if (st != MG_OK) return st;
   if (!(g->prec_mask & 1)) return MG_ERR_INVALID_ARG;
@@ -676,6 +762,7 @@ mg_status mg_solve_adjoint(mg_grid *g, double *lambda, const double *rhs, const 
 mg_status mg_boundary_adjoint(mg_grid *g, const double *lambda, const double *grad_u, double *grad_g,
                               void *stream) {
   if (!g || !lambda || !grad_u || !grad_g) return MG_ERR_INVALID_ARG;
+  if (g->dim == 3) return MG_ERR_UNSUPPORTED;
   cudaError_t e = launch_boundary_adjoint(*g, lambda, grad_u, grad_g, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_status("boundary adjoint", e);
   return MG_OK;
@@ -683,6 +770,7 @@ mg_status mg_boundary_adjoint(mg_grid *g, const double *lambda, const double *gr
 
 mg_status mg_pass_timer_begin(mg_grid *g, int level, int max_passes) {
   if (bad_level(g, level) || max_passes < 1 || max_passes > (1 << 20) || g->timer_ev) return MG_ERR_INVALID_ARG;
+  if (g->dim == 3) return MG_ERR_UNSUPPORTED;
   g->timer_ev = new (std::nothrow) cudaEvent_t[4 * (size_t)max_passes];
   if (!g->timer_ev) return MG_ERR_ALLOC;
   for (int k = 0; k < 4 * max_passes; ++k) {

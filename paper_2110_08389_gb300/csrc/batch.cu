@@ -293,6 +293,7 @@ mg_status mg_batch_create(mg_batch **out, int count, mg_grid *const *grids) {
   std::vector<Grid *> gs(count);
   for (int i = 0; i < count; ++i) {
     if (!grids[i]) return MG_ERR_INVALID_ARG;
+    if (grids[i]->dim != 2) return MG_ERR_UNSUPPORTED;
     gs[i] = grids[i];
   }
   std::vector<Grid *> sorted(gs);

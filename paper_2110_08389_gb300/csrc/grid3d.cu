@@ -1,0 +1,927 @@
+// grid3d.cu -- 3D grids (Sec. 7): the level hierarchy, the 3D tweed blocks,
+// their colour passes on the warp path, the 7-point defect with full-weighting
+// restriction, trilinear prolongation, the coarsest direct solve, the FP64
+// norms and refinement steps, and the cycle of Sec. 4 on them.
+//
+// 3D tweed (Sec. 7): starting from the eight corner points, lines run
+// perpendicular to the nearest wall.  With the index distances to the
+// nearer wall d_x = min(i, nx-i), d_y, d_z sorted as d1 <= d2 <= d3, a block
+// is a connected set of interior nodes with equal (d2, d3): a point, a line
+// turning at most at its ends, or a star of m = 3, 4 or 6 legs around one
+// branch node (m = 6 at the centre of a cube).  A block is red (relaxed
+// first) when d2 + d3 is even, so the corner points are red; adjacent nodes
+// either share (d2, d3) or differ by one in d2 + d3, so blocks of one colour
+// never touch.  Transfers are the tensor products of the 1D factors of the
+// 2D rules of Sec. 4: full weighting (1/4, 1/2, 1/4) per axis, trilinear
+// prolongation.  Each block is solved exactly on the warp path: the same
+// partition method as in 2D (warp_common.cuh), with six directions and up to
+// six nodes attached to a junction.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "solve.h"
+#include "warp_common.cuh"
+
+namespace tmg {
+
+namespace {
+
+template <typename T>
+struct C6 {
+  const T *W, *E, *S, *N, *B, *T_;
+};
+template <typename T>
+C6<T> coefs3(const Level3 &L);
+template <>
+C6<double> coefs3<double>(const Level3 &L) {
+  return {L.c64[0], L.c64[1], L.c64[2], L.c64[3], L.c64[4], L.c64[5]};
+}
+template <>
+C6<float> coefs3<float>(const Level3 &L) {
+  return {L.c32[0], L.c32[1], L.c32[2], L.c32[3], L.c32[4], L.c32[5]};
+}
+
+// coefficient of row (i, j, k) towards direction d (0..5 = +x -x +y -y +z -z)
+template <typename T>
+__device__ __forceinline__ T cdir(const C6<T> &c, unsigned d, int i, int j, int k) {
+  switch (d) {
+    case 0: return __ldg(c.E + i);
+    case 1: return __ldg(c.W + i);
+    case 2: return __ldg(c.N + j);
+    case 3: return __ldg(c.S + j);
+    case 4: return __ldg(c.T_ + k);
+    default: return __ldg(c.B + k);
+  }
+}
+
+constexpr int WARP3_KMAX = 8, WARP3_WMAX = 8, WARP3_KPREF = 4;
+
+// ------------------------------------------------------------ the kernel --
+// One sequence of 32*W*K slots per CTA of W warps (the warp path of
+// warp_line.cu, seq_line_kernel, with six directions).
+template <typename T, int K, int W>
+__global__ void __launch_bounds__(32 * W) seq3_kernel(const WNode3 *__restrict__ nodes,
+                                                      const WBlock3 *__restrict__ blks, C6<T> cp, int nx1, int ny1,
+                                                      T *__restrict__ u, const T *__restrict__ f) {
+  constexpr int NT = 32 * W, N = NT * K;
+  extern __shared__ __align__(16) unsigned char sm3[];
+  T *sa = reinterpret_cast<T *>(sm3);
+  T *sb = sa + N, *sc = sb + N, *sd = sc + N, *sz = sd + N;
+  T *rep = sz + N;
+  T *red = rep + 4 * NT;
+  T *xjs = red + 8 * NT;
+  int *sp = reinterpret_cast<int *>(xjs + 2);
+  const int t = threadIdx.x, lane = t & 31;
+  const size_t plane = (size_t)nx1 * ny1;
+  const uint2 *nd = reinterpret_cast<const uint2 *>(nodes) + (size_t)blockIdx.x * N;
+  pdl_trigger();
+  // the junction: coefficient towards attached node e (thread e < natt)
+  const WBlock3 *jbp = blks + blockIdx.x;
+  struct {
+    uint32_t ijk, adirs;
+  } jb;
+  jb.ijk = jbp->ijk;
+  jb.adirs = jbp->adirs;
+  const bool has_j = jbp->has_j != 0;
+  const int natt = jbp->natt;
+  T kp = T(0), cJ = T(1);
+  int ji = 0, jj = 0, jk = 0;
+  unsigned att = 0;
+  if (has_j) {
+    ji = (int)(jb.ijk & 1023u); jj = (int)((jb.ijk >> 10) & 1023u); jk = (int)(jb.ijk >> 20);
+    for (int e = 0; e < natt; ++e) att |= 1u << ((jb.adirs >> (3 * e)) & 7u);
+    if (t < natt) kp = cdir(cp, (jb.adirs >> (3 * t)) & 7u, ji, jj, jk);
+    cJ = T(0);
+    for (unsigned d = 0; d < 6; ++d) cJ -= cdir(cp, d, ji, jj, jk);
+  }
+  pdl_wait();  // u and f from here on
+  // ---- 1. staging (thread t: nodes NT*q + t)
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const uint2 dsc = __ldg(nd + NT * q + t);
+    const unsigned fl = dsc.y;
+    const bool valid = (fl & WN3_VALID) != 0u;
+    const int i = (int)(dsc.x & 1023u), j = (int)((dsc.x >> 10) & 1023u), k = (int)(dsc.x >> 20);
+    const unsigned pd = (fl & WN3_PRED) ? (fl & 7u) : 7u, sd_ = (fl & WN3_SUCC) ? ((fl >> 4) & 7u) : 7u,
+                   jd = (fl & WN3_JUNC) ? ((fl >> 8) & 7u) : 7u;
+    const size_t p = (size_t)k * plane + (size_t)j * nx1 + i;
+    const size_t off[6] = {1, (size_t)0 - 1, (size_t)nx1, (size_t)0 - nx1, plane, (size_t)0 - plane};
+    T a = T(0), c = T(0), z = T(0), b = T(0), r = valid ? __ldg(f + p) : T(0);
+#pragma unroll
+    for (unsigned d = 0; d < 6; ++d) {
+      const T cd = cdir(cp, d, i, j, k);
+      b -= cd;
+      const bool outside = valid && d != pd && d != sd_ && d != jd;
+      if (outside) r -= cd * u[p + off[d]];
+      if (d == pd) a = cd;
+      if (d == sd_) c = cd;
+      if (d == jd) z = -cd;
+    }
+    const int s = NT * q + t, sl = wslot(s);
+    sa[sl] = a;
+    sc[sl] = c;
+    sz[sl] = z;
+    sb[sl] = valid ? b : T(1);
+    sd[sl] = r;
+    sp[s] = valid ? (int)p : -1;
+  }
+  T rJ = T(0);
+  size_t pJ = 0;
+  if (has_j && t == 0) {
+    pJ = (size_t)jk * plane + (size_t)jj * nx1 + ji;
+    rJ = __ldg(f + pJ);
+    const size_t off[6] = {1, (size_t)-1, (size_t)nx1, (size_t)0 - nx1, plane, (size_t)0 - plane};
+#pragma unroll
+    for (unsigned d = 0; d < 6; ++d)
+      if (!(att & (1u << d))) rJ -= cdir(cp, d, ji, jj, jk) * u[pJ + off[d]];
+  }
+  __syncthreads();
+
+  // ---- 2. forward sweep per thread
+  const int base = t * K;
+  Sweep<T, K> sw;
+  sw.run(base, sa, sb, sc, sd, sz);
+  rep[t] = sw.Y0; rep[NT + t] = sw.Z0; rep[2 * NT + t] = sw.W0; rep[3 * NT + t] = sw.V0;
+  __syncthreads();
+
+  // ---- 3. separator rows, cyclic reduction through shared memory
+  const int ss = wslot(base + K - 1);
+  T A, C, Ry, Rz;
+  {
+    const bool last = t == NT - 1;
+    const T Yn = last ? T(0) : rep[t + 1], Zn = last ? T(0) : rep[NT + t + 1];
+    const T Wn = last ? T(0) : rep[2 * NT + t + 1], Vn = last ? T(0) : rep[3 * NT + t + 1];
+    const T a = sa[ss], c = sc[ss];
+    const T r = recip(sb[ss] - a * sw.cl + c * Wn);
+    A = a * sw.wl * r;
+    C = c * Vn * r;
+    Ry = (sd[ss] - a * sw.yl - c * Yn) * r;
+    Rz = (sz[ss] - a * sw.zl - c * Zn) * r;
+  }
+  red[t] = A; red[NT + t] = C; red[2 * NT + t] = Ry; red[3 * NT + t] = Rz;
+  __syncthreads();
+  int cur = 0;
+#pragma unroll
+  for (int dd = 1; dd < NT; dd <<= 1) {
+    const T *rb = red + 4 * NT * cur;
+    T Am = T(0), Cm = T(0), Ym = T(0), Zm = T(0), Ap = T(0), Cp = T(0), Yp = T(0), Zp = T(0);
+    if (t >= dd) { Am = rb[t - dd]; Cm = rb[NT + t - dd]; Ym = rb[2 * NT + t - dd]; Zm = rb[3 * NT + t - dd]; }
+    if (t + dd < NT) { Ap = rb[t + dd]; Cp = rb[NT + t + dd]; Yp = rb[2 * NT + t + dd]; Zp = rb[3 * NT + t + dd]; }
+    const T r = recip(T(1) - A * Cm - C * Ap);
+    const T nA = -A * Am * r, nC = -C * Cp * r;
+    const T nY = (Ry - A * Ym - C * Yp) * r, nZ = (Rz - A * Zm - C * Zp) * r;
+    A = nA; C = nC; Ry = nY; Rz = nZ;
+    cur ^= 1;
+    T *wb = red + 4 * NT * cur;
+    wb[t] = A; wb[NT + t] = C; wb[2 * NT + t] = Ry; wb[3 * NT + t] = Rz;
+    __syncthreads();
+  }
+  {
+    const T *rb = red + 4 * NT * cur;
+    const T Sym = t > 0 ? rb[2 * NT + t - 1] : T(0), Szm = t > 0 ? rb[3 * NT + t - 1] : T(0);
+    sw.back(base, Sym, Szm, Ry, Rz, sa, sb);
+  }
+  __syncthreads();
+
+  // ---- 5. junction value (warp 0; up to six attached nodes), write back
+  T xJ = T(0);
+  if (has_j) {
+    if (t < 32) {
+      T sy = T(0), szz = T(0);
+      if (lane < natt) {
+        const int s = jbp->as[lane];
+        sy = kp * sa[wslot(s)];
+        szz = kp * sb[wslot(s)];
+      }
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        sy += __shfl_xor_sync(0xFFFFFFFFu, sy, o);
+        szz += __shfl_xor_sync(0xFFFFFFFFu, szz, o);
+      }
+      if (t == 0) {
+        const T x = (rJ - sy) / (cJ + szz);
+        xjs[0] = x;
+        u[pJ] = x;
+      }
+    }
+    __syncthreads();
+    xJ = xjs[0];
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const int s = NT * q + t;
+    const int p = sp[s];
+    if (p >= 0) {
+      const int sl = wslot(s);
+      u[p] = sa[sl] + xJ * sb[sl];
+    }
+  }
+}
+
+template <typename T, int K, int W>
+constexpr size_t seq3_smem() {
+  return (size_t)32 * W * K * (5 * sizeof(T) + sizeof(int)) + sizeof(T) * (12 * 32 * W + 2);
+}
+
+template <typename T, int K, int W>
+cudaError_t launch3_kw(const Level3 &L, const WarpList3 &w, T *u, const T *f, cudaStream_t s) {
+  count_launch(1);
+  return launch_pdl(seq3_kernel<T, K, W>, dim3(w.nwarp), dim3(32 * W), seq3_smem<T, K, W>(), s,
+                    (const WNode3 *)w.node, (const WBlock3 *)w.blk, coefs3<T>(L), L.nx + 1, L.ny + 1, u, f);
+}
+template <typename T, int K>
+cudaError_t launch3_k(const Level3 &L, const WarpList3 &w, T *u, const T *f, cudaStream_t s) {
+  switch (w.W) {
+    case 1: return launch3_kw<T, K, 1>(L, w, u, f, s);
+    case 2: return launch3_kw<T, K, 2>(L, w, u, f, s);
+    case 4: return launch3_kw<T, K, 4>(L, w, u, f, s);
+    case 8: return launch3_kw<T, K, 8>(L, w, u, f, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <typename T>
+cudaError_t launch_warp3(const Level3 &L, const WarpList3 &w, T *u, const T *f, cudaStream_t s) {
+  if (w.nwarp == 0) return cudaSuccess;
+  switch (w.K) {
+    case 1: return launch3_k<T, 1>(L, w, u, f, s);
+    case 2: return launch3_k<T, 2>(L, w, u, f, s);
+    case 4: return launch3_k<T, 4>(L, w, u, f, s);
+    case 8: return launch3_k<T, 8>(L, w, u, f, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template <typename T, int K>
+cudaError_t opt_in3() {
+  cudaError_t e = cudaSuccess;
+  const int ws[4] = {1, 2, 4, 8};
+  for (int a = 0; a < 4 && e == cudaSuccess; ++a) {
+    switch (ws[a]) {
+      case 1: e = cudaFuncSetAttribute(seq3_kernel<T, K, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seq3_smem<T, K, 1>()); break;
+      case 2: e = cudaFuncSetAttribute(seq3_kernel<T, K, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seq3_smem<T, K, 2>()); break;
+      case 4: e = cudaFuncSetAttribute(seq3_kernel<T, K, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seq3_smem<T, K, 4>()); break;
+      default: e = cudaFuncSetAttribute(seq3_kernel<T, K, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seq3_smem<T, K, 8>()); break;
+    }
+  }
+  return e;
+}
+cudaError_t prepare3() {
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = opt_in3<float, 1>();
+  if (e == cudaSuccess) e = opt_in3<float, 2>();
+  if (e == cudaSuccess) e = opt_in3<float, 4>();
+  if (e == cudaSuccess) e = opt_in3<float, 8>();
+  if (e == cudaSuccess) e = opt_in3<double, 1>();
+  if (e == cudaSuccess) e = opt_in3<double, 2>();
+  if (e == cudaSuccess) e = opt_in3<double, 4>();
+  if (e == cudaSuccess) e = opt_in3<double, 8>();
+  return e;
+}
+
+// ----------------------------------------------------------- transfers --
+constexpr int T3 = 128;  // threads per CTA of the grid kernels (x along i)
+
+// d = f - L u at the interior nodes of a level (boundary of d not written)
+template <typename T>
+__global__ void __launch_bounds__(T3) defect3_kernel(C6<T> c, int nx, int ny, int nz, const T *__restrict__ u,
+                                                     const T *__restrict__ f, T *__restrict__ d) {
+  pdl_trigger();
+  const int i = 1 + blockIdx.x * T3 + threadIdx.x, j = 1 + blockIdx.y, k = 1 + blockIdx.z;
+  const T ci = i < nx ? __ldg(c.W + i) : T(0), ce = i < nx ? __ldg(c.E + i) : T(0);
+  const T cs = __ldg(c.S + j), cn = __ldg(c.N + j), cb = __ldg(c.B + k), ct = __ldg(c.T_ + k);
+  pdl_wait();
+  if (i >= nx) return;
+  const int nx1 = nx + 1;
+  const size_t plane = (size_t)nx1 * (ny + 1), p = (size_t)k * plane + (size_t)j * nx1 + i;
+  const T cc = -((ci + ce) + (cs + cn) + (cb + ct));
+  d[p] = f[p] - (ci * u[p - 1] + ce * u[p + 1] + cs * u[p - nx1] + cn * u[p + nx1] + cb * u[p - plane] +
+                 ct * u[p + plane] + cc * u[p]);
+}
+
+// full weighting of the fine defect onto the coarse interior (tensor
+// product of 1/4, 1/2, 1/4); the coarse correction uc is zeroed
+template <typename T>
+__global__ void __launch_bounds__(T3) restrict3_kernel(int nx, int ny, int nxc, int nyc, int nzc,
+                                                       const T *__restrict__ d, T *__restrict__ fc,
+                                                       T *__restrict__ uc) {
+  pdl_trigger();
+  pdl_wait();
+  const int I = 1 + blockIdx.x * T3 + threadIdx.x, J = 1 + blockIdx.y, K = 1 + blockIdx.z;
+  if (I >= nxc) return;
+  const int nx1 = nx + 1;
+  const size_t plane = (size_t)nx1 * (ny + 1);
+  const T w[3] = {T(0.25), T(0.5), T(0.25)};
+  T v = T(0);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const T *row = d + (size_t)(2 * K + c - 1) * plane + (size_t)(2 * J + b - 1) * nx1 + 2 * I - 1;
+      v += w[c] * w[b] * ((w[0] * row[0] + w[1] * row[1]) + w[2] * row[2]);
+    }
+  const size_t q = ((size_t)K * (nyc + 1) + J) * (nxc + 1) + I;
+  fc[q] = v;
+  if (uc) uc[q] = T(0);
+}
+
+// trilinear prolongation of the coarse correction, added to the fine interior
+template <typename T>
+__global__ void __launch_bounds__(T3) prolong3_kernel(int nx, int ny, int nxc, int nyc, const T *__restrict__ uc,
+                                                      T *__restrict__ u) {
+  pdl_trigger();
+  pdl_wait();
+  const int i = 1 + blockIdx.x * T3 + threadIdx.x, j = 1 + blockIdx.y, k = 1 + blockIdx.z;
+  if (i >= nx) return;
+  const int c1 = nxc + 1;
+  const size_t cplane = (size_t)c1 * (nyc + 1);
+  const int i0 = i >> 1, i1 = (i + 1) >> 1, j0 = j >> 1, j1 = (j + 1) >> 1, k0 = k >> 1, k1 = (k + 1) >> 1;
+  const T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1), wk = (k & 1) ? T(0.5) : T(1);
+  // odd index: both coarse neighbours (weight 1/2 each); even: the coarse
+  // node itself (i0 == i1, counted once)
+  auto at = [&](int a, int b, int c) { return uc[(size_t)c * cplane + (size_t)b * c1 + a]; };
+  T v = at(i0, j0, k0);
+  if (i & 1) v += at(i1, j0, k0);
+  if (j & 1) { v += at(i0, j1, k0); if (i & 1) v += at(i1, j1, k0); }
+  if (k & 1) {
+    T w2 = at(i0, j0, k1);
+    if (i & 1) w2 += at(i1, j0, k1);
+    if (j & 1) { w2 += at(i0, j1, k1); if (i & 1) w2 += at(i1, j1, k1); }
+    v += w2;
+  }
+  u[((size_t)k * (ny + 1) + j) * (nx + 1) + i] += wi * wj * wk * v;
+}
+
+// coarsest level: x = A^{-1} b in FP64, b = f - boundary neighbours
+constexpr int CS3_THREADS = 1024;
+template <typename T>
+__global__ void __launch_bounds__(CS3_THREADS) coarse3_kernel(C6<double> c, int nx, int ny, int nz,
+                                                              const double *__restrict__ inv, T *__restrict__ u,
+                                                              const T *__restrict__ f) {
+  extern __shared__ double cb3[];
+  pdl_trigger();
+  pdl_wait();
+  const int mx = nx - 1, my = ny - 1, n = mx * my * (nz - 1), nx1 = nx + 1;
+  const size_t plane = (size_t)nx1 * (ny + 1);
+  for (int r = threadIdx.x; r < n; r += blockDim.x) {
+    const int i = r % mx + 1, j = (r / mx) % my + 1, k = r / (mx * my) + 1;
+    const size_t p = (size_t)k * plane + (size_t)j * nx1 + i;
+    double b = (double)f[p];
+    if (i == 1) b -= c.W[i] * (double)u[p - 1];
+    if (i == nx - 1) b -= c.E[i] * (double)u[p + 1];
+    if (j == 1) b -= c.S[j] * (double)u[p - nx1];
+    if (j == ny - 1) b -= c.N[j] * (double)u[p + nx1];
+    if (k == 1) b -= c.B[k] * (double)u[p - plane];
+    if (k == nz - 1) b -= c.T_[k] * (double)u[p + plane];
+    cb3[r] = b;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = threadIdx.x >> 5; r < n; r += nw) {
+    double x = 0.0;
+    for (int q = lane; q < n; q += 32) x += inv[(size_t)r * n + q] * cb3[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) {
+      const int i = r % mx + 1, j = (r / mx) % my + 1, k = r / (mx * my) + 1;
+      u[(size_t)k * plane + (size_t)j * nx1 + i] = (T)x;
+    }
+  }
+}
+
+// ------------------------------------------------------- FP64 norms etc --
+constexpr int N3_THREADS = 256;
+
+__device__ __forceinline__ double block_sum3(double s) {
+  __shared__ double ss[N3_THREADS];
+  ss[threadIdx.x] = s;
+  __syncthreads();
+  for (int h = N3_THREADS / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) ss[threadIdx.x] += ss[threadIdx.x + h];
+    __syncthreads();
+  }
+  return ss[0];
+}
+
+// Sum of squares of r = f - L u over the interior (bnd_only: r = f - B u_b,
+// the boundary neighbours alone).  CTA b takes interior rows (j, k) with
+// row index b, b + gridDim.x, ...; each thread its columns in order, so the
+// sum does not depend on timing.  With r32: stores float(r), zeroes e32.
+__global__ void __launch_bounds__(N3_THREADS) norm3_stage1(C6<double> c, int nx, int ny, int nz,
+                                                           const double *__restrict__ u, const double *__restrict__ f,
+                                                           int bnd_only, float *__restrict__ r32,
+                                                           float *__restrict__ e32, double *__restrict__ part) {
+  const int nx1 = nx + 1, rows = (ny - 1) * (nz - 1);
+  const size_t plane = (size_t)nx1 * (ny + 1);
+  double s = 0.0;
+  for (int row = blockIdx.x; row < rows; row += gridDim.x) {
+    const int j = 1 + row % (ny - 1), k = 1 + row / (ny - 1);
+    const double cs = __ldg(c.S + j), cn = __ldg(c.N + j), cb = __ldg(c.B + k), ct = __ldg(c.T_ + k);
+    const size_t base = (size_t)k * plane + (size_t)j * nx1;
+    for (int i = 1 + threadIdx.x; i < nx; i += N3_THREADS) {
+      const size_t p = base + i;
+      double r = f[p];
+      const double cw = __ldg(c.W + i), ce = __ldg(c.E + i);
+      if (bnd_only) {
+        if (i == 1) r -= cw * u[p - 1];
+        if (i == nx - 1) r -= ce * u[p + 1];
+        if (j == 1) r -= cs * u[p - nx1];
+        if (j == ny - 1) r -= cn * u[p + nx1];
+        if (k == 1) r -= cb * u[p - plane];
+        if (k == nz - 1) r -= ct * u[p + plane];
+      } else {
+        const double cc = (cw + ce) + (cs + cn) + (cb + ct);
+        r -= cw * u[p - 1] + ce * u[p + 1] + cs * u[p - nx1] + cn * u[p + nx1] + cb * u[p - plane] +
+             ct * u[p + plane] - cc * u[p];
+      }
+      if (r32) { r32[p] = (float)r; e32[p] = 0.0f; }
+      s = fma(r, r, s);
+    }
+  }
+  s = block_sum3(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(N3_THREADS) norm3_stage2(const double *__restrict__ part, int npart,
+                                                           double *__restrict__ out) {
+  double s = 0.0;
+  for (int k = threadIdx.x; k < npart; k += N3_THREADS) s += part[k];
+  s = block_sum3(s);
+  if (threadIdx.x == 0) out[0] = s;
+}
+
+// u64 += e32 (update = 1) or u64 := 0 (update = 0) at interior nodes
+__global__ void __launch_bounds__(T3) interior3_kernel(int nx, int ny, double *__restrict__ u,
+                                                       const float *__restrict__ e, int update) {
+  const int i = 1 + blockIdx.x * T3 + threadIdx.x, j = 1 + blockIdx.y, k = 1 + blockIdx.z;
+  if (i >= nx) return;
+  const size_t p = ((size_t)k * (ny + 1) + j) * (nx + 1) + i;
+  u[p] = update ? u[p] + (double)e[p] : 0.0;
+}
+
+dim3 interior_grid(const Level3 &L) { return dim3((L.nx - 1 + T3 - 1) / T3, L.ny - 1, L.nz - 1); }
+
+// ------------------------------------------------------------ host setup --
+inline int dir_between(int nx1, size_t plane, long long p, long long q) {
+  const long long d = q - p;
+  if (d == 1) return 0;
+  if (d == -1) return 1;
+  if (d == nx1) return 2;
+  if (d == -(long long)nx1) return 3;
+  if (d == (long long)plane) return 4;
+  return 5;
+}
+
+// The tweed blocks of one level: chains (node offsets in order) and the
+// junction with its attached legs; false if a block is neither a line nor a
+// star (a side with an odd number of intervals closes loops).
+struct HBlock3 {
+  std::vector<std::vector<long long>> chains;
+  long long junc = -1;
+  std::vector<int> leg_dir;  // per chain: direction from its last node to the junction
+  int colour = 0;
+  int nodes = 0;
+};
+
+bool blocks3(const Level3 &L, std::vector<HBlock3> &out) {
+  const int nx = L.nx, ny = L.ny, nz = L.nz, nx1 = nx + 1;
+  const size_t plane = (size_t)nx1 * (ny + 1), nn = L.nn;
+  auto ijk = [&](size_t p, int &i, int &j, int &k) { i = (int)(p % nx1); j = (int)((p / nx1) % (ny + 1)); k = (int)(p / plane); };
+  auto inside = [&](int i, int j, int k) { return i > 0 && i < nx && j > 0 && j < ny && k > 0 && k < nz; };
+  auto key = [&](int i, int j, int k) {
+    int a = std::min(i, nx - i), b = std::min(j, ny - j), c = std::min(k, nz - k);
+    if (a > b) std::swap(a, b);
+    if (b > c) std::swap(b, c);
+    if (a > b) std::swap(a, b);
+    return std::make_pair(b, c);
+  };
+  std::vector<int> par(nn);
+  std::iota(par.begin(), par.end(), 0);
+  auto fnd = [&](int x) {
+    while (par[x] != x) { par[x] = par[par[x]]; x = par[x]; }
+    return x;
+  };
+  const long long step[6] = {1, -1, nx1, -(long long)nx1, (long long)plane, -(long long)plane};
+  const int di[6] = {1, -1, 0, 0, 0, 0}, dj[6] = {0, 0, 1, -1, 0, 0}, dk[6] = {0, 0, 0, 0, 1, -1};
+  for (int k = 1; k < nz; ++k)
+    for (int j = 1; j < ny; ++j)
+      for (int i = 1; i < nx; ++i) {
+        const auto kp = key(i, j, k);
+        const size_t p = (size_t)k * plane + (size_t)j * nx1 + i;
+        for (int d = 0; d < 6; d += 2) {
+          const int ii = i + di[d], jj = j + dj[d], kk = k + dk[d];
+          if (!inside(ii, jj, kk) || key(ii, jj, kk) != kp) continue;
+          const int r1 = fnd((int)p), r2 = fnd((int)(p + step[d]));
+          if (r1 != r2) par[r1] = r2;
+        }
+      }
+  std::vector<int> id(nn, -1);
+  std::vector<std::vector<long long>> members;
+  for (int k = 1; k < nz; ++k)
+    for (int j = 1; j < ny; ++j)
+      for (int i = 1; i < nx; ++i) {
+        const size_t p = (size_t)k * plane + (size_t)j * nx1 + i;
+        const int r = fnd((int)p);
+        if (id[r] < 0) { id[r] = (int)members.size(); members.emplace_back(); }
+        members[id[r]].push_back((long long)p);
+      }
+  auto owner = [&](long long p) { return id[fnd((int)p)]; };
+  for (size_t b = 0; b < members.size(); ++b) {
+    const auto &mb = members[b];
+    HBlock3 hb;
+    hb.nodes = (int)mb.size();
+    int i, j, k;
+    ijk((size_t)mb[0], i, j, k);
+    const auto kk0 = key(i, j, k);
+    hb.colour = ((kk0.first + kk0.second) % 2 == 0) ? 0 : 1;
+    // in-block neighbours
+    auto nbrs = [&](long long p, std::vector<long long> &nb) {
+      nb.clear();
+      int a, c, e;
+      ijk((size_t)p, a, c, e);
+      for (int d = 0; d < 6; ++d)
+        if (inside(a + di[d], c + dj[d], e + dk[d]) && owner(p + step[d]) == (int)b) nb.push_back(p + step[d]);
+    };
+    std::vector<long long> nb;
+    long long branch = -1;
+    int nbranch = 0, edges2 = 0;
+    long long endpoint = mb[0];
+    for (long long p : mb) {
+      nbrs(p, nb);
+      edges2 += (int)nb.size();
+      if (nb.size() >= 3) { branch = p; ++nbranch; }
+      if (nb.size() <= 1) endpoint = p;
+    }
+    if (edges2 / 2 != hb.nodes - 1 || nbranch > 1) return false;
+    auto walk = [&](long long prev, long long cur, std::vector<long long> &chain) {
+      chain.push_back(cur);
+      while (true) {
+        nbrs(cur, nb);
+        long long next = -1;
+        for (long long q : nb)
+          if (q != prev) next = q;
+        if (next < 0) break;
+        prev = cur;
+        cur = next;
+        chain.push_back(cur);
+      }
+    };
+    if (branch >= 0) {
+      hb.junc = branch;
+      std::vector<long long> legs;
+      nbrs(branch, legs);
+      for (long long q : legs) {
+        std::vector<long long> leg;
+        walk(branch, q, leg);                        // q .. tip
+        std::reverse(leg.begin(), leg.end());        // tip .. q (q next to the junction)
+        hb.leg_dir.push_back(dir_between(nx1, plane, q, branch));
+        hb.chains.push_back(std::move(leg));
+      }
+      hb.nodes -= 1;  // chain nodes only
+    } else {
+      std::vector<long long> line;
+      walk(-1, endpoint, line);
+      hb.chains.push_back(std::move(line));
+    }
+    out.push_back(std::move(hb));
+  }
+  return true;
+}
+
+// Sequences of one colour (first fit, largest blocks first, at most one
+// junction per sequence), K and W as in 2D (warp_line.cu) with at most 8
+// nodes per thread (both precisions use the same lists).
+mg_status warp_list3(const Level3 &L, const std::vector<HBlock3> &all, int colour, WarpList3 &Wl) {
+  std::vector<int> idx;
+  int maxn = 1, total = 0;
+  for (size_t b = 0; b < all.size(); ++b)
+    if (all[b].colour == colour) {
+      idx.push_back((int)b);
+      maxn = std::max(maxn, all[b].nodes);
+      total += all[b].nodes + (all[b].junc >= 0 ? 1 : 0);
+    }
+  if (idx.empty()) return MG_OK;
+  if (maxn > 32 * WARP3_WMAX * WARP3_KMAX) return MG_ERR_SIZE;
+  int K = 1, NW = 1;
+  while (32 * K < maxn && K < WARP3_KPREF) K *= 2;
+  while (32 * NW * K < maxn) NW *= 2;
+  while (NW > WARP3_WMAX) {
+    K *= 2;
+    NW = 1;
+    while (32 * NW * K < maxn) NW *= 2;
+  }
+  const int cap = 32 * NW * K;
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return all[a].nodes > all[b].nodes; });
+  struct Bin { int used = 0; bool junc = false; std::vector<int> blocks; };
+  std::vector<Bin> bins;
+  for (int b : idx) {
+    const bool j = all[b].junc >= 0;
+    size_t w = 0;
+    while (w < bins.size() && (bins[w].used + all[b].nodes > cap || (j && bins[w].junc))) ++w;
+    if (w == bins.size()) bins.emplace_back();
+    bins[w].used += all[b].nodes;
+    bins[w].junc |= j;
+    bins[w].blocks.push_back(b);
+  }
+  const int nx1 = L.nx + 1;
+  const size_t plane = (size_t)nx1 * (L.ny + 1);
+  std::vector<WNode3> nodes(bins.size() * (size_t)cap);
+  std::vector<WBlock3> blk(bins.size());
+  std::memset(nodes.data(), 0, sizeof(WNode3) * nodes.size());
+  std::memset(blk.data(), 0, sizeof(WBlock3) * blk.size());
+  auto pack = [&](long long p) {
+    const uint32_t i = (uint32_t)(p % nx1), j = (uint32_t)((p / nx1) % (L.ny + 1)), k = (uint32_t)(p / plane);
+    return i | (j << 10) | (k << 20);
+  };
+  for (size_t w = 0; w < bins.size(); ++w) {
+    WBlock3 &jb = blk[w];
+    int s = 0;
+    for (int b : bins[w].blocks) {
+      const HBlock3 &hb = all[b];
+      if (hb.junc >= 0) { jb.has_j = 1; jb.ijk = pack(hb.junc); }
+      for (size_t c = 0; c < hb.chains.size(); ++c) {
+        const auto &ch = hb.chains[c];
+        const int m = (int)ch.size();
+        for (int r = 0; r < m; ++r) {
+          uint32_t fl = WN3_VALID;
+          if (r > 0) fl |= WN3_PRED | (uint32_t)dir_between(nx1, plane, ch[r], ch[r - 1]);
+          if (r < m - 1) fl |= WN3_SUCC | ((uint32_t)dir_between(nx1, plane, ch[r], ch[r + 1]) << 4);
+          if (hb.junc >= 0 && r == m - 1) {
+            const int dj = hb.leg_dir[c];
+            fl |= WN3_JUNC | ((uint32_t)dj << 8);
+            jb.as[jb.natt] = (uint16_t)s;
+            jb.adirs |= (uint32_t)(dj ^ 1) << (3 * jb.natt);
+            ++jb.natt;
+          }
+          WNode3 &nd = nodes[w * (size_t)cap + s];
+          nd.ijk = pack(ch[r]);
+          nd.fl = fl;
+          ++s;
+        }
+      }
+    }
+  }
+  const size_t bn = (sizeof(WNode3) * nodes.size() + 15) & ~size_t(15);
+  char *mem = nullptr;
+  cudaError_t e = cudaMalloc(&mem, bn + sizeof(WBlock3) * blk.size());
+  if (e != cudaSuccess) { set_error("cudaMalloc(3D warp list)", e); return MG_ERR_ALLOC; }
+  Wl.mem = mem;
+  Wl.node = reinterpret_cast<WNode3 *>(mem);
+  Wl.blk = reinterpret_cast<WBlock3 *>(mem + bn);
+  e = cudaMemcpy(Wl.node, nodes.data(), sizeof(WNode3) * nodes.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(Wl.blk, blk.data(), sizeof(WBlock3) * blk.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { set_error("cudaMemcpy(3D warp list)", e); return MG_ERR_CUDA; }
+  Wl.nwarp = (int)bins.size();
+  Wl.K = K;
+  Wl.W = NW;
+  Wl.total_nodes = total;
+  return MG_OK;
+}
+
+template <typename T>
+T *lev_u(Grid &g, int l);
+template <>
+double *lev_u<double>(Grid &g, int l) { return g.g3->lev[l].u64; }
+template <>
+float *lev_u<float>(Grid &g, int l) { return g.g3->lev[l].u32; }
+template <typename T>
+T *lev_f(Grid &g, int l);
+template <>
+double *lev_f<double>(Grid &g, int l) { return g.g3->lev[l].f64; }
+template <>
+float *lev_f<float>(Grid &g, int l) { return g.g3->lev[l].f32; }
+template <typename T>
+T *defect_scratch(Grid &g);
+template <>
+double *defect_scratch<double>(Grid &g) { return g.g3->d64; }
+template <>
+float *defect_scratch<float>(Grid &g) { return g.g3->d32; }
+
+}  // namespace
+
+// --------------------------------------------------------------- entries --
+
+mg_status setup3(Grid &g, const int64_t *n, const double *const *coords) {
+  g.dim = 3;
+  g.g3 = new (std::nothrow) Grid3;
+  if (!g.g3) return MG_ERR_ALLOC;
+  Grid3 &G = *g.g3;
+  int cx = (int)n[0], cy = (int)n[1], cz = (int)n[2];
+  std::vector<double> xs(coords[0], coords[0] + cx + 1), ys(coords[1], coords[1] + cy + 1),
+      zs(coords[2], coords[2] + cz + 1);
+  while (true) {
+    Level3 L;
+    L.nx = cx; L.ny = cy; L.nz = cz;
+    L.nn = (size_t)(cx + 1) * (cy + 1) * (cz + 1);
+    L.hx = xs; L.hy = ys; L.hz = zs;
+    axis_coefficients(xs, L.hc[0], L.hc[1]);
+    axis_coefficients(ys, L.hc[2], L.hc[3]);
+    axis_coefficients(zs, L.hc[4], L.hc[5]);
+    G.lev.push_back(std::move(L));
+    if (cx % 2 || cy % 2 || cz % 2 || cx / 2 < 2 || cy / 2 < 2 || cz / 2 < 2 || std::max(cx, std::max(cy, cz)) <= 8)
+      break;
+    std::vector<double> xn(cx / 2 + 1), yn(cy / 2 + 1), zn(cz / 2 + 1);
+    for (int i = 0; i <= cx / 2; ++i) xn[i] = xs[2 * i];
+    for (int j = 0; j <= cy / 2; ++j) yn[j] = ys[2 * j];
+    for (int k = 0; k <= cz / 2; ++k) zn[k] = zs[2 * k];
+    xs.swap(xn); ys.swap(yn); zs.swap(zn);
+    cx /= 2; cy /= 2; cz /= 2;
+  }
+  g.nlev = (int)G.lev.size();
+  TRY_CUDA("3D kernel attributes", prepare3());
+  const bool want64 = g.prec_mask & 1, want32 = g.prec_mask & 2;
+  for (int l = 0; l < g.nlev; ++l) {
+    Level3 &L = G.lev[l];
+    const size_t len[6] = {(size_t)L.nx + 1, (size_t)L.nx + 1, (size_t)L.ny + 1, (size_t)L.ny + 1,
+                           (size_t)L.nz + 1, (size_t)L.nz + 1};
+    size_t tot = 0;
+    for (int a = 0; a < 6; ++a) tot += len[a];
+    TRY_CUDA("cudaMalloc(3D coefficients)", cudaMalloc(&L.dev_block, tot * (sizeof(double) + sizeof(float)) + 16));
+    double *dp = static_cast<double *>(L.dev_block);
+    float *fp = reinterpret_cast<float *>(dp + tot);
+    std::vector<double> hd;
+    std::vector<float> hf;
+    for (int a = 0; a < 6; ++a) {
+      L.c64[a] = dp + hd.size();
+      L.c32[a] = fp + hf.size();
+      for (double v : L.hc[a]) { hd.push_back(v); hf.push_back((float)v); }
+    }
+    TRY_CUDA("cudaMemcpy(3D coefficients)", cudaMemcpy(dp, hd.data(), sizeof(double) * tot, cudaMemcpyHostToDevice));
+    TRY_CUDA("cudaMemcpy(3D coefficients)", cudaMemcpy(fp, hf.data(), sizeof(float) * tot, cudaMemcpyHostToDevice));
+    if (l > 0) {
+      if (want64) {
+        TRY_CUDA("cudaMalloc(3D level)", cudaMalloc(&L.u64, sizeof(double) * L.nn));
+        TRY_CUDA("cudaMalloc(3D level)", cudaMalloc(&L.f64, sizeof(double) * L.nn));
+        TRY_CUDA("cudaMemset(3D level)", cudaMemset(L.u64, 0, sizeof(double) * L.nn));
+        TRY_CUDA("cudaMemset(3D level)", cudaMemset(L.f64, 0, sizeof(double) * L.nn));
+      }
+      if (want32) {
+        TRY_CUDA("cudaMalloc(3D level)", cudaMalloc(&L.u32, sizeof(float) * L.nn));
+        TRY_CUDA("cudaMalloc(3D level)", cudaMalloc(&L.f32, sizeof(float) * L.nn));
+        TRY_CUDA("cudaMemset(3D level)", cudaMemset(L.u32, 0, sizeof(float) * L.nn));
+        TRY_CUDA("cudaMemset(3D level)", cudaMemset(L.f32, 0, sizeof(float) * L.nn));
+      }
+    }
+    // tweed blocks of the smoothed levels
+    if (l + 1 < g.nlev) {
+      std::vector<HBlock3> blocks;
+      if (!blocks3(L, blocks)) {
+        set_error_text("3D tweed: a side with an odd number of intervals on a smoothed level");
+        return MG_ERR_UNSUPPORTED;
+      }
+      for (int c = 0; c < 2; ++c) TRY(warp_list3(L, blocks, c, L.wp[c]));
+    }
+  }
+  // coarsest level: dense inverse of the interior operator
+  {
+    const Level3 &L = G.lev[g.nlev - 1];
+    const int mx = L.nx - 1, my = L.ny - 1, mz = L.nz - 1, m = mx * my * mz;
+    if (m > 1024) return MG_ERR_SIZE;
+    G.cn = m;
+    std::vector<double> A((size_t)m * m, 0.0), inv;
+    for (int k = 1; k < L.nz; ++k)
+      for (int j = 1; j < L.ny; ++j)
+        for (int i = 1; i < L.nx; ++i) {
+          const int r = ((k - 1) * my + (j - 1)) * mx + (i - 1);
+          A[(size_t)r * m + r] = -(L.hc[0][i] + L.hc[1][i] + L.hc[2][j] + L.hc[3][j] + L.hc[4][k] + L.hc[5][k]);
+          if (i > 1) A[(size_t)r * m + r - 1] = L.hc[0][i];
+          if (i < L.nx - 1) A[(size_t)r * m + r + 1] = L.hc[1][i];
+          if (j > 1) A[(size_t)r * m + r - mx] = L.hc[2][j];
+          if (j < L.ny - 1) A[(size_t)r * m + r + mx] = L.hc[3][j];
+          if (k > 1) A[(size_t)r * m + r - mx * my] = L.hc[4][k];
+          if (k < L.nz - 1) A[(size_t)r * m + r + mx * my] = L.hc[5][k];
+        }
+    if (!invert(m, A, inv)) return MG_ERR_SIZE;
+    TRY_CUDA("cudaMalloc(3D coarse)", cudaMalloc(&G.cinv, sizeof(double) * inv.size()));
+    TRY_CUDA("cudaMemcpy(3D coarse)", cudaMemcpy(G.cinv, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice));
+  }
+  const size_t nn0 = G.lev[0].nn;
+  if (want64) TRY_CUDA("cudaMalloc(3D defect)", cudaMalloc(&G.d64, sizeof(double) * nn0));
+  if (want32) {
+    TRY_CUDA("cudaMalloc(3D defect)", cudaMalloc(&G.d32, sizeof(float) * nn0));
+    TRY_CUDA("cudaMalloc(e32)", cudaMalloc(&g.e32, sizeof(float) * nn0));
+    TRY_CUDA("cudaMalloc(r32)", cudaMalloc(&g.r32, sizeof(float) * nn0));
+    TRY_CUDA("cudaMemset(e32)", cudaMemset(g.e32, 0, sizeof(float) * nn0));
+    TRY_CUDA("cudaMemset(r32)", cudaMemset(g.r32, 0, sizeof(float) * nn0));
+  }
+  return MG_OK;
+}
+
+void free3(Grid &g) {
+  if (!g.g3) return;
+  for (Level3 &L : g.g3->lev) {
+    cudaFree(L.dev_block);
+    cudaFree(L.u64); cudaFree(L.f64); cudaFree(L.u32); cudaFree(L.f32);
+    for (int c = 0; c < 2; ++c) cudaFree(L.wp[c].mem);
+  }
+  cudaFree(g.g3->cinv);
+  cudaFree(g.g3->d64);
+  cudaFree(g.g3->d32);
+  delete g.g3;
+  g.g3 = nullptr;
+}
+
+template <typename T>
+mg_status colour_pass3(Grid &g, int l, int colour, T *u, const T *f, cudaStream_t s) {
+  Level3 &L = g.g3->lev[l];
+  if (l + 1 >= g.nlev) return MG_ERR_UNSUPPORTED;  // the coarsest level is solved directly
+  return cuda_status("3D tweed pass", launch_warp3<T>(L, L.wp[colour], u, f, s));
+}
+
+template <typename T>
+mg_status residual3(Grid &g, int l, const T *u, const T *f, T *d, cudaStream_t s) {
+  const Level3 &L = g.g3->lev[l];
+  TRY_CUDA("cudaMemsetAsync(3D defect)", cudaMemsetAsync(d, 0, sizeof(T) * L.nn, s));
+  count_launch(1);
+  return cuda_status("3D defect", launch_pdl(defect3_kernel<T>, interior_grid(L), dim3(T3), 0, s, coefs3<T>(L), L.nx,
+                                             L.ny, L.nz, u, f, d));
+}
+
+template <typename T>
+mg_status residual_restrict3(Grid &g, int l, const T *u, const T *f, T *fc, T *uc, cudaStream_t s) {
+  const Level3 &F = g.g3->lev[l], &C = g.g3->lev[l + 1];
+  T *d = defect_scratch<T>(g);
+  count_launch(2);
+  TRY_CUDA("3D defect", launch_pdl(defect3_kernel<T>, interior_grid(F), dim3(T3), 0, s, coefs3<T>(F), F.nx, F.ny,
+                                   F.nz, u, f, d));
+  return cuda_status("3D restriction", launch_pdl(restrict3_kernel<T>, interior_grid(C), dim3(T3), 0, s, F.nx, F.ny,
+                                                  C.nx, C.ny, C.nz, (const T *)d, fc, uc));
+}
+
+template <typename T>
+mg_status prolong_add3(Grid &g, int l, const T *uc, T *u, cudaStream_t s) {
+  const Level3 &F = g.g3->lev[l], &C = g.g3->lev[l + 1];
+  count_launch(1);
+  return cuda_status("3D prolongation", launch_pdl(prolong3_kernel<T>, interior_grid(F), dim3(T3), 0, s, F.nx, F.ny,
+                                                   C.nx, C.ny, uc, u));
+}
+
+template <typename T>
+mg_status coarse_solve3(Grid &g, T *u, const T *f, cudaStream_t s) {
+  const Level3 &L = g.g3->lev[g.nlev - 1];
+  if (g.g3->cn <= 0) return MG_OK;
+  count_launch(1);
+  return cuda_status("3D coarse solve", launch_pdl(coarse3_kernel<T>, dim3(1), dim3(CS3_THREADS),
+                                                   sizeof(double) * g.g3->cn, s, coefs3<double>(L), L.nx, L.ny, L.nz,
+                                                   (const double *)g.g3->cinv, u, f));
+}
+
+// One relaxation (red pass, black pass) and the cycle of Sec. 4 steps (2)-(6).
+template <typename T>
+mg_status cycle3(Grid &g, const mg_params &p, int l, T *u, const T *f, cudaStream_t s) {
+  if (l == g.nlev - 1) return coarse_solve3<T>(g, u, f, s);
+  for (int k = 0; k < p.nu1; ++k) {
+    TRY(colour_pass3<T>(g, l, 0, u, f, s));
+    TRY(colour_pass3<T>(g, l, 1, u, f, s));
+  }
+  T *uc = lev_u<T>(g, l + 1), *fc = lev_f<T>(g, l + 1);
+  TRY(residual_restrict3<T>(g, l, u, f, fc, uc, s));
+  for (int k = 0; k < p.cycle; ++k) TRY(cycle3<T>(g, p, l + 1, uc, fc, s));
+  TRY(prolong_add3<T>(g, l, uc, u, s));
+  for (int k = 0; k < p.nu2; ++k) {
+    TRY(colour_pass3<T>(g, l, 0, u, f, s));
+    TRY(colour_pass3<T>(g, l, 1, u, f, s));
+  }
+  return MG_OK;
+}
+
+mg_status zero_interior3(Grid &g, double *u, cudaStream_t s) {
+  const Level3 &L = g.g3->lev[0];
+  interior3_kernel<<<interior_grid(L), T3, 0, s>>>(L.nx, L.ny, u, nullptr, 0);
+  count_launch(1);
+  return cuda_status("3D zero interior", cudaGetLastError());
+}
+
+mg_status ir_update3(Grid &g, double *u, const float *e, cudaStream_t s) {
+  const Level3 &L = g.g3->lev[0];
+  interior3_kernel<<<interior_grid(L), T3, 0, s>>>(L.nx, L.ny, u, e, 1);
+  count_launch(1);
+  return cuda_status("3D refinement update", cudaGetLastError());
+}
+
+mg_status norms3(Grid &g, const double *u, const double *f, int bnd_only, float *r32, float *e32, cudaStream_t s) {
+  const Level3 &L = g.g3->lev[0];
+  norm3_stage1<<<g.npartial, N3_THREADS, 0, s>>>(coefs3<double>(L), L.nx, L.ny, L.nz, u, f, bnd_only, r32, e32,
+                                                 g.partial);
+  norm3_stage2<<<1, N3_THREADS, 0, s>>>(g.partial, g.npartial, g.scal);
+  count_launch(2);
+  return cuda_status("3D norms", cudaGetLastError());
+}
+
+template mg_status colour_pass3<double>(Grid &, int, int, double *, const double *, cudaStream_t);
+template mg_status colour_pass3<float>(Grid &, int, int, float *, const float *, cudaStream_t);
+template mg_status cycle3<double>(Grid &, const mg_params &, int, double *, const double *, cudaStream_t);
+template mg_status cycle3<float>(Grid &, const mg_params &, int, float *, const float *, cudaStream_t);
+template mg_status residual3<double>(Grid &, int, const double *, const double *, double *, cudaStream_t);
+template mg_status residual3<float>(Grid &, int, const float *, const float *, float *, cudaStream_t);
+template mg_status residual_restrict3<double>(Grid &, int, const double *, const double *, double *, double *,
+                                              cudaStream_t);
+template mg_status residual_restrict3<float>(Grid &, int, const float *, const float *, float *, float *, cudaStream_t);
+template mg_status prolong_add3<double>(Grid &, int, const double *, double *, cudaStream_t);
+template mg_status prolong_add3<float>(Grid &, int, const float *, float *, cudaStream_t);
+template mg_status coarse_solve3<double>(Grid &, double *, const double *, cudaStream_t);
+template mg_status coarse_solve3<float>(Grid &, float *, const float *, cudaStream_t);
+
+}  // namespace tmg

@@ -140,6 +140,53 @@ constexpr int WK_PREF = 4, WK_MAX_F32 = 16, WK_MAX_F64 = 8, WW_MAX = 8;
 constexpr int WARP_MAX_SIDE = 2048;
 
 // ---------------------------------------------------------------------------
+// 3D grids (Sec. 7): tweed only, on the warp path.  Directions 0..5 = +x, -x,
+// +y, -y, +z, -z (coefficients E_i, W_i, N_j, S_j, T_k, B_k); the opposite
+// of d is d ^ 1.  A 3D node descriptor packs i | j << 10 | k << 20 and the
+// directions to its predecessor (bits 0-2, WN3_PRED), successor (bits 4-6,
+// WN3_SUCC) and junction (bits 8-10, WN3_JUNC); unused slots are zero.
+enum : uint32_t { WN3_PRED = 1u << 3, WN3_SUCC = 1u << 7, WN3_JUNC = 1u << 11, WN3_VALID = 1u << 12 };
+struct WNode3 {
+  uint32_t ijk, fl;
+};
+static_assert(sizeof(WNode3) == 8, "WNode3 layout");
+// The junction of a 3D sequence: attached node e (< natt <= 6) is node as[e]
+// of the sequence, in direction (adirs >> 3e) & 7 from the junction.
+struct WBlock3 {
+  uint32_t ijk;
+  uint8_t has_j, natt, pad[2];
+  uint32_t adirs;
+  uint16_t as[6];
+  uint8_t pad2[8];
+};
+static_assert(sizeof(WBlock3) == 32, "WBlock3 layout");
+struct WarpList3 {
+  int nwarp = 0, K = 0, W = 1, total_nodes = 0;
+  void *mem = nullptr;
+  WNode3 *node = nullptr;
+  WBlock3 *blk = nullptr;
+};
+struct Level3 {
+  int nx = 0, ny = 0, nz = 0;
+  size_t nn = 0;
+  std::vector<double> hx, hy, hz;
+  std::vector<double> hc[6];          // host coefficients W, E, S, N, B, T
+  double *c64[6] = {};                // device coefficients (same order)
+  float *c32[6] = {};
+  void *dev_block = nullptr;          // one allocation behind the coefficients
+  double *u64 = nullptr, *f64 = nullptr;  // coarse-level workspaces
+  float *u32 = nullptr, *f32 = nullptr;
+  WarpList3 wp[2];                    // [colour]: shared by both precisions
+};
+struct Grid3 {
+  std::vector<Level3> lev;
+  int cn = 0;
+  double *cinv = nullptr;             // dense inverse of the coarsest interior operator
+  double *d64 = nullptr;              // defect scratch of the finest level's size
+  float *d32 = nullptr;
+};
+
+// ---------------------------------------------------------------------------
 // Tiled line path (tweed and zebra on large levels).  Every block is a set of
 // legs that each start at a wall, plus at most one junction node (the
 // paper's m-legged form, Eq. mLThomas; m = 1 for a line from wall to wall).
@@ -223,6 +270,8 @@ struct Level {
 };
 
 struct Grid {
+  int dim = 2;
+  Grid3 *g3 = nullptr;               // dim == 3: the 3D levels (lev then stays empty)
   int nlev = 0;
   int sms = 1;                       // multiprocessors of the device the grid was set up on
   int prec_mask = 3;
@@ -270,6 +319,33 @@ constexpr int TILE_MIN_SIDE = 1024;
 // Kernels launched by this library in this process (mg_kernel_launches).
 extern std::atomic<unsigned long long> g_launches;
 inline void count_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+// ---- host helpers (api.cu): Sec. 2 coefficients of one axis; Gauss-Jordan
+// inverse with partial pivoting (false if singular)
+void axis_coefficients(const std::vector<double> &x, std::vector<double> &lo, std::vector<double> &hi);
+bool invert(int n, std::vector<double> &A, std::vector<double> &inv);
+
+// ---- 3D grids (grid3d.cu)
+mg_status setup3(Grid &g, const int64_t *n, const double *const *coords);
+void free3(Grid &g);
+template <typename T>
+mg_status colour_pass3(Grid &g, int l, int colour, T *u, const T *f, cudaStream_t s);
+template <typename T>
+mg_status cycle3(Grid &g, const mg_params &p, int l, T *u, const T *f, cudaStream_t s);
+template <typename T>
+mg_status residual3(Grid &g, int l, const T *u, const T *f, T *d, cudaStream_t s);
+template <typename T>
+mg_status residual_restrict3(Grid &g, int l, const T *u, const T *f, T *fc, T *uc, cudaStream_t s);
+template <typename T>
+mg_status prolong_add3(Grid &g, int l, const T *uc, T *u, cudaStream_t s);
+template <typename T>
+mg_status coarse_solve3(Grid &g, T *u, const T *f, cudaStream_t s);
+// the FP64 steps of a solve: interior of u := 0; norms into g.scal[0]
+// (bnd_only: ||f - B g||^2; with r32: the refinement residual, e32 := 0);
+// u += e32
+mg_status zero_interior3(Grid &g, double *u, cudaStream_t s);
+mg_status norms3(Grid &g, const double *u, const double *f, int bnd_only, float *r32, float *e32, cudaStream_t s);
+mg_status ir_update3(Grid &g, double *u, const float *e, cudaStream_t s);
 
 // ---- host helpers (setup.cu)
 mg_status build_worklists(Grid &g, int level, int wl, int prec);

@@ -90,7 +90,7 @@ using namespace tmg;
 namespace {
 
 bool bad_args(const mg_grid *g, int level, int dtype) {
-  if (!g || level < 0 || level >= g->nlev) return true;
+  if (!g || g->dim != 2 || level < 0 || level >= g->nlev) return true;
   return !(dtype == MG_F64 && (g->prec_mask & 1)) && !(dtype == MG_F32 && (g->prec_mask & 2));
 }
 

@@ -37,7 +37,8 @@ EXPORTS = ["mg_setup_grid", "mg_destroy", "mg_num_levels", "mg_level_shape", "mg
            "mg_residual", "mg_coarse_solve", "mg_vcycle", "mg_solve", "mg_solve_adjoint",
            "mg_default_params", "mg_status_string", "mg_last_error", "mg_kernel_launches",
            "mg_residual_norm_static", "mg_pass_timer_begin", "mg_pass_timer_end", "mg_boundary_adjoint", "mg_batch_create",
-           "mg_batch_destroy", "mg_batch_solve", "mg_set_line_path", "mg_get_line_path", "mg_autotune"]
+           "mg_batch_destroy", "mg_batch_solve", "mg_set_line_path", "mg_get_line_path", "mg_autotune",
+           "mg_level_dims", "mg_grid_dim"]
 
 
 class MGError(RuntimeError):
@@ -105,6 +106,8 @@ def load(path: str = LIB_PATH):
         "mg_set_line_path": (i, [vp, i, i, i, i, i]),
         "mg_get_line_path": (i, [vp, i, i, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
         "mg_autotune": (i, [vp, i, i, i, ctypes.POINTER(ctypes.c_double), vp]),
+        "mg_level_dims": (i, [vp, i, i64p]),
+        "mg_grid_dim": (i, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -180,16 +183,19 @@ def default_params(**kw) -> Params:
 
 
 class Grid:
-    """mg_setup_grid on host coordinate arrays x (nx+1) and y (ny+1)."""
+    """mg_setup_grid on host coordinate arrays x (nx+1) and y (ny+1), and z
+    (nz+1) for a 3D grid (Sec. 7; arrays then have shape (nz+1, ny+1, nx+1))."""
 
-    def __init__(self, x, y, precision_mask: int = 3, stream=None):
+    def __init__(self, x, y, z=None, precision_mask: int = 3, stream=None):
         self.lib = load()
-        self.x = np.ascontiguousarray(x, dtype=np.float64)
-        self.y = np.ascontiguousarray(y, dtype=np.float64)
-        n = (ctypes.c_int64 * 2)(len(self.x) - 1, len(self.y) - 1)
-        coords = (ctypes.c_void_p * 2)(self.x.ctypes.data, self.y.ctypes.data)
+        axes = [np.ascontiguousarray(a, dtype=np.float64) for a in ((x, y) if z is None else (x, y, z))]
+        self.x, self.y = axes[0], axes[1]
+        self.z = axes[2] if z is not None else None
+        self.dim = len(axes)
+        n = (ctypes.c_int64 * self.dim)(*[len(a) - 1 for a in axes])
+        coords = (ctypes.c_void_p * self.dim)(*[a.ctypes.data for a in axes])
         h = ctypes.c_void_p()
-        _check(self.lib.mg_setup_grid(ctypes.byref(h), 2, n, coords, precision_mask,
+        _check(self.lib.mg_setup_grid(ctypes.byref(h), self.dim, n, coords, precision_mask,
                                       _stream(stream) if stream is not None else None), "mg_setup_grid")
         self.h = h
 
@@ -209,9 +215,12 @@ class Grid:
         return self.lib.mg_num_levels(self.h)
 
     def shape(self, level: int = 0):
-        nx, ny = ctypes.c_int64(), ctypes.c_int64()
-        _check(self.lib.mg_level_shape(self.h, level, ctypes.byref(nx), ctypes.byref(ny)), "mg_level_shape")
-        return ny.value + 1, nx.value + 1
+        """Array shape of a level: (ny+1, nx+1), or (nz+1, ny+1, nx+1) in 3D."""
+        d = (ctypes.c_int64 * 3)()
+        _check(self.lib.mg_level_dims(self.h, level, d), "mg_level_dims")
+        if self.dim == 3:
+            return d[2] + 1, d[1] + 1, d[0] + 1
+        return d[1] + 1, d[0] + 1
 
     # ---- relaxation
     def smooth(self, u, f, smoother="tweed", sweeps=1, level=0, stream=None):

@@ -1,0 +1,148 @@
+"""3D grids (Sec. 7) through the C ABI against the 3D oracle: tweed colour
+passes on every smoothed level (FP64 to 1e-10, FP32 to the FP32 smoothing
+tolerance), the 7-point defect, full-weighting restriction, trilinear
+prolongation and coarsest solve, the FP64 solve history per cycle (1e-12 on
+the relative residual, 1 % on the convergence factor) and FP32 cycles with
+FP64 refinement to 1e-10."""
+import numpy as np
+import pytest
+
+from paper_2110_08389_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+GRIDS3 = [  # (nx, ny, nz, kind, ratio)
+    (8, 8, 8, "wall", 20.0),
+    (16, 12, 10, "wall", 50.0),
+    (32, 32, 32, "wall", 200.0),
+    (24, 16, 32, "centre", 5.0),
+]
+
+
+def coords3(nx, ny, nz, kind, ratio):
+    return tuple(I.coords(n, kind, ratio=ratio) for n in (nx, ny, nz))
+
+
+def pair(mg, oracle_mod, grid):
+    xyz = coords3(*grid)
+    return mg.Grid(*xyz), oracle_mod.Problem3(*xyz)
+
+
+def cuda(a, dtype="f64"):
+    import torch
+    return torch.tensor(a, dtype=torch.float64 if dtype == "f64" else torch.float32, device="cuda")
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.double().cpu().numpy()
+
+
+def rel_err(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("grid", GRIDS3, ids=lambda t: f"{t[0]}x{t[1]}x{t[2]}-{t[3]}")
+def test_colour_pass_3d(mg, oracle_mod, grid):
+    g, P = pair(mg, oracle_mod, grid)
+    assert g.nlev == P.nlev
+    rng = np.random.default_rng(11)
+    for lev in range(g.nlev - 1):
+        assert g.shape(lev) == P.shape(lev)
+        u0, f = rng.standard_normal(P.shape(lev)), rng.standard_normal(P.shape(lev))
+        for colour in (0, 1):
+            ref = P.colour_pass(u0.copy(), f, colour, lev)
+            ud = cuda(u0)
+            g.colour_pass(ud, cuda(f), "tweed", colour, level=lev)
+            assert rel_err(host(ud), ref) <= 1e-10, (lev, colour, rel_err(host(ud), ref))
+        # FP32: one relaxation on FP32-rounded data
+        u32 = u0.astype(np.float32).astype(np.float64)
+        f32 = f.astype(np.float32).astype(np.float64)
+        ref = P.smooth(u32.copy(), f32, lev)
+        ud = cuda(u32, "f32")
+        g.smooth(ud, cuda(f32, "f32"), "tweed", 1, level=lev)
+        assert rel_err(host(ud), ref) <= 2e-4, (lev, rel_err(host(ud), ref))
+
+
+@pytest.mark.parametrize("grid", GRIDS3[1:], ids=lambda t: f"{t[0]}x{t[1]}x{t[2]}-{t[3]}")
+def test_transfers_and_coarse_3d(mg, oracle_mod, grid):
+    import torch
+    g, P = pair(mg, oracle_mod, grid)
+    rng = np.random.default_rng(12)
+    for lev in range(g.nlev - 1):
+        u, f = rng.standard_normal(P.shape(lev)), rng.standard_normal(P.shape(lev))
+        d_ref = P.residual(u, f, lev)
+        d = torch.empty_like(cuda(u))
+        g.residual(cuda(u), cuda(f), d, level=lev)
+        assert rel_err(host(d), d_ref) <= 1e-12
+        fc = torch.zeros(P.shape(lev + 1), dtype=torch.float64, device="cuda")
+        uc = torch.ones_like(fc)
+        g.residual_restrict(cuda(u), cuda(f), fc, uc, level=lev)
+        fc_ref = P.restrict(d_ref, lev)
+        inner = (slice(1, -1),) * 3
+        assert rel_err(host(fc)[inner], fc_ref[inner]) <= 1e-12
+        assert (host(uc)[inner] == 0).all()
+        ucr = rng.standard_normal(P.shape(lev + 1))
+        ucr[0, :, :] = ucr[-1, :, :] = 0; ucr[:, 0, :] = ucr[:, -1, :] = 0; ucr[:, :, 0] = ucr[:, :, -1] = 0
+        ud = cuda(u)
+        g.prolong_add(cuda(ucr), ud, level=lev)
+        assert rel_err(host(ud), P.prolong_add(ucr, u.copy(), lev)) <= 1e-13
+    lc = g.nlev - 1
+    u, f = rng.standard_normal(P.shape(lc)), rng.standard_normal(P.shape(lc))
+    ref = P.direct_solve(u.copy(), f, lc)
+    ud = cuda(u)
+    g.coarse_solve(ud, cuda(f))
+    assert rel_err(host(ud), ref) <= 1e-10
+
+
+@pytest.mark.parametrize("grid", [(32, 32, 32, "wall", 200.0), (16, 12, 10, "wall", 50.0)],
+                         ids=lambda t: f"{t[0]}x{t[1]}x{t[2]}")
+def test_solve_history_3d(mg, oracle_mod, grid):
+    """FP64 V(2,2) cycles: the relative residual after every cycle within
+    1e-12 of the oracle's and the convergence factor within 1 %."""
+    g, P = pair(mg, oracle_mod, grid)
+    rng = np.random.default_rng(13)
+    f = rng.standard_normal(P.shape())
+    bnd = rng.standard_normal(P.shape())
+    bnd[1:-1, 1:-1, 1:-1] = 0.0
+    u_ref = bnd.copy()
+    hist_ref = P.solve(u_ref, f, nu1=2, nu2=2, tol=1e-10, max_cycles=60)
+    ud = cuda(bnd)
+    res = g.solve(ud, cuda(f), smoother="tweed", nu1=2, nu2=2, tol=1e-10, max_cycles=60, precision="f64")
+    assert res.status == mg.OK
+    assert res.cycles == len(hist_ref) - 1
+    assert np.abs(np.asarray(res.history) - hist_ref).max() <= 1e-12
+    k = len(hist_ref) - 1
+    fac_ref = (hist_ref[-1] / hist_ref[0]) ** (1.0 / k)
+    assert abs(res.conv_factor - fac_ref) <= 0.01 * fac_ref
+    assert rel_err(host(ud), u_ref) <= 1e-8
+
+
+def test_f32_refine_3d(mg, oracle_mod):
+    g, P = pair(mg, oracle_mod, (64, 64, 64, "wall", 200.0))
+    f = np.random.default_rng(14).standard_normal(P.shape())
+    ud = cuda(np.zeros(P.shape()))
+    res = g.solve(ud, cuda(f), smoother="tweed", nu1=2, nu2=2, tol=1e-10, precision="f32_refine", max_outer=40,
+                  max_cycles=400)
+    assert res.status == mg.OK and res.rel_res <= 1e-10
+    d = P.residual(host(ud), f)
+    assert np.linalg.norm(d[1:-1, 1:-1, 1:-1]) / np.linalg.norm(f[1:-1, 1:-1, 1:-1]) <= 1.5e-10
+
+
+def test_3d_unsupported_requests(mg):
+    import torch
+    xyz = coords3(8, 8, 8, "wall", 10.0)
+    g = mg.Grid(*xyz)
+    assert g.dim == 3 and mg.load().mg_grid_dim(g.h) == 3
+    u = torch.zeros(g.shape(), dtype=torch.float64, device="cuda")
+    for sm in ("wireframe", "zebra_x", "checkerboard"):
+        with pytest.raises(mg.MGError) as e:
+            g.colour_pass(u, u, sm, 0)
+        assert e.value.status == mg.ERR_UNSUPPORTED
+    with pytest.raises(mg.MGError) as e:
+        g.solve(u, u.clone() + 1, smoother="wireframe")
+    assert e.value.status == mg.ERR_UNSUPPORTED
+    with pytest.raises(mg.MGError) as e:
+        mg.Batch([g])
+    assert e.value.status == mg.ERR_UNSUPPORTED

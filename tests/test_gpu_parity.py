@@ -266,7 +266,10 @@ def test_errors_are_status_codes(mg):
     xb[4] = xb[3]
     co = (ctypes.c_void_p * 2)(xb.ctypes.data, xb.ctypes.data)
     assert lib.mg_setup_grid(ctypes.byref(h), 2, n, co, 3, None) == mg.ERR_SIZE
-    assert lib.mg_setup_grid(ctypes.byref(h), 3, n, co, 3, None) == mg.ERR_UNSUPPORTED
+    n3 = (ctypes.c_int64 * 3)(8, 8, 8)
+    co3 = (ctypes.c_void_p * 3)(xb.ctypes.data, xb.ctypes.data, xb.ctypes.data)
+    assert lib.mg_setup_grid(ctypes.byref(h), 3, n3, co3, 3, None) == mg.ERR_SIZE
+    assert lib.mg_setup_grid(ctypes.byref(h), 4, n3, co3, 3, None) == mg.ERR_INVALID_ARG
     g = mg.Grid(np.linspace(0, 1, 9), np.linspace(0, 1, 9))
     assert lib.mg_smooth(g.h, 5, 4, None, None, 1, 0, None) == mg.ERR_INVALID_ARG
     # NaN in f -> non-finite residual status, never a trap

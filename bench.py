@@ -55,8 +55,10 @@ def parse():
                     help="FP32 cycles per refinement step (each step gains at most ~1e-3 in FP32 on this grid)")
     ap.add_argument("--intervals", type=int, default=N_INTERVALS, help="intervals per side (4096: the 4097 x 4097 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="single", choices=["single", "batch"],
-                    help="single: the 4097^2 solve (default); batch: 256 mixed problems solved together")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "3d"],
+                    help="single: the 4097^2 solve (default); batch: 256 mixed problems solved together; "
+                         "3d: the 257^3 tweed solve")
+    ap.add_argument("--inner3d", type=int, default=8, help="FP32 cycles per refinement step of the 3d workload")
     return ap.parse_args()
 
 
@@ -326,12 +328,128 @@ def run_batch(args):
     barrier(pg)
 
 
+def run_3d(args):
+    """Config 5: 3D Poisson on 257^3, tanh stretching towards all six walls
+    (spacing ratio 200), 3D tweed V(2,2) with full weighting (Sec. 7), to
+    ||r||/||f|| <= 1e-10: FP32 cycles with FP64 refinement against FP64."""
+    import numpy as np
+    import torch
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2110_08389_gb300 import build, inputs as I, mg
+    build.build()
+    n = 256
+    c = I.c_for_ratio(n, 200.0)
+    x = I.wall_coords(n, c)
+    f_h = I.rhs_gaussian(n + 1, (n + 1) * (n + 1), 1).reshape(n + 1, n + 1, n + 1)
+    grid = mg.Grid(x, x, x)
+    stream = torch.cuda.current_stream()
+    f = torch.tensor(f_h, device=dev)
+    u = torch.zeros_like(f)
+    p32 = mg.default_params(smoother="tweed", nu1=2, nu2=2, precision="f32_refine", tol=TOL,
+                            inner_cycles=args.inner3d, max_outer=400, max_cycles=4000)
+    p64 = mg.default_params(smoother="tweed", nu1=2, nu2=2, precision="f64", tol=TOL, max_cycles=1000)
+    for _ in range(args.warmup):
+        res = grid.solve(u, f, p32)
+    torch.cuda.synchronize()
+    barrier(pg)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = mg.kernel_launches()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            res = grid.solve(u, f, p32)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = (mg.kernel_launches() - l0) // max(args.steps, 1)
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, pg, dev)
+    u32 = u.clone()
+    r64 = grid.solve(u, f, p64)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    r64 = grid.solve(u, f, p64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = max_over_ranks(e0.elapsed_time(e1), pg, dev)
+    err32 = float((u32 - u).abs().max() / u.abs().max())
+    # end to end with host buffers
+    f_pin = torch.tensor(f_h).pin_memory()
+    u_pin = torch.zeros_like(f_pin).pin_memory()
+    out_pin = torch.empty_like(f_pin).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    u.copy_(u_pin, non_blocking=True)
+    f.copy_(f_pin, non_blocking=True)
+    grid.solve(u, f, p32)
+    out_pin.copy_(u, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e = time.perf_counter() - t0
+    # roofline: FP32 3D tweed colour passes on the finest level, back to back
+    uf = torch.zeros(f.shape, dtype=torch.float32, device=dev)
+    ff = f.float()
+    for k in range(4):
+        grid.colour_pass(uf, ff, "tweed", k & 1)
+    torch.cuda.synchronize()
+    npass = 40
+    e0.record(stream)
+    for k in range(npass):
+        grid.colour_pass(uf, ff, "tweed", k & 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pass_ms = e0.elapsed_time(e1) / npass
+    nn = (n + 1) ** 3
+    algo_bytes = 2 * 4 * nn
+    peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = algo_bytes / (pass_ms * 1e-3) / 1e9
+    line = {"metric": "s to rel. residual 1e-10, 257^3 3D tweed MG: FP32+refine vs FP64",
+            "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"3D Poisson 257^3, wall tanh c={c:.6f} on all three axes (spacing ratio 200), "
+                                   "f~N(0,1) seed 1, 3D tweed V(2,2), full weighting, trilinear, to ||r||/||f||<=1e-10",
+                       "nodes": nn, "inner_cycles": args.inner3d,
+                       "l2": "inputs (u, f: 2 x 136 MB FP64) larger than L2 (129 MB)"},
+            "status": res.status, "rel_res": res.rel_res, "outer_iters": res.outer_iters,
+            "inner_cycles_total": res.cycles, "conv_factor": res.conv_factor,
+            "fp64": {"s": ms64 / 1e3, "cycles": r64.cycles, "rel_res": r64.rel_res, "status": r64.status,
+                     "conv_factor": r64.conv_factor},
+            "speedup_vs_fp64": ms64 / ms, "f32_refine_vs_f64_solution_maxrel": err32,
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 2 * 8 * nn, "d2h_bytes_per_step": 8 * nn},
+            "gpu_launches": int(launches),
+            "roofline": {"kernel": "FP32 3D tweed colour pass, finest level (seq3_kernel)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "pass_ms": pass_ms, "passes_timed": npass, "launches_per_pass": 1,
+                         "algo_bytes_per_pass": algo_bytes,
+                         "peak_source": "hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"},
+            "clocks": clk.summary()}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        P = oracle.Problem3(x, x, x)
+        uo = np.zeros_like(f_h)
+        P.cycle(uo, f_h, 2, 2)  # untimed: builds the block partitions
+        t0 = time.perf_counter()
+        P.cycle(uo, f_h, 2, 2)
+        per_cycle = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": per_cycle * r64.cycles, "unit": "s", "cores": 1, "kind": "oracle",
+                                "sample": f"1 FP64 V(2,2) cycle of the C 3D oracle (single thread) on the full grid "
+                                          f"(after 1 untimed) = {per_cycle:.2f} s/cycle, x {r64.cycles} cycles (the "
+                                          f"FP64 iteration count of this problem)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    barrier(pg)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.workload == "3d":
+        return run_3d(args)
     import numpy as np
     import torch
 

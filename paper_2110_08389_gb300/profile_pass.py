@@ -2,9 +2,10 @@
 profilers (ncu) and quick timing.
 
     python -m paper_2110_08389_gb300.profile_pass [--n 4096] [--smoother tweed]
-           [--dtype f32|f64] [--steps 3] [--ratio 1000]
+           [--dtype f32|f64] [--steps 3] [--ratio 1000] [--dim 2|3]
 
-The grid has n x n intervals, tanh-stretched toward the walls (Eq. tanh) for
+The grid has n x n (x n with --dim 3, tweed only) intervals, tanh-stretched
+toward the walls (Eq. tanh) for
 every smoother but wireframe, toward the centre (Eq. tanh_inv) for wireframe,
 with the given max/min spacing ratio; f ~ N(0, 1) (seed 1), u = 0.  Each step
 is one relaxation (red pass, then black pass) on the finest level.  Prints
@@ -22,6 +23,7 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--ratio", type=float, default=1000.0)
+    ap.add_argument("--dim", type=int, default=2, choices=[2, 3])
     args = ap.parse_args()
     import torch
     from . import inputs as I, mg
@@ -29,10 +31,11 @@ def main():
     kind = "centre" if args.smoother == "wireframe" else "wall"
     c = I.c_for_ratio(args.n, args.ratio, kind)
     x = I.centre_coords(args.n, c) if kind == "centre" else I.wall_coords(args.n, c)
-    g = mg.Grid(x, x)
+    g = mg.Grid(x, x) if args.dim == 2 else mg.Grid(x, x, x)
     dt = torch.float32 if args.dtype == "f32" else torch.float64
-    f = torch.tensor(I.rhs_gaussian(args.n + 1, args.n + 1, 1), device="cuda").to(dt)
-    u = torch.zeros((args.n + 1, args.n + 1), dtype=dt, device="cuda")
+    shape = g.shape(0)
+    f = torch.tensor(I.rhs_gaussian(shape[0], int(np_prod(shape[1:])), 1).reshape(shape), device="cuda").to(dt)
+    u = torch.zeros(shape, dtype=dt, device="cuda")
     g.smooth(u, f, args.smoother, 1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -42,7 +45,14 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(args.steps - 1, 1)
-    print(f"{args.smoother} {args.dtype} n={args.n}: {ms:.4f} ms/step over {args.steps - 1} timed steps")
+    print(f"{args.smoother} {args.dtype} n={args.n} dim={args.dim}: {ms:.4f} ms/step over {args.steps - 1} timed steps")
+
+
+def np_prod(a):
+    out = 1
+    for v in a:
+        out *= v
+    return out
 
 
 if __name__ == "__main__":

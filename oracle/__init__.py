@@ -88,15 +88,15 @@ def _load():
             "o3_level_coeffs": (None, [P, i, dp, dp, dp, dp, dp, dp]),
             "o3_apply": (None, [P, i, dp, dp]),
             "o3_residual": (None, [P, i, dp, dp, dp]),
-            "o3_colour_pass": (i, [P, i, i, dp, dp]),
-            "o3_smooth": (i, [P, i, dp, dp]),
+            "o3_colour_pass": (i, [P, i, i, i, dp, dp]),
+            "o3_smooth": (i, [P, i, i, dp, dp]),
             "o3_restrict": (None, [P, i, dp, dp]),
             "o3_prolong_add": (None, [P, i, dp, dp]),
             "o3_direct_solve": (i, [P, i, dp, dp]),
-            "o3_partition": (i, [P, i, ip, ip, i]),
-            "o3_block_solve": (i, [P, i, i, dp, dp]),
-            "o3_cycle": (i, [P, i, i, dp, dp]),
-            "o3_solve": (i, [P, i, i, d, i, dp, dp, dp, i]),
+            "o3_partition": (i, [P, i, i, ip, ip, i]),
+            "o3_block_solve": (i, [P, i, i, i, dp, dp]),
+            "o3_cycle": (i, [P, i, i, i, dp, dp]),
+            "o3_solve": (i, [P, i, i, i, d, i, dp, dp, dp, i]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -340,10 +340,14 @@ def quadratic_loss_gradient(P: Problem, f, g, u_target):
     return loss, u.reshape(ny1, nx1), grad_f.reshape(ny1, nx1), grad_g.reshape(ny1, nx1)
 
 
+SMOOTHERS3 = {"tweed": 0, "wireframe": 1}
+
+
 class Problem3:
-    """3D tweed multigrid oracle (mg_oracle3d.c, Sec. 7) for the Dirichlet
-    problem of Eq. (prob:DP) with a third axis.  Arrays are (nz+1, ny+1, nx+1),
-    x fastest; only interior values of f and boundary values of u are read."""
+    """3D tweed / wireframe multigrid oracle (mg_oracle3d.c, Sec. 7) for the
+    Dirichlet problem of Eq. (prob:DP) with a third axis.  Arrays are
+    (nz+1, ny+1, nx+1), x fastest; only interior values of f and boundary
+    values of u are read."""
 
     def __init__(self, x, y, z):
         self.lib = _load()
@@ -388,15 +392,15 @@ class Problem3:
         self.lib.o3_residual(self.h, lev, u, f, d)
         return d
 
-    def colour_pass(self, u, f, colour, lev: int = 0):
+    def colour_pass(self, u, f, colour, lev: int = 0, smoother="tweed"):
         assert u.dtype == np.float64 and u.flags.c_contiguous
-        if self.lib.o3_colour_pass(self.h, lev, colour, u, _f64(f)):
+        if self.lib.o3_colour_pass(self.h, lev, SMOOTHERS3[smoother], colour, u, _f64(f)):
             raise RuntimeError("oracle colour pass failed")
         return u
 
-    def smooth(self, u, f, lev: int = 0):
+    def smooth(self, u, f, lev: int = 0, smoother="tweed"):
         assert u.dtype == np.float64 and u.flags.c_contiguous
-        if self.lib.o3_smooth(self.h, lev, u, _f64(f)):
+        if self.lib.o3_smooth(self.h, lev, SMOOTHERS3[smoother], u, _f64(f)):
             raise RuntimeError("oracle smoothing failed")
         return u
 
@@ -416,31 +420,31 @@ class Problem3:
             raise RuntimeError("singular")
         return u
 
-    def partition(self, lev: int = 0):
+    def partition(self, lev: int = 0, smoother="tweed"):
         """(owner of every node, -1 off the interior; colour of every block)."""
         owner = np.empty(self.shape(lev), dtype=np.int32)
         cap = owner.size
         colour = np.empty(cap, dtype=np.int32)
-        nb = self.lib.o3_partition(self.h, lev, owner, colour, cap)
+        nb = self.lib.o3_partition(self.h, lev, SMOOTHERS3[smoother], owner, colour, cap)
         return owner, colour[:nb].copy()
 
-    def block_solve(self, b, u, f, lev: int = 0):
+    def block_solve(self, b, u, f, lev: int = 0, smoother="tweed"):
         assert u.dtype == np.float64 and u.flags.c_contiguous
-        if self.lib.o3_block_solve(self.h, lev, b, u, _f64(f)):
+        if self.lib.o3_block_solve(self.h, lev, SMOOTHERS3[smoother], b, u, _f64(f)):
             raise RuntimeError("block solve failed")
         return u
 
-    def cycle(self, u, f, nu1=2, nu2=2):
+    def cycle(self, u, f, nu1=2, nu2=2, smoother="tweed"):
         assert u.dtype == np.float64 and u.flags.c_contiguous
-        if self.lib.o3_cycle(self.h, nu1, nu2, u, _f64(f)):
+        if self.lib.o3_cycle(self.h, SMOOTHERS3[smoother], nu1, nu2, u, _f64(f)):
             raise RuntimeError("oracle cycle failed")
         return u
 
-    def solve(self, u, f, nu1=2, nu2=2, tol=1e-10, max_cycles=100, cap=256):
+    def solve(self, u, f, nu1=2, nu2=2, tol=1e-10, max_cycles=100, cap=256, smoother="tweed"):
         """Cycles until tol; returns the relative-residual history."""
         assert u.dtype == np.float64 and u.flags.c_contiguous
         hist = np.zeros(cap)
-        k = self.lib.o3_solve(self.h, nu1, nu2, tol, max_cycles, u, _f64(f), hist, cap)
+        k = self.lib.o3_solve(self.h, SMOOTHERS3[smoother], nu1, nu2, tol, max_cycles, u, _f64(f), hist, cap)
         if k < 0:
             raise RuntimeError("oracle solve failed")
         return hist[:min(k, cap - 1) + 1].copy()

@@ -13,9 +13,12 @@
  *   - 3D tweed blocks (Sec. 7): starting from the eight corner points, legs
  *     perpendicular to the nearest wall, m = 2 or 3 legs per block, m = 6 at
  *     the centre of a cube;
+ *   - 3D wireframe blocks (Sec. 7): the faces of concentric cuboids, as
+ *     concentric rings on each face and the cuboid's edge skeleton;
  *   - each block solved exactly (Sec. 3), here by Gaussian elimination on the
  *     block's tree (leaves first), which is the m-legged Thomas of
- *     Eq. (mLThomas) for a star;
+ *     Eq. (mLThomas) for a star, and by dense LU for blocks with loops (the
+ *     rings of Eq. CircTri and the edge skeletons);
  *   - red pass, then black pass; V-cycle of Sec. 4 with a direct solve on the
  *     coarsest level.
  *
@@ -37,6 +40,11 @@
  *       drop below 2 intervals; the coarsest level is solved by dense LU.
  *   Q5  the stop test is that of the 2D solve: ||f - L u||_2 / ||f - B g||_2
  *       over interior nodes.
+ *   Q6  a 3D wireframe block is a connected set of interior nodes with equal
+ *       (d1, d2): for d1 < d2 a ring around the centre of a cuboid face (or a
+ *       line or point where the face degenerates), for d1 = d2 the cuboid's
+ *       twelve edges with its eight corners.  Red when d1 + d2 is even, so the
+ *       outermost skeleton is red, as the outermost ring is in 2D (Sec. 3).
  */
 #include <math.h>
 #include <stdio.h>
@@ -66,10 +74,12 @@ typedef struct {
   int *pool;
 } part3_t;
 
+enum { O3_TWEED = 0, O3_WIREFRAME = 1 };
+
 typedef struct {
   int nlev;
   lev3_t lev[O3_MAXLEV];
-  part3_t part[O3_MAXLEV];
+  part3_t part[O3_MAXLEV][2];  /* [level][tweed, wireframe] */
   int cn;
   double *clu;
   int *cpiv;
@@ -167,13 +177,14 @@ static double sumsq_interior(const lev3_t *L, const double *a) {
 
 /* --------------------------------------------------------- tweed blocks -- */
 
-static void key3(const lev3_t *L, int i, int j, int k, int *d2, int *d3) {
+/* block key of a node: (d2, d3) for tweed (Q2), (d1, d2) for wireframe (Q6) */
+static void key3(const lev3_t *L, int sm, int i, int j, int k, int *k1, int *k2) {
   int a = imin3(i, L->nx - i), b = imin3(j, L->ny - j), c = imin3(k, L->nz - k), t;
   if (a > b) { t = a; a = b; b = t; }
   if (b > c) { t = b; b = c; c = t; }
   if (a > b) { t = a; a = b; b = t; }
-  *d2 = b;
-  *d3 = c;
+  if (sm == O3_WIREFRAME) { *k1 = a; *k2 = b; }
+  else { *k1 = b; *k2 = c; }
 }
 
 static int uf_find(int *par, int x) {
@@ -181,8 +192,8 @@ static int uf_find(int *par, int x) {
   return x;
 }
 
-static int build_part(o3_problem *P, int lev) {
-  part3_t *T = &P->part[lev];
+static int build_part(o3_problem *P, int lev, int sm) {
+  part3_t *T = &P->part[lev][sm];
   if (T->built) return 0;
   const lev3_t *L = &P->lev[lev];
   const size_t nn = nn3(L);
@@ -193,12 +204,12 @@ static int build_part(o3_problem *P, int lev) {
     for (int j = 1; j < L->ny; ++j)
       for (int i = 1; i < L->nx; ++i) {
         int a2, a3;
-        key3(L, i, j, k, &a2, &a3);
+        key3(L, sm, i, j, k, &a2, &a3);
         for (int d = 1; d < 6; d += 2) {  /* +x, +y, +z */
           const int ii = i + DI[d], jj = j + DJ[d], kk = k + DK[d];
           if (!interior3(L, ii, jj, kk)) continue;
           int b2, b3;
-          key3(L, ii, jj, kk, &b2, &b3);
+          key3(L, sm, ii, jj, kk, &b2, &b3);
           if (a2 == b2 && a3 == b3) {
             const int r1 = uf_find(par, (int)I3(L, i, j, k)), r2 = uf_find(par, (int)I3(L, ii, jj, kk));
             if (r1 != r2) par[r1] = r2;
@@ -269,7 +280,7 @@ static int build_part(o3_problem *P, int lev) {
       const int p = B->node[0];
       const int i = p % (L->nx + 1), j = (p / (L->nx + 1)) % (L->ny + 1), k = p / ((L->nx + 1) * (L->ny + 1));
       int d2, d3;
-      key3(L, i, j, k, &d2, &d3);
+      key3(L, sm, i, j, k, &d2, &d3);
       B->colour = ((d2 + d3) % 2 == 0) ? 0 : 1;
     }
   }
@@ -356,16 +367,17 @@ static int solve_block3(const lev3_t *L, const part3_t *T, int b, double *u, con
   return 0;
 }
 
-int o3_colour_pass(o3_problem *P, int lev, int colour, double *u, const double *f) {
-  if (build_part(P, lev)) return -1;
-  const part3_t *T = &P->part[lev];
+int o3_colour_pass(o3_problem *P, int lev, int sm, int colour, double *u, const double *f) {
+  if (sm != O3_TWEED && sm != O3_WIREFRAME) return -1;
+  if (build_part(P, lev, sm)) return -1;
+  const part3_t *T = &P->part[lev][sm];
   for (int b = 0; b < T->nblock; ++b)
     if (T->blk[b].colour == colour && solve_block3(&P->lev[lev], T, b, u, f)) return -1;
   return 0;
 }
 
-int o3_smooth(o3_problem *P, int lev, double *u, const double *f) {
-  return o3_colour_pass(P, lev, 0, u, f) || o3_colour_pass(P, lev, 1, u, f);
+int o3_smooth(o3_problem *P, int lev, int sm, double *u, const double *f) {
+  return o3_colour_pass(P, lev, sm, 0, u, f) || o3_colour_pass(P, lev, sm, 1, u, f);
 }
 
 /* ------------------------------------------------------------ transfers -- */
@@ -525,7 +537,7 @@ void o3_destroy(o3_problem *P) {
   for (int k = 0; k < O3_MAXLEV; ++k) {
     lev3_t *L = &P->lev[k];
     free(L->x); free(L->y); free(L->z); free(L->W); free(L->E); free(L->S); free(L->N); free(L->B); free(L->T);
-    free(P->part[k].blk); free(P->part[k].owner); free(P->part[k].pool);
+    for (int sm = 0; sm < 2; ++sm) { free(P->part[k][sm].blk); free(P->part[k][sm].owner); free(P->part[k][sm].pool); }
     for (int s = 0; s < 3; ++s) free(P->work[k][s]);
   }
   free(P->clu); free(P->cpiv);
@@ -545,41 +557,45 @@ void o3_level_coeffs(o3_problem *P, int lev, double *W, double *E, double *S, do
 
 /* block owner of every node (-1 off the interior) and the colour of every
    block; returns the number of blocks */
-int o3_partition(o3_problem *P, int lev, int *owner, int *colour, int max_blocks) {
-  if (build_part(P, lev)) return -1;
-  const part3_t *T = &P->part[lev];
+int o3_partition(o3_problem *P, int lev, int sm, int *owner, int *colour, int max_blocks) {
+  if (sm != O3_TWEED && sm != O3_WIREFRAME) return -1;
+  if (build_part(P, lev, sm)) return -1;
+  const part3_t *T = &P->part[lev][sm];
   memcpy(owner, T->owner, sizeof(int) * nn3(&P->lev[lev]));
   for (int b = 0; b < T->nblock && b < max_blocks; ++b) colour[b] = T->blk[b].colour;
   return T->nblock;
 }
 
-int o3_block_solve(o3_problem *P, int lev, int b, double *u, const double *f) {
-  if (build_part(P, lev)) return -1;
-  if (b < 0 || b >= P->part[lev].nblock) return -1;
-  return solve_block3(&P->lev[lev], &P->part[lev], b, u, f);
+int o3_block_solve(o3_problem *P, int lev, int sm, int b, double *u, const double *f) {
+  if (sm != O3_TWEED && sm != O3_WIREFRAME) return -1;
+  if (build_part(P, lev, sm)) return -1;
+  if (b < 0 || b >= P->part[lev][sm].nblock) return -1;
+  return solve_block3(&P->lev[lev], &P->part[lev][sm], b, u, f);
 }
 
 /* --------------------------------------------------------------- cycles -- */
 
-static int cycle3(o3_problem *P, int nu1, int nu2, int lev, double *u, const double *f) {
+static int cycle3(o3_problem *P, int sm, int nu1, int nu2, int lev, double *u, const double *f) {
   if (lev == P->nlev - 1) return coarse3(P, u, f);
-  for (int s = 0; s < nu1; ++s) if (o3_smooth(P, lev, u, f)) return -1;
+  for (int s = 0; s < nu1; ++s) if (o3_smooth(P, lev, sm, u, f)) return -1;
   double *d = P->work[lev][2], *uc = P->work[lev + 1][0], *fc = P->work[lev + 1][1];
   o3_residual(P, lev, u, f, d);
   o3_restrict(P, lev, d, fc);
   memset(uc, 0, sizeof(double) * nn3(&P->lev[lev + 1]));
-  if (cycle3(P, nu1, nu2, lev + 1, uc, fc)) return -1;
+  if (cycle3(P, sm, nu1, nu2, lev + 1, uc, fc)) return -1;
   o3_prolong_add(P, lev, uc, u);
-  for (int s = 0; s < nu2; ++s) if (o3_smooth(P, lev, u, f)) return -1;
+  for (int s = 0; s < nu2; ++s) if (o3_smooth(P, lev, sm, u, f)) return -1;
   return 0;
 }
 
-int o3_cycle(o3_problem *P, int nu1, int nu2, double *u, const double *f) { return cycle3(P, nu1, nu2, 0, u, f); }
+int o3_cycle(o3_problem *P, int sm, int nu1, int nu2, double *u, const double *f) {
+  return cycle3(P, sm, nu1, nu2, 0, u, f);
+}
 
 /* V(nu1, nu2) cycles from u until ||f - L u|| / ||f - B g|| <= tol (Q5) or
    max_cycles; hist[k] = that ratio after cycle k (hist[0] before the first).
    Returns the number of cycles, -1 on failure. */
-int o3_solve(o3_problem *P, int nu1, int nu2, double tol, int max_cycles, double *u, const double *f,
+int o3_solve(o3_problem *P, int sm, int nu1, int nu2, double tol, int max_cycles, double *u, const double *f,
              double *hist, int cap) {
   const lev3_t *L = &P->lev[0];
   const size_t nn = nn3(L);
@@ -597,7 +613,7 @@ int o3_solve(o3_problem *P, int nu1, int nu2, double tol, int max_cycles, double
   if (cap > 0) hist[0] = rel;
   int k = 0;
   while (rel > tol && k < max_cycles) {
-    if (o3_cycle(P, nu1, nu2, u, f)) { free(d); free(g); return -1; }
+    if (o3_cycle(P, sm, nu1, nu2, u, f)) { free(d); free(g); return -1; }
     ++k;
     o3_residual(P, 0, u, f, d);
     rel = sqrt(sumsq_interior(L, d)) / fn;

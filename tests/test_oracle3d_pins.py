@@ -1,8 +1,10 @@
-"""Pins of the 3D tweed oracle (oracle/mg_oracle3d.c, Sec. 7) against what the
-paper and the mathematics fix: block shapes the paper describes, exact block
-solves against a dense library solve, the properties of the 7-point operator,
-the tensor-product transfers, and the multigrid solve against a dense LU solve
-and against a manufactured solution (second-order convergence)."""
+"""Pins of the 3D tweed and wireframe oracle (oracle/mg_oracle3d.c, Sec. 7)
+against what the paper and the mathematics fix: block shapes the paper
+describes, the disjointness of the two motifs and their complement (Sec. 7,
+complementarity), exact block solves against a dense library solve, the
+properties of the 7-point operator, the tensor-product transfers, and the
+multigrid solve against a dense LU solve and against a manufactured solution
+(second-order convergence)."""
 import numpy as np
 import pytest
 
@@ -88,16 +90,17 @@ def test_cube_centre_block_has_six_legs(n):
     assert (owner == b).sum() == 6 * (c - 1) + 1
 
 
+@pytest.mark.parametrize("smoother", ["tweed", "wireframe"])
 @pytest.mark.parametrize("dims", [(8, 6, 10), (7, 6, 5)])
-def test_block_solve_equals_dense_solve(dims):
-    """Every block solve (tree elimination; dense for the loops of odd sides)
-    equals numpy's dense solve of that block's system, the other nodes held
-    fixed (Sec. 3: exact block relaxation)."""
+def test_block_solve_equals_dense_solve(dims, smoother):
+    """Every block solve (tree elimination; dense for loops) equals numpy's
+    dense solve of that block's system, the other nodes held fixed (Sec. 3:
+    exact block relaxation)."""
     P = oracle.Problem3(*grid3(*dims, "wall", 50.0))
     rng = np.random.default_rng(3)
     shape = P.shape()
     u0, f = rng.standard_normal(shape), rng.standard_normal(shape)
-    owner, colour = P.partition()
+    owner, colour = P.partition(smoother=smoother)
     co = P.coeffs()
     for b in range(len(colour)):
         nodes = [tuple(x) for x in np.argwhere(owner == b)]
@@ -116,20 +119,21 @@ def test_block_solve_equals_dense_solve(dims):
                     r[n] -= c6[d] * u0[q]
         x = np.linalg.solve(A, r)
         u = u0.copy()
-        P.block_solve(b, u, f)
+        P.block_solve(b, u, f, smoother=smoother)
         got = np.array([u[p] for p in nodes])
         assert np.abs(got - x).max() <= 1e-12 * max(1.0, np.abs(x).max()), b
         mask = owner != b
         assert np.array_equal(u[mask], u0[mask])
 
 
-def test_colour_pass_zeroes_the_relaxed_rows():
+@pytest.mark.parametrize("smoother", ["tweed", "wireframe"])
+def test_colour_pass_zeroes_the_relaxed_rows(smoother):
     P = oracle.Problem3(*grid3(12, 10, 8, "wall", 200.0))
     rng = np.random.default_rng(4)
     u0, f = rng.standard_normal(P.shape()), rng.standard_normal(P.shape())
-    owner, colour = P.partition()
+    owner, colour = P.partition(smoother=smoother)
     for c in (0, 1):
-        u = P.colour_pass(u0.copy(), f, c)
+        u = P.colour_pass(u0.copy(), f, c, smoother=smoother)
         d = P.residual(u, f)
         scale = np.abs(P.apply(np.abs(u)) * 0 + f).max() + np.abs(P.coeffs()["W"]).max() * np.abs(u).max() * 6
         relaxed = (owner >= 0) & (colour[np.maximum(owner, 0)] == c)
@@ -182,8 +186,9 @@ def test_transfers_are_tensor_products():
     assert np.allclose(u[inner], ref[inner], rtol=0, atol=1e-12)
 
 
-def test_multigrid_solve_equals_dense_lu():
-    x, y, z = grid3(16, 16, 8, "wall", 100.0)
+@pytest.mark.parametrize("smoother,kind,nz,ratio", [("tweed", "wall", 8, 100.0), ("wireframe", "centre", 16, 10.0)])
+def test_multigrid_solve_equals_dense_lu(smoother, kind, nz, ratio):
+    x, y, z = grid3(16, 16, nz, kind, ratio)
     P = oracle.Problem3(x, y, z)
     assert P.nlev == 2
     rng = np.random.default_rng(5)
@@ -192,7 +197,7 @@ def test_multigrid_solve_equals_dense_lu():
     g[1:-1, 1:-1, 1:-1] = 0.0
     ref = P.direct_solve(g.copy(), f)
     u = g.copy()
-    hist = P.solve(u, f, nu1=2, nu2=2, tol=1e-12, max_cycles=60)
+    hist = P.solve(u, f, nu1=2, nu2=2, tol=1e-12, max_cycles=60, smoother=smoother)
     assert hist[-1] <= 1e-12 and len(hist) < 40
     assert np.abs(u - ref).max() <= 1e-9 * np.abs(ref).max()
 
@@ -226,3 +231,137 @@ def test_tweed_cycles_converge_on_stretched_grid():
     hist = P.solve(u, f, nu1=1, nu2=1, tol=1e-10, max_cycles=40)
     assert hist[-1] <= 1e-10
     assert (hist[-1] / hist[0]) ** (1.0 / (len(hist) - 1)) < 0.35
+
+
+def block_graph(owner):
+    """Per block: node count, in-block edge count, in-block degree of every
+    interior node (a brute-force walk over the grid, independent of the
+    oracle's construction)."""
+    nb = owner.max() + 1
+    sizes = np.bincount(owner[owner >= 0], minlength=nb)
+    edges = np.zeros(nb, dtype=np.int64)
+    deg = np.zeros(owner.shape, dtype=np.int64)
+    for k, j, i in interior_nodes(owner.shape):
+        for di, dj, dk in DIRS[1::2]:
+            kk, jj, ii = k + dk, j + dj, i + di
+            if owner[kk, jj, ii] >= 0 and owner[kk, jj, ii] == owner[k, j, i]:
+                edges[owner[k, j, i]] += 1
+                deg[k, j, i] += 1
+                deg[kk, jj, ii] += 1
+    return sizes, edges, deg
+
+
+def classify(owner, b, sizes, edges, deg):
+    d = deg[owner == b]
+    n, e = sizes[b], edges[b]
+    if n == 1:
+        return "point"
+    if e == n - 1 and d.max() <= 2:
+        return "path"
+    if e == n and (d == 2).all():
+        return "ring"
+    if e == n + 4 and (d == 3).sum() == 8 and (d[d != 3] == 2).all():
+        return "skeleton"
+    return "other"
+
+
+@pytest.mark.parametrize("dims", [(10, 10, 10), (10, 8, 6), (16, 12, 10), (8, 8, 16)])
+def test_wireframe_blocks_are_rings_on_cuboid_faces_and_edge_skeletons(dims):
+    """Sec. 7: wireframe blocks cover the faces of concentric cuboids; on each
+    cuboid the twelve edges form one block (eight three-way corners, a graph
+    with five independent loops), and every face carries concentric rings
+    (Eq. CircTri systems), closing in a line or a point at the face centre."""
+    P = oracle.Problem3(*grid3(*dims, "centre", 20.0))
+    owner, colour = P.partition(smoother="wireframe")
+    sizes, edges, deg = block_graph(owner)
+    kinds = [classify(owner, b, sizes, edges, deg) for b in range(len(colour))]
+    assert "other" not in kinds
+    nx, ny, nz = dims
+    # one skeleton per concentric cuboid whose three sides are all at least 2
+    n_skel = sum(1 for t in range(1, min(dims) // 2) if min(nx, ny, nz) - 2 * t >= 2)
+    assert kinds.count("skeleton") == n_skel
+    # the outermost skeleton (through the corner node (1, 1, 1)) is red: the
+    # relaxation starts at the domain faces
+    b0 = owner[1, 1, 1]
+    assert kinds[b0] == "skeleton" and colour[b0] == 0
+    # skeleton nodes are exactly the nodes whose two smallest wall distances
+    # are equal (d1 == d2) on a cuboid with no flat side; on a flat cuboid
+    # (its smallest side 0) those nodes close a ring, a line or a point
+    for k, j, i in interior_nodes(owner.shape):
+        a = sorted([min(i, nx - i), min(j, ny - j), min(k, nz - k)])
+        solid = min(dims) - 2 * a[0] >= 2
+        assert (kinds[owner[k, j, i]] == "skeleton") == (a[0] == a[1] and solid), (k, j, i)
+    # neighbouring blocks differ in colour
+    for k, j, i in interior_nodes(owner.shape):
+        for di, dj, dk in DIRS[1::2]:
+            kk, jj, ii = k + dk, j + dj, i + di
+            a, b = owner[k, j, i], owner[kk, jj, ii]
+            if b >= 0 and a != b:
+                assert colour[a] != colour[b]
+
+
+@pytest.mark.parametrize("n", [8, 12])
+def test_wireframe_cube_has_point_blocks_at_face_centres(n):
+    """Sec. 7: with nx = ny = nz a point relaxation sits at the centre of each
+    face of each concentric cuboid."""
+    P = oracle.Problem3(*grid3(n, n, n, "centre", 20.0))
+    owner, _ = P.partition(smoother="wireframe")
+    sizes = np.bincount(owner[owner >= 0])
+    c = n // 2
+    for t in range(1, c):
+        for p in [(t, c, c), (n - t, c, c), (c, t, c), (c, n - t, c), (c, c, t), (c, c, n - t)]:
+            if t < c:
+                assert sizes[owner[p]] == 1, (t, p)
+
+
+@pytest.mark.parametrize("dims", [(10, 10, 10), (12, 8, 6)])
+def test_tweed_and_wireframe_are_disjoint_and_leave_the_complementary_wires(dims):
+    """Sec. 7 (complementarity): the in-block wires of the tweed and wireframe
+    motifs never overlap, and every wire left over connects two nodes that
+    keep the smallest and largest of their three wall distances, the
+    complementary wireframe motif that circles the cuboids' corners."""
+    P = oracle.Problem3(*grid3(*dims))
+    ot, _ = P.partition(smoother="tweed")
+    ow, _ = P.partition(smoother="wireframe")
+    nx, ny, nz = dims
+
+    def srt(k, j, i):
+        return sorted([min(i, nx - i), min(j, ny - j), min(k, nz - k)])
+
+    counts = {"tweed": 0, "wireframe": 0, "rest": 0}
+    for k, j, i in interior_nodes(ot.shape):
+        for di, dj, dk in DIRS[1::2]:
+            kk, jj, ii = k + dk, j + dj, i + di
+            if ot[kk, jj, ii] < 0:
+                continue
+            in_t = ot[k, j, i] == ot[kk, jj, ii]
+            in_w = ow[k, j, i] == ow[kk, jj, ii]
+            assert not (in_t and in_w), (k, j, i)
+            if in_t:
+                counts["tweed"] += 1
+            elif in_w:
+                counts["wireframe"] += 1
+            else:
+                a, b = srt(k, j, i), srt(kk, jj, ii)
+                assert a[0] == b[0] and a[2] == b[2] and a[1] != b[1]
+                counts["rest"] += 1
+    assert min(counts.values()) > 0
+
+
+def test_wireframe_cycles_converge_on_centre_clustered_grid():
+    """3D wireframe V(2,2) cycles on a grid clustered towards the centre
+    (Eq. tanh_inv on every axis), the case wireframe is built for: faster
+    than tweed there.  (Near the centre planes' intersections the cells are
+    thin in two directions at once, which line blocks do not cover, so the
+    rate stays well above the 2D one.)"""
+    x, y, z = grid3(32, 32, 32, "centre", 10.0)
+    P = oracle.Problem3(x, y, z)
+    f = np.random.default_rng(7).standard_normal(P.shape())
+    u = np.zeros(P.shape())
+    hist = P.solve(u, f, nu1=2, nu2=2, tol=1e-10, max_cycles=60, smoother="wireframe")
+    assert hist[-1] <= 1e-10
+    rho_w = (hist[-1] / hist[0]) ** (1.0 / (len(hist) - 1))
+    u = np.zeros(P.shape())
+    ht = P.solve(u, f, nu1=2, nu2=2, tol=1e-10, max_cycles=60, smoother="tweed")
+    rho_t = (ht[-1] / ht[0]) ** (1.0 / (len(ht) - 1))
+    assert rho_w < 0.6 and rho_w < 0.8 * rho_t, (rho_w, rho_t)

@@ -376,7 +376,10 @@ int o3_colour_pass(o3_problem *P, int lev, int sm, int colour, double *u, const 
   return 0;
 }
 
+/* one relaxation: red pass, black pass; sm = 2 is the alternating scheme of
+   Sec. 3 applied in 3D, one tweed relaxation followed by one wireframe one */
 int o3_smooth(o3_problem *P, int lev, int sm, double *u, const double *f) {
+  if (sm == 2) return o3_smooth(P, lev, O3_TWEED, u, f) || o3_smooth(P, lev, O3_WIREFRAME, u, f);
   return o3_colour_pass(P, lev, sm, 0, u, f) || o3_colour_pass(P, lev, sm, 1, u, f);
 }
 

@@ -395,8 +395,14 @@ mg_status check_params(const Grid *g, const mg_params *p) {
   if (p->precision == MG_PREC_F32_REFINE && !(g->prec_mask & 2)) return MG_ERR_INVALID_ARG;
   if (p->precision != MG_PREC_F64 && p->precision != MG_PREC_F32_REFINE) return MG_ERR_INVALID_ARG;
   if (!(p->tol >= 0.0) || p->max_cycles < 0 || p->max_outer < 0 || p->inner_cycles < 1) return MG_ERR_INVALID_ARG;
-  // 3D grids: the tweed smoother with full weighting (Sec. 7)
-  if (g->dim == 3 && (p->smoother != MG_SMOOTH_TWEED || p->restriction != MG_RESTRICT_FW)) return MG_ERR_UNSUPPORTED;
+  // 3D grids: tweed, wireframe or both alternating, with full weighting (Sec. 7)
+  if (g->dim == 3 && ((p->smoother != MG_SMOOTH_TWEED && p->smoother != MG_SMOOTH_WIREFRAME &&
+                       p->smoother != MG_SMOOTH_ALT_TW) ||
+                      p->restriction != MG_RESTRICT_FW))
+    return MG_ERR_UNSUPPORTED;
+  if (g->dim == 3 && p->smoother != MG_SMOOTH_TWEED)
+    for (int l = 0; l + 1 < g->nlev; ++l)
+      if (!g->g3->lev[l].wf_ok) return MG_ERR_UNSUPPORTED;
   return MG_OK;
 }
 
@@ -619,9 +625,10 @@ mg_status mg_colour_pass(mg_grid *g, int level, int smoother, int colour, void *
     return MG_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (g->dim == 3) {
-    if (smoother != MG_SMOOTH_TWEED) return MG_ERR_UNSUPPORTED;
-    if (dtype == MG_F64) return colour_pass3<double>(*g, level, colour, (double *)u, (const double *)f, s);
-    return colour_pass3<float>(*g, level, colour, (float *)u, (const float *)f, s);
+    if (smoother != MG_SMOOTH_TWEED && smoother != MG_SMOOTH_WIREFRAME) return MG_ERR_UNSUPPORTED;
+    const int sm = smoother == MG_SMOOTH_WIREFRAME ? SM3_WIREFRAME : SM3_TWEED;
+    if (dtype == MG_F64) return colour_pass3<double>(*g, level, sm, colour, (double *)u, (const double *)f, s);
+    return colour_pass3<float>(*g, level, sm, colour, (float *)u, (const float *)f, s);
   }
   if (dtype == MG_F64) return colour_pass<double>(*g, level, smoother, colour, (double *)u, (const double *)f, s);
   return colour_pass<float>(*g, level, smoother, colour, (float *)u, (const float *)f, s);
@@ -633,12 +640,16 @@ mg_status mg_smooth(mg_grid *g, int level, int smoother, void *u, const void *f,
   if (smoother < 0 || smoother > MG_SMOOTH_ALT_TW) return MG_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (g->dim == 3) {
-    if (smoother != MG_SMOOTH_TWEED) return MG_ERR_UNSUPPORTED;
+    if (smoother != MG_SMOOTH_TWEED && smoother != MG_SMOOTH_WIREFRAME && smoother != MG_SMOOTH_ALT_TW)
+      return MG_ERR_UNSUPPORTED;
+    const int order[2] = {smoother == MG_SMOOTH_WIREFRAME ? MG_SMOOTH_WIREFRAME : MG_SMOOTH_TWEED,
+                          smoother == MG_SMOOTH_ALT_TW ? MG_SMOOTH_WIREFRAME : -1};
     for (int k = 0; k < sweeps; ++k)
-      for (int c = 0; c < 2; ++c) {
-        const mg_status st = mg_colour_pass(g, level, smoother, c, u, f, dtype, stream);
-        if (st != MG_OK) return st;
-      }
+      for (int m = 0; m < 2 && order[m] >= 0; ++m)
+        for (int c = 0; c < 2; ++c) {
+          const mg_status st = mg_colour_pass(g, level, order[m], c, u, f, dtype, stream);
+          if (st != MG_OK) return st;
+        }
     return MG_OK;
   }
   for (int k = 0; k < sweeps; ++k) {

@@ -60,44 +60,187 @@ __device__ __forceinline__ T cdir(const C6<T> &c, unsigned d, int i, int j, int 
 
 constexpr int WARP3_KMAX = 8, WARP3_WMAX = 8, WARP3_KPREF = 4;
 
+// Skeleton CTAs of a launch: edge scratch rows (a, b, c, r, zA, zB), each
+// `stride` values long.
+template <typename T>
+struct SkelArgs {
+  const WSkel3 *skel;
+  T *scr;
+  size_t stride;
+  int nskel;
+};
+
+__device__ __forceinline__ void unpack3(uint32_t v, int &i, int &j, int &k) {
+  i = (int)(v & 1023u); j = (int)((v >> 10) & 1023u); k = (int)(v >> 20);
+}
+
+// One wireframe edge skeleton per CTA (Sec. 7; the wireframe extension of
+// the Thomas algorithm): every edge is a tridiagonal chain between two
+// corners, eliminated by Thomas with three right-hand sides (the data, and
+// the responses to unit values at its two corners); the eight corner rows
+// then form an 8 x 8 system, solved by elimination (an M-matrix: no
+// pivoting); the edges are recombined from the corner values.
+__device__ __forceinline__ long long step3(unsigned d, int nx1, long long plane) {
+  const long long m = d < 2 ? 1 : (d < 4 ? (long long)nx1 : plane);
+  return (d & 1u) ? -m : m;
+}
+
+template <typename T>
+__device__ __noinline__ void skel_cta(const WSkel3 *__restrict__ S, T *__restrict__ scr, size_t stride,
+                                      const T *__restrict__ cW, const T *__restrict__ cE, const T *__restrict__ cS,
+                                      const T *__restrict__ cN, const T *__restrict__ cB, const T *__restrict__ cT,
+                                      int nx1, int ny1, T *__restrict__ u, const T *__restrict__ f) {
+  __shared__ T M[8][9];
+  __shared__ T X[8];
+  const C6<T> cp{cW, cE, cS, cN, cB, cT};
+  const int t = threadIdx.x, nt = blockDim.x;
+  const long long plane = (long long)nx1 * ny1;
+  const int e0 = (int)S->eoff[0], e12 = (int)S->eoff[12];
+  T *rA = scr, *rB = rA + stride, *rC = rB + stride, *rR = rC + stride, *rZA = rR + stride, *rZB = rZA + stride;
+  pdl_wait();
+  // 1. staging: the chain rows of every edge node
+  for (int q = e0 + t; q < e12; q += nt) {
+    int e = 0;
+    while ((int)S->eoff[e + 1] <= q) ++e;
+    const int sidx = q - (int)S->eoff[e];
+    const unsigned d = S->ed[e];
+    int i, j, k;
+    unpack3(S->cijk[S->ea[e]], i, j, k);
+    const long long p = (long long)k * plane + (long long)j * nx1 + i + (long long)(sidx + 1) * step3(d, nx1, plane);
+    const int pi = (int)(p % nx1), pj = (int)((p / nx1) % ny1), pk = (int)(p / plane);
+    T bb = T(0), r = __ldg(f + p), aa = T(0), cc = T(0);
+#pragma unroll
+    for (unsigned dd = 0; dd < 6; ++dd) {
+      const T cd = cdir(cp, dd, pi, pj, pk);
+      bb -= cd;
+      if (dd == (d ^ 1u)) aa = cd;
+      else if (dd == d) cc = cd;
+      else r -= cd * u[p + step3(dd, nx1, plane)];
+    }
+    rA[q] = aa; rB[q] = bb; rC[q] = cc; rR[q] = r;
+  }
+  __syncthreads();
+  // 2. Thomas per edge (thread e): columns y (data), zA, zB (unit corner values)
+  if (t < 12) {
+    const int o = (int)S->eoff[t], m = (int)S->eoff[t + 1] - o;
+    T cpv = T(0), y = T(0), za = T(0), cl = T(0), inv = T(0);
+    for (int s = 0; s < m; ++s) {
+      const T a = rA[o + s];
+      inv = T(1) / (rB[o + s] - a * cpv);
+      cl = rC[o + s];
+      cpv = cl * inv;
+      y = (rR[o + s] - a * y) * inv;
+      za = ((s == 0 ? -a : T(0)) - a * za) * inv;
+      rC[o + s] = cpv; rR[o + s] = y; rZA[o + s] = za;
+    }
+    T zb = -cl * inv;  // the last row's coupling to corner eb
+    if (m > 0) rZB[o + m - 1] = zb;
+    for (int s = m - 2; s >= 0; --s) {
+      const T c = rC[o + s];
+      y = rR[o + s] - c * y;
+      za = rZA[o + s] - c * za;
+      zb = -c * zb;
+      rR[o + s] = y; rZA[o + s] = za; rZB[o + s] = zb;
+    }
+  }
+  __syncthreads();
+  // 3. corner rows (thread q), then elimination (thread 0)
+  if (t < 8) {
+    int i, j, k;
+    unpack3(S->cijk[t], i, j, k);
+    const long long p = (long long)k * plane + (long long)j * nx1 + i;
+    for (int c = 0; c < 8; ++c) M[t][c] = T(0);
+    unsigned inblk = 0;
+    T diag = T(0), rhs = __ldg(f + p);
+    for (int e = 0; e < 12; ++e) {
+      const int o = (int)S->eoff[e], m = (int)S->eoff[e + 1] - o;
+      if (S->ea[e] == t) {  // the edge's first node is next to this corner
+        const unsigned d = S->ed[e];
+        inblk |= 1u << d;
+        const T kc = cdir(cp, d, i, j, k);
+        M[t][t] += kc * rZA[o];
+        M[t][S->eb[e]] += kc * rZB[o];
+        rhs -= kc * rR[o];
+      } else if (S->eb[e] == t) {
+        const unsigned d = S->ed[e] ^ 1u;
+        inblk |= 1u << d;
+        const T kc = cdir(cp, d, i, j, k);
+        M[t][S->ea[e]] += kc * rZA[o + m - 1];
+        M[t][t] += kc * rZB[o + m - 1];
+        rhs -= kc * rR[o + m - 1];
+      }
+    }
+    for (unsigned d = 0; d < 6; ++d) {
+      const T cd = cdir(cp, d, i, j, k);
+      diag -= cd;
+      if (!(inblk & (1u << d))) rhs -= cd * u[p + step3(d, nx1, plane)];
+    }
+    M[t][t] += diag;
+    M[t][8] = rhs;
+  }
+  __syncthreads();
+  if (t == 0) {
+    for (int c = 0; c < 8; ++c) {
+      const T ip = T(1) / M[c][c];
+      for (int r = c + 1; r < 8; ++r) {
+        const T l = M[r][c] * ip;
+        for (int q = c; q < 9; ++q) M[r][q] -= l * M[c][q];
+      }
+    }
+    for (int c = 7; c >= 0; --c) {
+      T v = M[c][8];
+      for (int q = c + 1; q < 8; ++q) v -= M[c][q] * X[q];
+      X[c] = v / M[c][c];
+    }
+  }
+  __syncthreads();
+  // 4. write back
+  if (t < 8) {
+    int i, j, k;
+    unpack3(S->cijk[t], i, j, k);
+    u[(long long)k * plane + (long long)j * nx1 + i] = X[t];
+  }
+  for (int q = e0 + t; q < e12; q += nt) {
+    int e = 0;
+    while ((int)S->eoff[e + 1] <= q) ++e;
+    const int sidx = q - (int)S->eoff[e];
+    int i, j, k;
+    unpack3(S->cijk[S->ea[e]], i, j, k);
+    const long long p = (long long)k * plane + (long long)j * nx1 + i + (long long)(sidx + 1) * step3(S->ed[e], nx1, plane);
+    u[p] = rR[q] + X[S->ea[e]] * rZA[q] + X[S->eb[e]] * rZB[q];
+  }
+}
+
 // ------------------------------------------------------------ the kernel --
 // One sequence of 32*W*K slots per CTA of W warps (the warp path of
-// warp_line.cu, seq_line_kernel, with six directions).
+// warp_line.cu, seq_line_kernel, with six directions), holding the chains of
+// whole blocks and up to WJ3_MAX junctions (tweed star centres, nodes that
+// close wireframe rings).  The first sk.nskel CTAs of a launch each solve a
+// wireframe edge skeleton instead.
 template <typename T, int K, int W>
 __global__ void __launch_bounds__(32 * W) seq3_kernel(const WNode3 *__restrict__ nodes,
-                                                      const WBlock3 *__restrict__ blks, C6<T> cp, int nx1, int ny1,
-                                                      T *__restrict__ u, const T *__restrict__ f) {
+                                                      const WJunc3 *__restrict__ juncs, const int *__restrict__ jofs,
+                                                      C6<T> cp, int nx1, int ny1, T *__restrict__ u,
+                                                      const T *__restrict__ f, const SkelArgs<T> sk) {
+  pdl_trigger();
+  if ((int)blockIdx.x < sk.nskel) {
+    skel_cta<T>(sk.skel + blockIdx.x, sk.scr, sk.stride, cp.W, cp.E, cp.S, cp.N, cp.B, cp.T_, nx1, ny1, u, f);
+    return;
+  }
   constexpr int NT = 32 * W, N = NT * K;
   extern __shared__ __align__(16) unsigned char sm3[];
   T *sa = reinterpret_cast<T *>(sm3);
   T *sb = sa + N, *sc = sb + N, *sd = sc + N, *sz = sd + N;
   T *rep = sz + N;
   T *red = rep + 4 * NT;
-  T *xjs = red + 8 * NT;
-  int *sp = reinterpret_cast<int *>(xjs + 2);
-  const int t = threadIdx.x, lane = t & 31;
+  T *xjs = red + 8 * NT;             // junction values, then their rows' diagonal and rhs
+  T *jcs = xjs + WJ3_MAX, *jrs = jcs + WJ3_MAX;
+  int *sp = reinterpret_cast<int *>(jrs + WJ3_MAX);
+  unsigned char *sj = reinterpret_cast<unsigned char *>(sp + N);  // junction of each slot's block
+  const int t = threadIdx.x, lane = t & 31, cta = (int)blockIdx.x - sk.nskel;
   const size_t plane = (size_t)nx1 * ny1;
-  const uint2 *nd = reinterpret_cast<const uint2 *>(nodes) + (size_t)blockIdx.x * N;
-  pdl_trigger();
-  // the junction: coefficient towards attached node e (thread e < natt)
-  const WBlock3 *jbp = blks + blockIdx.x;
-  struct {
-    uint32_t ijk, adirs;
-  } jb;
-  jb.ijk = jbp->ijk;
-  jb.adirs = jbp->adirs;
-  const bool has_j = jbp->has_j != 0;
-  const int natt = jbp->natt;
-  T kp = T(0), cJ = T(1);
-  int ji = 0, jj = 0, jk = 0;
-  unsigned att = 0;
-  if (has_j) {
-    ji = (int)(jb.ijk & 1023u); jj = (int)((jb.ijk >> 10) & 1023u); jk = (int)(jb.ijk >> 20);
-    for (int e = 0; e < natt; ++e) att |= 1u << ((jb.adirs >> (3 * e)) & 7u);
-    if (t < natt) kp = cdir(cp, (jb.adirs >> (3 * t)) & 7u, ji, jj, jk);
-    cJ = T(0);
-    for (unsigned d = 0; d < 6; ++d) cJ -= cdir(cp, d, ji, jj, jk);
-  }
+  const uint2 *nd = reinterpret_cast<const uint2 *>(nodes) + (size_t)cta * N;
+  const int j0 = __ldg(jofs + cta), nj = __ldg(jofs + cta + 1) - j0;
   pdl_wait();  // u and f from here on
   // ---- 1. staging (thread t: nodes NT*q + t)
 #pragma unroll
@@ -128,16 +271,27 @@ __global__ void __launch_bounds__(32 * W) seq3_kernel(const WNode3 *__restrict__
     sb[sl] = valid ? b : T(1);
     sd[sl] = r;
     sp[s] = valid ? (int)p : -1;
+    sj[s] = (unsigned char)((fl >> WN3_JSHIFT) & 31u);
   }
-  T rJ = T(0);
-  size_t pJ = 0;
-  if (has_j && t == 0) {
-    pJ = (size_t)jk * plane + (size_t)jj * nx1 + ji;
-    rJ = __ldg(f + pJ);
-    const size_t off[6] = {1, (size_t)-1, (size_t)nx1, (size_t)0 - nx1, plane, (size_t)0 - plane};
+  // junction rows (thread e: junction e): diagonal and right-hand side
+  if (t < nj) {
+    const uint32_t Jijk = __ldg(&juncs[j0 + t].ijk), Jadirs = __ldg(&juncs[j0 + t].adirs);
+    const int Jnatt = juncs[j0 + t].natt;
+    int ji, jj, jk;
+    unpack3(Jijk, ji, jj, jk);
+    unsigned att = 0;
+    for (int e = 0; e < Jnatt; ++e) att |= 1u << ((Jadirs >> (3 * e)) & 7u);
+    const size_t pJ = (size_t)jk * plane + (size_t)jj * nx1 + ji;
+    T rJ = __ldg(f + pJ), cJ = T(0);
+    const size_t off[6] = {1, (size_t)0 - 1, (size_t)nx1, (size_t)0 - nx1, plane, (size_t)0 - plane};
 #pragma unroll
-    for (unsigned d = 0; d < 6; ++d)
-      if (!(att & (1u << d))) rJ -= cdir(cp, d, ji, jj, jk) * u[pJ + off[d]];
+    for (unsigned d = 0; d < 6; ++d) {
+      const T cd = cdir(cp, d, ji, jj, jk);
+      cJ -= cd;
+      if (!(att & (1u << d))) rJ -= cd * u[pJ + off[d]];
+    }
+    jcs[t] = cJ;
+    jrs[t] = rJ;
   }
   __syncthreads();
 
@@ -187,29 +341,28 @@ __global__ void __launch_bounds__(32 * W) seq3_kernel(const WNode3 *__restrict__
   }
   __syncthreads();
 
-  // ---- 5. junction value (warp 0; up to six attached nodes), write back
-  T xJ = T(0);
-  if (has_j) {
+  // ---- 5. junction values (lane e of warp 0: junction e), write back
+  if (nj > 0) {
     if (t < 32) {
-      T sy = T(0), szz = T(0);
-      if (lane < natt) {
-        const int s = jbp->as[lane];
-        sy = kp * sa[wslot(s)];
-        szz = kp * sb[wslot(s)];
+      T x = T(0);
+      if (t < nj) {
+        const uint32_t Jijk = __ldg(&juncs[j0 + t].ijk), Jadirs = __ldg(&juncs[j0 + t].adirs);
+        const int Jnatt = juncs[j0 + t].natt;
+        int ji, jj, jk;
+        unpack3(Jijk, ji, jj, jk);
+        T sy = T(0), szz = T(0);
+        for (int e = 0; e < Jnatt; ++e) {
+          const T kp = cdir(cp, (Jadirs >> (3 * e)) & 7u, ji, jj, jk);
+          const int sl = wslot(juncs[j0 + t].as[e]);
+          sy += kp * sa[sl];
+          szz += kp * sb[sl];
+        }
+        x = (jrs[t] - sy) / (jcs[t] + szz);
+        u[(size_t)jk * plane + (size_t)jj * nx1 + ji] = x;
       }
-#pragma unroll
-      for (int o = 1; o < 8; o <<= 1) {
-        sy += __shfl_xor_sync(0xFFFFFFFFu, sy, o);
-        szz += __shfl_xor_sync(0xFFFFFFFFu, szz, o);
-      }
-      if (t == 0) {
-        const T x = (rJ - sy) / (cJ + szz);
-        xjs[0] = x;
-        u[pJ] = x;
-      }
+      xjs[lane] = x;
     }
     __syncthreads();
-    xJ = xjs[0];
   }
 #pragma unroll
   for (int q = 0; q < K; ++q) {
@@ -217,40 +370,46 @@ __global__ void __launch_bounds__(32 * W) seq3_kernel(const WNode3 *__restrict__
     const int p = sp[s];
     if (p >= 0) {
       const int sl = wslot(s);
-      u[p] = sa[sl] + xJ * sb[sl];
+      u[p] = nj > 0 ? sa[sl] + xjs[sj[s]] * sb[sl] : sa[sl];
     }
   }
 }
 
 template <typename T, int K, int W>
 constexpr size_t seq3_smem() {
-  return (size_t)32 * W * K * (5 * sizeof(T) + sizeof(int)) + sizeof(T) * (12 * 32 * W + 2);
+  return (size_t)32 * W * K * (5 * sizeof(T) + sizeof(int) + 1) + sizeof(T) * (12 * 32 * W + 3 * WJ3_MAX);
+}
+
+template <typename T>
+SkelArgs<T> skel_args(const Grid3 &G, const WarpList3 &w) {
+  return {w.skel, reinterpret_cast<T *>(G.skel_scr), G.skel_len, w.nskel};
 }
 
 template <typename T, int K, int W>
-cudaError_t launch3_kw(const Level3 &L, const WarpList3 &w, T *u, const T *f, cudaStream_t s) {
+cudaError_t launch3_kw(const Grid3 &G, const Level3 &L, const WarpList3 &w, T *u, const T *f, cudaStream_t s) {
   count_launch(1);
-  return launch_pdl(seq3_kernel<T, K, W>, dim3(w.nwarp), dim3(32 * W), seq3_smem<T, K, W>(), s,
-                    (const WNode3 *)w.node, (const WBlock3 *)w.blk, coefs3<T>(L), L.nx + 1, L.ny + 1, u, f);
+  return launch_pdl(seq3_kernel<T, K, W>, dim3(w.nskel + w.nwarp), dim3(32 * W), seq3_smem<T, K, W>(), s,
+                    (const WNode3 *)w.node, (const WJunc3 *)w.junc, (const int *)w.jofs, coefs3<T>(L), L.nx + 1,
+                    L.ny + 1, u, f, skel_args<T>(G, w));
 }
 template <typename T, int K>
-cudaError_t launch3_k(const Level3 &L, const WarpList3 &w, T *u, const T *f, cudaStream_t s) {
+cudaError_t launch3_k(const Grid3 &G, const Level3 &L, const WarpList3 &w, T *u, const T *f, cudaStream_t s) {
   switch (w.W) {
-    case 1: return launch3_kw<T, K, 1>(L, w, u, f, s);
-    case 2: return launch3_kw<T, K, 2>(L, w, u, f, s);
-    case 4: return launch3_kw<T, K, 4>(L, w, u, f, s);
-    case 8: return launch3_kw<T, K, 8>(L, w, u, f, s);
+    case 1: return launch3_kw<T, K, 1>(G, L, w, u, f, s);
+    case 2: return launch3_kw<T, K, 2>(G, L, w, u, f, s);
+    case 4: return launch3_kw<T, K, 4>(G, L, w, u, f, s);
+    case 8: return launch3_kw<T, K, 8>(G, L, w, u, f, s);
     default: return cudaErrorInvalidValue;
   }
 }
 template <typename T>
-cudaError_t launch_warp3(const Level3 &L, const WarpList3 &w, T *u, const T *f, cudaStream_t s) {
-  if (w.nwarp == 0) return cudaSuccess;
+cudaError_t launch_warp3(const Grid3 &G, const Level3 &L, const WarpList3 &w, T *u, const T *f, cudaStream_t s) {
+  if (w.nwarp + w.nskel == 0) return cudaSuccess;
   switch (w.K) {
-    case 1: return launch3_k<T, 1>(L, w, u, f, s);
-    case 2: return launch3_k<T, 2>(L, w, u, f, s);
-    case 4: return launch3_k<T, 4>(L, w, u, f, s);
-    case 8: return launch3_k<T, 8>(L, w, u, f, s);
+    case 1: return launch3_k<T, 1>(G, L, w, u, f, s);
+    case 2: return launch3_k<T, 2>(G, L, w, u, f, s);
+    case 4: return launch3_k<T, 4>(G, L, w, u, f, s);
+    case 8: return launch3_k<T, 8>(G, L, w, u, f, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -474,18 +633,29 @@ inline int dir_between(int nx1, size_t plane, long long p, long long q) {
   return 5;
 }
 
-// The tweed blocks of one level: chains (node offsets in order) and the
-// junction with its attached legs; false if a block is neither a line nor a
-// star (a side with an odd number of intervals closes loops).
+// The blocks of one level for one smoother (tweed: level sets of (d2, d3) of
+// the sorted wall distances; wireframe: of (d1, d2)), as chains of node
+// offsets in order.  A chain may end next to the block's junction (a tweed
+// star's centre, or the node chosen to close a wireframe ring); a wireframe
+// edge skeleton is kept as its corners and edges.  False if a block is none
+// of: a line, a star, a ring, a cuboid's edge skeleton (a side with an odd
+// number of intervals closes other loops).
+struct HSkelEdge {
+  int a = 0, b = 0, dir = 0;
+  std::vector<long long> nodes;  // interior nodes in order from corner a
+};
 struct HBlock3 {
   std::vector<std::vector<long long>> chains;
+  std::vector<int> jfirst, jlast;  // per chain: direction from its first / last node to the junction, or -1
   long long junc = -1;
-  std::vector<int> leg_dir;  // per chain: direction from its last node to the junction
+  bool skel = false;
+  long long corner[8] = {};
+  std::vector<HSkelEdge> edges;
   int colour = 0;
-  int nodes = 0;
+  int nodes = 0;  // chain nodes (the junction and the skeleton not counted)
 };
 
-bool blocks3(const Level3 &L, std::vector<HBlock3> &out) {
+bool blocks3(const Level3 &L, int sm, std::vector<HBlock3> &out) {
   const int nx = L.nx, ny = L.ny, nz = L.nz, nx1 = nx + 1;
   const size_t plane = (size_t)nx1 * (ny + 1), nn = L.nn;
   auto ijk = [&](size_t p, int &i, int &j, int &k) { i = (int)(p % nx1); j = (int)((p / nx1) % (ny + 1)); k = (int)(p / plane); };
@@ -495,7 +665,7 @@ bool blocks3(const Level3 &L, std::vector<HBlock3> &out) {
     if (a > b) std::swap(a, b);
     if (b > c) std::swap(b, c);
     if (a > b) std::swap(a, b);
-    return std::make_pair(b, c);
+    return sm == SM3_WIREFRAME ? std::make_pair(a, b) : std::make_pair(b, c);
   };
   std::vector<int> par(nn);
   std::iota(par.begin(), par.end(), 0);
@@ -528,6 +698,7 @@ bool blocks3(const Level3 &L, std::vector<HBlock3> &out) {
         members[id[r]].push_back((long long)p);
       }
   auto owner = [&](long long p) { return id[fnd((int)p)]; };
+  std::vector<long long> nb;
   for (size_t b = 0; b < members.size(); ++b) {
     const auto &mb = members[b];
     HBlock3 hb;
@@ -537,72 +708,139 @@ bool blocks3(const Level3 &L, std::vector<HBlock3> &out) {
     const auto kk0 = key(i, j, k);
     hb.colour = ((kk0.first + kk0.second) % 2 == 0) ? 0 : 1;
     // in-block neighbours
-    auto nbrs = [&](long long p, std::vector<long long> &nb) {
-      nb.clear();
+    auto nbrs = [&](long long p, std::vector<long long> &v) {
+      v.clear();
       int a, c, e;
       ijk((size_t)p, a, c, e);
       for (int d = 0; d < 6; ++d)
-        if (inside(a + di[d], c + dj[d], e + dk[d]) && owner(p + step[d]) == (int)b) nb.push_back(p + step[d]);
+        if (inside(a + di[d], c + dj[d], e + dk[d]) && owner(p + step[d]) == (int)b) v.push_back(p + step[d]);
     };
-    std::vector<long long> nb;
-    long long branch = -1;
-    int nbranch = 0, edges2 = 0;
+    std::vector<long long> branch;
+    int edges2 = 0, maxdeg = 0;
     long long endpoint = mb[0];
     for (long long p : mb) {
       nbrs(p, nb);
       edges2 += (int)nb.size();
-      if (nb.size() >= 3) { branch = p; ++nbranch; }
+      maxdeg = std::max(maxdeg, (int)nb.size());
+      if (nb.size() >= 3) branch.push_back(p);
       if (nb.size() <= 1) endpoint = p;
     }
-    if (edges2 / 2 != hb.nodes - 1 || nbranch > 1) return false;
-    auto walk = [&](long long prev, long long cur, std::vector<long long> &chain) {
-      chain.push_back(cur);
+    const int edges = edges2 / 2;
+    // follows the chain from cur (coming from prev) until a tip, a node with
+    // three or more in-block neighbours (kept as the chain's last entry) or
+    // the node `stop` (not kept); returns the node it stopped on
+    auto walk = [&](long long prev, long long cur, long long stop, std::vector<long long> &chain) {
+      std::vector<long long> v;
       while (true) {
-        nbrs(cur, nb);
+        chain.push_back(cur);
+        nbrs(cur, v);
+        if (v.size() > 2) return cur;
         long long next = -1;
-        for (long long q : nb)
+        for (long long q : v)
           if (q != prev) next = q;
-        if (next < 0) break;
+        if (next < 0) return cur;
+        if (next == stop) return next;
         prev = cur;
         cur = next;
-        chain.push_back(cur);
       }
     };
-    if (branch >= 0) {
-      hb.junc = branch;
-      std::vector<long long> legs;
-      nbrs(branch, legs);
-      for (long long q : legs) {
-        std::vector<long long> leg;
-        walk(branch, q, leg);                        // q .. tip
-        std::reverse(leg.begin(), leg.end());        // tip .. q (q next to the junction)
-        hb.leg_dir.push_back(dir_between(nx1, plane, q, branch));
-        hb.chains.push_back(std::move(leg));
+    if (edges == hb.nodes - 1 && branch.size() <= 1) {
+      if (!branch.empty()) {  // a star: legs tip .. node next to the centre
+        const long long c0 = branch[0];
+        hb.junc = c0;
+        std::vector<long long> legs;
+        nbrs(c0, legs);
+        for (long long q : legs) {
+          std::vector<long long> leg;
+          walk(c0, q, -1, leg);
+          std::reverse(leg.begin(), leg.end());
+          hb.jfirst.push_back(-1);
+          hb.jlast.push_back(dir_between(nx1, plane, q, c0));
+          hb.chains.push_back(std::move(leg));
+        }
+        hb.nodes -= 1;
+      } else {  // a line (or a point)
+        std::vector<long long> line;
+        walk(-1, endpoint, -1, line);
+        hb.chains.push_back(std::move(line));
+        hb.jfirst.push_back(-1);
+        hb.jlast.push_back(-1);
       }
-      hb.nodes -= 1;  // chain nodes only
+    } else if (edges == hb.nodes && maxdeg == 2 && hb.nodes >= 4) {  // a ring, closed by its first node
+      const long long c0 = mb[0];
+      std::vector<long long> two, ring;
+      nbrs(c0, two);
+      walk(c0, two[0], c0, ring);
+      if ((int)ring.size() != hb.nodes - 1 || ring.back() != two[1]) return false;
+      hb.junc = c0;
+      hb.jfirst.push_back(dir_between(nx1, plane, ring.front(), c0));
+      hb.jlast.push_back(dir_between(nx1, plane, ring.back(), c0));
+      hb.chains.push_back(std::move(ring));
+      hb.nodes -= 1;
+    } else if (sm == SM3_WIREFRAME && branch.size() == 8 && edges == hb.nodes + 4 && maxdeg == 3) {
+      // a cuboid's edge skeleton: eight corners, twelve edges between them
+      hb.skel = true;
+      for (int c = 0; c < 8; ++c) hb.corner[c] = branch[c];
+      auto corner_of = [&](long long p) {
+        for (int c = 0; c < 8; ++c)
+          if (hb.corner[c] == p) return c;
+        return -1;
+      };
+      for (int c = 0; c < 8; ++c) {
+        std::vector<long long> v;
+        nbrs(hb.corner[c], v);
+        for (long long q : v) {
+          if (corner_of(q) >= 0) return false;  // adjacent corners: no edge nodes
+          HSkelEdge e;
+          const long long end = walk(hb.corner[c], q, -1, e.nodes);
+          e.nodes.pop_back();  // the walk stops on the far corner
+          const int cb = corner_of(end);
+          if (cb < 0 || e.nodes.empty()) return false;
+          if (cb < c) continue;  // each edge once, from its lower corner
+          e.a = c;
+          e.b = cb;
+          e.dir = dir_between(nx1, plane, hb.corner[c], q);
+          // a straight edge: node s at the corner plus s + 1 steps (the
+          // skeleton kernel recomputes the positions this way)
+          const long long st = step[e.dir];
+          for (size_t r = 0; r < e.nodes.size(); ++r)
+            if (e.nodes[r] != hb.corner[c] + (long long)(r + 1) * st) return false;
+          if (end != hb.corner[c] + (long long)(e.nodes.size() + 1) * st) return false;
+          hb.edges.push_back(std::move(e));
+        }
+      }
+      if (hb.edges.size() != 12) return false;
+      int sum = 8;
+      for (const auto &e : hb.edges) sum += (int)e.nodes.size();
+      if (sum != (int)mb.size()) return false;
+      hb.nodes = 0;
     } else {
-      std::vector<long long> line;
-      walk(-1, endpoint, line);
-      hb.chains.push_back(std::move(line));
+      return false;
     }
     out.push_back(std::move(hb));
   }
   return true;
 }
 
-// Sequences of one colour (first fit, largest blocks first, at most one
-// junction per sequence), K and W as in 2D (warp_line.cu) with at most 8
-// nodes per thread (both precisions use the same lists).
+// Sequences of one colour (first fit among the open sequences, largest blocks
+// first, at most WJ3_MAX junctions per sequence), K and W as in 2D
+// (warp_line.cu) with at most 8 nodes per thread (both precisions use the
+// same lists), and the colour's edge skeletons.
 mg_status warp_list3(const Level3 &L, const std::vector<HBlock3> &all, int colour, WarpList3 &Wl) {
-  std::vector<int> idx;
-  int maxn = 1, total = 0;
-  for (size_t b = 0; b < all.size(); ++b)
-    if (all[b].colour == colour) {
-      idx.push_back((int)b);
-      maxn = std::max(maxn, all[b].nodes);
-      total += all[b].nodes + (all[b].junc >= 0 ? 1 : 0);
+  std::vector<int> idx, sk;
+  int maxn = 1, total = 0, skn = 0;
+  for (size_t b = 0; b < all.size(); ++b) {
+    if (all[b].colour != colour) continue;
+    if (all[b].skel) {
+      sk.push_back((int)b);
+      for (const auto &e : all[b].edges) skn += (int)e.nodes.size();
+      continue;
     }
-  if (idx.empty()) return MG_OK;
+    idx.push_back((int)b);
+    maxn = std::max(maxn, all[b].nodes);
+    total += all[b].nodes + (all[b].junc >= 0 ? 1 : 0);
+  }
+  if (idx.empty() && sk.empty()) return MG_OK;
   if (maxn > 32 * WARP3_WMAX * WARP3_KMAX) return MG_ERR_SIZE;
   int K = 1, NW = 1;
   while (32 * K < maxn && K < WARP3_KPREF) K *= 2;
@@ -614,46 +852,56 @@ mg_status warp_list3(const Level3 &L, const std::vector<HBlock3> &all, int colou
   }
   const int cap = 32 * NW * K;
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return all[a].nodes > all[b].nodes; });
-  struct Bin { int used = 0; bool junc = false; std::vector<int> blocks; };
+  struct Bin { int used = 0, nj = 0; std::vector<int> blocks; };
   std::vector<Bin> bins;
   for (int b : idx) {
-    const bool j = all[b].junc >= 0;
-    size_t w = 0;
-    while (w < bins.size() && (bins[w].used + all[b].nodes > cap || (j && bins[w].junc))) ++w;
+    const int nj = all[b].junc >= 0 ? 1 : 0, n = all[b].nodes;
+    // first fit among the 64 newest bins (blocks arrive largest first)
+    size_t w = bins.size() > 64 ? bins.size() - 64 : 0;
+    while (w < bins.size() && (bins[w].used + n > cap || bins[w].nj + nj > WJ3_MAX)) ++w;
     if (w == bins.size()) bins.emplace_back();
-    bins[w].used += all[b].nodes;
-    bins[w].junc |= j;
+    bins[w].used += n;
+    bins[w].nj += nj;
     bins[w].blocks.push_back(b);
   }
   const int nx1 = L.nx + 1;
   const size_t plane = (size_t)nx1 * (L.ny + 1);
   std::vector<WNode3> nodes(bins.size() * (size_t)cap);
-  std::vector<WBlock3> blk(bins.size());
+  std::vector<WJunc3> jn;
+  std::vector<int> jofs(bins.size() + 1, 0);
+  std::vector<WSkel3> skel(sk.size());
   std::memset(nodes.data(), 0, sizeof(WNode3) * nodes.size());
-  std::memset(blk.data(), 0, sizeof(WBlock3) * blk.size());
+  std::memset(skel.data(), 0, sizeof(WSkel3) * skel.size());
   auto pack = [&](long long p) {
     const uint32_t i = (uint32_t)(p % nx1), j = (uint32_t)((p / nx1) % (L.ny + 1)), k = (uint32_t)(p / plane);
     return i | (j << 10) | (k << 20);
   };
   for (size_t w = 0; w < bins.size(); ++w) {
-    WBlock3 &jb = blk[w];
+    jofs[w] = (int)jn.size();
     int s = 0;
     for (int b : bins[w].blocks) {
       const HBlock3 &hb = all[b];
-      if (hb.junc >= 0) { jb.has_j = 1; jb.ijk = pack(hb.junc); }
+      const uint32_t jl = (uint32_t)(jn.size() - jofs[w]);
+      WJunc3 *jb = nullptr;
+      if (hb.junc >= 0) {
+        jn.emplace_back();
+        jb = &jn.back();
+        std::memset(jb, 0, sizeof(WJunc3));
+        jb->ijk = pack(hb.junc);
+      }
       for (size_t c = 0; c < hb.chains.size(); ++c) {
         const auto &ch = hb.chains[c];
         const int m = (int)ch.size();
         for (int r = 0; r < m; ++r) {
-          uint32_t fl = WN3_VALID;
+          uint32_t fl = WN3_VALID | (jb ? jl << WN3_JSHIFT : 0u);
           if (r > 0) fl |= WN3_PRED | (uint32_t)dir_between(nx1, plane, ch[r], ch[r - 1]);
           if (r < m - 1) fl |= WN3_SUCC | ((uint32_t)dir_between(nx1, plane, ch[r], ch[r + 1]) << 4);
-          if (hb.junc >= 0 && r == m - 1) {
-            const int dj = hb.leg_dir[c];
+          const int dj = r == m - 1 && hb.jlast[c] >= 0 ? hb.jlast[c] : (r == 0 ? hb.jfirst[c] : -1);
+          if (jb && dj >= 0) {
             fl |= WN3_JUNC | ((uint32_t)dj << 8);
-            jb.as[jb.natt] = (uint16_t)s;
-            jb.adirs |= (uint32_t)(dj ^ 1) << (3 * jb.natt);
-            ++jb.natt;
+            jb->as[jb->natt] = (uint16_t)s;
+            jb->adirs |= (uint32_t)(dj ^ 1) << (3 * jb->natt);
+            ++jb->natt;
           }
           WNode3 &nd = nodes[w * (size_t)cap + s];
           nd.ijk = pack(ch[r]);
@@ -663,20 +911,43 @@ mg_status warp_list3(const Level3 &L, const std::vector<HBlock3> &all, int colou
       }
     }
   }
-  const size_t bn = (sizeof(WNode3) * nodes.size() + 15) & ~size_t(15);
+  jofs[bins.size()] = (int)jn.size();
+  int off = 0;
+  for (size_t q = 0; q < sk.size(); ++q) {
+    const HBlock3 &hb = all[sk[q]];
+    WSkel3 &S = skel[q];
+    for (int c = 0; c < 8; ++c) S.cijk[c] = pack(hb.corner[c]);
+    for (int e = 0; e < 12; ++e) {
+      S.eoff[e] = (uint32_t)off;
+      S.ea[e] = (uint8_t)hb.edges[e].a;
+      S.eb[e] = (uint8_t)hb.edges[e].b;
+      S.ed[e] = (uint8_t)hb.edges[e].dir;
+      off += (int)hb.edges[e].nodes.size();
+    }
+    S.eoff[12] = (uint32_t)off;
+  }
+  auto al = [](size_t v) { return (v + 15) & ~size_t(15); };
+  const size_t b_nodes = al(sizeof(WNode3) * nodes.size()), b_jn = al(sizeof(WJunc3) * jn.size()),
+               b_jofs = al(sizeof(int) * jofs.size()), b_sk = al(sizeof(WSkel3) * skel.size());
   char *mem = nullptr;
-  cudaError_t e = cudaMalloc(&mem, bn + sizeof(WBlock3) * blk.size());
+  cudaError_t e = cudaMalloc(&mem, b_nodes + b_jn + b_jofs + b_sk);
   if (e != cudaSuccess) { set_error("cudaMalloc(3D warp list)", e); return MG_ERR_ALLOC; }
   Wl.mem = mem;
   Wl.node = reinterpret_cast<WNode3 *>(mem);
-  Wl.blk = reinterpret_cast<WBlock3 *>(mem + bn);
-  e = cudaMemcpy(Wl.node, nodes.data(), sizeof(WNode3) * nodes.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(Wl.blk, blk.data(), sizeof(WBlock3) * blk.size(), cudaMemcpyHostToDevice);
+  Wl.junc = reinterpret_cast<WJunc3 *>(mem + b_nodes);
+  Wl.jofs = reinterpret_cast<int *>(mem + b_nodes + b_jn);
+  Wl.skel = reinterpret_cast<WSkel3 *>(mem + b_nodes + b_jn + b_jofs);
+  if (!nodes.empty()) e = cudaMemcpy(Wl.node, nodes.data(), sizeof(WNode3) * nodes.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !jn.empty()) e = cudaMemcpy(Wl.junc, jn.data(), sizeof(WJunc3) * jn.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(Wl.jofs, jofs.data(), sizeof(int) * jofs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !skel.empty()) e = cudaMemcpy(Wl.skel, skel.data(), sizeof(WSkel3) * skel.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { set_error("cudaMemcpy(3D warp list)", e); return MG_ERR_CUDA; }
   Wl.nwarp = (int)bins.size();
   Wl.K = K;
   Wl.W = NW;
   Wl.total_nodes = total;
+  Wl.nskel = (int)sk.size();
+  Wl.skel_nodes = skn;
   return MG_OK;
 }
 
@@ -764,14 +1035,21 @@ mg_status setup3(Grid &g, const int64_t *n, const double *const *coords) {
         TRY_CUDA("cudaMemset(3D level)", cudaMemset(L.f32, 0, sizeof(float) * L.nn));
       }
     }
-    // tweed blocks of the smoothed levels
+    // tweed and wireframe blocks of the smoothed levels
     if (l + 1 < g.nlev) {
       std::vector<HBlock3> blocks;
-      if (!blocks3(L, blocks)) {
+      if (!blocks3(L, SM3_TWEED, blocks)) {
         set_error_text("3D tweed: a side with an odd number of intervals on a smoothed level");
         return MG_ERR_UNSUPPORTED;
       }
-      for (int c = 0; c < 2; ++c) TRY(warp_list3(L, blocks, c, L.wp[c]));
+      for (int c = 0; c < 2; ++c) TRY(warp_list3(L, blocks, c, L.wp[SM3_TWEED][c]));
+      blocks.clear();
+      L.wf_ok = blocks3(L, SM3_WIREFRAME, blocks);
+      if (L.wf_ok)
+        for (int c = 0; c < 2; ++c) {
+          TRY(warp_list3(L, blocks, c, L.wp[SM3_WIREFRAME][c]));
+          G.skel_len = std::max(G.skel_len, (size_t)L.wp[SM3_WIREFRAME][c].skel_nodes);
+        }
     }
   }
   // coarsest level: dense inverse of the interior operator
@@ -798,6 +1076,8 @@ mg_status setup3(Grid &g, const int64_t *n, const double *const *coords) {
     TRY_CUDA("cudaMemcpy(3D coarse)", cudaMemcpy(G.cinv, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice));
   }
   const size_t nn0 = G.lev[0].nn;
+  if (G.skel_len > 0)
+    TRY_CUDA("cudaMalloc(3D skeleton scratch)", cudaMalloc(&G.skel_scr, sizeof(double) * 6 * G.skel_len));
   if (want64) TRY_CUDA("cudaMalloc(3D defect)", cudaMalloc(&G.d64, sizeof(double) * nn0));
   if (want32) {
     TRY_CUDA("cudaMalloc(3D defect)", cudaMalloc(&G.d32, sizeof(float) * nn0));
@@ -814,9 +1094,11 @@ void free3(Grid &g) {
   for (Level3 &L : g.g3->lev) {
     cudaFree(L.dev_block);
     cudaFree(L.u64); cudaFree(L.f64); cudaFree(L.u32); cudaFree(L.f32);
-    for (int c = 0; c < 2; ++c) cudaFree(L.wp[c].mem);
+    for (int m = 0; m < 2; ++m)
+      for (int c = 0; c < 2; ++c) cudaFree(L.wp[m][c].mem);
   }
   cudaFree(g.g3->cinv);
+  cudaFree(g.g3->skel_scr);
   cudaFree(g.g3->d64);
   cudaFree(g.g3->d32);
   delete g.g3;
@@ -824,10 +1106,15 @@ void free3(Grid &g) {
 }
 
 template <typename T>
-mg_status colour_pass3(Grid &g, int l, int colour, T *u, const T *f, cudaStream_t s) {
+mg_status colour_pass3(Grid &g, int l, int sm, int colour, T *u, const T *f, cudaStream_t s) {
   Level3 &L = g.g3->lev[l];
   if (l + 1 >= g.nlev) return MG_ERR_UNSUPPORTED;  // the coarsest level is solved directly
-  return cuda_status("3D tweed pass", launch_warp3<T>(L, L.wp[colour], u, f, s));
+  if (sm == SM3_WIREFRAME && !L.wf_ok) {
+    set_error_text("3D wireframe: a block of this level is not a ring, line, point or cuboid edge skeleton");
+    return MG_ERR_UNSUPPORTED;
+  }
+  return cuda_status(sm == SM3_WIREFRAME ? "3D wireframe pass" : "3D tweed pass",
+                     launch_warp3<T>(*g.g3, L, L.wp[sm][colour], u, f, s));
 }
 
 template <typename T>
@@ -868,22 +1155,28 @@ mg_status coarse_solve3(Grid &g, T *u, const T *f, cudaStream_t s) {
                                                    (const double *)g.g3->cinv, u, f));
 }
 
-// One relaxation (red pass, black pass) and the cycle of Sec. 4 steps (2)-(6).
+// One relaxation (red pass, black pass; alternating tweed/wireframe: one of
+// each) and the cycle of Sec. 4 steps (2)-(6).
+template <typename T>
+mg_status smooth3(Grid &g, int l, int smoother, T *u, const T *f, cudaStream_t s) {
+  if (smoother == MG_SMOOTH_ALT_TW) {
+    TRY(smooth3<T>(g, l, MG_SMOOTH_TWEED, u, f, s));
+    return smooth3<T>(g, l, MG_SMOOTH_WIREFRAME, u, f, s);
+  }
+  const int sm = smoother == MG_SMOOTH_WIREFRAME ? SM3_WIREFRAME : SM3_TWEED;
+  TRY(colour_pass3<T>(g, l, sm, 0, u, f, s));
+  return colour_pass3<T>(g, l, sm, 1, u, f, s);
+}
+
 template <typename T>
 mg_status cycle3(Grid &g, const mg_params &p, int l, T *u, const T *f, cudaStream_t s) {
   if (l == g.nlev - 1) return coarse_solve3<T>(g, u, f, s);
-  for (int k = 0; k < p.nu1; ++k) {
-    TRY(colour_pass3<T>(g, l, 0, u, f, s));
-    TRY(colour_pass3<T>(g, l, 1, u, f, s));
-  }
+  for (int k = 0; k < p.nu1; ++k) TRY(smooth3<T>(g, l, p.smoother, u, f, s));
   T *uc = lev_u<T>(g, l + 1), *fc = lev_f<T>(g, l + 1);
   TRY(residual_restrict3<T>(g, l, u, f, fc, uc, s));
   for (int k = 0; k < p.cycle; ++k) TRY(cycle3<T>(g, p, l + 1, uc, fc, s));
   TRY(prolong_add3<T>(g, l, uc, u, s));
-  for (int k = 0; k < p.nu2; ++k) {
-    TRY(colour_pass3<T>(g, l, 0, u, f, s));
-    TRY(colour_pass3<T>(g, l, 1, u, f, s));
-  }
+  for (int k = 0; k < p.nu2; ++k) TRY(smooth3<T>(g, l, p.smoother, u, f, s));
   return MG_OK;
 }
 
@@ -910,8 +1203,8 @@ mg_status norms3(Grid &g, const double *u, const double *f, int bnd_only, float 
   return cuda_status("3D norms", cudaGetLastError());
 }
 
-template mg_status colour_pass3<double>(Grid &, int, int, double *, const double *, cudaStream_t);
-template mg_status colour_pass3<float>(Grid &, int, int, float *, const float *, cudaStream_t);
+template mg_status colour_pass3<double>(Grid &, int, int, int, double *, const double *, cudaStream_t);
+template mg_status colour_pass3<float>(Grid &, int, int, int, float *, const float *, cudaStream_t);
 template mg_status cycle3<double>(Grid &, const mg_params &, int, double *, const double *, cudaStream_t);
 template mg_status cycle3<float>(Grid &, const mg_params &, int, float *, const float *, cudaStream_t);
 template mg_status residual3<double>(Grid &, int, const double *, const double *, double *, cudaStream_t);

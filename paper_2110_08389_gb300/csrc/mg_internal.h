@@ -140,32 +140,52 @@ constexpr int WK_PREF = 4, WK_MAX_F32 = 16, WK_MAX_F64 = 8, WW_MAX = 8;
 constexpr int WARP_MAX_SIDE = 2048;
 
 // ---------------------------------------------------------------------------
-// 3D grids (Sec. 7): tweed only, on the warp path.  Directions 0..5 = +x, -x,
-// +y, -y, +z, -z (coefficients E_i, W_i, N_j, S_j, T_k, B_k); the opposite
-// of d is d ^ 1.  A 3D node descriptor packs i | j << 10 | k << 20 and the
-// directions to its predecessor (bits 0-2, WN3_PRED), successor (bits 4-6,
-// WN3_SUCC) and junction (bits 8-10, WN3_JUNC); unused slots are zero.
+// 3D grids (Sec. 7): tweed and wireframe on the warp path.  Directions 0..5 =
+// +x, -x, +y, -y, +z, -z (coefficients E_i, W_i, N_j, S_j, T_k, B_k); the
+// opposite of d is d ^ 1.  A 3D node descriptor packs i | j << 10 | k << 20
+// and the directions to its predecessor (bits 0-2, WN3_PRED), successor
+// (bits 4-6, WN3_SUCC) and junction (bits 8-10, WN3_JUNC); bits 16-20 hold
+// the index, within its sequence, of the junction of the node's block.
+// Unused slots are zero.
 enum : uint32_t { WN3_PRED = 1u << 3, WN3_SUCC = 1u << 7, WN3_JUNC = 1u << 11, WN3_VALID = 1u << 12 };
+constexpr int WN3_JSHIFT = 16, WJ3_MAX = 32;  // at most 32 junctions per sequence
 struct WNode3 {
   uint32_t ijk, fl;
 };
 static_assert(sizeof(WNode3) == 8, "WNode3 layout");
-// The junction of a 3D sequence: attached node e (< natt <= 6) is node as[e]
-// of the sequence, in direction (adirs >> 3e) & 7 from the junction.
-struct WBlock3 {
+// A junction of a 3D sequence: the centre of a tweed star (natt = its legs)
+// or the node that closes a wireframe ring (natt = 2, both ends of the ring's
+// chain).  Attached node e (< natt <= 6) is node as[e] of the sequence, in
+// direction (adirs >> 3e) & 7 from the junction.
+struct WJunc3 {
   uint32_t ijk;
-  uint8_t has_j, natt, pad[2];
+  uint8_t natt, pad[3];
   uint32_t adirs;
   uint16_t as[6];
   uint8_t pad2[8];
 };
-static_assert(sizeof(WBlock3) == 32, "WBlock3 layout");
+static_assert(sizeof(WJunc3) == 32, "WJunc3 layout");
+// A wireframe edge skeleton (Sec. 7): the twelve edges of a concentric
+// cuboid.  Corner c at cijk[c]; edge e runs from corner ea[e] towards corner
+// eb[e] in direction ed[e], its interior nodes at scratch positions
+// [eoff[e], eoff[e + 1]) in order from corner ea[e].
+struct WSkel3 {
+  uint32_t cijk[8];
+  uint32_t eoff[13];
+  uint8_t ea[12], eb[12], ed[12];
+  uint8_t pad[8];
+};
+static_assert(sizeof(WSkel3) == 128, "WSkel3 layout");
 struct WarpList3 {
   int nwarp = 0, K = 0, W = 1, total_nodes = 0;
+  int nskel = 0, skel_nodes = 0;      // skeleton CTAs (launched first) and their interior edge nodes
   void *mem = nullptr;
   WNode3 *node = nullptr;
-  WBlock3 *blk = nullptr;
+  WJunc3 *junc = nullptr;
+  int *jofs = nullptr;                // sequence w owns junctions [jofs[w], jofs[w + 1])
+  WSkel3 *skel = nullptr;
 };
+enum { SM3_TWEED = 0, SM3_WIREFRAME = 1 };
 struct Level3 {
   int nx = 0, ny = 0, nz = 0;
   size_t nn = 0;
@@ -176,7 +196,8 @@ struct Level3 {
   void *dev_block = nullptr;          // one allocation behind the coefficients
   double *u64 = nullptr, *f64 = nullptr;  // coarse-level workspaces
   float *u32 = nullptr, *f32 = nullptr;
-  WarpList3 wp[2];                    // [colour]: shared by both precisions
+  WarpList3 wp[2][2];                 // [SM3_*][colour]: shared by both precisions
+  bool wf_ok = false;                 // wireframe blocks are all rings, lines, points and skeletons
 };
 struct Grid3 {
   std::vector<Level3> lev;
@@ -184,6 +205,8 @@ struct Grid3 {
   double *cinv = nullptr;             // dense inverse of the coarsest interior operator
   double *d64 = nullptr;              // defect scratch of the finest level's size
   float *d32 = nullptr;
+  double *skel_scr = nullptr;         // skeleton edge scratch: 6 rows of skel_len values
+  size_t skel_len = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -329,7 +352,7 @@ bool invert(int n, std::vector<double> &A, std::vector<double> &inv);
 mg_status setup3(Grid &g, const int64_t *n, const double *const *coords);
 void free3(Grid &g);
 template <typename T>
-mg_status colour_pass3(Grid &g, int l, int colour, T *u, const T *f, cudaStream_t s);
+mg_status colour_pass3(Grid &g, int l, int sm, int colour, T *u, const T *f, cudaStream_t s);  // sm: SM3_*
 template <typename T>
 mg_status cycle3(Grid &g, const mg_params &p, int l, T *u, const T *f, cudaStream_t s);
 template <typename T>

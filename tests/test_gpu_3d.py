@@ -1,9 +1,9 @@
-"""3D grids (Sec. 7) through the C ABI against the 3D oracle: tweed colour
-passes on every smoothed level (FP64 to 1e-10, FP32 to the FP32 smoothing
-tolerance), the 7-point defect, full-weighting restriction, trilinear
-prolongation and coarsest solve, the FP64 solve history per cycle (1e-12 on
-the relative residual, 1 % on the convergence factor) and FP32 cycles with
-FP64 refinement to 1e-10."""
+"""3D grids (Sec. 7) through the C ABI against the 3D oracle: tweed and
+wireframe colour passes on every smoothed level (FP64 to 1e-10, FP32 to the
+FP32 smoothing tolerance), the 7-point defect, full-weighting restriction,
+trilinear prolongation and coarsest solve, the FP64 solve history per cycle
+(1e-12 on the relative residual, 1 % on the convergence factor) and FP32
+cycles with FP64 refinement to 1e-10."""
 import numpy as np
 import pytest
 
@@ -43,8 +43,9 @@ def rel_err(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
+@pytest.mark.parametrize("smoother", ["tweed", "wireframe"])
 @pytest.mark.parametrize("grid", GRIDS3, ids=lambda t: f"{t[0]}x{t[1]}x{t[2]}-{t[3]}")
-def test_colour_pass_3d(mg, oracle_mod, grid):
+def test_colour_pass_3d(mg, oracle_mod, grid, smoother):
     g, P = pair(mg, oracle_mod, grid)
     assert g.nlev == P.nlev
     rng = np.random.default_rng(11)
@@ -52,16 +53,16 @@ def test_colour_pass_3d(mg, oracle_mod, grid):
         assert g.shape(lev) == P.shape(lev)
         u0, f = rng.standard_normal(P.shape(lev)), rng.standard_normal(P.shape(lev))
         for colour in (0, 1):
-            ref = P.colour_pass(u0.copy(), f, colour, lev)
+            ref = P.colour_pass(u0.copy(), f, colour, lev, smoother=smoother)
             ud = cuda(u0)
-            g.colour_pass(ud, cuda(f), "tweed", colour, level=lev)
+            g.colour_pass(ud, cuda(f), smoother, colour, level=lev)
             assert rel_err(host(ud), ref) <= 1e-10, (lev, colour, rel_err(host(ud), ref))
         # FP32: one relaxation on FP32-rounded data
         u32 = u0.astype(np.float32).astype(np.float64)
         f32 = f.astype(np.float32).astype(np.float64)
-        ref = P.smooth(u32.copy(), f32, lev)
+        ref = P.smooth(u32.copy(), f32, lev, smoother=smoother)
         ud = cuda(u32, "f32")
-        g.smooth(ud, cuda(f32, "f32"), "tweed", 1, level=lev)
+        g.smooth(ud, cuda(f32, "f32"), smoother, 1, level=lev)
         assert rel_err(host(ud), ref) <= 2e-4, (lev, rel_err(host(ud), ref))
 
 
@@ -96,9 +97,12 @@ def test_transfers_and_coarse_3d(mg, oracle_mod, grid):
     assert rel_err(host(ud), ref) <= 1e-10
 
 
-@pytest.mark.parametrize("grid", [(32, 32, 32, "wall", 200.0), (16, 12, 10, "wall", 50.0)],
-                         ids=lambda t: f"{t[0]}x{t[1]}x{t[2]}")
-def test_solve_history_3d(mg, oracle_mod, grid):
+@pytest.mark.parametrize("grid,smoother", [((32, 32, 32, "wall", 200.0), "tweed"), ((16, 12, 10, "wall", 50.0), "tweed"),
+                                           ((32, 32, 32, "centre", 10.0), "wireframe"),
+                                           ((24, 16, 32, "centre", 5.0), "wireframe"),
+                                           ((32, 32, 32, "wall", 50.0), "alt_tw")],
+                         ids=lambda t: f"{t[0]}x{t[1]}x{t[2]}-{t[3]}" if isinstance(t, tuple) else t)
+def test_solve_history_3d(mg, oracle_mod, grid, smoother):
     """FP64 V(2,2) cycles: the relative residual after every cycle within
     1e-12 of the oracle's and the convergence factor within 1 %."""
     g, P = pair(mg, oracle_mod, grid)
@@ -107,9 +111,9 @@ def test_solve_history_3d(mg, oracle_mod, grid):
     bnd = rng.standard_normal(P.shape())
     bnd[1:-1, 1:-1, 1:-1] = 0.0
     u_ref = bnd.copy()
-    hist_ref = P.solve(u_ref, f, nu1=2, nu2=2, tol=1e-10, max_cycles=60)
+    hist_ref = P.solve(u_ref, f, nu1=2, nu2=2, tol=1e-10, max_cycles=60, smoother=smoother)
     ud = cuda(bnd)
-    res = g.solve(ud, cuda(f), smoother="tweed", nu1=2, nu2=2, tol=1e-10, max_cycles=60, precision="f64")
+    res = g.solve(ud, cuda(f), smoother=smoother, nu1=2, nu2=2, tol=1e-10, max_cycles=60, precision="f64")
     assert res.status == mg.OK
     assert res.cycles == len(hist_ref) - 1
     assert np.abs(np.asarray(res.history) - hist_ref).max() <= 1e-12
@@ -119,11 +123,12 @@ def test_solve_history_3d(mg, oracle_mod, grid):
     assert rel_err(host(ud), u_ref) <= 1e-8
 
 
-def test_f32_refine_3d(mg, oracle_mod):
-    g, P = pair(mg, oracle_mod, (64, 64, 64, "wall", 200.0))
+@pytest.mark.parametrize("smoother,kind,ratio", [("tweed", "wall", 200.0), ("wireframe", "centre", 10.0)])
+def test_f32_refine_3d(mg, oracle_mod, smoother, kind, ratio):
+    g, P = pair(mg, oracle_mod, (64, 64, 64, kind, ratio))
     f = np.random.default_rng(14).standard_normal(P.shape())
     ud = cuda(np.zeros(P.shape()))
-    res = g.solve(ud, cuda(f), smoother="tweed", nu1=2, nu2=2, tol=1e-10, precision="f32_refine", max_outer=40,
+    res = g.solve(ud, cuda(f), smoother=smoother, nu1=2, nu2=2, tol=1e-10, precision="f32_refine", max_outer=40,
                   max_cycles=400)
     assert res.status == mg.OK and res.rel_res <= 1e-10
     d = P.residual(host(ud), f)
@@ -136,13 +141,29 @@ def test_3d_unsupported_requests(mg):
     g = mg.Grid(*xyz)
     assert g.dim == 3 and mg.load().mg_grid_dim(g.h) == 3
     u = torch.zeros(g.shape(), dtype=torch.float64, device="cuda")
-    for sm in ("wireframe", "zebra_x", "checkerboard"):
+    for sm in ("zebra_x", "checkerboard"):
         with pytest.raises(mg.MGError) as e:
             g.colour_pass(u, u, sm, 0)
         assert e.value.status == mg.ERR_UNSUPPORTED
-    with pytest.raises(mg.MGError) as e:
-        g.solve(u, u.clone() + 1, smoother="wireframe")
-    assert e.value.status == mg.ERR_UNSUPPORTED
+    for sm in ("zebra_y", "alt_zebra"):
+        with pytest.raises(mg.MGError) as e:
+            g.solve(u, u.clone() + 1, smoother=sm)
+        assert e.value.status == mg.ERR_UNSUPPORTED
     with pytest.raises(mg.MGError) as e:
         mg.Batch([g])
     assert e.value.status == mg.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("dims", [(16, 16, 16), (24, 16, 32), (64, 48, 32)])
+def test_wireframe_skeleton_and_rings_3d(mg, oracle_mod, dims):
+    """A red then a black wireframe pass on the finest level of grids with
+    many cuboid skeletons and rings of every size: FP64 against the oracle."""
+    g, P = pair(mg, oracle_mod, (*dims, "centre", 20.0))
+    rng = np.random.default_rng(15)
+    u0, f = rng.standard_normal(P.shape()), rng.standard_normal(P.shape())
+    ref = u0.copy()
+    ud = cuda(u0)
+    for colour in (0, 1):
+        ref = P.colour_pass(ref, f, colour, smoother="wireframe")
+        g.colour_pass(ud, cuda(f), "wireframe", colour)
+    assert rel_err(host(ud), ref) <= 1e-10

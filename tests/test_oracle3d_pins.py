@@ -365,3 +365,20 @@ def test_wireframe_cycles_converge_on_centre_clustered_grid():
     ht = P.solve(u, f, nu1=2, nu2=2, tol=1e-10, max_cycles=60, smoother="tweed")
     rho_t = (ht[-1] / ht[0]) ** (1.0 / (len(ht) - 1))
     assert rho_w < 0.6 and rho_w < 0.8 * rho_t, (rho_w, rho_t)
+
+
+def test_alternating_is_tweed_then_wireframe_and_converges_on_both_clusterings():
+    """Sec. 3's alternating scheme in 3D: one step is a tweed relaxation then
+    a wireframe relaxation, and its cycles converge on grids clustered toward
+    the walls and toward the centre."""
+    P = oracle.Problem3(*grid3(12, 10, 8, "wall", 30.0))
+    rng = np.random.default_rng(8)
+    u0, f = rng.standard_normal(P.shape()), rng.standard_normal(P.shape())
+    a = P.smooth(u0.copy(), f, smoother="alt_tw")
+    b = P.smooth(P.smooth(u0.copy(), f, smoother="tweed"), f, smoother="wireframe")
+    assert np.array_equal(a, b)
+    for kind, ratio in (("wall", 100.0), ("centre", 10.0)):
+        P = oracle.Problem3(*grid3(32, 32, 32, kind, ratio))
+        u = np.zeros(P.shape())
+        h = P.solve(u, f=rng.standard_normal(P.shape()), nu1=2, nu2=2, tol=1e-10, max_cycles=40, smoother="alt_tw")
+        assert h[-1] <= 1e-10 and (h[-1] / h[0]) ** (1.0 / (len(h) - 1)) < 0.6, (kind, len(h))

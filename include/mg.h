@@ -118,8 +118,11 @@ typedef struct {
  * is the 7-point one with B_k, T_k over z built like S_j, N_j.  3D grids
  * offer the tweed smoother (blocks: the level sets of the two larger sorted
  * wall distances, lines perpendicular to the nearest wall, stars of up to six
- * legs), full weighting and trilinear prolongation (tensor products of the 1D
- * factors of Sec. 4), mg_colour_pass, mg_smooth(_tweed), mg_residual,
+ * legs), the wireframe smoother (level sets of the two smaller ones: rings on
+ * the faces of concentric cuboids and each cuboid's twelve-edge skeleton),
+ * both alternating (MG_SMOOTH_ALT_TW), full weighting and trilinear
+ * prolongation (tensor products of the 1D factors of Sec. 4),
+ * mg_colour_pass, mg_smooth(_tweed, _wireframe), mg_residual,
  * mg_residual_restrict, mg_prolong_add, mg_coarse_solve, mg_vcycle and
  * mg_solve in both precisions; other smoothers and the other entry points
  * return MG_ERR_UNSUPPORTED.  Sides that are odd on a smoothed level are

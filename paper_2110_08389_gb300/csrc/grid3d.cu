@@ -1,444 +1,43 @@
-// grid3d.cu -- 3D grids (Sec. 7): the level hierarchy, the 3D tweed blocks,
-// their colour passes on the warp path, the 7-point defect with full-weighting
-// restriction, trilinear prolongation, the coarsest direct solve, the FP64
-// norms and refinement steps, and the cycle of Sec. 4 on them.
+// grid3d.cu -- 3D grids (Sec. 7): the level hierarchy, the 3D tweed and
+// wireframe blocks, their colour passes on the warp path (kernels in
+// seq3.cuh), the 7-point defect with full-weighting restriction, trilinear
+// prolongation, the coarsest direct solve, the FP64 norms and refinement
+// steps, and the cycle of Sec. 4 on them.
 //
-// 3D tweed (Sec. 7): starting from the eight corner points, lines run
-// perpendicular to the nearest wall.  With the index distances to the
-// nearer wall d_x = min(i, nx-i), d_y, d_z sorted as d1 <= d2 <= d3, a block
-// is a connected set of interior nodes with equal (d2, d3): a point, a line
-// turning at most at its ends, or a star of m = 3, 4 or 6 legs around one
-// branch node (m = 6 at the centre of a cube).  A block is red (relaxed
-// first) when d2 + d3 is even, so the corner points are red; adjacent nodes
-// either share (d2, d3) or differ by one in d2 + d3, so blocks of one colour
-// never touch.  Transfers are the tensor products of the 1D factors of the
-// 2D rules of Sec. 4: full weighting (1/4, 1/2, 1/4) per axis, trilinear
-// prolongation.  Each block is solved exactly on the warp path: the same
-// partition method as in 2D (warp_common.cuh), with six directions and up to
-// six nodes attached to a junction.
+// With the index distances to the nearer wall d_x = min(i, nx-i), d_y, d_z
+// sorted as d1 <= d2 <= d3:
+//   3D tweed (Sec. 7): lines run perpendicular to the nearest wall, starting
+//     from the eight corner points.  A block is a connected set of interior
+//     nodes with equal (d2, d3): a point, a line turning at most at its ends,
+//     or a star of m = 3, 4 or 6 legs around one branch node (m = 6 at the
+//     centre of a cube).  Red (relaxed first) when d2 + d3 is even, so the
+//     corner points are red.
+//   3D wireframe (Sec. 7): blocks cover the faces of concentric cuboids.  A
+//     block is a connected set of interior nodes with equal (d1, d2): for
+//     d1 < d2 a ring around the centre of a cuboid face (a line or a point
+//     where the face's rings close), for d1 = d2 the twelve edges of the
+//     cuboid with its eight corners (the wireframe itself).  Red when d1 + d2
+//     is even, so the outermost skeleton is red.
+// Adjacent nodes either share the key or differ by one in its sum (all sides
+// even), so blocks of one colour never touch.  Transfers are the tensor
+// products of the 1D factors of the 2D rules of Sec. 4: full weighting
+// (1/4, 1/2, 1/4) per axis, trilinear prolongation.  Each block is solved
+// exactly: lines, stars and rings on the warp path (a ring as the line left
+// when one node is taken out, that node then a junction with two attached
+// ends), skeletons by one CTA each (Thomas per edge, then the corners).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <functional>
 #include <numeric>
 #include <vector>
 
-#include "solve.h"
-#include "warp_common.cuh"
+#include "seq3.cuh"
 
 namespace tmg {
 
 namespace {
-
-template <typename T>
-struct C6 {
-  const T *W, *E, *S, *N, *B, *T_;
-};
-template <typename T>
-C6<T> coefs3(const Level3 &L);
-template <>
-C6<double> coefs3<double>(const Level3 &L) {
-  return {L.c64[0], L.c64[1], L.c64[2], L.c64[3], L.c64[4], L.c64[5]};
-}
-template <>
-C6<float> coefs3<float>(const Level3 &L) {
-  return {L.c32[0], L.c32[1], L.c32[2], L.c32[3], L.c32[4], L.c32[5]};
-}
-
-// coefficient of row (i, j, k) towards direction d (0..5 = +x -x +y -y +z -z)
-template <typename T>
-__device__ __forceinline__ T cdir(const C6<T> &c, unsigned d, int i, int j, int k) {
-  switch (d) {
-    case 0: return __ldg(c.E + i);
-    case 1: return __ldg(c.W + i);
-    case 2: return __ldg(c.N + j);
-    case 3: return __ldg(c.S + j);
-    case 4: return __ldg(c.T_ + k);
-    default: return __ldg(c.B + k);
-  }
-}
-
-constexpr int WARP3_KMAX = 8, WARP3_WMAX = 8, WARP3_KPREF = 4;
-
-// Skeleton CTAs of a launch: edge scratch rows (a, b, c, r, zA, zB), each
-// `stride` values long.
-template <typename T>
-struct SkelArgs {
-  const WSkel3 *skel;
-  T *scr;
-  size_t stride;
-  int nskel;
-};
-
-__device__ __forceinline__ void unpack3(uint32_t v, int &i, int &j, int &k) {
-  i = (int)(v & 1023u); j = (int)((v >> 10) & 1023u); k = (int)(v >> 20);
-}
-
-// One wireframe edge skeleton per CTA (Sec. 7; the wireframe extension of
-// the Thomas algorithm): every edge is a tridiagonal chain between two
-// corners, eliminated by Thomas with three right-hand sides (the data, and
-// the responses to unit values at its two corners); the eight corner rows
-// then form an 8 x 8 system, solved by elimination (an M-matrix: no
-// pivoting); the edges are recombined from the corner values.
-__device__ __forceinline__ long long step3(unsigned d, int nx1, long long plane) {
-  const long long m = d < 2 ? 1 : (d < 4 ? (long long)nx1 : plane);
-  return (d & 1u) ? -m : m;
-}
-
-template <typename T>
-__device__ __noinline__ void skel_cta(const WSkel3 *__restrict__ S, T *__restrict__ scr, size_t stride,
-                                      const T *__restrict__ cW, const T *__restrict__ cE, const T *__restrict__ cS,
-                                      const T *__restrict__ cN, const T *__restrict__ cB, const T *__restrict__ cT,
-                                      int nx1, int ny1, T *__restrict__ u, const T *__restrict__ f) {
-  __shared__ T M[8][9];
-  __shared__ T X[8];
-  const C6<T> cp{cW, cE, cS, cN, cB, cT};
-  const int t = threadIdx.x, nt = blockDim.x;
-  const long long plane = (long long)nx1 * ny1;
-  const int e0 = (int)S->eoff[0], e12 = (int)S->eoff[12];
-  T *rA = scr, *rB = rA + stride, *rC = rB + stride, *rR = rC + stride, *rZA = rR + stride, *rZB = rZA + stride;
-  pdl_wait();
-  // 1. staging: the chain rows of every edge node
-  for (int q = e0 + t; q < e12; q += nt) {
-    int e = 0;
-    while ((int)S->eoff[e + 1] <= q) ++e;
-    const int sidx = q - (int)S->eoff[e];
-    const unsigned d = S->ed[e];
-    int i, j, k;
-    unpack3(S->cijk[S->ea[e]], i, j, k);
-    const long long p = (long long)k * plane + (long long)j * nx1 + i + (long long)(sidx + 1) * step3(d, nx1, plane);
-    const int pi = (int)(p % nx1), pj = (int)((p / nx1) % ny1), pk = (int)(p / plane);
-    T bb = T(0), r = __ldg(f + p), aa = T(0), cc = T(0);
-#pragma unroll
-    for (unsigned dd = 0; dd < 6; ++dd) {
-      const T cd = cdir(cp, dd, pi, pj, pk);
-      bb -= cd;
-      if (dd == (d ^ 1u)) aa = cd;
-      else if (dd == d) cc = cd;
-      else r -= cd * u[p + step3(dd, nx1, plane)];
-    }
-    rA[q] = aa; rB[q] = bb; rC[q] = cc; rR[q] = r;
-  }
-  __syncthreads();
-  // 2. Thomas per edge (thread e): columns y (data), zA, zB (unit corner values)
-  if (t < 12) {
-    const int o = (int)S->eoff[t], m = (int)S->eoff[t + 1] - o;
-    T cpv = T(0), y = T(0), za = T(0), cl = T(0), inv = T(0);
-    for (int s = 0; s < m; ++s) {
-      const T a = rA[o + s];
-      inv = T(1) / (rB[o + s] - a * cpv);
-      cl = rC[o + s];
-      cpv = cl * inv;
-      y = (rR[o + s] - a * y) * inv;
-      za = ((s == 0 ? -a : T(0)) - a * za) * inv;
-      rC[o + s] = cpv; rR[o + s] = y; rZA[o + s] = za;
-    }
-    T zb = -cl * inv;  // the last row's coupling to corner eb
-    if (m > 0) rZB[o + m - 1] = zb;
-    for (int s = m - 2; s >= 0; --s) {
-      const T c = rC[o + s];
-      y = rR[o + s] - c * y;
-      za = rZA[o + s] - c * za;
-      zb = -c * zb;
-      rR[o + s] = y; rZA[o + s] = za; rZB[o + s] = zb;
-    }
-  }
-  __syncthreads();
-  // 3. corner rows (thread q), then elimination (thread 0)
-  if (t < 8) {
-    int i, j, k;
-    unpack3(S->cijk[t], i, j, k);
-    const long long p = (long long)k * plane + (long long)j * nx1 + i;
-    for (int c = 0; c < 8; ++c) M[t][c] = T(0);
-    unsigned inblk = 0;
-    T diag = T(0), rhs = __ldg(f + p);
-    for (int e = 0; e < 12; ++e) {
-      const int o = (int)S->eoff[e], m = (int)S->eoff[e + 1] - o;
-      if (S->ea[e] == t) {  // the edge's first node is next to this corner
-        const unsigned d = S->ed[e];
-        inblk |= 1u << d;
-        const T kc = cdir(cp, d, i, j, k);
-        M[t][t] += kc * rZA[o];
-        M[t][S->eb[e]] += kc * rZB[o];
-        rhs -= kc * rR[o];
-      } else if (S->eb[e] == t) {
-        const unsigned d = S->ed[e] ^ 1u;
-        inblk |= 1u << d;
-        const T kc = cdir(cp, d, i, j, k);
-        M[t][S->ea[e]] += kc * rZA[o + m - 1];
-        M[t][t] += kc * rZB[o + m - 1];
-        rhs -= kc * rR[o + m - 1];
-      }
-    }
-    for (unsigned d = 0; d < 6; ++d) {
-      const T cd = cdir(cp, d, i, j, k);
-      diag -= cd;
-      if (!(inblk & (1u << d))) rhs -= cd * u[p + step3(d, nx1, plane)];
-    }
-    M[t][t] += diag;
-    M[t][8] = rhs;
-  }
-  __syncthreads();
-  if (t == 0) {
-    for (int c = 0; c < 8; ++c) {
-      const T ip = T(1) / M[c][c];
-      for (int r = c + 1; r < 8; ++r) {
-        const T l = M[r][c] * ip;
-        for (int q = c; q < 9; ++q) M[r][q] -= l * M[c][q];
-      }
-    }
-    for (int c = 7; c >= 0; --c) {
-      T v = M[c][8];
-      for (int q = c + 1; q < 8; ++q) v -= M[c][q] * X[q];
-      X[c] = v / M[c][c];
-    }
-  }
-  __syncthreads();
-  // 4. write back
-  if (t < 8) {
-    int i, j, k;
-    unpack3(S->cijk[t], i, j, k);
-    u[(long long)k * plane + (long long)j * nx1 + i] = X[t];
-  }
-  for (int q = e0 + t; q < e12; q += nt) {
-    int e = 0;
-    while ((int)S->eoff[e + 1] <= q) ++e;
-    const int sidx = q - (int)S->eoff[e];
-    int i, j, k;
-    unpack3(S->cijk[S->ea[e]], i, j, k);
-    const long long p = (long long)k * plane + (long long)j * nx1 + i + (long long)(sidx + 1) * step3(S->ed[e], nx1, plane);
-    u[p] = rR[q] + X[S->ea[e]] * rZA[q] + X[S->eb[e]] * rZB[q];
-  }
-}
-
-// ------------------------------------------------------------ the kernel --
-// One sequence of 32*W*K slots per CTA of W warps (the warp path of
-// warp_line.cu, seq_line_kernel, with six directions), holding the chains of
-// whole blocks and up to WJ3_MAX junctions (tweed star centres, nodes that
-// close wireframe rings).  The first sk.nskel CTAs of a launch each solve a
-// wireframe edge skeleton instead.
-template <typename T, int K, int W>
-__global__ void __launch_bounds__(32 * W) seq3_kernel(const WNode3 *__restrict__ nodes,
-                                                      const WJunc3 *__restrict__ juncs, const int *__restrict__ jofs,
-                                                      C6<T> cp, int nx1, int ny1, T *__restrict__ u,
-                                                      const T *__restrict__ f, const SkelArgs<T> sk) {
-  pdl_trigger();
-  if ((int)blockIdx.x < sk.nskel) {
-    skel_cta<T>(sk.skel + blockIdx.x, sk.scr, sk.stride, cp.W, cp.E, cp.S, cp.N, cp.B, cp.T_, nx1, ny1, u, f);
-    return;
-  }
-  constexpr int NT = 32 * W, N = NT * K;
-  extern __shared__ __align__(16) unsigned char sm3[];
-  T *sa = reinterpret_cast<T *>(sm3);
-  T *sb = sa + N, *sc = sb + N, *sd = sc + N, *sz = sd + N;
-  T *rep = sz + N;
-  T *red = rep + 4 * NT;
-  T *xjs = red + 8 * NT;             // junction values, then their rows' diagonal and rhs
-  T *jcs = xjs + WJ3_MAX, *jrs = jcs + WJ3_MAX;
-  int *sp = reinterpret_cast<int *>(jrs + WJ3_MAX);
-  unsigned char *sj = reinterpret_cast<unsigned char *>(sp + N);  // junction of each slot's block
-  const int t = threadIdx.x, lane = t & 31, cta = (int)blockIdx.x - sk.nskel;
-  const size_t plane = (size_t)nx1 * ny1;
-  const uint2 *nd = reinterpret_cast<const uint2 *>(nodes) + (size_t)cta * N;
-  const int j0 = __ldg(jofs + cta), nj = __ldg(jofs + cta + 1) - j0;
-  pdl_wait();  // u and f from here on
-  // ---- 1. staging (thread t: nodes NT*q + t)
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    const uint2 dsc = __ldg(nd + NT * q + t);
-    const unsigned fl = dsc.y;
-    const bool valid = (fl & WN3_VALID) != 0u;
-    const int i = (int)(dsc.x & 1023u), j = (int)((dsc.x >> 10) & 1023u), k = (int)(dsc.x >> 20);
-    const unsigned pd = (fl & WN3_PRED) ? (fl & 7u) : 7u, sd_ = (fl & WN3_SUCC) ? ((fl >> 4) & 7u) : 7u,
-                   jd = (fl & WN3_JUNC) ? ((fl >> 8) & 7u) : 7u;
-    const size_t p = (size_t)k * plane + (size_t)j * nx1 + i;
-    const size_t off[6] = {1, (size_t)0 - 1, (size_t)nx1, (size_t)0 - nx1, plane, (size_t)0 - plane};
-    T a = T(0), c = T(0), z = T(0), b = T(0), r = valid ? __ldg(f + p) : T(0);
-#pragma unroll
-    for (unsigned d = 0; d < 6; ++d) {
-      const T cd = cdir(cp, d, i, j, k);
-      b -= cd;
-      const bool outside = valid && d != pd && d != sd_ && d != jd;
-      if (outside) r -= cd * u[p + off[d]];
-      if (d == pd) a = cd;
-      if (d == sd_) c = cd;
-      if (d == jd) z = -cd;
-    }
-    const int s = NT * q + t, sl = wslot(s);
-    sa[sl] = a;
-    sc[sl] = c;
-    sz[sl] = z;
-    sb[sl] = valid ? b : T(1);
-    sd[sl] = r;
-    sp[s] = valid ? (int)p : -1;
-    sj[s] = (unsigned char)((fl >> WN3_JSHIFT) & 31u);
-  }
-  // junction rows (thread e: junction e): diagonal and right-hand side
-  if (t < nj) {
-    const uint32_t Jijk = __ldg(&juncs[j0 + t].ijk), Jadirs = __ldg(&juncs[j0 + t].adirs);
-    const int Jnatt = juncs[j0 + t].natt;
-    int ji, jj, jk;
-    unpack3(Jijk, ji, jj, jk);
-    unsigned att = 0;
-    for (int e = 0; e < Jnatt; ++e) att |= 1u << ((Jadirs >> (3 * e)) & 7u);
-    const size_t pJ = (size_t)jk * plane + (size_t)jj * nx1 + ji;
-    T rJ = __ldg(f + pJ), cJ = T(0);
-    const size_t off[6] = {1, (size_t)0 - 1, (size_t)nx1, (size_t)0 - nx1, plane, (size_t)0 - plane};
-#pragma unroll
-    for (unsigned d = 0; d < 6; ++d) {
-      const T cd = cdir(cp, d, ji, jj, jk);
-      cJ -= cd;
-      if (!(att & (1u << d))) rJ -= cd * u[pJ + off[d]];
-    }
-    jcs[t] = cJ;
-    jrs[t] = rJ;
-  }
-  __syncthreads();
-
-  // ---- 2. forward sweep per thread
-  const int base = t * K;
-  Sweep<T, K> sw;
-  sw.run(base, sa, sb, sc, sd, sz);
-  rep[t] = sw.Y0; rep[NT + t] = sw.Z0; rep[2 * NT + t] = sw.W0; rep[3 * NT + t] = sw.V0;
-  __syncthreads();
-
-  // ---- 3. separator rows, cyclic reduction through shared memory
-  const int ss = wslot(base + K - 1);
-  T A, C, Ry, Rz;
-  {
-    const bool last = t == NT - 1;
-    const T Yn = last ? T(0) : rep[t + 1], Zn = last ? T(0) : rep[NT + t + 1];
-    const T Wn = last ? T(0) : rep[2 * NT + t + 1], Vn = last ? T(0) : rep[3 * NT + t + 1];
-    const T a = sa[ss], c = sc[ss];
-    const T r = recip(sb[ss] - a * sw.cl + c * Wn);
-    A = a * sw.wl * r;
-    C = c * Vn * r;
-    Ry = (sd[ss] - a * sw.yl - c * Yn) * r;
-    Rz = (sz[ss] - a * sw.zl - c * Zn) * r;
-  }
-  red[t] = A; red[NT + t] = C; red[2 * NT + t] = Ry; red[3 * NT + t] = Rz;
-  __syncthreads();
-  int cur = 0;
-#pragma unroll
-  for (int dd = 1; dd < NT; dd <<= 1) {
-    const T *rb = red + 4 * NT * cur;
-    T Am = T(0), Cm = T(0), Ym = T(0), Zm = T(0), Ap = T(0), Cp = T(0), Yp = T(0), Zp = T(0);
-    if (t >= dd) { Am = rb[t - dd]; Cm = rb[NT + t - dd]; Ym = rb[2 * NT + t - dd]; Zm = rb[3 * NT + t - dd]; }
-    if (t + dd < NT) { Ap = rb[t + dd]; Cp = rb[NT + t + dd]; Yp = rb[2 * NT + t + dd]; Zp = rb[3 * NT + t + dd]; }
-    const T r = recip(T(1) - A * Cm - C * Ap);
-    const T nA = -A * Am * r, nC = -C * Cp * r;
-    const T nY = (Ry - A * Ym - C * Yp) * r, nZ = (Rz - A * Zm - C * Zp) * r;
-    A = nA; C = nC; Ry = nY; Rz = nZ;
-    cur ^= 1;
-    T *wb = red + 4 * NT * cur;
-    wb[t] = A; wb[NT + t] = C; wb[2 * NT + t] = Ry; wb[3 * NT + t] = Rz;
-    __syncthreads();
-  }
-  {
-    const T *rb = red + 4 * NT * cur;
-    const T Sym = t > 0 ? rb[2 * NT + t - 1] : T(0), Szm = t > 0 ? rb[3 * NT + t - 1] : T(0);
-    sw.back(base, Sym, Szm, Ry, Rz, sa, sb);
-  }
-  __syncthreads();
-
-  // ---- 5. junction values (lane e of warp 0: junction e), write back
-  if (nj > 0) {
-    if (t < 32) {
-      T x = T(0);
-      if (t < nj) {
-        const uint32_t Jijk = __ldg(&juncs[j0 + t].ijk), Jadirs = __ldg(&juncs[j0 + t].adirs);
-        const int Jnatt = juncs[j0 + t].natt;
-        int ji, jj, jk;
-        unpack3(Jijk, ji, jj, jk);
-        T sy = T(0), szz = T(0);
-        for (int e = 0; e < Jnatt; ++e) {
-          const T kp = cdir(cp, (Jadirs >> (3 * e)) & 7u, ji, jj, jk);
-          const int sl = wslot(juncs[j0 + t].as[e]);
-          sy += kp * sa[sl];
-          szz += kp * sb[sl];
-        }
-        x = (jrs[t] - sy) / (jcs[t] + szz);
-        u[(size_t)jk * plane + (size_t)jj * nx1 + ji] = x;
-      }
-      xjs[lane] = x;
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    const int s = NT * q + t;
-    const int p = sp[s];
-    if (p >= 0) {
-      const int sl = wslot(s);
-      u[p] = nj > 0 ? sa[sl] + xjs[sj[s]] * sb[sl] : sa[sl];
-    }
-  }
-}
-
-template <typename T, int K, int W>
-constexpr size_t seq3_smem() {
-  return (size_t)32 * W * K * (5 * sizeof(T) + sizeof(int) + 1) + sizeof(T) * (12 * 32 * W + 3 * WJ3_MAX);
-}
-
-template <typename T>
-SkelArgs<T> skel_args(const Grid3 &G, const WarpList3 &w) {
-  return {w.skel, reinterpret_cast<T *>(G.skel_scr), G.skel_len, w.nskel};
-}
-
-template <typename T, int K, int W>
-cudaError_t launch3_kw(const Grid3 &G, const Level3 &L, const WarpList3 &w, T *u, const T *f, cudaStream_t s) {
-  count_launch(1);
-  return launch_pdl(seq3_kernel<T, K, W>, dim3(w.nskel + w.nwarp), dim3(32 * W), seq3_smem<T, K, W>(), s,
-                    (const WNode3 *)w.node, (const WJunc3 *)w.junc, (const int *)w.jofs, coefs3<T>(L), L.nx + 1,
-                    L.ny + 1, u, f, skel_args<T>(G, w));
-}
-template <typename T, int K>
-cudaError_t launch3_k(const Grid3 &G, const Level3 &L, const WarpList3 &w, T *u, const T *f, cudaStream_t s) {
-  switch (w.W) {
-    case 1: return launch3_kw<T, K, 1>(G, L, w, u, f, s);
-    case 2: return launch3_kw<T, K, 2>(G, L, w, u, f, s);
-    case 4: return launch3_kw<T, K, 4>(G, L, w, u, f, s);
-    case 8: return launch3_kw<T, K, 8>(G, L, w, u, f, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-template <typename T>
-cudaError_t launch_warp3(const Grid3 &G, const Level3 &L, const WarpList3 &w, T *u, const T *f, cudaStream_t s) {
-  if (w.nwarp + w.nskel == 0) return cudaSuccess;
-  switch (w.K) {
-    case 1: return launch3_k<T, 1>(G, L, w, u, f, s);
-    case 2: return launch3_k<T, 2>(G, L, w, u, f, s);
-    case 4: return launch3_k<T, 4>(G, L, w, u, f, s);
-    case 8: return launch3_k<T, 8>(G, L, w, u, f, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-template <typename T, int K>
-cudaError_t opt_in3() {
-  cudaError_t e = cudaSuccess;
-  const int ws[4] = {1, 2, 4, 8};
-  for (int a = 0; a < 4 && e == cudaSuccess; ++a) {
-    switch (ws[a]) {
-      case 1: e = cudaFuncSetAttribute(seq3_kernel<T, K, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seq3_smem<T, K, 1>()); break;
-      case 2: e = cudaFuncSetAttribute(seq3_kernel<T, K, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seq3_smem<T, K, 2>()); break;
-      case 4: e = cudaFuncSetAttribute(seq3_kernel<T, K, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seq3_smem<T, K, 4>()); break;
-      default: e = cudaFuncSetAttribute(seq3_kernel<T, K, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)seq3_smem<T, K, 8>()); break;
-    }
-  }
-  return e;
-}
-cudaError_t prepare3() {
-  cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = opt_in3<float, 1>();
-  if (e == cudaSuccess) e = opt_in3<float, 2>();
-  if (e == cudaSuccess) e = opt_in3<float, 4>();
-  if (e == cudaSuccess) e = opt_in3<float, 8>();
-  if (e == cudaSuccess) e = opt_in3<double, 1>();
-  if (e == cudaSuccess) e = opt_in3<double, 2>();
-  if (e == cudaSuccess) e = opt_in3<double, 4>();
-  if (e == cudaSuccess) e = opt_in3<double, 8>();
-  return e;
-}
 
 // ----------------------------------------------------------- transfers --
 constexpr int T3 = 128;  // threads per CTA of the grid kernels (x along i)
@@ -822,11 +421,13 @@ bool blocks3(const Level3 &L, int sm, std::vector<HBlock3> &out) {
   return true;
 }
 
-// Sequences of one colour (first fit among the open sequences, largest blocks
-// first, at most WJ3_MAX junctions per sequence), K and W as in 2D
-// (warp_line.cu) with at most 8 nodes per thread (both precisions use the
-// same lists), and the colour's edge skeletons.
-mg_status warp_list3(const Level3 &L, const std::vector<HBlock3> &all, int colour, WarpList3 &Wl) {
+// Sequences of one colour (first fit, largest blocks first), K and W as in
+// 2D (warp_line.cu) with at most 8 nodes per thread (both precisions use the
+// same lists), and the colour's edge skeletons.  multi: up to WJ3_MAX
+// junctions per sequence (wireframe rings), listed per sequence through
+// jofs; otherwise at most one, the sequence's own junction record.
+mg_status warp_list3(const Level3 &L, const std::vector<HBlock3> &all, int colour, bool multi, WarpList3 &Wl) {
+  const int jmax = multi ? WJ3_MAX : 1;
   std::vector<int> idx, sk;
   int maxn = 1, total = 0, skn = 0;
   for (size_t b = 0; b < all.size(); ++b) {
@@ -854,15 +455,32 @@ mg_status warp_list3(const Level3 &L, const std::vector<HBlock3> &all, int colou
   std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return all[a].nodes > all[b].nodes; });
   struct Bin { int used = 0, nj = 0; std::vector<int> blocks; };
   std::vector<Bin> bins;
+  // first fit: a max-tree over the free slots of every possible bin finds
+  // the leftmost bin with room (log time per block)
+  int P2 = 1;
+  while (P2 < (int)idx.size()) P2 *= 2;
+  std::vector<int> fr(2 * (size_t)P2, cap);
+  auto first_fit = [&](int lo, int n) {  // leftmost bin >= lo with >= n free slots, or -1
+    std::function<int(int, int, int)> go = [&](int v, int l, int r) -> int {
+      if (r <= lo || fr[v] < n) return -1;
+      if (r - l == 1) return l;
+      const int m = (l + r) / 2, a = go(2 * v, l, m);
+      return a >= 0 ? a : go(2 * v + 1, m, r);
+    };
+    return go(1, 0, P2);
+  };
   for (int b : idx) {
     const int nj = all[b].junc >= 0 ? 1 : 0, n = all[b].nodes;
-    // first fit among the 64 newest bins (blocks arrive largest first)
-    size_t w = bins.size() > 64 ? bins.size() - 64 : 0;
-    while (w < bins.size() && (bins[w].used + n > cap || bins[w].nj + nj > WJ3_MAX)) ++w;
-    if (w == bins.size()) bins.emplace_back();
+    int w = first_fit(0, n);
+    while (w >= 0 && w < (int)bins.size() && bins[w].nj + nj > jmax) w = first_fit(w + 1, n);
+    if (w < 0) return MG_ERR_SIZE;  // cannot happen: every block fits an empty bin
+    while ((int)bins.size() <= w) bins.emplace_back();
     bins[w].used += n;
     bins[w].nj += nj;
     bins[w].blocks.push_back(b);
+    int v = P2 + w;
+    fr[v] = cap - bins[w].used;
+    for (v >>= 1; v >= 1; v >>= 1) fr[v] = std::max(fr[2 * v], fr[2 * v + 1]);
   }
   const int nx1 = L.nx + 1;
   const size_t plane = (size_t)nx1 * (L.ny + 1);
@@ -878,15 +496,21 @@ mg_status warp_list3(const Level3 &L, const std::vector<HBlock3> &all, int colou
   };
   for (size_t w = 0; w < bins.size(); ++w) {
     jofs[w] = (int)jn.size();
+    if (!multi) {  // one record per sequence, natt = 0 without a junction
+      jn.emplace_back();
+      std::memset(&jn.back(), 0, sizeof(WJunc3));
+    }
     int s = 0;
     for (int b : bins[w].blocks) {
       const HBlock3 &hb = all[b];
-      const uint32_t jl = (uint32_t)(jn.size() - jofs[w]);
+      const uint32_t jl = multi ? (uint32_t)(jn.size() - jofs[w]) : 0u;
       WJunc3 *jb = nullptr;
       if (hb.junc >= 0) {
-        jn.emplace_back();
+        if (multi) {
+          jn.emplace_back();
+          std::memset(&jn.back(), 0, sizeof(WJunc3));
+        }
         jb = &jn.back();
-        std::memset(jb, 0, sizeof(WJunc3));
         jb->ijk = pack(hb.junc);
       }
       for (size_t c = 0; c < hb.chains.size(); ++c) {
@@ -948,6 +572,7 @@ mg_status warp_list3(const Level3 &L, const std::vector<HBlock3> &all, int colou
   Wl.total_nodes = total;
   Wl.nskel = (int)sk.size();
   Wl.skel_nodes = skn;
+  Wl.multi = multi;
   return MG_OK;
 }
 
@@ -1001,7 +626,8 @@ mg_status setup3(Grid &g, const int64_t *n, const double *const *coords) {
     cx /= 2; cy /= 2; cz /= 2;
   }
   g.nlev = (int)G.lev.size();
-  TRY_CUDA("3D kernel attributes", prepare3());
+  TRY_CUDA("3D kernel attributes", prepare3_t<false>());
+  TRY_CUDA("3D kernel attributes", prepare_seq3_multi());
   const bool want64 = g.prec_mask & 1, want32 = g.prec_mask & 2;
   for (int l = 0; l < g.nlev; ++l) {
     Level3 &L = G.lev[l];
@@ -1042,12 +668,12 @@ mg_status setup3(Grid &g, const int64_t *n, const double *const *coords) {
         set_error_text("3D tweed: a side with an odd number of intervals on a smoothed level");
         return MG_ERR_UNSUPPORTED;
       }
-      for (int c = 0; c < 2; ++c) TRY(warp_list3(L, blocks, c, L.wp[SM3_TWEED][c]));
+      for (int c = 0; c < 2; ++c) TRY(warp_list3(L, blocks, c, false, L.wp[SM3_TWEED][c]));
       blocks.clear();
       L.wf_ok = blocks3(L, SM3_WIREFRAME, blocks);
       if (L.wf_ok)
         for (int c = 0; c < 2; ++c) {
-          TRY(warp_list3(L, blocks, c, L.wp[SM3_WIREFRAME][c]));
+          TRY(warp_list3(L, blocks, c, true, L.wp[SM3_WIREFRAME][c]));
           G.skel_len = std::max(G.skel_len, (size_t)L.wp[SM3_WIREFRAME][c].skel_nodes);
         }
     }
@@ -1114,7 +740,8 @@ mg_status colour_pass3(Grid &g, int l, int sm, int colour, T *u, const T *f, cud
     return MG_ERR_UNSUPPORTED;
   }
   return cuda_status(sm == SM3_WIREFRAME ? "3D wireframe pass" : "3D tweed pass",
-                     launch_warp3<T>(*g.g3, L, L.wp[sm][colour], u, f, s));
+                     L.wp[sm][colour].multi ? launch_seq3_multi<T>(*g.g3, L, L.wp[sm][colour], u, f, s)
+                                            : launch_warp3_t<T, false>(*g.g3, L, L.wp[sm][colour], u, f, s));
 }
 
 template <typename T>

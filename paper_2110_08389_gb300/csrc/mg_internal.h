@@ -179,10 +179,12 @@ static_assert(sizeof(WSkel3) == 128, "WSkel3 layout");
 struct WarpList3 {
   int nwarp = 0, K = 0, W = 1, total_nodes = 0;
   int nskel = 0, skel_nodes = 0;      // skeleton CTAs (launched first) and their interior edge nodes
+  bool multi = false;                 // several junctions per sequence (wireframe lists)
   void *mem = nullptr;
   WNode3 *node = nullptr;
   WJunc3 *junc = nullptr;
-  int *jofs = nullptr;                // sequence w owns junctions [jofs[w], jofs[w + 1])
+  int *jofs = nullptr;                // multi: sequence w owns junctions [jofs[w], jofs[w + 1]);
+                                      // otherwise junc[w] is sequence w's (natt = 0: none)
   WSkel3 *skel = nullptr;
 };
 enum { SM3_TWEED = 0, SM3_WIREFRAME = 1 };

@@ -4,7 +4,7 @@ profilers (ncu) and quick timing.
     python -m paper_2110_08389_gb300.profile_pass [--n 4096] [--smoother tweed]
            [--dtype f32|f64] [--steps 3] [--ratio 1000] [--dim 2|3]
 
-The grid has n x n (x n with --dim 3, tweed only) intervals, tanh-stretched
+The grid has n x n (x n with --dim 3: tweed or wireframe) intervals, tanh-stretched
 toward the walls (Eq. tanh) for
 every smoother but wireframe, toward the centre (Eq. tanh_inv) for wireframe,
 with the given max/min spacing ratio; f ~ N(0, 1) (seed 1), u = 0.  Each step

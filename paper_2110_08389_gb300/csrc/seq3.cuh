@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(32 * W) seq3_single_kernel(const WNode3 *__res
 // nodes that close rings; sequence w owns juncs[jofs[w] .. jofs[w + 1])),
 // and the first sk.nskel CTAs of a launch each solve an edge skeleton.
 template <typename T, int K, int W>
-__global__ void __launch_bounds__(32 * W) seq3_multi_kernel(const WNode3 *__restrict__ nodes,
+__global__ void __launch_bounds__(32 * W, sizeof(T) == 4 ? 32 / W : 1) seq3_multi_kernel(const WNode3 *__restrict__ nodes,
                                                       const WJunc3 *__restrict__ juncs, const int *__restrict__ jofs,
                                                       C6<T> cp, int nx1, int ny1, T *__restrict__ u,
                                                       const T *__restrict__ f, const SkelArgs<T> sk) {

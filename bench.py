@@ -419,7 +419,7 @@ def run_3d(args):
             "speedup_vs_fp64": ms64 / ms, "f32_refine_vs_f64_solution_maxrel": err32,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 2 * 8 * nn, "d2h_bytes_per_step": 8 * nn},
             "gpu_launches": int(launches),
-            "roofline": {"kernel": "FP32 3D tweed colour pass, finest level (seq3_kernel)", "bound": "hbm",
+            "roofline": {"kernel": "FP32 3D tweed colour pass, finest level (seq3_single_kernel)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "pass_ms": pass_ms, "passes_timed": npass, "launches_per_pass": 1,
                          "algo_bytes_per_pass": algo_bytes,

@@ -255,9 +255,15 @@ def run_batch(args):
     batch = mg.Batch(grids)
     # the paper's pairing (Sec. 6): tweed for wall clustering, wireframe for
     # clustering towards the centre
-    params = [mg.default_params(smoother="wireframe" if kind == "centre" else "tweed", nu1=args.nu[0],
-                                nu2=args.nu[1], precision="f32_refine", tol=TOL, inner_cycles=args.inner,
-                                max_outer=20, max_cycles=200) for (_, _, kind, _) in probs]
+    # early_stop: a problem gives up once its last refinement step's rate
+    # cannot reach the tolerance within the steps left (the centre-clustered
+    # problems wireframe cannot converge, Sec. 6); the same batch without it
+    # is timed once below and must converge the same problems
+    def batch_params(early):
+        return [mg.default_params(smoother="wireframe" if kind == "centre" else "tweed", nu1=args.nu[0],
+                                  nu2=args.nu[1], precision="f32_refine", tol=TOL, inner_cycles=args.inner,
+                                  max_outer=20, max_cycles=200, early_stop=early) for (_, _, kind, _) in probs]
+    params = batch_params(1)
     # line-tile shapes by the autotuner: every path and warp shape of every
     # level is timed once per (level shape, smoother); later grids with the
     # same level shapes take the remembered choice
@@ -287,6 +293,18 @@ def run_batch(args):
     ok = sum(1 for r in res if r.status == mg.OK and r.rel_res <= TOL)
     ok_kind = {kind: sum(1 for r, p in zip(res, probs) if p[2] == kind and r.status == mg.OK)
                for kind in ("wall", "centre")}
+    # the same batch without the early stop, once
+    params_full = batch_params(0)
+    batch.solve(us, fs, params_full)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    res_full = batch.solve(us, fs, params_full)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    full = {"s": e0.elapsed_time(e1) / 1e3,
+            "converged": sum(1 for r in res_full if r.status == mg.OK and r.rel_res <= TOL),
+            "same_converged_set": [r.status == mg.OK for r in res_full] == [r.status == mg.OK for r in res],
+            "inner_cycles_total": sum(r.cycles for r in res_full)}
     # the same problems one after another
     torch.cuda.synchronize()
     e0.record(stream)
@@ -314,9 +332,11 @@ def run_batch(args):
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "256 problems, n+1 in {129,257,513,1025}^2 uniform, spacing ratio log-uniform "
                                    "[10,1000], wall/centre by coin flip (seed 2), f~N(0,1), tweed (wall) / wireframe "
-                                   "(centre) V(1,1), FW, to ||r||/||f||<=1e-10", "nodes_total": nodes, "problems": len(probs),
+                                   "(centre) V(1,1), FW, to ||r||/||f||<=1e-10 or an early stop once a problem's rate cannot reach it "
+                                   "within 20 refinement steps", "nodes_total": nodes, "problems": len(probs),
                        "sizes": {str(s + 1): sum(1 for p in probs if p[0] == s) for s in BATCH_SIZES}},
-            "converged": ok, "converged_by_clustering": ok_kind,
+            "converged": ok, "converged_by_clustering": ok_kind, "early_stop": 1,
+            "inner_cycles_total": sum(r.cycles for r in res), "without_early_stop": full,
             "line_paths": {"autotune_s": tune_s, "chosen": choices},
             "smoothers": "tweed (wall-clustered), wireframe (centre-clustered)",
             "problems_per_s": len(probs) / (ms / 1e3),

@@ -80,7 +80,7 @@ typedef enum { MG_RESTRICT_HW = 0, MG_RESTRICT_FW = 1 } mg_restriction;
 
 /* Solver parameters (Sec. 4).  mg_default_params() fills the defaults:
  * tweed, V(2,2), full weighting, FP64, tol 1e-10, 100 cycles, 8 outer
- * iterations, 4 inner cycles, zero initial guess.                            */
+ * iterations, 3 inner cycles, zero initial guess, no early stop.             */
 typedef struct {
   int smoother;          /* mg_smoother                                          */
   int nu1, nu2;          /* pre- / post-smoothing relaxations (>= 0)             */
@@ -91,6 +91,11 @@ typedef struct {
   int max_outer;         /* cap on refinement iterations (FP32+refine)           */
   int inner_cycles;      /* FP32 cycles per refinement iteration (default 3)     */
   int use_initial_guess; /* 0: interior of u is zeroed first; 1: u is the guess  */
+  int early_stop;        /* 1: give up (MG_ERR_NOT_CONVERGED) once, from the 3rd */
+                         /* cycle (FP64) or refinement iteration on, the last    */
+                         /* step's reduction, kept for the steps left under the  */
+                         /* caps, cannot reach tol (or the step did not reduce)  */
+  int reserved;          /* must be 0                                            */
   double tol;            /* stop when ||f - L u||_2 / ||f||_2 <= tol (interior)   */
 } mg_params;
 

@@ -395,6 +395,7 @@ mg_status check_params(const Grid *g, const mg_params *p) {
   if (p->precision == MG_PREC_F32_REFINE && !(g->prec_mask & 2)) return MG_ERR_INVALID_ARG;
   if (p->precision != MG_PREC_F64 && p->precision != MG_PREC_F32_REFINE) return MG_ERR_INVALID_ARG;
   if (!(p->tol >= 0.0) || p->max_cycles < 0 || p->max_outer < 0 || p->inner_cycles < 1) return MG_ERR_INVALID_ARG;
+  if ((p->early_stop != 0 && p->early_stop != 1) || p->reserved != 0) return MG_ERR_INVALID_ARG;
   // 3D grids: tweed, wireframe or both alternating, with full weighting (Sec. 7)
   if (g->dim == 3 && ((p->smoother != MG_SMOOTH_TWEED && p->smoother != MG_SMOOTH_WIREFRAME &&
                        p->smoother != MG_SMOOTH_ALT_TW) ||
@@ -484,6 +485,7 @@ void consume_value(SolveState &q, double v) {
       q.cycles += p.inner_cycles;
       q.outer += 1;
     }
+    q.prev = q.rel;
     q.rel = std::sqrt(v) / q.fn;
     record(q.info, f64 ? q.cycles : q.outer, q.rel);
   }
@@ -491,6 +493,14 @@ void consume_value(SolveState &q, double v) {
   if (!std::isfinite(q.rel)) { q.st = MG_ERR_NONFINITE; return finish(q); }
   const bool limit = f64 ? q.cycles >= p.max_cycles : (q.outer >= p.max_outer || q.cycles >= p.max_cycles);
   if (limit || q.rel > 1e3 * q.rel0) { q.st = MG_ERR_NOT_CONVERGED; return finish(q); }
+  // early stop: at the last step's rate the steps left under the caps fall short
+  const int steps = f64 ? q.cycles : q.outer;
+  if (p.early_stop && q.phase == 2 && steps >= 3 && q.prev > 0.0) {
+    const double rate = q.rel / q.prev;
+    const int left = f64 ? p.max_cycles - q.cycles
+                         : std::min(p.max_outer - q.outer, (p.max_cycles - q.cycles) / p.inner_cycles);
+    if (rate >= 1.0 || q.rel * std::pow(rate, (double)left) > p.tol) { q.st = MG_ERR_NOT_CONVERGED; return finish(q); }
+  }
 }
 
 static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params &p, mg_info *info,
@@ -522,6 +532,8 @@ void mg_default_params(mg_params *p) {
   p->max_outer = 8;
   p->inner_cycles = 3;
   p->use_initial_guess = 0;
+  p->early_stop = 0;
+  p->reserved = 0;
   p->tol = 1e-10;
 }
 

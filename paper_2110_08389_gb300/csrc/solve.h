@@ -21,7 +21,7 @@ struct SolveState {
   int phase = 0;  // 0: scale norm, 1: initial residual, 2: iterating
   bool done = false;
   mg_status st = MG_OK;
-  double fn = 0.0, rel = 0.0, rel0 = 0.0;
+  double fn = 0.0, rel = 0.0, rel0 = 0.0, prev = 0.0;  // prev: rel before the last step
   int cycles = 0, outer = 0;
 };
 

@@ -51,7 +51,8 @@ class Params(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("cycle", ctypes.c_int), ("restriction", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("max_outer", ctypes.c_int), ("inner_cycles", ctypes.c_int),
-                ("use_initial_guess", ctypes.c_int), ("tol", ctypes.c_double)]
+                ("use_initial_guess", ctypes.c_int), ("early_stop", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("tol", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):

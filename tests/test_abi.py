@@ -57,3 +57,37 @@ def test_missing_library_fails_loudly(tmp_path):
             mg.load(str(tmp_path / "missing.so"))
     finally:
         mg._lib = saved
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structs have the header's field offsets and sizes
+    (checked by a small C program built with gcc against include/mg.h)."""
+    import subprocess
+    from paper_2110_08389_gb300 import mg
+    structs = {"mg_params": mg.Params, "mg_info": mg.Info}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "mg.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for field, _ in py._fields_:
+            lines.append(f'  printf("{cname} {field} %zu\\n", offsetof({cname}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            c, k, v = line.split()
+            got[(c, k)] = int(v)
+    for cname, py in structs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for field, _ in py._fields_:
+            assert got[(cname, field)] == getattr(py, field).offset, (cname, field)
+
+
+def test_default_params():
+    from paper_2110_08389_gb300 import mg
+    p = mg.default_params()
+    assert (p.smoother, p.nu1, p.nu2, p.inner_cycles, p.early_stop, p.reserved) == (mg.TWEED, 2, 2, 3, 0, 0)

@@ -32,15 +32,24 @@ SEED = 1
 TOL = 1e-10
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "tweed_pass_f32_4097_traffic.json")
-# sources whose change invalidates the stored ncu traffic of the tiled pass
-TRAFFIC_SOURCES = ["tiles.cu", "tile_setup.cu", "mg_internal.h"]
+# sources whose change invalidates the stored ncu traffic of the tiled pass:
+# the tiled kernels, their setup, the launch helpers, and the tiled-path part
+# of the internal header (from its "Tiled line path" comment to the Level
+# struct); the rest of that header (other paths' structs, declarations) does
+# not enter the tiled kernels
+TRAFFIC_SOURCES = ["tiles.cu", "tile_setup.cu", "device_util.cuh", "mg_internal.h#tiled"]
 
 
 def traffic_key():
     import hashlib
     h = hashlib.sha256()
     for name in TRAFFIC_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2110_08389_gb300", "csrc", name), "rb").read())
+        fn, _, part = name.partition("#")
+        text = open(os.path.join(ROOT, "paper_2110_08389_gb300", "csrc", fn), "rb").read()
+        if part == "tiled":
+            a = text.index(b"// Tiled line path")
+            text = text[a:text.index(b"struct Level {", a)]
+        h.update(text)
     return h.hexdigest()
 
 
@@ -55,6 +64,8 @@ def parse():
                     help="FP32 cycles per refinement step (each step gains at most ~1e-3 in FP32 on this grid)")
     ap.add_argument("--intervals", type=int, default=N_INTERVALS, help="intervals per side (4096: the 4097 x 4097 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--coarse-direct", type=int, default=1, choices=[0, 1],
+                    help="FP32 cycles solve the finest level of at most 64x64 intervals directly (2D workload)")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "3d"],
                     help="single: the 4097^2 solve (default); batch: 256 mixed problems solved together; "
                          "3d: the 257^3 tweed solve")
@@ -485,7 +496,8 @@ def main():
     f = torch.tensor(f_h, device=dev)
     u = torch.zeros((n1, n1), dtype=torch.float64, device=dev)
     p32 = mg.default_params(smoother="tweed", nu1=args.nu[0], nu2=args.nu[1], precision="f32_refine",
-                            tol=TOL, inner_cycles=args.inner, max_outer=20, max_cycles=200)
+                            tol=TOL, inner_cycles=args.inner, max_outer=20, max_cycles=200,
+                            coarse_direct=args.coarse_direct)
     p64 = mg.default_params(smoother="tweed", nu1=args.nu[0], nu2=args.nu[1], precision="f64", tol=TOL,
                             max_cycles=200)
 
@@ -566,6 +578,9 @@ def main():
             "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic", "config": config_dict(args, c),
+            "coarse_direct": (f"the FP32 cycles stop at level {grid.direct_level} ({grid.shape(grid.direct_level)[0]}^2) and "
+                              "solve it directly (one kernel); FP64 cycles use every level"
+                              if args.coarse_direct and grid.direct_level >= 0 else "off"),
             "status": status32, "rel_res": rel32, "outer_iters": outer32, "inner_cycles_total": cyc32,
             "fp64": {"s": ms64 / 1e3, "cycles": r64.cycles, "rel_res": r64.rel_res, "status": r64.status},
             "speedup_vs_fp64": ms64 / ms, "f32_refine_vs_f64_solution_maxrel": err32,

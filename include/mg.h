@@ -95,7 +95,9 @@ typedef struct {
                          /* cycle (FP64) or refinement iteration on, the last    */
                          /* step's reduction, kept for the steps left under the  */
                          /* caps, cannot reach tol (or the step did not reduce)  */
-  int reserved;          /* must be 0                                            */
+  int coarse_direct;     /* 1: the FP32 cycles solve the level mg_direct_level() */
+                         /* names exactly (one kernel) instead of cycling below  */
+                         /* it; FP64 cycles are not affected (default 0)         */
   double tol;            /* stop when ||f - L u||_2 / ||f||_2 <= tol (interior)   */
 } mg_params;
 
@@ -188,6 +190,19 @@ mg_status mg_residual(mg_grid *grid, int level, const void *u, const void *f, vo
 /* Direct solve of the coarsest level (dense LU, FP64 arithmetic for both
  * dtypes).  The boundary values of u enter the right-hand side.              */
 mg_status mg_coarse_solve(mg_grid *grid, void *u, const void *f, int dtype, void *stream);
+
+/* The level the FP32 cycles solve directly under mg_params.coarse_direct:
+ * the finest level below the finest one with both sides at most 64
+ * intervals, or -1 (no such level, a 3D grid, or no FP32 workspaces).       */
+int mg_direct_level(const mg_grid *grid);
+
+/* Direct solve of that level's interior system in FP32 (u, f: float arrays
+ * of the level's shape; the boundary values of u enter the right-hand side)
+ * by the fast diagonalisation of the operator's Kronecker-sum form: the 1D
+ * factors, symmetrised by the diagonal D of Sec. 2's symmetry, are
+ * eigen-decomposed once at setup; a solve is four dense products in one CTA.
+ * MG_ERR_UNSUPPORTED when mg_direct_level() is -1.                          */
+mg_status mg_direct_solve(mg_grid *grid, void *u, const void *f, void *stream);
 
 /* One cycle (params->cycle: V or W) on the finest level, in the dtype of
  * params->precision (MG_PREC_F64 -> double arrays, MG_PREC_F32_REFINE ->

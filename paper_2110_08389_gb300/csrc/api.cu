@@ -77,6 +77,7 @@ static void free_grid(Grid *g) {
       }
   }
   cudaFree(g->cinv);
+  cudaFree(g->fd_tr);
   cudaFree(g->r64); cudaFree(g->e32); cudaFree(g->r32);
   cudaFree(g->partial); cudaFree(g->scal);
   cudaFree(g->tile_rows); cudaFree(g->tile_d); cudaFree(g->tile_x);
@@ -212,6 +213,7 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
   const size_t nn0 = g->lev[0].nn;
   if (want32) { TRY(dalloc(&g->e32, nn0, "cudaMalloc(e32)")); TRY(dalloc(&g->r32, nn0, "cudaMalloc(r32)")); }
   if (want64) TRY(dalloc(&g->r64, nn0, "cudaMalloc(adjoint scratch)"));
+  TRY(setup_direct_level(*g));
   TRY(setup_solver_state(g));
   // block work lists of every line smoother on every level, so that no later
   // call allocates
@@ -315,6 +317,12 @@ static mg_status smooth(Grid &g, int l, int smoother, T *u, const T *f, cudaStre
 template <typename T>
 static mg_status cycle_rec(Grid &g, const mg_params &p, int l, T *u, const T *f, cudaStream_t s) {
   if (g.dim == 3) return cycle3<T>(g, p, l, u, f, s);
+  if constexpr (sizeof(T) == 4) {
+    if (p.coarse_direct && l == g.fd_level) {
+      TRY_CUDA("direct level solve", launch_direct_level(g, (float *)u, (const float *)f, s));
+      return MG_OK;
+    }
+  }
   if (l == g.nlev - 1) {
     TRY_CUDA("coarse solve", launch_coarse_solve<T>(g, u, f, s));
     return MG_OK;
@@ -345,7 +353,7 @@ static mg_status run_cycles(Grid &g, const mg_params &p, int ncyc, T *u, const T
     for (int k = 0; k < ncyc; ++k) TRY(cycle_rec<T>(g, p, 0, u, f, s));
     return MG_OK;
   }
-  const int key[8] = {(int)sizeof(T), p.smoother, p.nu1, p.nu2, p.cycle, p.restriction, ncyc, 0};
+  const int key[8] = {(int)sizeof(T), p.smoother, p.nu1, p.nu2, p.cycle, p.restriction, ncyc, p.coarse_direct};
   Grid::GraphEntry *ge = nullptr;
   for (auto &x : g.graphs)
     if (x.u == u && x.f == f && std::memcmp(x.key, key, sizeof(key)) == 0) { ge = &x; break; }
@@ -395,7 +403,9 @@ mg_status check_params(const Grid *g, const mg_params *p) {
   if (p->precision == MG_PREC_F32_REFINE && !(g->prec_mask & 2)) return MG_ERR_INVALID_ARG;
   if (p->precision != MG_PREC_F64 && p->precision != MG_PREC_F32_REFINE) return MG_ERR_INVALID_ARG;
   if (!(p->tol >= 0.0) || p->max_cycles < 0 || p->max_outer < 0 || p->inner_cycles < 1) return MG_ERR_INVALID_ARG;
-  if ((p->early_stop != 0 && p->early_stop != 1) || p->reserved != 0) return MG_ERR_INVALID_ARG;
+  if ((p->early_stop != 0 && p->early_stop != 1) || (p->coarse_direct != 0 && p->coarse_direct != 1))
+    return MG_ERR_INVALID_ARG;
+  if (g->dim == 3 && p->coarse_direct) return MG_ERR_UNSUPPORTED;
   // 3D grids: tweed, wireframe or both alternating, with full weighting (Sec. 7)
   if (g->dim == 3 && ((p->smoother != MG_SMOOTH_TWEED && p->smoother != MG_SMOOTH_WIREFRAME &&
                        p->smoother != MG_SMOOTH_ALT_TW) ||
@@ -533,7 +543,7 @@ void mg_default_params(mg_params *p) {
   p->inner_cycles = 3;
   p->use_initial_guess = 0;
   p->early_stop = 0;
-  p->reserved = 0;
+  p->coarse_direct = 0;
   p->tol = 1e-10;
 }
 
@@ -736,6 +746,15 @@ mg_status mg_coarse_solve(mg_grid *g, void *u, const void *f, int dtype, void *s
   cudaError_t e = dtype == MG_F64 ? launch_coarse_solve<double>(*g, (double *)u, (const double *)f, s)
                                   : launch_coarse_solve<float>(*g, (float *)u, (const float *)f, s);
   return cuda_status("coarse solve", e);
+}
+
+int mg_direct_level(const mg_grid *g) { return g && g->dim == 2 ? g->fd_level : -1; }
+
+mg_status mg_direct_solve(mg_grid *g, void *u, const void *f, void *stream) {
+  if (!g || !u || !f) return MG_ERR_INVALID_ARG;
+  if (g->dim != 2 || g->fd_level < 0) return MG_ERR_UNSUPPORTED;
+  return cuda_status("direct level solve",
+                     launch_direct_level(*g, (float *)u, (const float *)f, static_cast<cudaStream_t>(stream)));
 }
 
 mg_status mg_vcycle(mg_grid *g, void *u, const void *f, const mg_params *p, void *stream) {

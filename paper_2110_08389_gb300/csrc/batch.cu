@@ -351,7 +351,7 @@ mg_status mg_batch_solve(mg_batch *b, double *const *u, const double *const *f, 
     for (int i = 0; i < n; ++i) {
       if (used[i]) continue;
       const mg_params &p = q[i].p;
-      const bool packable = p.precision == MG_PREC_F32_REFINE && warp_everywhere(*q[i].g, p.smoother);
+      const bool packable = p.precision == MG_PREC_F32_REFINE && !p.coarse_direct && warp_everywhere(*q[i].g, p.smoother);
       Group G;
       G.members.push_back(i);
       used[i] = true;

@@ -304,6 +304,10 @@ struct Grid {
   // coarsest level: dense inverse of the interior operator (FP64, row-major)
   int cn = 0;
   double *cinv = nullptr;
+  // level solved directly by the FP32 cycles when mg_params.coarse_direct is
+  // set (fd.cu): -1 if none; its transforms (FP32)
+  int fd_level = -1;
+  float *fd_tr = nullptr;
   // finest-level FP64/FP32 scratch for the refinement loop and norms
   double *r64 = nullptr;             // adjoint scratch: the scaled right-hand side (finest)
   float *e32 = nullptr, *r32 = nullptr;
@@ -349,6 +353,12 @@ inline void count_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std
 // inverse with partial pivoting (false if singular)
 void axis_coefficients(const std::vector<double> &x, std::vector<double> &lo, std::vector<double> &hi);
 bool invert(int n, std::vector<double> &A, std::vector<double> &inv);
+
+// ---- direct level solve (fd.cu): levels with both sides at most this many
+// intervals qualify; the finest such level below the finest one is chosen
+constexpr int FD_MAX_SIDE = 64;
+mg_status setup_direct_level(Grid &g);
+cudaError_t launch_direct_level(const Grid &g, float *u, const float *f, cudaStream_t s);
 
 // ---- 3D grids (grid3d.cu)
 mg_status setup3(Grid &g, const int64_t *n, const double *const *coords);

@@ -38,7 +38,7 @@ EXPORTS = ["mg_setup_grid", "mg_destroy", "mg_num_levels", "mg_level_shape", "mg
            "mg_default_params", "mg_status_string", "mg_last_error", "mg_kernel_launches",
            "mg_residual_norm_static", "mg_pass_timer_begin", "mg_pass_timer_end", "mg_boundary_adjoint", "mg_batch_create",
            "mg_batch_destroy", "mg_batch_solve", "mg_set_line_path", "mg_get_line_path", "mg_autotune",
-           "mg_level_dims", "mg_grid_dim"]
+           "mg_level_dims", "mg_grid_dim", "mg_direct_level", "mg_direct_solve"]
 
 
 class MGError(RuntimeError):
@@ -51,7 +51,7 @@ class Params(ctypes.Structure):
     _fields_ = [("smoother", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("cycle", ctypes.c_int), ("restriction", ctypes.c_int), ("precision", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("max_outer", ctypes.c_int), ("inner_cycles", ctypes.c_int),
-                ("use_initial_guess", ctypes.c_int), ("early_stop", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("use_initial_guess", ctypes.c_int), ("early_stop", ctypes.c_int), ("coarse_direct", ctypes.c_int),
                 ("tol", ctypes.c_double)]
 
 
@@ -88,6 +88,8 @@ def load(path: str = LIB_PATH):
         "mg_prolong_add": (i, [vp, i, vp, vp, i, vp]),
         "mg_residual": (i, [vp, i, vp, vp, vp, i, vp]),
         "mg_coarse_solve": (i, [vp, vp, vp, i, vp]),
+        "mg_direct_level": (i, [vp]),
+        "mg_direct_solve": (i, [vp, vp, vp, vp]),
         "mg_vcycle": (i, [vp, vp, vp, ctypes.POINTER(Params), vp]),
         "mg_solve": (i, [vp, vp, vp, ctypes.POINTER(Params), ctypes.POINTER(Info), vp]),
         "mg_solve_adjoint": (i, [vp, vp, vp, ctypes.POINTER(Params), ctypes.POINTER(Info), vp]),
@@ -314,6 +316,16 @@ class Grid:
     def coarse_solve(self, u, f, stream=None):
         _check(self.lib.mg_coarse_solve(self.h, _ptr(u), _ptr(f), _dtype_code(u), _stream(stream)),
                "mg_coarse_solve")
+        return u
+
+    @property
+    def direct_level(self) -> int:
+        """Level the FP32 cycles solve directly under coarse_direct=1 (-1: none)."""
+        return int(self.lib.mg_direct_level(self.h))
+
+    def direct_solve(self, u, f, stream=None):
+        """FP32 direct solve of the direct level's interior system (in place)."""
+        _check(self.lib.mg_direct_solve(self.h, _ptr(u), _ptr(f), _stream(stream)), "mg_direct_solve")
         return u
 
     # ---- cycles and solves

@@ -90,4 +90,4 @@ def test_struct_layouts_match_the_header(tmp_path):
 def test_default_params():
     from paper_2110_08389_gb300 import mg
     p = mg.default_params()
-    assert (p.smoother, p.nu1, p.nu2, p.inner_cycles, p.early_stop, p.reserved) == (mg.TWEED, 2, 2, 3, 0, 0)
+    assert (p.smoother, p.nu1, p.nu2, p.inner_cycles, p.early_stop, p.coarse_direct) == (mg.TWEED, 2, 2, 3, 0, 0)

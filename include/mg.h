@@ -244,8 +244,9 @@ void mg_batch_destroy(mg_batch *batch);
  * mg_solve) for every i, with params[0] for all (nparams = 1) or params[i]
  * for problem i (nparams = count; e.g. tweed for wall-clustered and
  * wireframe for centre-clustered grids, Sec. 6).  Problems whose grids have
- * the same shape and whose parameters are equal (MG_PREC_F32_REFINE, every
- * line pass on the warp path of mg_set_line_path) form packed groups: each
+ * the same shape and whose parameters are equal (MG_PREC_F32_REFINE,
+ * coarse_direct 0, every line pass on the warp path of mg_set_line_path)
+ * form packed groups: each
  * kernel of their solve is one launch for the whole group, and the FP32
  * cycles of a refinement step are one CUDA graph per group (captured on the
  * first call and reused while the grids' line paths stay).  Groups and the

@@ -170,6 +170,12 @@ def kernel_launches() -> int:
 
 
 def default_params(**kw) -> Params:
+    """mg_default_params() with fields overridden by keyword: smoother (name or
+    code), nu1, nu2, cycle ("V"/"W"), restriction ("hw"/"fw"), precision
+    ("f64"/"f32_refine"), max_cycles, max_outer, inner_cycles,
+    use_initial_guess, early_stop (give up once the last step's rate cannot
+    reach tol within the caps), coarse_direct (FP32 cycles solve the direct
+    level exactly), tol."""
     p = Params()
     load().mg_default_params(ctypes.byref(p))
     for k, v in kw.items():
@@ -349,6 +355,11 @@ class Grid:
                            hist[: info.history_len].copy())
 
     def solve(self, u, f, params: Params | None = None, stream=None, history_cap=256, raise_on_fail=False, **kw):
+        """mg_solve: u (float64 CUDA tensor, boundary values set; the solution on
+        return), f (float64); params or default_params(**kw).  Returns a
+        Result with the status, cycles, residual history and convergence
+        factor; raises MGError on a status other than OK / NOT_CONVERGED /
+        NONFINITE (and on those too with raise_on_fail)."""
         return self._solve(self.lib.mg_solve, "mg_solve", u, f, params, stream, history_cap, kw, raise_on_fail)
 
     def solve_adjoint(self, lam, rhs, params: Params | None = None, stream=None, history_cap=256,

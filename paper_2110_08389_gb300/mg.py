@@ -357,7 +357,7 @@ class Grid:
     def solve(self, u, f, params: Params | None = None, stream=None, history_cap=256, raise_on_fail=False, **kw):
         """mg_solve: u (float64 CUDA tensor, boundary values set; the solution on
         return), f (float64); params or default_params(**kw).  Returns a
-        Result with the status, cycles, residual history and convergence
+        SolveResult with the status, cycles, residual history and convergence
         factor; raises MGError on a status other than OK / NOT_CONVERGED /
         NONFINITE (and on those too with raise_on_fail)."""
         return self._solve(self.lib.mg_solve, "mg_solve", u, f, params, stream, history_cap, kw, raise_on_fail)

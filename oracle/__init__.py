@@ -340,7 +340,7 @@ def quadratic_loss_gradient(P: Problem, f, g, u_target):
     return loss, u.reshape(ny1, nx1), grad_f.reshape(ny1, nx1), grad_g.reshape(ny1, nx1)
 
 
-SMOOTHERS3 = {"tweed": 0, "wireframe": 1, "alt_tw": 2}
+SMOOTHERS3 = {"tweed": 0, "wireframe": 1, "complementary": 2, "alt_tw": 3, "triplet": 4}
 
 
 class Problem3:

@@ -1,5 +1,5 @@
 /*
- * mg_oracle3d.c -- plain, slow, FP64 CPU oracle for 3D tweed multigrid
+ * mg_oracle3d.c -- plain, slow, FP64 CPU oracle for 3D tweed / wireframe multigrid
  * (Bewley, Mashayek, Cavaglieri & Luchini, arXiv:2110.08389, Sec. 7).
  *
  * TEST INFRASTRUCTURE ONLY.  Nothing in the product library may link, load or
@@ -15,6 +15,9 @@
  *     the centre of a cube;
  *   - 3D wireframe blocks (Sec. 7): the faces of concentric cuboids, as
  *     concentric rings on each face and the cuboid's edge skeleton;
+ *   - 3D complementary wireframe blocks (Sec. 7): on the same cuboid faces,
+ *     orthogonal to the wireframe, the corner points alone and lines that
+ *     circle each cuboid's corners (six joined "+" shapes on a cube);
  *   - each block solved exactly (Sec. 3), here by Gaussian elimination on the
  *     block's tree (leaves first), which is the m-legged Thomas of
  *     Eq. (mLThomas) for a star, and by dense LU for blocks with loops (the
@@ -45,6 +48,12 @@
  *       line or point where the face degenerates), for d1 = d2 the cuboid's
  *       twelve edges with its eight corners.  Red when d1 + d2 is even, so the
  *       outermost skeleton is red, as the outermost ring is in 2D (Sec. 3).
+ *   Q7  a complementary wireframe block is a connected set of interior nodes
+ *       with equal (d1, d3), red when d1 + d3 is even, so the corner points
+ *       (d1 = d3 = 1) are red.  A step between neighbours changes exactly one
+ *       of d1, d2, d3 when every side is even, so the three motifs share no
+ *       wire and cover every wire.  The triplet step (Sec. 7) is one tweed,
+ *       one wireframe and one complementary relaxation, in that order.
  */
 #include <math.h>
 #include <stdio.h>
@@ -74,12 +83,14 @@ typedef struct {
   int *pool;
 } part3_t;
 
-enum { O3_TWEED = 0, O3_WIREFRAME = 1 };
+enum { O3_TWEED = 0, O3_WIREFRAME = 1, O3_COMPLEMENTARY = 2, O3_NMOTIF = 3 };
+/* o3_smooth also takes the sequences of Sec. 7: */
+enum { O3_ALT_TW = 3 /* tweed, then wireframe */, O3_TRIPLET = 4 /* tweed, wireframe, complementary */ };
 
 typedef struct {
   int nlev;
   lev3_t lev[O3_MAXLEV];
-  part3_t part[O3_MAXLEV][2];  /* [level][tweed, wireframe] */
+  part3_t part[O3_MAXLEV][O3_NMOTIF];  /* [level][tweed, wireframe, complementary] */
   int cn;
   double *clu;
   int *cpiv;
@@ -177,13 +188,15 @@ static double sumsq_interior(const lev3_t *L, const double *a) {
 
 /* --------------------------------------------------------- tweed blocks -- */
 
-/* block key of a node: (d2, d3) for tweed (Q2), (d1, d2) for wireframe (Q6) */
+/* block key of a node: (d2, d3) for tweed (Q2), (d1, d2) for wireframe (Q6),
+   (d1, d3) for complementary wireframe (Q7) */
 static void key3(const lev3_t *L, int sm, int i, int j, int k, int *k1, int *k2) {
   int a = imin3(i, L->nx - i), b = imin3(j, L->ny - j), c = imin3(k, L->nz - k), t;
   if (a > b) { t = a; a = b; b = t; }
   if (b > c) { t = b; b = c; c = t; }
   if (a > b) { t = a; a = b; b = t; }
   if (sm == O3_WIREFRAME) { *k1 = a; *k2 = b; }
+  else if (sm == O3_COMPLEMENTARY) { *k1 = a; *k2 = c; }
   else { *k1 = b; *k2 = c; }
 }
 
@@ -368,7 +381,7 @@ static int solve_block3(const lev3_t *L, const part3_t *T, int b, double *u, con
 }
 
 int o3_colour_pass(o3_problem *P, int lev, int sm, int colour, double *u, const double *f) {
-  if (sm != O3_TWEED && sm != O3_WIREFRAME) return -1;
+  if (sm < 0 || sm >= O3_NMOTIF) return -1;
   if (build_part(P, lev, sm)) return -1;
   const part3_t *T = &P->part[lev][sm];
   for (int b = 0; b < T->nblock; ++b)
@@ -376,10 +389,14 @@ int o3_colour_pass(o3_problem *P, int lev, int sm, int colour, double *u, const 
   return 0;
 }
 
-/* one relaxation: red pass, black pass; sm = 2 is the alternating scheme of
-   Sec. 3 applied in 3D, one tweed relaxation followed by one wireframe one */
+/* one relaxation: red pass, black pass; O3_ALT_TW is the alternating scheme
+   of Sec. 3 applied in 3D (a tweed relaxation, then a wireframe one) and
+   O3_TRIPLET the triplet of Sec. 7 (tweed, wireframe, complementary) */
 int o3_smooth(o3_problem *P, int lev, int sm, double *u, const double *f) {
-  if (sm == 2) return o3_smooth(P, lev, O3_TWEED, u, f) || o3_smooth(P, lev, O3_WIREFRAME, u, f);
+  if (sm == O3_ALT_TW) return o3_smooth(P, lev, O3_TWEED, u, f) || o3_smooth(P, lev, O3_WIREFRAME, u, f);
+  if (sm == O3_TRIPLET)
+    return o3_smooth(P, lev, O3_TWEED, u, f) || o3_smooth(P, lev, O3_WIREFRAME, u, f) ||
+           o3_smooth(P, lev, O3_COMPLEMENTARY, u, f);
   return o3_colour_pass(P, lev, sm, 0, u, f) || o3_colour_pass(P, lev, sm, 1, u, f);
 }
 
@@ -540,7 +557,7 @@ void o3_destroy(o3_problem *P) {
   for (int k = 0; k < O3_MAXLEV; ++k) {
     lev3_t *L = &P->lev[k];
     free(L->x); free(L->y); free(L->z); free(L->W); free(L->E); free(L->S); free(L->N); free(L->B); free(L->T);
-    for (int sm = 0; sm < 2; ++sm) { free(P->part[k][sm].blk); free(P->part[k][sm].owner); free(P->part[k][sm].pool); }
+    for (int sm = 0; sm < O3_NMOTIF; ++sm) { free(P->part[k][sm].blk); free(P->part[k][sm].owner); free(P->part[k][sm].pool); }
     for (int s = 0; s < 3; ++s) free(P->work[k][s]);
   }
   free(P->clu); free(P->cpiv);
@@ -561,7 +578,7 @@ void o3_level_coeffs(o3_problem *P, int lev, double *W, double *E, double *S, do
 /* block owner of every node (-1 off the interior) and the colour of every
    block; returns the number of blocks */
 int o3_partition(o3_problem *P, int lev, int sm, int *owner, int *colour, int max_blocks) {
-  if (sm != O3_TWEED && sm != O3_WIREFRAME) return -1;
+  if (sm < 0 || sm >= O3_NMOTIF) return -1;
   if (build_part(P, lev, sm)) return -1;
   const part3_t *T = &P->part[lev][sm];
   memcpy(owner, T->owner, sizeof(int) * nn3(&P->lev[lev]));
@@ -570,7 +587,7 @@ int o3_partition(o3_problem *P, int lev, int sm, int *owner, int *colour, int ma
 }
 
 int o3_block_solve(o3_problem *P, int lev, int sm, int b, double *u, const double *f) {
-  if (sm != O3_TWEED && sm != O3_WIREFRAME) return -1;
+  if (sm < 0 || sm >= O3_NMOTIF) return -1;
   if (build_part(P, lev, sm)) return -1;
   if (b < 0 || b >= P->part[lev][sm].nblock) return -1;
   return solve_block3(&P->lev[lev], &P->part[lev][sm], b, u, f);

@@ -90,7 +90,7 @@ def test_cube_centre_block_has_six_legs(n):
     assert (owner == b).sum() == 6 * (c - 1) + 1
 
 
-@pytest.mark.parametrize("smoother", ["tweed", "wireframe"])
+@pytest.mark.parametrize("smoother", ["tweed", "wireframe", "complementary"])
 @pytest.mark.parametrize("dims", [(8, 6, 10), (7, 6, 5)])
 def test_block_solve_equals_dense_solve(dims, smoother):
     """Every block solve (tree elimination; dense for loops) equals numpy's
@@ -126,7 +126,7 @@ def test_block_solve_equals_dense_solve(dims, smoother):
         assert np.array_equal(u[mask], u0[mask])
 
 
-@pytest.mark.parametrize("smoother", ["tweed", "wireframe"])
+@pytest.mark.parametrize("smoother", ["tweed", "wireframe", "complementary"])
 def test_colour_pass_zeroes_the_relaxed_rows(smoother):
     P = oracle.Problem3(*grid3(12, 10, 8, "wall", 200.0))
     rng = np.random.default_rng(4)
@@ -382,3 +382,64 @@ def test_alternating_is_tweed_then_wireframe_and_converges_on_both_clusterings()
         u = np.zeros(P.shape())
         h = P.solve(u, f=rng.standard_normal(P.shape()), nu1=2, nu2=2, tol=1e-10, max_cycles=40, smoother="alt_tw")
         assert h[-1] <= 1e-10 and (h[-1] / h[0]) ** (1.0 / (len(h) - 1)) < 0.6, (kind, len(h))
+
+
+@pytest.mark.parametrize("dims", [(10, 10, 10), (12, 8, 6), (16, 12, 10)])
+def test_three_motifs_cover_every_wire_once(dims):
+    """Sec. 7: tweed, wireframe and complementary wireframe together hold every
+    wire of the grid between interior nodes, each in exactly one motif."""
+    P = oracle.Problem3(*grid3(*dims))
+    owners = [P.partition(smoother=sm)[0] for sm in ("tweed", "wireframe", "complementary")]
+    for k, j, i in interior_nodes(owners[0].shape):
+        for di, dj, dk in DIRS[1::2]:
+            kk, jj, ii = k + dk, j + dj, i + di
+            if owners[0][kk, jj, ii] < 0:
+                continue
+            held = [int(o[k, j, i] == o[kk, jj, ii]) for o in owners]
+            assert sum(held) == 1, ((k, j, i), (kk, jj, ii), held)
+
+
+@pytest.mark.parametrize("n", [10, 12])
+def test_complementary_cube_blocks(n):
+    """Sec. 7, complementary wireframe on a cube: the 8 corner points are point
+    relaxations (red), and on every concentric cuboid the lines join into one
+    block of six "+" shapes centred on the faces (six nodes with four in-block
+    neighbours, at the face centres); every other block is a point or a ring."""
+    P = oracle.Problem3(*grid3(n, n, n))
+    owner, colour = P.partition(smoother="complementary")
+    sizes, edges, deg = block_graph(owner)
+    for i in (1, n - 1):
+        for j in (1, n - 1):
+            for k in (1, n - 1):
+                b = owner[k, j, i]
+                assert sizes[b] == 1 and colour[b] == 0
+    c = n // 2
+    plus = 0
+    for b in range(len(colour)):
+        d = deg[owner == b]
+        if (d == 4).any():
+            plus += 1
+            centres = sorted(tuple(p) for p in np.argwhere((owner == b) & (deg == 4)))
+            t = min(centres[0])
+            expect = sorted([(c, c, t), (c, c, n - t), (c, t, c), (c, n - t, c), (t, c, c), (n - t, c, c)])
+            assert centres == expect, (b, centres)
+            assert (d[d != 4] == 2).all() and edges[b] == sizes[b] + 6
+        else:
+            assert sizes[b] == 1 or (edges[b] == sizes[b] and (d == 2).all()), b
+    assert plus == sum(1 for t in range(1, c) if n - 2 * t >= 2)
+
+
+def test_triplet_beats_single_motifs_on_mixed_clustering():
+    """Sec. 7: for stretching in several directions the paper proposes
+    triplets of sweeps (tweed, wireframe, complementary).  On a grid clustered
+    toward the walls in x and toward the centre in y the triplet's V(1,1)
+    cycles converge faster than those of any one motif or of the tweed /
+    wireframe pair."""
+    n = 32
+    P = oracle.Problem3(I.coords(n, "wall", ratio=100.0), I.coords(n, "centre", ratio=10.0), I.uniform_coords(n))
+    f = np.random.default_rng(9).standard_normal(P.shape())
+    rate = {}
+    for sm in ("tweed", "wireframe", "complementary", "alt_tw", "triplet"):
+        h = P.solve(np.zeros(P.shape()), f, nu1=1, nu2=1, tol=1e-10, max_cycles=12, smoother=sm)
+        rate[sm] = (h[-1] / h[0]) ** (1.0 / (len(h) - 1))
+    assert rate["triplet"] < 0.9 * min(v for k, v in rate.items() if k != "triplet"), rate

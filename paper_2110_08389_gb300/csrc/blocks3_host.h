@@ -77,7 +77,9 @@ inline bool blocks3(const Level3 &L, int sm, std::vector<HBlock3> &out) {
           if (r1 != r2) par[r1] = r2;
         }
       }
-  std::vector<int> id(nn, -1);
+  // block of every node (-1 off the interior): an interior node's six
+  // neighbours are all inside the array, so in-block tests need no bounds
+  std::vector<int> id(nn, -1), own(nn, -1);
   std::vector<std::vector<long long>> members;
   for (int k = 1; k < nz; ++k)
     for (int j = 1; j < ny; ++j)
@@ -85,10 +87,12 @@ inline bool blocks3(const Level3 &L, int sm, std::vector<HBlock3> &out) {
         const size_t p = (size_t)k * plane + (size_t)j * nx1 + i;
         const int r = fnd((int)p);
         if (id[r] < 0) { id[r] = (int)members.size(); members.emplace_back(); }
+        own[p] = id[r];
         members[id[r]].push_back((long long)p);
       }
-  auto owner = [&](long long p) { return id[fnd((int)p)]; };
-  std::vector<long long> nb;
+  std::vector<int>().swap(par);
+  std::vector<int>().swap(id);
+  std::vector<long long> nb, wv;
   for (size_t b = 0; b < members.size(); ++b) {
     const auto &mb = members[b];
     HBlock3 hb;
@@ -100,10 +104,8 @@ inline bool blocks3(const Level3 &L, int sm, std::vector<HBlock3> &out) {
     // in-block neighbours
     auto nbrs = [&](long long p, std::vector<long long> &v) {
       v.clear();
-      int a, c, e;
-      ijk((size_t)p, a, c, e);
       for (int d = 0; d < 6; ++d)
-        if (inside(a + di[d], c + dj[d], e + dk[d]) && owner(p + step[d]) == (int)b) v.push_back(p + step[d]);
+        if (own[p + step[d]] == (int)b) v.push_back(p + step[d]);
     };
     std::vector<long long> branch;
     int edges2 = 0, maxdeg = 0;
@@ -120,7 +122,7 @@ inline bool blocks3(const Level3 &L, int sm, std::vector<HBlock3> &out) {
     // three or more in-block neighbours (kept as the chain's last entry) or
     // the node `stop` (not kept); returns the node it stopped on
     auto walk = [&](long long prev, long long cur, long long stop, std::vector<long long> &chain) {
-      std::vector<long long> v;
+      std::vector<long long> &v = wv;
       while (true) {
         chain.push_back(cur);
         nbrs(cur, v);

@@ -31,6 +31,7 @@
 #include <new>
 #include <functional>
 #include <numeric>
+#include <thread>
 #include <vector>
 
 #include "blocks3_host.h"
@@ -465,17 +466,22 @@ mg_status setup3(Grid &g, const int64_t *n, const double *const *coords) {
     }
     // tweed and wireframe blocks of the smoothed levels
     if (l + 1 < g.nlev) {
-      std::vector<HBlock3> blocks;
-      if (!blocks3(L, SM3_TWEED, blocks)) {
+      // the two builds are independent host work: the wireframe one runs on
+      // a second thread
+      std::vector<HBlock3> blocks, wblocks;
+      bool wf_ok = false;
+      std::thread wf([&] { wf_ok = blocks3(L, SM3_WIREFRAME, wblocks); });
+      const bool tw_ok = blocks3(L, SM3_TWEED, blocks);
+      wf.join();
+      if (!tw_ok) {
         set_error_text("3D tweed: a side with an odd number of intervals on a smoothed level");
         return MG_ERR_UNSUPPORTED;
       }
       for (int c = 0; c < 2; ++c) TRY(warp_list3(L, blocks, c, false, L.wp[SM3_TWEED][c]));
-      blocks.clear();
-      L.wf_ok = blocks3(L, SM3_WIREFRAME, blocks);
+      L.wf_ok = wf_ok;
       if (L.wf_ok)
         for (int c = 0; c < 2; ++c) {
-          TRY(warp_list3(L, blocks, c, true, L.wp[SM3_WIREFRAME][c]));
+          TRY(warp_list3(L, wblocks, c, true, L.wp[SM3_WIREFRAME][c]));
           G.skel_len = std::max(G.skel_len, (size_t)L.wp[SM3_WIREFRAME][c].skel_nodes);
         }
     }

@@ -34,7 +34,7 @@
 #include <thread>
 #include <vector>
 
-#include "blocks3_host.h"
+#include "pack3_host.h"
 #include "seq3.cuh"
 
 namespace tmg {
@@ -224,135 +224,16 @@ __global__ void __launch_bounds__(T3) interior3_kernel(int nx, int ny, double *_
 dim3 interior_grid(const Level3 &L) { return dim3((L.nx - 1 + T3 - 1) / T3, L.ny - 1, L.nz - 1); }
 
 // ------------------------------------------------------------ host setup --
-// Sequences of one colour (first fit, largest blocks first), K and W as in
-// 2D (warp_line.cu) with at most 8 nodes per thread (both precisions use the
-// same lists), and the colour's edge skeletons.  multi: up to WJ3_MAX
-// junctions per sequence (wireframe rings), listed per sequence through
-// jofs; otherwise at most one, the sequence's own junction record.
+// The warp lists of one colour on the device (pack3_host.h lays them out).
 mg_status warp_list3(const Level3 &L, const std::vector<HBlock3> &all, int colour, bool multi, WarpList3 &Wl) {
-  const int jmax = multi ? WJ3_MAX : 1;
-  std::vector<int> idx, sk;
-  int maxn = 1, total = 0, skn = 0;
-  for (size_t b = 0; b < all.size(); ++b) {
-    if (all[b].colour != colour) continue;
-    if (all[b].skel) {
-      sk.push_back((int)b);
-      for (const auto &e : all[b].edges) skn += (int)e.nodes.size();
-      continue;
-    }
-    idx.push_back((int)b);
-    maxn = std::max(maxn, all[b].nodes);
-    total += all[b].nodes + (all[b].junc >= 0 ? 1 : 0);
-  }
-  if (idx.empty() && sk.empty()) return MG_OK;
-  if (maxn > 32 * WARP3_WMAX * WARP3_KMAX) return MG_ERR_SIZE;
-  int K = 1, NW = 1;
-  while (32 * K < maxn && K < WARP3_KPREF) K *= 2;
-  while (32 * NW * K < maxn) NW *= 2;
-  while (NW > WARP3_WMAX) {
-    K *= 2;
-    NW = 1;
-    while (32 * NW * K < maxn) NW *= 2;
-  }
-  const int cap = 32 * NW * K;
-  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return all[a].nodes > all[b].nodes; });
-  struct Bin { int used = 0, nj = 0; std::vector<int> blocks; };
-  std::vector<Bin> bins;
-  // first fit: a max-tree over the free slots of every possible bin finds
-  // the leftmost bin with room (log time per block)
-  int P2 = 1;
-  while (P2 < (int)idx.size()) P2 *= 2;
-  std::vector<int> fr(2 * (size_t)P2, cap);
-  auto first_fit = [&](int lo, int n) {  // leftmost bin >= lo with >= n free slots, or -1
-    std::function<int(int, int, int)> go = [&](int v, int l, int r) -> int {
-      if (r <= lo || fr[v] < n) return -1;
-      if (r - l == 1) return l;
-      const int m = (l + r) / 2, a = go(2 * v, l, m);
-      return a >= 0 ? a : go(2 * v + 1, m, r);
-    };
-    return go(1, 0, P2);
-  };
-  for (int b : idx) {
-    const int nj = all[b].junc >= 0 ? 1 : 0, n = all[b].nodes;
-    int w = first_fit(0, n);
-    while (w >= 0 && w < (int)bins.size() && bins[w].nj + nj > jmax) w = first_fit(w + 1, n);
-    if (w < 0) return MG_ERR_SIZE;  // cannot happen: every block fits an empty bin
-    while ((int)bins.size() <= w) bins.emplace_back();
-    bins[w].used += n;
-    bins[w].nj += nj;
-    bins[w].blocks.push_back(b);
-    int v = P2 + w;
-    fr[v] = cap - bins[w].used;
-    for (v >>= 1; v >= 1; v >>= 1) fr[v] = std::max(fr[2 * v], fr[2 * v + 1]);
-  }
-  const int nx1 = L.nx + 1;
-  const size_t plane = (size_t)nx1 * (L.ny + 1);
-  std::vector<WNode3> nodes(bins.size() * (size_t)cap);
-  std::vector<WJunc3> jn;
-  std::vector<int> jofs(bins.size() + 1, 0);
-  std::vector<WSkel3> skel(sk.size());
-  std::memset(nodes.data(), 0, sizeof(WNode3) * nodes.size());
-  std::memset(skel.data(), 0, sizeof(WSkel3) * skel.size());
-  auto pack = [&](long long p) {
-    const uint32_t i = (uint32_t)(p % nx1), j = (uint32_t)((p / nx1) % (L.ny + 1)), k = (uint32_t)(p / plane);
-    return i | (j << 10) | (k << 20);
-  };
-  for (size_t w = 0; w < bins.size(); ++w) {
-    jofs[w] = (int)jn.size();
-    if (!multi) {  // one record per sequence, natt = 0 without a junction
-      jn.emplace_back();
-      std::memset(&jn.back(), 0, sizeof(WJunc3));
-    }
-    int s = 0;
-    for (int b : bins[w].blocks) {
-      const HBlock3 &hb = all[b];
-      const uint32_t jl = multi ? (uint32_t)(jn.size() - jofs[w]) : 0u;
-      WJunc3 *jb = nullptr;
-      if (hb.junc >= 0) {
-        if (multi) {
-          jn.emplace_back();
-          std::memset(&jn.back(), 0, sizeof(WJunc3));
-        }
-        jb = &jn.back();
-        jb->ijk = pack(hb.junc);
-      }
-      for (size_t c = 0; c < hb.chains.size(); ++c) {
-        const auto &ch = hb.chains[c];
-        const int m = (int)ch.size();
-        for (int r = 0; r < m; ++r) {
-          uint32_t fl = WN3_VALID | (jb ? jl << WN3_JSHIFT : 0u);
-          if (r > 0) fl |= WN3_PRED | (uint32_t)dir_between(nx1, plane, ch[r], ch[r - 1]);
-          if (r < m - 1) fl |= WN3_SUCC | ((uint32_t)dir_between(nx1, plane, ch[r], ch[r + 1]) << 4);
-          const int dj = r == m - 1 && hb.jlast[c] >= 0 ? hb.jlast[c] : (r == 0 ? hb.jfirst[c] : -1);
-          if (jb && dj >= 0) {
-            fl |= WN3_JUNC | ((uint32_t)dj << 8);
-            jb->as[jb->natt] = (uint16_t)s;
-            jb->adirs |= (uint32_t)(dj ^ 1) << (3 * jb->natt);
-            ++jb->natt;
-          }
-          WNode3 &nd = nodes[w * (size_t)cap + s];
-          nd.ijk = pack(ch[r]);
-          nd.fl = fl;
-          ++s;
-        }
-      }
-    }
-  }
-  jofs[bins.size()] = (int)jn.size();
-  int off = 0;
-  for (size_t q = 0; q < sk.size(); ++q) {
-    const HBlock3 &hb = all[sk[q]];
-    WSkel3 &S = skel[q];
-    for (int c = 0; c < 8; ++c) S.cijk[c] = pack(hb.corner[c]);
-    for (int e = 0; e < 12; ++e) {
-      S.eoff[e] = (uint32_t)off;
-      S.ea[e] = (uint8_t)hb.edges[e].a;
-      S.eb[e] = (uint8_t)hb.edges[e].b;
-      S.ed[e] = (uint8_t)hb.edges[e].dir;
-      off += (int)hb.edges[e].nodes.size();
-    }
-    S.eoff[12] = (uint32_t)off;
-  }
+  Pack3 pk;
+  const mg_status st = pack3(L, all, colour, multi, pk);
+  if (st != MG_OK) return st;
+  if (pk.nwarp == 0 && pk.skel.empty()) return MG_OK;
+  const std::vector<WNode3> &nodes = pk.nodes;
+  const std::vector<WJunc3> &jn = pk.jn;
+  const std::vector<int> &jofs = pk.jofs;
+  const std::vector<WSkel3> &skel = pk.skel;
   auto al = [](size_t v) { return (v + 15) & ~size_t(15); };
   const size_t b_nodes = al(sizeof(WNode3) * nodes.size()), b_jn = al(sizeof(WJunc3) * jn.size()),
                b_jofs = al(sizeof(int) * jofs.size()), b_sk = al(sizeof(WSkel3) * skel.size());
@@ -369,12 +250,12 @@ mg_status warp_list3(const Level3 &L, const std::vector<HBlock3> &all, int colou
   if (e == cudaSuccess) e = cudaMemcpy(Wl.jofs, jofs.data(), sizeof(int) * jofs.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !skel.empty()) e = cudaMemcpy(Wl.skel, skel.data(), sizeof(WSkel3) * skel.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { set_error("cudaMemcpy(3D warp list)", e); return MG_ERR_CUDA; }
-  Wl.nwarp = (int)bins.size();
-  Wl.K = K;
-  Wl.W = NW;
-  Wl.total_nodes = total;
-  Wl.nskel = (int)sk.size();
-  Wl.skel_nodes = skn;
+  Wl.nwarp = pk.nwarp;
+  Wl.K = pk.K;
+  Wl.W = pk.W;
+  Wl.total_nodes = pk.total_nodes;
+  Wl.nskel = (int)skel.size();
+  Wl.skel_nodes = pk.skel_nodes;
   Wl.multi = multi;
   return MG_OK;
 }

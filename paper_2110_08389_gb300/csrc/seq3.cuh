@@ -44,7 +44,6 @@ __device__ __forceinline__ T cdir(const C6<T> &c, unsigned d, int i, int j, int 
   }
 }
 
-constexpr int WARP3_KMAX = 8, WARP3_WMAX = 8, WARP3_KPREF = 4;
 
 // Skeleton CTAs of a launch: edge scratch rows (a, b, c, r, zA, zB), each
 // `stride` values long.

@@ -25,6 +25,7 @@
 
 #include "mg_internal.h"
 #include "blocks.h"
+#include "pack2_host.h"
 
 namespace tmg {
 
@@ -190,88 +191,10 @@ mg_status upload(const Packed &P, int nt, WorkList &W) {
 // place).  Leaves W.nwarp = 0 when the largest block does not fit WW_MAX
 // warps of kmax nodes per lane.
 mg_status build_warplist(const std::vector<HBlock> &blocks, int kmax, int kpref, WarpList &W) {
-  std::vector<int> n(blocks.size(), 0);
-  int maxn = 1, total = 0;
-  for (size_t b = 0; b < blocks.size(); ++b) {
-    for (const HChain &c : blocks[b].ch)
-      for (const HSeg &sg : c.s) n[b] += sg.len;
-    maxn = std::max(maxn, n[b]);
-    total += n[b] + (blocks[b].junc ? 1 : 0);
-  }
-  if (blocks.empty() || maxn > 32 * WW_MAX * kmax) return MG_OK;
-  int K = 1, NW = 1;
-  while (32 * K < maxn && K < std::min(kpref, kmax)) K *= 2;
-  while (32 * NW * K < maxn) NW *= 2;
-  while (NW > WW_MAX) {
-    K *= 2;
-    NW = 1;
-    while (32 * NW * K < maxn) NW *= 2;
-  }
-  const int cap = 32 * NW * K;
-  std::vector<int> order(blocks.size());
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
-  struct Bin {
-    int used = 0;
-    bool junc = false;
-    std::vector<int> blocks;
-  };
-  std::vector<Bin> bins;
-  for (int b : order) {
-    size_t w = 0;
-    while (w < bins.size() && (bins[w].used + n[b] > cap || (blocks[b].junc && bins[w].junc))) ++w;
-    if (w == bins.size()) bins.emplace_back();
-    bins[w].used += n[b];
-    bins[w].junc |= blocks[b].junc;
-    bins[w].blocks.push_back(b);
-  }
-  std::vector<WNode> nodes(bins.size() * (size_t)cap);
-  std::vector<WBlock> blk(bins.size());
-  std::memset(nodes.data(), 0, sizeof(WNode) * nodes.size());
-  std::memset(blk.data(), 0, sizeof(WBlock) * blk.size());
-  for (size_t w = 0; w < bins.size(); ++w) {
-    WBlock &jb = blk[w];
-    int s = 0;
-    for (int b : bins[w].blocks) {
-      const HBlock &hb = blocks[b];
-      if (hb.junc) {
-        jb.has_j = 1;
-        jb.ji = (uint16_t)hb.ji;
-        jb.jj = (uint16_t)hb.jj;
-      }
-      for (const HChain &c : hb.ch) {
-        // the chain's nodes in order, with the direction of the step that
-        // reaches each node (its segment's direction)
-        std::vector<std::tuple<int, int, int>> cn;
-        for (const HSeg &sg : c.s)
-          for (int t = 0; t < sg.len; ++t) cn.emplace_back(sg.i0 + t * step_i(sg.dir), sg.j0 + t * step_j(sg.dir), sg.dir);
-        const int m = (int)cn.size();
-        for (int r = 0; r < m; ++r) {
-          uint32_t fl = WN_VALID;
-          if (r > 0) fl |= WN_PRED | (uint32_t)(std::get<2>(cn[r]) ^ 1);
-          if (r < m - 1) fl |= WN_SUCC | ((uint32_t)std::get<2>(cn[r + 1]) << 3);
-          int jd = -1;
-          if (r == 0 && c.fj) jd = std::get<2>(cn[0]) ^ 1;
-          if (r == m - 1 && c.lj) {
-            if (jd >= 0) return MG_OK;  // a one-node chain on both sides of the junction: not supported here
-            jd = c.ljdir;
-          }
-          if (jd >= 0) {
-            if (!hb.junc || jb.natt >= 4) return MG_OK;
-            fl |= WN_JUNC | ((uint32_t)jd << 6);
-            jb.as[jb.natt] = (uint16_t)s;
-            jb.adirs |= (uint8_t)((jd ^ 1) << (2 * jb.natt));
-            ++jb.natt;
-          }
-          WNode &nd = nodes[w * (size_t)cap + s];
-          nd.i = (uint16_t)std::get<0>(cn[r]);
-          nd.j = (uint16_t)std::get<1>(cn[r]);
-          nd.fl = fl;
-          ++s;
-        }
-      }
-    }
-  }
+  Pack2 pk;
+  if (!pack2(blocks, kmax, kpref, pk)) return MG_OK;
+  const std::vector<WNode> &nodes = pk.nodes;
+  const std::vector<WBlock> &blk = pk.blk;
   const size_t bn = (sizeof(WNode) * nodes.size() + 15) & ~size_t(15);
   char *mem = nullptr;
   cudaError_t e = cudaMalloc(&mem, bn + sizeof(WBlock) * blk.size());
@@ -282,10 +205,10 @@ mg_status build_warplist(const std::vector<HBlock> &blocks, int kmax, int kpref,
   e = cudaMemcpy(W.node, nodes.data(), sizeof(WNode) * nodes.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(W.blk, blk.data(), sizeof(WBlock) * blk.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { set_error("cudaMemcpy(warp list)", e); return MG_ERR_CUDA; }
-  W.nwarp = (int)bins.size();
-  W.K = K;
-  W.W = NW;
-  W.total_nodes = total;
+  W.nwarp = pk.nwarp;
+  W.K = pk.K;
+  W.W = pk.W;
+  W.total_nodes = pk.total_nodes;
   return MG_OK;
 }
 

@@ -33,11 +33,11 @@ TOL = 1e-10
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "tweed_pass_f32_4097_traffic.json")
 # sources whose change invalidates the stored ncu traffic of the tiled pass:
-# the tiled kernels, their setup, the launch helpers, and the tiled-path part
+# the tiled kernels, their setup and layout, the launch helpers, and the tiled-path part
 # of the internal header (from its "Tiled line path" comment to the Level
 # struct); the rest of that header (other paths' structs, declarations) does
 # not enter the tiled kernels
-TRAFFIC_SOURCES = ["tiles.cu", "tile_setup.cu", "device_util.cuh", "mg_internal.h#tiled"]
+TRAFFIC_SOURCES = ["tiles.cu", "tile_setup.cu", "tile_host.h", "device_util.cuh", "mg_internal.h#tiled"]
 
 
 def traffic_key():

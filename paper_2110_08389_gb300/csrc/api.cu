@@ -505,11 +505,10 @@ void consume_value(SolveState &q, double v) {
   if (limit || q.rel > 1e3 * q.rel0) { q.st = MG_ERR_NOT_CONVERGED; return finish(q); }
   // early stop: at the last step's rate the steps left under the caps fall short
   const int steps = f64 ? q.cycles : q.outer;
-  if (p.early_stop && q.phase == 2 && steps >= 3 && q.prev > 0.0) {
-    const double rate = q.rel / q.prev;
+  if (p.early_stop && q.phase == 2) {
     const int left = f64 ? p.max_cycles - q.cycles
                          : std::min(p.max_outer - q.outer, (p.max_cycles - q.cycles) / p.inner_cycles);
-    if (rate >= 1.0 || q.rel * std::pow(rate, (double)left) > p.tol) { q.st = MG_ERR_NOT_CONVERGED; return finish(q); }
+    if (hopeless(steps, q.rel, q.prev, left, p.tol)) { q.st = MG_ERR_NOT_CONVERGED; return finish(q); }
   }
 }
 

@@ -1,6 +1,8 @@
 // solve.h -- the solve state machine shared by mg_solve (api.cu) and
 // mg_batch_solve (batch.cu).
 #pragma once
+#include <cmath>
+
 #include "mg_internal.h"
 
 namespace tmg {
@@ -24,6 +26,16 @@ struct SolveState {
   double fn = 0.0, rel = 0.0, rel0 = 0.0, prev = 0.0;  // prev: rel before the last step
   int cycles = 0, outer = 0;
 };
+
+// The early stop (mg_params.early_stop): from the third step on, true when
+// the last step did not reduce the relative residual (rel / prev >= 1) or
+// when, kept at that rate for the `left` steps the caps allow, it would stay
+// above tol.
+inline bool hopeless(int steps, double rel, double prev, int left, double tol) {
+  if (steps < 3 || !(prev > 0.0)) return false;
+  const double rate = rel / prev;
+  return rate >= 1.0 || rel * std::pow(rate, (double)left) > tol;
+}
 
 mg_status check_params(const Grid *g, const mg_params *p);
 mg_status enqueue(SolveState &q);

@@ -87,7 +87,10 @@ typedef struct {
   int cycle;             /* mg_cycle: 1 = V, 2 = W                               */
   int restriction;       /* mg_restriction (prolongation is always bilinear)     */
   int precision;         /* mg_precision                                         */
-  int max_cycles;        /* cap on cycles (FP64) or on inner cycles (FP32+refine)*/
+  int max_cycles;        /* cap on cycles (FP64) or on inner cycles (FP32+refine:*/
+                         /* checked after each refinement step, which runs all  */
+                         /* inner_cycles, so the count can end up to            */
+                         /* inner_cycles - 1 past the cap)                       */
   int max_outer;         /* cap on refinement iterations (FP32+refine)           */
   int inner_cycles;      /* FP32 cycles per refinement iteration (default 3)     */
   int use_initial_guess; /* 0: interior of u is zeroed first; 1: u is the guess  */
@@ -291,12 +294,16 @@ const char *mg_last_error(void);
  * (nx+1 each) and S, N (ny+1 each), u and f of shape (ny+1) x (nx+1), FP64.
  * Its scratch is a static device array of 4 x 16384 doubles (one partial per
  * interior row), so ny - 1 may not exceed 16384: larger grids return
- * MG_ERR_SIZE with a message in mg_last_error().  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  All calls on a device share the
- * array: calls whose kernels overlap on the GPU (different streams without
- * ordering) race and give wrong results.  No entry needs clearing: each call
- * writes every partial it reads.  Enqueued on `stream`; no synchronisation.   */
+ * MG_ERR_SIZE with a message in mg_last_error().  Every call made outside a
+ * stream capture looks up the array's device address (cudaGetSymbolAddress)
+ * for the current device; a call made while `stream` is being captured uses
+ * the address found by an earlier uncaptured call on that device, so make a
+ * first call before any stream capture (and again after a cudaDeviceReset);
+ * without one a captured call returns MG_ERR_INVALID_ARG.  All calls on a
+ * device share the array: calls whose kernels overlap on the GPU (different
+ * streams without ordering) race and give wrong results.  No entry needs
+ * clearing: each call writes every partial it reads.  The maxima propagate
+ * NaN, like the sums.  Enqueued on `stream`; no synchronisation.             */
 mg_status mg_residual_norm_static(int64_t nx, int64_t ny, const double *W, const double *E,
                                   const double *S, const double *N, const double *u, const double *f,
                                   double *out, void *stream);

@@ -506,8 +506,7 @@ void consume_value(SolveState &q, double v) {
   // early stop: at the last step's rate the steps left under the caps fall short
   const int steps = f64 ? q.cycles : q.outer;
   if (p.early_stop && q.phase == 2) {
-    const int left = f64 ? p.max_cycles - q.cycles
-                         : std::min(p.max_outer - q.outer, (p.max_cycles - q.cycles) / p.inner_cycles);
+    const int left = steps_left(f64, p.max_cycles, p.max_outer, p.inner_cycles, q.cycles, q.outer);
     if (hopeless(steps, q.rel, q.prev, left, p.tol)) { q.st = MG_ERR_NOT_CONVERGED; return finish(q); }
   }
 }

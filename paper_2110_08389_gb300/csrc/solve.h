@@ -37,6 +37,20 @@ inline bool hopeless(int steps, double rel, double prev, int left, double tol) {
   return rate >= 1.0 || rel * std::pow(rate, (double)left) > tol;
 }
 
+// Steps the caps still allow after `cycles` cycles and `outer` refinement
+// steps.  FP64: one cycle per step, max_cycles - cycles.  FP32+refine: every
+// step runs all inner_cycles and the caps are checked after it, so a step
+// still starts while cycles < max_cycles (the last one may end past
+// max_cycles): ceil((max_cycles - cycles) / inner_cycles), and at most
+// max_outer - outer.
+inline int steps_left(bool f64, int max_cycles, int max_outer, int inner_cycles, int cycles, int outer) {
+  const int c = max_cycles - cycles;
+  if (f64) return c > 0 ? c : 0;
+  const int by_cycles = c > 0 ? (c + inner_cycles - 1) / inner_cycles : 0;
+  const int by_outer = max_outer - outer > 0 ? max_outer - outer : 0;
+  return by_cycles < by_outer ? by_cycles : by_outer;
+}
+
 mg_status check_params(const Grid *g, const mg_params *p);
 mg_status enqueue(SolveState &q);
 // the norm the step computed: its grid's pinned copy (consume) or any value

@@ -356,3 +356,66 @@ def test_stretching_maps():
     d = np.diff(x)
     assert d[31] < d[0] and np.allclose(x + x[::-1], 1.0)
     assert I.c_for_ratio(4096, 1000.0) == pytest.approx(4.147788, abs=1e-5)
+
+
+# ------------------------------------------------------------------ W-cycle
+# Sec. 4 names the W-cycle only among "other cycling strategies"; these pins
+# come from the mathematics of the cycle (gamma = 2 coarse visits per level).
+
+def test_w_cycle_equals_v_cycle_on_two_levels(oracle_mod):
+    """With two levels the coarse level is solved exactly, so the second
+    coarse visit sees a zero defect and changes nothing: one W-cycle equals
+    one V-cycle bit for bit.  Catches a second visit that adds its correction
+    again or starts from a stale coarse right-hand side."""
+    P = _prob(oracle_mod, 16, 12, "wall", 2.0)
+    assert P.nlev == 2
+    rng = np.random.default_rng(21)
+    g = rng.standard_normal(P.shape())
+    f = rng.standard_normal(P.shape())
+    for sm in ("checkerboard", "tweed", "alt_tw"):
+        uv, uw = g.copy(), g.copy()
+        for _ in range(3):
+            P.cycle(uv, f, sm, 1, 1, gamma=1)
+            P.cycle(uw, f, sm, 1, 1, gamma=2)
+        assert np.array_equal(uv, uw), sm
+
+
+@pytest.mark.parametrize("smoother", ["checkerboard", "tweed", "alt_zebra"])
+def test_w_cycle_converges_to_dense_lu(oracle_mod, smoother):
+    """On a three-level stretched grid the W(1,1) iteration converges to the
+    dense-LU solution of Eq. (prob:DP), boundary data included.  Catches a
+    W-cycle whose coarse visits leave a wrong fixed point (a dropped or
+    doubled correction, a transposed transfer)."""
+    P = _prob(oracle_mod, 32, 24, "wall", 2.0)
+    assert P.nlev == 3
+    rng = np.random.default_rng(22)
+    g = rng.standard_normal(P.shape())
+    f = rng.standard_normal(P.shape())
+    ref = P.direct_solve(g, f)
+    u, hist, _ = P.solve(g, f, smoother, 1, 1, gamma=2, tol=1e-13, max_cycles=200)
+    assert hist[-1] <= 1e-13
+    assert np.abs(u - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("smoother,rho", [("checkerboard", 0.0739), ("alt_zebra", 0.0391), ("tweed", 0.0621)])
+def test_w_cycle_factor_matches_two_grid_radius(oracle_mod, smoother, rho):
+    """A W-cycle solves each coarse problem almost exactly (two visits, each
+    reducing the coarse error by the cycle's own small factor), so on four
+    levels its asymptotic factor is the two-grid spectral radius of Sec. 5.
+    Table 1 (uniform grid, full weighting, nu = nu1 + nu2 = 2): checkerboard
+    .0739, alternating zebra .0391, tweed .0621 (R7: 64 intervals).  The
+    factor is the last-cycle residual ratio after 30 renormalised W(1,1)
+    cycles from a random error with f = 0.  A W-cycle that restarts its
+    second coarse visit from zero is a V-cycle, whose factor here is .115 for
+    checkerboard and .053 for alternating zebra, and fails this pin."""
+    P = _prob(oracle_mod, 64)
+    assert P.nlev == 4
+    u = I.random_field(65, 65, seed=23)
+    f = np.zeros_like(u)
+    ratio = None
+    for _ in range(30):
+        r0 = np.linalg.norm(P.residual(u, f)[1:-1, 1:-1])
+        u /= r0
+        P.cycle(u, f, smoother, 1, 1, gamma=2)
+        ratio = np.linalg.norm(P.residual(u, f)[1:-1, 1:-1])
+    assert abs(ratio / rho - 1.0) <= 0.03, (smoother, ratio, rho)

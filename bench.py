@@ -30,13 +30,18 @@ N_INTERVALS = 4096
 RATIO = 1000.0
 SEED = 1
 TOL = 1e-10
+# The timed solve of the 4097^2 workload (tests/test_gpu_fullsize.py runs exactly
+# this): tweed V(1,1), full weighting, FP32 cycles (3 per refinement step)
+# with the FP64 residual, update and coarsest solve of the refinement loop.
+HEADLINE = dict(smoother="tweed", nu1=1, nu2=1, precision="f32_refine", tol=TOL, inner_cycles=3, max_outer=20,
+                max_cycles=200, coarse_direct=0)
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "tweed_pass_f32_4097_traffic.json")
 # sources whose change invalidates the stored ncu traffic of the tiled pass:
 # the tiled kernels, their setup and layout, the launch helpers, and the tiled-path part
 # of the internal header (from its "Tiled line path" comment to the Level
-# struct); the rest of that header (other paths' structs, declarations) does
-# not enter the tiled kernels
+# struct, less the cluster pass's structs); the rest of that header (other
+# paths' structs, declarations) does not enter the tiled kernels
 TRAFFIC_SOURCES = ["tiles.cu", "tile_setup.cu", "tile_host.h", "device_util.cuh", "mg_internal.h#tiled"]
 
 
@@ -47,8 +52,11 @@ def traffic_key():
         fn, _, part = name.partition("#")
         text = open(os.path.join(ROOT, "paper_2110_08389_gb300", "csrc", fn), "rb").read()
         if part == "tiled":
+            # the tiled path's structs, without the cluster pass's (a separate kernel)
             a = text.index(b"// Tiled line path")
-            text = text[a:text.index(b"struct Level {", a)]
+            b = text.index(b"// Cluster pass", a)
+            c = text.index(b"// Shapes of the line-solve kernel", b)
+            text = text[a:b] + text[c:text.index(b"struct Level {", c)]
         h.update(text)
     return h.hexdigest()
 
@@ -59,13 +67,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--nu", type=int, nargs=2, default=[1, 1])
-    ap.add_argument("--inner", type=int, default=3,
+    ap.add_argument("--nu", type=int, nargs=2, default=[HEADLINE["nu1"], HEADLINE["nu2"]])
+    ap.add_argument("--inner", type=int, default=HEADLINE["inner_cycles"],
                     help="FP32 cycles per refinement step (each step gains at most ~1e-3 in FP32 on this grid)")
     ap.add_argument("--intervals", type=int, default=N_INTERVALS, help="intervals per side (4096: the 4097 x 4097 workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--coarse-direct", type=int, default=1, choices=[0, 1],
-                    help="FP32 cycles solve the finest level of at most 64x64 intervals directly (2D workload)")
+    ap.add_argument("--coarse-direct", type=int, default=HEADLINE["coarse_direct"], choices=[0, 1],
+                    help="1: the FP32 cycles solve the finest level of at most 64x64 intervals directly, in FP32 "
+                         "(default 0: every level down to the FP64 coarsest solve)")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "3d"],
                     help="single: the 4097^2 solve (default); batch: 256 mixed problems solved together; "
                          "3d: the 257^3 tweed solve")
@@ -495,9 +504,8 @@ def main():
     stream = torch.cuda.current_stream()
     f = torch.tensor(f_h, device=dev)
     u = torch.zeros((n1, n1), dtype=torch.float64, device=dev)
-    p32 = mg.default_params(smoother="tweed", nu1=args.nu[0], nu2=args.nu[1], precision="f32_refine",
-                            tol=TOL, inner_cycles=args.inner, max_outer=20, max_cycles=200,
-                            coarse_direct=args.coarse_direct)
+    p32 = mg.default_params(**dict(HEADLINE, nu1=args.nu[0], nu2=args.nu[1], inner_cycles=args.inner,
+                                   coarse_direct=args.coarse_direct))
     p64 = mg.default_params(smoother="tweed", nu1=args.nu[0], nu2=args.nu[1], precision="f64", tol=TOL,
                             max_cycles=200)
 

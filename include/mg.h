@@ -332,7 +332,7 @@ mg_status mg_pass_timer_end(mg_grid *g, int64_t *passes, double *stage_ms, doubl
 
 /* ---- line-solve paths and their autotuner.  A colour pass of a line
  * smoother (zebra, tweed, wireframe; Sec. 3) can be laid out on the GPU in
- * three ways; each solves every block of the colour exactly, they differ only
+ * four ways; each solves every block of the colour exactly, they differ only
  * in how the work is spread over threads (and so in rounding order and
  * speed).  The paper's solver is serial; these have no counterpart there.    */
 typedef enum {
@@ -342,7 +342,12 @@ typedef enum {
   MG_PATH_WARP = 1,  /* blocks laid end to end in sequences of 32*W*K nodes, one
                         per CTA of W warps; K consecutive nodes per thread     */
   MG_PATH_TILED = 2, /* 32 x 32-node tiles of parallel legs: three kernels     */
-  MG_PATH_CTA = 3    /* whole blocks per CTA, 32-node chunks per thread         */
+  MG_PATH_CTA = 3,   /* whole blocks per CTA, 32-node chunks per thread         */
+  MG_PATH_CLUSTER = 4 /* the tiles of the tiled path, each group of blocks on
+                        one thread-block cluster, in one kernel with every
+                        intermediate in shared memory (FP32 only; measured
+                        slower than the tiled path on GB300, so never chosen
+                        by the built-in rule)                                  */
 } mg_line_path;
 
 /* Sets the path of the colour passes of `smoother` (MG_SMOOTH_ZEBRA_X,
@@ -352,7 +357,9 @@ typedef enum {
  * other paths.  MG_ERR_UNSUPPORTED if the level's blocks do not fit the path:
  * the warp path takes blocks of up to 4096 nodes in FP32 and 2048 in FP64;
  * the tiled path exists for tweed and zebra on levels whose sides are both at
- * least 1024 intervals.  The previous choice then stays.  May allocate and
+ * least 1024 intervals; the cluster path exists in FP32 where the tiled path
+ * does, the device runs clusters of 8 CTAs, and every group of the tiled
+ * path fits 8 CTAs of 16 tiles.  The previous choice then stays.  May allocate and
  * free device memory (work lists); synchronises the device and drops the
  * grid's captured cycle graphs.                                              */
 mg_status mg_set_line_path(mg_grid *grid, int level, int smoother, int dtype, int path, int k);

@@ -70,6 +70,7 @@ static void free_grid(Grid *g) {
     for (int w = 0; w < WL_COUNT; ++w)
       for (int c = 0; c < 2; ++c) {
         cudaFree(L.tl[w][c].mem);
+        cudaFree(L.cp[w][c].mem);
         for (int p = 0; p < 2; ++p) {
           for (int z = 0; z < 2; ++z) cudaFree(L.wl[w][p][c][z].mem);
           cudaFree(L.wp[w][p][c].mem);
@@ -162,6 +163,8 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
   TRY_CUDA("setup start (latched error)", cudaGetLastError());
   TRY_CUDA("line kernel attributes", prepare_line_kernels());
   TRY_CUDA("warp kernel attributes", prepare_warp_kernels());
+  TRY_CUDA("cluster kernel attributes", prepare_cluster_kernel());
+  g->cluster_ok = (g->prec_mask & 2) && cluster_pass_capacity() > 0;
   const bool want64 = g->prec_mask & 1, want32 = g->prec_mask & 2;
   for (int l = 0; l < g->nlev; ++l) {
     Level &L = g->lev[l];
@@ -225,6 +228,8 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
       TRY_CUDA("setup work lists (latched error)", cudaGetLastError());
       TRY(build_tiles(*g, l, wl));
       TRY_CUDA("setup tiles (latched error)", cudaGetLastError());
+      TRY(build_cluster_plans(*g, l, wl));
+      TRY_CUDA("setup cluster plans (latched error)", cudaGetLastError());
     }
   if (g->tile_cap > 0) {
     // scratch of the tiled path, sized for FP64 (FP32 uses the first half)
@@ -277,8 +282,16 @@ static mg_status colour_pass(Grid &g, int l, int smoother, int colour, T *u, con
   const bool has_tiles = tl && (tl->ntile > 0 || tl->nblock > 0);
   const bool warp = wl >= 0 && L.wp[wl][prec][colour].nwarp > 0 &&
                     (chosen == MG_PATH_AUTO || chosen == MG_PATH_WARP);
-  const bool tiled = !warp && has_tiles && (chosen == MG_PATH_AUTO || chosen == MG_PATH_TILED);
+  const bool clustered = !warp && sizeof(T) == 4 && wl >= 0 && L.cp[wl][colour].ncta > 0 &&
+                         chosen == MG_PATH_CLUSTER;
+  const bool tiled = !warp && !clustered && has_tiles && (chosen == MG_PATH_AUTO || chosen == MG_PATH_TILED);
   cudaEvent_t *ev = timer_slot(g, l);
+  if constexpr (sizeof(T) == 4) {
+    if (clustered) {
+      TRY_CUDA("cluster line pass", launch_cluster_pass(L, L.cp[wl][colour], u, f, s, ev));
+      return MG_OK;
+    }
+  }
   if (tiled) {
     TRY_CUDA("tiled line pass", launch_tile_pass<T>(g, L, *tl, u, f, s, ev));
     return MG_OK;

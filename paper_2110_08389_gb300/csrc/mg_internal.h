@@ -263,6 +263,96 @@ struct TileList {
   BlockDesc *block = nullptr;   // 32 per group (unused entries have nleg = junc = 0)
 };
 
+// Cluster pass (FP32 tweed and zebra on the tiled levels): the three stages of
+// the tiled path in ONE kernel, the chunk right-hand sides and reduced rows
+// kept in shared memory.  The tiles of a group of blocks are spread over the
+// CTAs of one thread-block cluster, at most CL_TILES tiles per CTA; each CTA
+//   1. computes its chunks' right-hand sides and reduced rows (partition
+//      method, as tile_reduce) into shared memory;
+//   2. after a cluster barrier, solves some of the group's blocks: Thomas on
+//      the reduced rows of each leg from the wall to the junction, the
+//      junction row, back-substitution (as tile_couple), reading and writing
+//      the rows and chunk end values where they lie, in the shared memory of
+//      the CTA that holds the chunk (DSMEM);
+//   3. after a second cluster barrier, expands its chunks (Thomas between the
+//      known end values) into u.
+// Blocks are the paper's m-legged systems (Eq. mLThomas); the elimination is
+// that of the tiled path.  A group of one block (the centre cross, the
+// T-blocks of a rectangle) is laid out "compact": the lanes of a tile are 32
+// consecutive chunks of one leg instead of 32 parallel legs.
+constexpr int CL_TILES = 16;      // tiles (32 chunks each) per CTA
+constexpr int CL_CTAS = 8;        // CTAs per cluster (portable maximum)
+constexpr int CL_WARPS = 8;       // warps per CTA
+constexpr int CL_MAXSEG = CL_CTAS;  // segments per leg (one per CTA of its group)
+constexpr int CL_LEGROWS = 1536;    // (c', d') places of the legs one CTA solves
+
+enum : uint8_t { CT_COMPACT = 1 };
+struct CTile {
+  uint16_t base;   // run coordinate of slot 0 (regular tiles)
+  uint8_t dir;     // run direction (DIR_*)
+  uint8_t kind;    // 0 or CT_COMPACT
+  uint32_t pad;
+};
+static_assert(sizeof(CTile) == 8, "CTile layout");
+struct CLane {
+  uint16_t line;   // fixed coordinate of the run
+  uint8_t q1;      // active slots [0, q1) (0: unused lane)
+  uint8_t flags;   // TL_FIRST / TL_LAST_J / TL_LAST_W, as TileLane
+  uint16_t cbase;  // compact tiles: run coordinate of the lane's slot 0
+  uint16_t pad;
+};
+static_assert(sizeof(CLane) == 8, "CLane layout");
+// One CTA: tiles [tile0, tile0 + ntile) of the plan, segments [seg0, seg0 +
+// nseg); its group's CTAs are cluster ranks rank0 .. rank0 + ngr - 1 and this
+// one is rank0 + grank.  group < 0: an idle CTA that only fills its cluster.
+struct CCta {
+  int32_t tile0, group, seg0;
+  uint16_t nseg;
+  uint8_t ntile, grank, rank0, ngr, nleg, pad;
+};
+static_assert(sizeof(CCta) == 20, "CCta layout");
+// A segment: nchunk consecutive chunks of one leg held by one CTA, the first
+// (nearest the wall) at CTA-local chunk slot slot0 = tile * 32 + lane, the
+// next ones stride slots further (32 for regular tiles, 1 for compact ones).
+// Each chunk has two reduced rows, but a last chunk of one node (one = 1)
+// has one.
+struct CSeg {
+  uint16_t slot0, nchunk;
+  uint8_t stride, one, pad[2];
+};
+static_assert(sizeof(CSeg) == 8, "CSeg layout");
+// A block of a group: junction node, legs, and direction junction -> last
+// node of leg l in bits 2l..2l+1 (as BlockDesc).
+struct CBlock {
+  uint16_t ji, jj;
+  uint8_t nleg, junc, jdirs, pad;
+};
+static_assert(sizeof(CBlock) == 8, "CBlock layout");
+// Leg l of block b of a group (record l * 32 + b): its segments from the wall
+// to the junction, segment s held by cluster rank rank[s] as segment slot[s]
+// of that CTA's list.
+struct CChain {
+  uint8_t nseg;
+  uint8_t rank[CL_MAXSEG];
+  uint8_t slot[CL_MAXSEG];
+  uint8_t pad;
+  uint16_t roff;   // first of its rows' places in the solving CTA's (c', d') store
+  uint16_t nrow;   // reduced rows of the leg
+  uint16_t pad2;
+};
+static_assert(sizeof(CChain) == 24, "CChain layout");
+struct ClusterPlan {
+  int ncta = 0;        // a multiple of CL_CTAS (0: the level has no cluster pass)
+  int ntile = 0, nseg = 0, ngroup = 0;
+  void *mem = nullptr;
+  CTile *tile = nullptr;
+  CLane *lane = nullptr;   // 32 per tile
+  CCta *cta = nullptr;
+  CSeg *seg = nullptr;
+  CBlock *block = nullptr; // 32 per group
+  CChain *chain = nullptr; // 128 per group
+};
+
 // Shapes of the line-solve kernel: 32 nodes per chunk (one thread each);
 // blocks of up to NT_SMALL*32 unknowns go to CTAs of NT_SMALL threads (two
 // resident per SM), larger ones (wireframe rings) to CTAs of NT_LARGE.
@@ -288,6 +378,7 @@ struct Level {
   bool wl_built[WL_COUNT][2] = {};    // [smoother][precision 0=f64,1=f32]
   bool tl_built[WL_COUNT] = {};
   TileList tl[WL_COUNT][2];           // [smoother][colour]: tiled path (empty: use the work lists)
+  ClusterPlan cp[WL_COUNT][2];        // [smoother][colour]: cluster pass (FP32; ncta = 0: none)
   WorkList wl[WL_COUNT][2][2][2];     // [smoother][precision][colour][small, large]
   WarpList wp[WL_COUNT][2][2];        // [smoother][precision][colour]: warp path (nwarp = 0: unused)
   int path[WL_COUNT][2] = {};         // [smoother][precision]: MG_PATH_* (0 = the built-in rule)
@@ -299,6 +390,7 @@ struct Grid {
   Grid3 *g3 = nullptr;               // dim == 3: the 3D levels (lev then stays empty)
   int nlev = 0;
   int sms = 1;                       // multiprocessors of the device the grid was set up on
+  bool cluster_ok = false;           // FP32 grid on a device that runs the cluster pass
   int prec_mask = 3;
   std::vector<Level> lev;
   // coarsest level: dense inverse of the interior operator (FP64, row-major)
@@ -397,6 +489,9 @@ const char *set_error(const char *where, cudaError_t e);
 void set_error_text(const char *msg);
 
 mg_status build_tiles(Grid &g, int level, int wl);
+// (cluster_setup.cu) the cluster pass plans of both colours of a tiled level
+// (none where a colour's groups do not fit a cluster, or on FP64-only grids)
+mg_status build_cluster_plans(Grid &g, int level, int wl);
 // Dynamic shared memory opt-in of the line kernels on the current device
 // (called by mg_setup_grid).
 cudaError_t prepare_line_kernels();
@@ -406,6 +501,13 @@ cudaError_t prepare_warp_kernels();
 template <typename T>
 cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &t, T *u, const T *f, cudaStream_t s,
                              cudaEvent_t *ev);
+// The cluster pass (FP32) of one colour; ev as launch_tile_pass (ev[0] before
+// the kernel, ev[1..3] after it).
+cudaError_t launch_cluster_pass(const Level &L, const ClusterPlan &cp, float *u, const float *f, cudaStream_t s,
+                                cudaEvent_t *ev);
+cudaError_t prepare_cluster_kernel();
+// Clusters of the cluster pass the current device holds at once (0: none).
+int cluster_pass_capacity();
 
 // ---- kernel launchers (smooth.cu, transfer.cu).  All return cudaError_t of
 // the launch (cudaGetLastError).

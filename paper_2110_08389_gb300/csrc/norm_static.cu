@@ -27,9 +27,16 @@ constexpr int THREADS = 256;
 // a device; every entry a call reads was written earlier in that same call.
 static __device__ __align__(256) double g_row_scratch[4 * MAX_ROWS];
 
-// Device address of g_row_scratch, looked up once per device.
+// Device address of g_row_scratch per device: looked up by every call made
+// outside a stream capture (so that a context re-created after
+// cudaDeviceReset gets its own address), and taken from this cache by calls
+// made while their stream is being captured.
 std::mutex g_addr_mutex;
 double *g_addr[MAX_DEVICES] = {};
+
+// max that propagates NaN (fmax would drop it): once a NaN has entered m it
+// stays, so a non-finite residual shows in the max norms as in the sums.
+__device__ __forceinline__ double max_nan(double m, double v) { return (v > m || v != v) ? v : m; }
 
 __device__ __forceinline__ void reduce2(double &s, double &m) {
   __shared__ double ss[THREADS], sm[THREADS];
@@ -38,7 +45,7 @@ __device__ __forceinline__ void reduce2(double &s, double &m) {
   for (int h = THREADS / 2; h > 0; h >>= 1) {
     if ((int)threadIdx.x < h) {
       ss[threadIdx.x] += ss[threadIdx.x + h];
-      sm[threadIdx.x] = fmax(sm[threadIdx.x], sm[threadIdx.x + h]);
+      sm[threadIdx.x] = max_nan(sm[threadIdx.x], sm[threadIdx.x + h]);
     }
     __syncthreads();
   }
@@ -59,8 +66,8 @@ __global__ void __launch_bounds__(THREADS) row_norms(int nx, const double *__res
     const double w = W[i], e = E[i], s = S[j], n = N[j];
     const double lu = w * u[p - 1] + e * u[p + 1] + s * u[p - nx1] + n * u[p + nx1] - ((w + e) + (s + n)) * u[p];
     const double r = f[p] - lu;
-    rs += r * r; rm = fmax(rm, fabs(r));
-    fs += f[p] * f[p]; fm = fmax(fm, fabs(f[p]));
+    rs += r * r; rm = max_nan(rm, fabs(r));
+    fs += f[p] * f[p]; fm = max_nan(fm, fabs(f[p]));
   }
   reduce2(rs, rm);
   reduce2(fs, fm);
@@ -77,8 +84,8 @@ __global__ void __launch_bounds__(THREADS) rows_total(int rows, const double *__
                                                       double *__restrict__ out) {
   double rs = 0.0, rm = 0.0, fs = 0.0, fm = 0.0;
   for (int k = threadIdx.x; k < rows; k += THREADS) {
-    rs += scratch[k]; rm = fmax(rm, scratch[MAX_ROWS + k]);
-    fs += scratch[2 * MAX_ROWS + k]; fm = fmax(fm, scratch[3 * MAX_ROWS + k]);
+    rs += scratch[k]; rm = max_nan(rm, scratch[MAX_ROWS + k]);
+    fs += scratch[2 * MAX_ROWS + k]; fm = max_nan(fm, scratch[3 * MAX_ROWS + k]);
   }
   reduce2(rs, rm);
   reduce2(fs, fm);
@@ -106,20 +113,28 @@ extern "C" mg_status mg_residual_norm_static(int64_t nx, int64_t ny, const doubl
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) { set_error("cudaGetDevice", e); return MG_ERR_CUDA; }
   if (dev < 0 || dev >= MAX_DEVICES) return MG_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(s, &cs);
+  if (e != cudaSuccess) { set_error("cudaStreamIsCapturing", e); return MG_ERR_CUDA; }
   double *scratch;
   {
-    // set-up, once per device, with that device current: the host-side name
-    // g_row_scratch is only a stand-in, the kernels need its device address
+    // set-up, with the device current: the host-side name g_row_scratch is
+    // only a stand-in, the kernels need its device address.  Looked up on
+    // every call outside a capture; a captured call uses the address an
+    // earlier uncaptured call on this device found.
     std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
       void *p = nullptr;
       e = cudaGetSymbolAddress(&p, g_row_scratch);
       if (e != cudaSuccess) { set_error("cudaGetSymbolAddress(row scratch)", e); return MG_ERR_CUDA; }
       g_addr[dev] = static_cast<double *>(p);
+    } else if (!g_addr[dev]) {
+      set_error_text("mg_residual_norm_static: the first call on a device must come before any stream capture");
+      return MG_ERR_INVALID_ARG;
     }
     scratch = g_addr[dev];
   }
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int rows = (int)(ny - 1);
   row_norms<<<rows, THREADS, 0, s>>>((int)nx, W, E, S, N, u, f, scratch);
   rows_total<<<1, THREADS, 0, s>>>(rows, scratch, out);

@@ -18,12 +18,15 @@ bool has_tiles(const Level &L, int wl) {
   return true;
 }
 
+bool has_cluster(const Level &L, int wl) { return L.cp[wl][0].ncta > 0 && L.cp[wl][1].ncta > 0; }
+
 // Sets the path of (level, wl, prec); the caller has validated the arguments.
 mg_status set_path(Grid &g, int level, int wl, int prec, int path, int k) {
   Level &L = g.lev[level];
   mg_status st = build_worklists(g, level, wl, prec);
   if (st != MG_OK) return st;
   if (path == MG_PATH_TILED && !has_tiles(L, wl)) return MG_ERR_UNSUPPORTED;
+  if (path == MG_PATH_CLUSTER && (prec != 1 || !has_cluster(L, wl))) return MG_ERR_UNSUPPORTED;
   // the warp lists are rebuilt for the warp path, and back to the built-in
   // ones when leaving a warp path with another shape
   const bool rebuild = path == MG_PATH_WARP || L.kpref[wl][prec] != 0;
@@ -123,7 +126,7 @@ mg_status time_passes(mg_grid *g, int level, int smoother, int dtype, int reps, 
 extern "C" {
 
 mg_status mg_set_line_path(mg_grid *g, int level, int smoother, int dtype, int path, int k) {
-  if (bad_args(g, level, dtype) || path < MG_PATH_AUTO || path > MG_PATH_CTA) return MG_ERR_INVALID_ARG;
+  if (bad_args(g, level, dtype) || path < MG_PATH_AUTO || path > MG_PATH_CLUSTER) return MG_ERR_INVALID_ARG;
   if (!(k == 0 || k == 1 || k == 2 || k == 4 || k == 8 || k == 16)) return MG_ERR_INVALID_ARG;
   const int wl = wl_of(smoother);
   if (wl < 0) return MG_ERR_INVALID_ARG;
@@ -192,12 +195,12 @@ mg_status mg_autotune(mg_grid *g, int smoother, int dtype, int reps, double *tim
       }
       if (reps <= 0) continue;
       // candidates: the warp path with each preferred k (distinct shapes
-      // only), the tiled path, the CTA path
+      // only), the cluster path, the tiled path, the CTA path
       Choice best{-1, 0, 0.0};
       std::vector<std::array<int, 2>> shapes;
-      const int cand[7][2] = {{MG_PATH_WARP, 1}, {MG_PATH_WARP, 2}, {MG_PATH_WARP, 4}, {MG_PATH_WARP, 8},
-                              {MG_PATH_WARP, 16}, {MG_PATH_TILED, 0}, {MG_PATH_CTA, 0}};
-      for (int c = 0; c < 7 && st == MG_OK; ++c) {
+      const int cand[8][2] = {{MG_PATH_WARP, 1}, {MG_PATH_WARP, 2}, {MG_PATH_WARP, 4}, {MG_PATH_WARP, 8},
+                              {MG_PATH_WARP, 16}, {MG_PATH_CLUSTER, 0}, {MG_PATH_TILED, 0}, {MG_PATH_CTA, 0}};
+      for (int c = 0; c < 8 && st == MG_OK; ++c) {
         const mg_status ps = set_path(*g, l, wl, prec, cand[c][0], cand[c][1]);
         if (ps == MG_ERR_UNSUPPORTED) continue;
         if (ps != MG_OK) { st = ps; break; }

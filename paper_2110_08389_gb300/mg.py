@@ -26,8 +26,8 @@ SMOOTHERS = {"checkerboard": CHECKERBOARD, "zebra_x": ZEBRA_X, "zebra_y": ZEBRA_
 F64, F32 = 0, 1
 PREC_F64, PREC_F32_REFINE = 0, 1
 HW, FW = 0, 1
-PATH_AUTO, PATH_WARP, PATH_TILED, PATH_CTA = range(4)
-PATHS = {"auto": PATH_AUTO, "warp": PATH_WARP, "tiled": PATH_TILED, "cta": PATH_CTA}
+PATH_AUTO, PATH_WARP, PATH_TILED, PATH_CTA, PATH_CLUSTER = range(5)
+PATHS = {"auto": PATH_AUTO, "warp": PATH_WARP, "tiled": PATH_TILED, "cta": PATH_CTA, "cluster": PATH_CLUSTER}
 PATH_NAMES = {v: k for k, v in PATHS.items()}
 DTYPES = {"f64": F64, "f32": F32}
 

@@ -94,22 +94,28 @@ def colour_mask(P, colour):
     return m
 
 
-def gpu_pass(mg, grid, u_in, f, colour, dtype):
+def gpu_pass(mg, grid, u_in, f, colour, dtype, path="auto"):
     import torch
     ud = torch.tensor(u_in.astype(dtype), device="cuda")
     fd = torch.tensor(f.astype(dtype), device="cuda")
-    grid.colour_pass(ud, fd, "tweed", colour)
+    dt = "f64" if dtype == np.float64 else "f32"
+    grid.set_line_path(0, "tweed", dt, path)
+    try:
+        grid.colour_pass(ud, fd, "tweed", colour)
+    finally:
+        grid.set_line_path(0, "tweed", dt, "auto")
     torch.cuda.synchronize()
     return ud.cpu().numpy()
 
 
-@pytest.mark.parametrize("dtype", [np.float64, np.float32], ids=["f64", "f32"])
+@pytest.mark.parametrize("dtype,path", [(np.float64, "auto"), (np.float32, "auto"), (np.float32, "cluster")],
+                         ids=["f64", "f32", "f32-cluster"])
 @pytest.mark.parametrize("colour", [0, 1])
-def test_fullsize_pass_backward_error(mg, grid, big, dtype, colour):
+def test_fullsize_pass_backward_error(mg, grid, big, dtype, path, colour):
     _, f, P = big
     u_in = I.random_field(N + 1, N + 1, 11 + colour).astype(dtype)
     f_t = f.astype(dtype)
-    out = gpu_pass(mg, grid, u_in, f_t, colour, dtype)
+    out = gpu_pass(mg, grid, u_in, f_t, colour, dtype, path)
     mine = colour_mask(P, colour)
     # the other colour and the boundary are not written
     assert np.array_equal(out[~mine], u_in[~mine])
@@ -180,13 +186,15 @@ def test_fullsize_solve_f64_matches_oracle(mg, grid, big, oracle_solution, linv_
 
 
 def test_fullsize_solve_f32_refine(mg, grid, big, oracle_solution, linv_norm):
-    """The configuration bench.py times: V(1,1), 3 FP32 cycles per refinement step."""
+    """The configuration bench.py times, parameter for parameter (bench.HEADLINE:
+    V(1,1), 3 FP32 cycles per refinement step, every level down to the FP64
+    coarsest solve)."""
     import torch
+    from bench import HEADLINE
     _, f, P = big
     u_ref, _ = oracle_solution
     ud = torch.zeros((N + 1, N + 1), dtype=torch.float64, device="cuda")
-    res = grid.solve(ud, torch.tensor(f, device="cuda"), smoother="tweed", nu1=1, nu2=1, tol=1e-10,
-                     precision="f32_refine", inner_cycles=3, max_outer=20, max_cycles=200)
+    res = grid.solve(ud, torch.tensor(f, device="cuda"), **HEADLINE)
     assert res.status == mg.OK and res.rel_res <= 1e-10
     u = ud.cpu().numpy()
     r = P.residual(u, f)

@@ -1,6 +1,6 @@
-"""Every line-solve path (warp sequences of each shape, tiled, CTA) against the
-oracle on every level where the blocks fit it, and the autotuner that picks
-among them (mg_set_line_path / mg_get_line_path / mg_autotune).
+"""Every line-solve path (warp sequences of each shape, cluster, tiled, CTA)
+against the oracle on every level where the blocks fit it, and the autotuner
+that picks among them (mg_set_line_path / mg_get_line_path / mg_autotune).
 
 The paths differ only in how a colour pass is spread over the GPU; each must
 give the exact block solves of Sec. 3, so the FP64 tolerance is the one of the
@@ -37,7 +37,7 @@ def rel_err(a, b):
 def pass_cases(g, level, smoother, dtype, mg):
     """(label, path, k) for every path that level takes, one per distinct shape."""
     out, seen = [], set()
-    for path, ks in (("warp", WARP_KS), ("tiled", [0]), ("cta", [0])):
+    for path, ks in (("warp", WARP_KS), ("cluster", [0]), ("tiled", [0]), ("cta", [0])):
         for k in ks:
             try:
                 g.set_line_path(level, smoother, dtype, path, k)
@@ -94,13 +94,47 @@ def test_f32_warp_shapes(mg, oracle_mod):
     f = rng.standard_normal(P.shape(0)).astype(np.float32).astype(np.float64)
     refs = [P.colour_pass(u0.copy(), f, "tweed", colour, 0) for colour in (0, 1)]
     cases = pass_cases(g, 0, "tweed", "f32", mg)
-    assert {c[1] for c in cases} == {"warp", "tiled", "cta"}
+    assert {c[1] for c in cases} == {"warp", "cluster", "tiled", "cta"}
     for label, path, k in cases:
         g.set_line_path(0, "tweed", "f32", path, k)
         for colour in (0, 1):
             ud = cuda(u0, "f32")
             g.colour_pass(ud, cuda(f, "f32"), "tweed", colour, level=0)
             assert rel_err(host(ud), refs[colour]) <= 2e-4, (label, colour)
+
+
+@pytest.mark.parametrize("grid,smoother", [
+    ((1024, 1024, "wall", 3.0), "tweed"),     # L-blocks over up to 4 CTAs, the centre cross compact
+    ((1024, 1024, "wall", 3.0), "zebra_x"),   # lines of 32 chunks over 2 CTAs
+    ((1024, 1024, "wall", 3.0), "zebra_y"),
+    ((2048, 1024, "wall", 2.0), "tweed"),     # T-blocks (compact) and wall-to-wall lines
+    ((1088, 1600, "centre", 1.5), "tweed"),   # ragged chunks and tiles, T-blocks
+], ids=lambda v: f"{v[0]}x{v[1]}-{v[2]}" if isinstance(v, tuple) else v)
+def test_cluster_pass_f32(mg, oracle_mod, grid, smoother):
+    """The cluster path's FP32 colour passes against the FP64 oracle on
+    FP32-rounded data (the FP32 smoothing tolerance), and against the FP32
+    tiled path, which solves the same blocks in another grouping; the
+    other colour and the boundary stay untouched bit for bit."""
+    nx, ny, kind, c = grid
+    x, y = coords(nx, kind, c), coords(ny, kind, c)
+    g, P = mg.Grid(x, y), oracle_mod.Problem(x, y)
+    rng = np.random.default_rng(9)
+    u0 = rng.standard_normal(P.shape(0)).astype(np.float32).astype(np.float64)
+    f = rng.standard_normal(P.shape(0)).astype(np.float32).astype(np.float64)
+    for colour in (0, 1):
+        ref = P.colour_pass(u0.copy(), f, smoother, colour, 0)
+        got = {}
+        for path in ("cluster", "tiled"):
+            g.set_line_path(0, smoother, "f32", path)
+            assert g.line_path(0, smoother, "f32")[0] == path
+            ud = cuda(u0, "f32")
+            g.colour_pass(ud, cuda(f, "f32"), smoother, colour, level=0)
+            got[path] = host(ud)
+        g.set_line_path(0, smoother, "f32", "auto")
+        same = ref == u0
+        assert np.array_equal(got["cluster"][same], u0[same])
+        assert rel_err(got["cluster"], ref) <= 2e-4, (colour, rel_err(got["cluster"], ref))
+        assert rel_err(got["cluster"], got["tiled"]) <= 2e-4
 
 
 def test_default_paths_and_unsupported(mg):
@@ -116,11 +150,14 @@ def test_default_paths_and_unsupported(mg):
         g.set_line_path(0, "wireframe", "f64", "warp")
     assert e.value.status == mg.ERR_UNSUPPORTED
     assert g.line_path(0, "wireframe", "f64")[0] == "cta"
-    # no tiled lists below 1024 intervals, nor for wireframe
+    # no tiled lists below 1024 intervals, nor for wireframe; no cluster
+    # path there either, nor in FP64
     small = mg.Grid(coords(64, "wall", 3.0), coords(64, "wall", 3.0))
-    for grid, lev, sm in ((small, 0, "tweed"), (g, 0, "wireframe")):
+    for grid, lev, sm, dt, path in ((small, 0, "tweed", "f32", "tiled"), (g, 0, "wireframe", "f32", "tiled"),
+                                    (small, 0, "tweed", "f32", "cluster"), (g, 0, "wireframe", "f32", "cluster"),
+                                    (g, 0, "tweed", "f64", "cluster")):
         with pytest.raises(mg.MGError) as e:
-            grid.set_line_path(lev, sm, "f32", "tiled")
+            grid.set_line_path(lev, sm, dt, path)
         assert e.value.status == mg.ERR_UNSUPPORTED
     with pytest.raises(mg.MGError) as e:
         g.set_line_path(0, "tweed", "f32", "warp", 3)

@@ -79,6 +79,8 @@ def parse():
                     help="single: the 4097^2 solve (default); batch: 256 mixed problems solved together; "
                          "3d: the 257^3 tweed solve")
     ap.add_argument("--inner3d", type=int, default=8, help="FP32 cycles per refinement step of the 3d workload")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="single workload: skip the smoother matrix and the batch and 3d lines added to the JSON line")
     return ap.parse_args()
 
 
@@ -180,14 +182,93 @@ def barrier(pg):
         pg.barrier()
 
 
+# ------------------------------------------------------------------ extras
+
+# The comparison of 4097^2 solves: tweed and wireframe on the grids they are
+# made for (wall and centre clustering, spacing ratio 1000) against
+# checkerboard and alternating zebra on the same grids, and wireframe and
+# alternating zebra on milder centre clustering (c = 1.5 and 2.0, where
+# Sec. 6 places the limit of their convergence near c = 2.3); V(1,1) and
+# V(2,2); FP64 and FP32+refine.  Caps: 100 FP64 cycles, 20 refinement steps;
+# the early stop ends solves whose rate cannot reach 1e-10 under those caps.
+MATRIX_GRIDS = [("wall ratio 1000", "wall", None, ("tweed", "checkerboard", "alt_zebra")),
+                ("centre ratio 1000", "centre", None, ("wireframe", "checkerboard", "alt_zebra")),
+                ("centre c=1.5", "centre", 1.5, ("wireframe", "alt_zebra")),
+                ("centre c=2.0", "centre", 2.0, ("wireframe", "alt_zebra"))]
+STATUS = {0: "ok", 4: "not converged", 5: "non-finite"}
+
+
+def smoother_matrix(mg, torch, dev, n, f_h):
+    """One timed solve (after an untimed one) per (grid, smoother, cycle,
+    precision) of MATRIX_GRIDS; GPU time from CUDA events."""
+    from paper_2110_08389_gb300 import inputs as I
+    f = torch.tensor(f_h, device=dev)
+    u = torch.zeros_like(f)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    for label, kind, c, smoothers in MATRIX_GRIDS:
+        if c is None:
+            c = I.c_for_ratio(n, RATIO, kind)
+        x = I.centre_coords(n, c) if kind == "centre" else I.wall_coords(n, c)
+        grid = mg.Grid(x, x)
+        for sm in smoothers:
+            for nu in (1, 2):
+                for prec in ("f64", "f32_refine"):
+                    p = mg.default_params(smoother=sm, nu1=nu, nu2=nu, precision=prec, tol=TOL, max_cycles=100,
+                                          max_outer=20, inner_cycles=3, early_stop=1)
+                    grid.solve(u, f, p)
+                    torch.cuda.synchronize()
+                    e0.record(stream)
+                    r = grid.solve(u, f, p)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    out.append({"grid": label, "c": round(c, 6), "smoother": sm, "cycle": f"V({nu},{nu})",
+                                "precision": prec, "status": STATUS.get(r.status, str(r.status)),
+                                "s": e0.elapsed_time(e1) / 1e3, "cycles": r.cycles, "outer_iters": r.outer_iters,
+                                "rel_res": r.rel_res, "conv_factor": r.conv_factor})
+        grid.close()
+        del grid
+    return out
+
+
+def workload_line(workload, args):
+    """The JSON line of `bench.py --workload <workload>` (1 timed step after 1
+    warm-up, no CPU baseline), run as a child process; None if it failed."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--workload", workload, "--steps", "1", "--warmup", "1",
+           "--no-cpu-baseline"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    for ln in r.stdout.splitlines()[::-1]:
+        if ln.startswith("{"):
+            return json.loads(ln)
+    return {"error": f"exit {r.returncode}: {r.stderr.strip()[-300:]}"}
+
+
+def host_cpu():
+    """Host cores and CPU model, for the CPU baseline."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
 # ------------------------------------------------------------------ oracle
 
-def oracle_cycles(x, f, nu, steps, warmup):
-    """Time V-cycles of the CPU oracle on the full workload from u = 0.
-    Returns (seconds per timed cycle, cycles to TOL, how that count was got)."""
+def oracle_cycles(x, f, nu, steps, warmup, threads=1):
+    """Time V-cycles of the CPU oracle on the full workload from u = 0, its
+    colour passes on `threads` threads (the blocks of a colour are independent;
+    the result does not depend on the count).  Returns (seconds per timed
+    cycle, cycles to TOL, how that count was got)."""
     import numpy as np
     import oracle
     oracle.build()
+    oracle.threads(threads)
     P = oracle.Problem(x, x)
     u = np.zeros_like(f)
     fn = math.sqrt(float(np.sum(f[1:-1, 1:-1] ** 2)))
@@ -605,13 +686,37 @@ def main():
                          "peak_source": "hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"},
             "clocks": clk.summary()}
 
+    if rank == 0 and world == 1 and not args.no_extras:
+        # smoother comparison at full size, then the batched and 3D workloads
+        # (child processes, so that their grids do not share this one's memory)
+        del grid
+        torch.cuda.empty_cache()
+        line["smoother_matrix"] = smoother_matrix(mg, torch, dev, args.intervals, f_h)
+        torch.cuda.empty_cache()
+        for wl in ("batch", "3d"):
+            sub = workload_line(wl, args)
+            keep = ("metric", "value", "unit", "config", "status", "rel_res", "outer_iters", "inner_cycles_total",
+                    "converged", "converged_by_clustering", "sequential_s", "speedup_vs_sequential", "fp64",
+                    "speedup_vs_fp64", "e2e", "gpu_launches", "roofline", "problems_per_s", "error")
+            line[wl] = {k: v for k, v in sub.items() if k in keep}
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
         per_cycle, _, _ = oracle_cycles(x, f_h, args.nu, 3, 1)
         cycles = r64.cycles
+        allc = os.cpu_count() or 1
+        per_cycle_all, _, _ = oracle_cycles(x, f_h, args.nu, 3, 1, threads=allc)
+        threads_all = oracle.threads(0)
         line["cpu_baseline"] = {"value": per_cycle * cycles, "unit": "s", "cores": 1, "kind": "oracle",
                                 "sample": f"mean of 3 FP64 V({args.nu[0]},{args.nu[1]}) cycles of the C oracle "
                                           f"(single thread) on the full grid (after 1 untimed) = {per_cycle:.2f} "
-                                          f"s/cycle, x {cycles} cycles (the FP64 iteration count of this problem)"}
+                                          f"s/cycle, x {cycles} cycles (the FP64 iteration count of this problem)",
+                                "all_cores": {"value": per_cycle_all * cycles, "unit": "s", "cores": threads_all,
+                                              "s_per_cycle": per_cycle_all,
+                                              "sample": "the same, the oracle's colour passes on every host core "
+                                                        "(OpenMP over the independent blocks of a colour; the "
+                                                        "residual and the transfers stay serial)"},
+                                "host": host_cpu()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     barrier(pg)

@@ -43,7 +43,11 @@ def build(force: bool = False) -> str:
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC3))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, _SRC3, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, _SRC3, "-lm"]
+        # OpenMP over the decoupled blocks of a colour pass where the compiler
+        # has it (same results with any thread count); plain C otherwise
+        if subprocess.call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -63,6 +67,7 @@ def _load():
             "or_create": (P, [i, i, dp, dp]),
             "or_destroy": (None, [P]),
             "or_num_levels": (i, [P]),
+            "or_threads": (i, [i]),
             "or_level_shape": (None, [P, i, ctypes.POINTER(i), ctypes.POINTER(i)]),
             "or_level_coeffs": (None, [P, i, dp, dp, dp, dp]),
             "or_apply": (None, [P, i, dp, dp]),
@@ -104,6 +109,12 @@ def _load():
             fn.argtypes = args
         _lib = lib
         return lib
+
+
+def threads(n: int = 0) -> int:
+    """Threads of the oracle's colour passes (OpenMP builds; n <= 0 keeps the
+    count).  Returns the count in effect (1 for a plain build)."""
+    return int(_load().or_threads(int(n)))
 
 
 def _f64(a):

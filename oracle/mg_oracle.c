@@ -46,6 +46,9 @@
  *       right-hand side of the interior system (f when the boundary data g
  *       vanish).
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -347,7 +350,9 @@ static void scratch_need(scratch_t *s, int m) {
   s->x = realloc(s->x, sizeof(double) * m); s->cp = realloc(s->cp, sizeof(double) * m);
   s->rp = realloc(s->rp, sizeof(double) * m); s->z = realloc(s->z, sizeof(double) * m);
 }
-static scratch_t g_scr;
+/* one scratch per thread: the blocks of a colour pass may be solved by
+ * several threads (OpenMP builds); the arithmetic of each block is the same */
+static _Thread_local scratch_t g_scr;
 
 /* Exact solve of one block, written into u (Sec. 3).                        */
 static void solve_block(const level_t *L, const partition_t *T, int b, double *u, const double *f) {
@@ -443,6 +448,12 @@ static void solve_block(const level_t *L, const partition_t *T, int b, double *u
 static int base_pass(or_problem *P, int lev, int sm, int colour, double *u, const double *f) {
   if (build_partition(P, lev, sm)) return -1;
   partition_t *T = &P->part[lev][sm];
+  /* the blocks of one colour are decoupled (Sec. 3): each reads only nodes of
+     the other colour and writes only its own, so they may run in any order
+     or at once, with the same result */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
   for (int b = 0; b < T->nblock; ++b)
     if (T->blk[b].colour == colour) solve_block(&P->lev[lev], T, b, u, f);
   return 0;
@@ -667,6 +678,18 @@ void or_destroy(or_problem *P) {
 }
 
 int or_num_levels(or_problem *P) { return P->nlev; }
+
+/* Threads of the colour passes in OpenMP builds (1 in plain builds); n <= 0
+ * keeps the current count.  Returns the count in effect.                    */
+int or_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 void or_level_shape(or_problem *P, int lev, int *nx, int *ny) { *nx = P->lev[lev].nx; *ny = P->lev[lev].ny; }
 void or_level_coeffs(or_problem *P, int lev, double *W, double *E, double *S, double *N) {
   level_t *L = &P->lev[lev];

@@ -384,9 +384,14 @@ int o3_colour_pass(o3_problem *P, int lev, int sm, int colour, double *u, const 
   if (sm < 0 || sm >= O3_NMOTIF) return -1;
   if (build_part(P, lev, sm)) return -1;
   const part3_t *T = &P->part[lev][sm];
+  /* the blocks of one colour are decoupled: any order, or at once */
+  int bad = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
+#endif
   for (int b = 0; b < T->nblock; ++b)
-    if (T->blk[b].colour == colour && solve_block3(&P->lev[lev], T, b, u, f)) return -1;
-  return 0;
+    if (T->blk[b].colour == colour && solve_block3(&P->lev[lev], T, b, u, f)) bad |= 1;
+  return bad ? -1 : 0;
 }
 
 /* one relaxation: red pass, black pass; O3_ALT_TW is the alternating scheme

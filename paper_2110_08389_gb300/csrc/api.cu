@@ -169,17 +169,19 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
   for (int l = 0; l < g->nlev; ++l) {
     Level &L = g->lev[l];
     const size_t a = L.nx + 1, b = L.ny + 1;
-    // doubles: W E x (a each), S N y (b each); floats after them
-    const size_t nd = 3 * a + 3 * b, nf = 2 * a + 2 * b;
+    // doubles: W E x W+E (a each), S N y (b each); floats after them
+    const size_t nd = 4 * a + 3 * b, nf = 2 * a + 2 * b;
     const size_t bytes = sizeof(double) * nd + sizeof(float) * nf + 16;
     TRY_CUDA("cudaMalloc(coefficients)", cudaMalloc(&L.dev_block, bytes));
     double *dp = static_cast<double *>(L.dev_block);
     L.W64 = dp; L.E64 = dp + a; L.xd = dp + 2 * a; L.S64 = dp + 3 * a; L.N64 = dp + 3 * a + b; L.yd = dp + 3 * a + 2 * b;
+    L.WE64 = dp + 3 * a + 3 * b;
     float *fp = reinterpret_cast<float *>(dp + nd);
     L.W32 = fp; L.E32 = fp + a; L.S32 = fp + 2 * a; L.N32 = fp + 2 * a + b;
     std::vector<double> hd(nd);
     std::vector<float> hf(nf);
     for (size_t i = 0; i < a; ++i) { hd[i] = L.hW[i]; hd[a + i] = L.hE[i]; hd[2 * a + i] = L.hx[i]; }
+    for (size_t i = 0; i < a; ++i) hd[3 * a + 3 * b + i] = L.hW[i] + L.hE[i];
     for (size_t j = 0; j < b; ++j) { hd[3 * a + j] = L.hS[j]; hd[3 * a + b + j] = L.hN[j]; hd[3 * a + 2 * b + j] = L.hy[j]; }
     for (size_t i = 0; i < a; ++i) { hf[i] = (float)L.hW[i]; hf[a + i] = (float)L.hE[i]; }
     for (size_t j = 0; j < b; ++j) { hf[2 * a + j] = (float)L.hS[j]; hf[2 * a + b + j] = (float)L.hN[j]; }

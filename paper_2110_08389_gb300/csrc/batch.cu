@@ -202,7 +202,7 @@ void build_tables(mg_batch &b, Group &G, double *const *u, const double *const *
     reinterpret_cast<CoarseArgs<float> *>(h + G.coarse)[k] =
         CoarseArgs<float>{level_coefs<double>(Lc), g.cinv, lu(nl - 1), lf(nl - 1)};
     reinterpret_cast<NormArgs *>(h + G.norm)[k] =
-        NormArgs{level_coefs<double>(g.lev[0]), u[i], f[i], g.r32, g.e32, g.partial,
+        NormArgs{level_coefs<double>(g.lev[0]), g.lev[0].WE64, u[i], f[i], g.r32, g.e32, g.partial,
                  reinterpret_cast<double *>(b.dev + G.base + G.out) + k};
     reinterpret_cast<UpdateArgs *>(h + G.upd)[k] = UpdateArgs{u[i], g.e32};
     reinterpret_cast<int *>(h + G.active)[k] = 1;

@@ -371,6 +371,7 @@ struct Level {
   double *W64 = nullptr, *E64 = nullptr, *S64 = nullptr, *N64 = nullptr;
   float *W32 = nullptr, *E32 = nullptr, *S32 = nullptr, *N32 = nullptr;
   double *xd = nullptr, *yd = nullptr;  // device copies of the coordinates
+  double *WE64 = nullptr;               // W_i + E_i per column (the FP64 defect's diagonal part)
   void *dev_block = nullptr;            // one allocation behind the arrays above
   // workspaces of coarse levels (level 0 uses the caller's arrays)
   double *u64 = nullptr, *f64 = nullptr;

@@ -35,6 +35,7 @@ struct CoarseArgs {  // direct solve of the coarsest level
 };
 struct NormArgs {  // FP64 norms (and refinement residual) of the finest level
   Coefs<double> c;
+  const double *we;  // W_i + E_i per column
   const double *u, *f;
   float *r32, *e32;
   double *part, *out;

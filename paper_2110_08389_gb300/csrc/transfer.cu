@@ -319,9 +319,13 @@ __device__ __forceinline__ double block_sum(double s) {
 // CTA b takes interior rows 1 + b, 1 + b + gridDim.x, ...; every thread its
 // columns in order, so the result does not depend on timing.  With r32 set
 // (refinement mode) it also stores float(r) and zeroes the FP32 correction
-// e32 for the cycles that follow.  FP64 issue is the bound on GB300: 9 FP64
-// operations per node.
-__global__ void __launch_bounds__(NORM_THREADS) norm_stage1(CoefQ<double> c, int nx, int ny,
+// e32 for the cycles that follow.  FP64 issue is the bound on GB300 (about
+// two FP64 operations per SM per clock): the defect takes 7 per node, with
+// W_i + E_i per column precomputed (we) and f folded into the FMA chain,
+//   r = f + C u_c - W u_w - E u_e - S u_s - N u_n,  C = (W + E) + (S + N),
+// and the sum of squares one more.
+__global__ void __launch_bounds__(NORM_THREADS) norm_stage1(CoefQ<double> c, const double *__restrict__ we,
+                                                            int nx, int ny,
                                                             const double *__restrict__ u,
                                                             const double *__restrict__ f, int bnd_only,
                                                             float *__restrict__ r32, float *__restrict__ e32,
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(NORM_THREADS) norm_stage1(CoefQ<double> c, int
   if (tab) {  // packed launch: blockIdx.y selects the problem
     if (!active[blockIdx.y]) return;
     const NormArgs a = tab[blockIdx.y];
-    c = a.c; u = a.u; f = a.f; part = a.part;
+    c = a.c; we = a.we; u = a.u; f = a.f; part = a.part;
     if (r32) { r32 = a.r32; e32 = a.e32; }
   }
   const int nx1 = nx + 1;
@@ -349,9 +353,12 @@ __global__ void __launch_bounds__(NORM_THREADS) norm_stage1(CoefQ<double> c, int
         if (j == 1) r -= sj * u[p - nx1];
         if (j == ny - 1) r -= nj * u[p + nx1];
       } else if (u) {
-        const double w = __ldg(c.W + i), e = __ldg(c.E + i);
-        const double cc = (w + e) + snj;
-        r -= w * u[p - 1] + e * u[p + 1] + sj * u[p - nx1] + nj * u[p + nx1] - cc * u[p];
+        const double cc = __ldg(we + i) + snj;
+        r = fma(cc, u[p], r);
+        r = fma(-__ldg(c.W + i), u[p - 1], r);
+        r = fma(-__ldg(c.E + i), u[p + 1], r);
+        r = fma(-sj, u[p - nx1], r);
+        r = fma(-nj, u[p + nx1], r);
       }
       if (r32) { r32[p] = (float)r; e32[p] = 0.0f; }
       s = fma(r, r, s);
@@ -379,8 +386,8 @@ __global__ void __launch_bounds__(NORM_THREADS) norm_stage2(const double *__rest
 static cudaError_t norms(const Grid &g, const double *u, const double *f, int bnd_only, float *r32, float *e32,
                          cudaStream_t s) {
   const Level &L = g.lev[0];
-  norm_stage1<<<g.npartial, NORM_THREADS, 0, s>>>(cq<double>(L), L.nx, L.ny, u, f, bnd_only, r32, e32, g.partial,
-                                                  nullptr, nullptr);
+  norm_stage1<<<g.npartial, NORM_THREADS, 0, s>>>(cq<double>(L), L.WE64, L.nx, L.ny, u, f, bnd_only, r32, e32,
+                                                  g.partial, nullptr, nullptr);
   norm_stage2<<<1, NORM_THREADS, 0, s>>>(g.partial, g.npartial, g.scal, nullptr, nullptr);
   count_launch(2);
   return cudaGetLastError();
@@ -393,8 +400,9 @@ cudaError_t launch_norms_packed(const Grid &g, int bnd_only, int with_r32, const
   const Level &L = g.lev[0];
   const NormArgs *tab = static_cast<const NormArgs *>(pk.tab);
   float *mark = with_r32 ? reinterpret_cast<float *>(g.r32) : nullptr;
-  norm_stage1<<<dim3(g.npartial, pk.count), NORM_THREADS, 0, s>>>(cq<double>(L), L.nx, L.ny, nullptr, nullptr,
-                                                                  bnd_only, mark, mark, nullptr, tab, pk.active);
+  norm_stage1<<<dim3(g.npartial, pk.count), NORM_THREADS, 0, s>>>(cq<double>(L), L.WE64, L.nx, L.ny, nullptr,
+                                                                  nullptr, bnd_only, mark, mark, nullptr, tab,
+                                                                  pk.active);
   norm_stage2<<<pk.count, NORM_THREADS, 0, s>>>(nullptr, g.npartial, nullptr, tab, pk.active);
   count_launch(2);
   return cudaGetLastError();
@@ -416,6 +424,21 @@ cudaError_t launch_ir_residual(const Grid &g, const double *u, const double *f, 
 constexpr int EW_THREADS = 256;
 static dim3 row_grid(const Level &L) { return dim3(std::min((L.nx - 1 + EW_THREADS - 1) / EW_THREADS, 4), L.ny - 1); }
 
+// Exact widening of a float to a double from the IEEE-754 fields: the sign,
+// the exponent rebiased from 127 to 1023, the 23 mantissa bits moved up by 29.
+// Integer instructions only, which leaves GB300's scarce FP64 pipe to the
+// addition; zero and subnormal floats (exponent field 0) and Inf / NaN (255)
+// take the conversion instruction instead.
+__device__ __forceinline__ double widen(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned ex = (b >> 23) & 0xffu;
+  if (ex == 0u || ex == 0xffu) return (double)x;
+  const unsigned long long bits = ((unsigned long long)(b & 0x80000000u) << 32) |
+                                  ((unsigned long long)(ex + 896u) << 52) |
+                                  ((unsigned long long)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
 __global__ void __launch_bounds__(EW_THREADS) ir_update_kernel(int nx, double *__restrict__ u,
                                                                const float *__restrict__ e,
                                                                const UpdateArgs *__restrict__ tab,
@@ -427,7 +450,7 @@ __global__ void __launch_bounds__(EW_THREADS) ir_update_kernel(int nx, double *_
   }
   const size_t row = (size_t)(blockIdx.y + 1) * (nx + 1);
   for (int i = 1 + blockIdx.x * EW_THREADS + threadIdx.x; i < nx; i += gridDim.x * EW_THREADS)
-    u[row + i] += (double)e[row + i];
+    u[row + i] += widen(e[row + i]);
 }
 cudaError_t launch_ir_update(const Grid &g, double *u, const float *e, cudaStream_t s) {
   const Level &L = g.lev[0];

@@ -1,8 +1,14 @@
-"""Smoothing steps of one smoother on one synthetic problem, as a target for
-profilers (ncu) and quick timing.
+"""Smoothing steps of one smoother on one synthetic problem, or whole solves,
+as a target for profilers (ncu) and quick timing.
 
     python -m paper_2110_08389_gb300.profile_pass [--n 4096] [--smoother tweed]
            [--dtype f32|f64] [--steps 3] [--ratio 1000] [--dim 2|3]
+           [--path auto|tiled|cluster|warp|cta]
+    python -m paper_2110_08389_gb300.profile_pass --solve f32_refine|f64 [--n 4096] [--steps 2]
+
+With --solve, each step is one solve of the 2D wall-clustered problem to
+||r||/||f|| <= 1e-10 from u = 0 with the benchmark's parameters (tweed V(1,1),
+full weighting; FP32 cycles with FP64 refinement, or FP64).
 
 The grid has n x n (x n with --dim 3: tweed or wireframe) intervals, tanh-stretched
 toward the walls (Eq. tanh) for
@@ -24,9 +30,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--ratio", type=float, default=1000.0)
     ap.add_argument("--dim", type=int, default=2, choices=[2, 3])
+    ap.add_argument("--path", default="auto", help="line-solve path of the finest level (2D)")
+    ap.add_argument("--solve", default=None, choices=["f32_refine", "f64"])
     args = ap.parse_args()
     import torch
     from . import inputs as I, mg
+    if args.solve:
+        return solve_steps(args)
 
     kind = "centre" if args.smoother == "wireframe" else "wall"
     c = I.c_for_ratio(args.n, args.ratio, kind)
@@ -36,6 +46,8 @@ def main():
     shape = g.shape(0)
     f = torch.tensor(I.rhs_gaussian(shape[0], int(np_prod(shape[1:])), 1).reshape(shape), device="cuda").to(dt)
     u = torch.zeros(shape, dtype=dt, device="cuda")
+    if args.path != "auto":
+        g.set_line_path(0, args.smoother, args.dtype, args.path)
     g.smooth(u, f, args.smoother, 1)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -46,6 +58,26 @@ def main():
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / max(args.steps - 1, 1)
     print(f"{args.smoother} {args.dtype} n={args.n} dim={args.dim}: {ms:.4f} ms/step over {args.steps - 1} timed steps")
+
+
+def solve_steps(args):
+    import torch
+    from . import inputs as I, mg
+    c = I.c_for_ratio(args.n, args.ratio, "wall")
+    x = I.wall_coords(args.n, c)
+    g = mg.Grid(x, x)
+    f = torch.tensor(I.rhs_gaussian(args.n + 1, args.n + 1, 1), device="cuda")
+    p = mg.default_params(smoother="tweed", nu1=1, nu2=1, precision=args.solve, tol=1e-10, inner_cycles=3,
+                          max_outer=20, max_cycles=200)
+    for k in range(args.steps):
+        u = torch.zeros_like(f)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = g.solve(u, f, p)
+        e1.record()
+        torch.cuda.synchronize()
+        print(f"solve {k}: {args.solve} n={args.n} status {r.status} cycles {r.cycles} outer {r.outer_iters} "
+              f"rel {r.rel_res:.2e} {e0.elapsed_time(e1):.3f} ms")
 
 
 def np_prod(a):

@@ -80,7 +80,7 @@ static void free_grid(Grid *g) {
   cudaFree(g->cinv);
   cudaFree(g->fd_tr);
   cudaFree(g->r64); cudaFree(g->e32); cudaFree(g->r32);
-  cudaFree(g->partial); cudaFree(g->scal);
+  cudaFree(g->partial); cudaFree(g->scal); cudaFree(g->dev_status);
   cudaFree(g->tile_rows); cudaFree(g->tile_d); cudaFree(g->tile_x);
   if (g->hpinned) cudaFreeHost(g->hpinned);
   delete g;
@@ -133,6 +133,7 @@ static mg_status setup_solver_state(Grid *g) {
   g->npartial = 4 * sms;
   TRY(dalloc(&g->partial, 2 * (size_t)g->npartial, "cudaMalloc(partials)"));
   TRY(dalloc(&g->scal, 4, "cudaMalloc(scalars)"));
+  TRY(dalloc(&g->dev_status, 1, "cudaMalloc(device status)"));
   TRY_CUDA("cudaMallocHost", cudaMallocHost(&g->hpinned, 4 * sizeof(double)));
   TRY_CUDA("cudaStreamCreate(graph stream)", cudaStreamCreateWithFlags(&g->gs, cudaStreamNonBlocking));
   TRY_CUDA("cudaEventCreate(fork)", cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming));

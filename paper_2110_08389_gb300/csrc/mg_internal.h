@@ -408,6 +408,7 @@ struct Grid {
   double *hpinned = nullptr;         // pinned host mirror of the norm results
   int npartial = 0;
   double *scal = nullptr;            // device scalars (reduced norms)
+  unsigned *dev_status = nullptr;    // bits set by kernels that found a fault (DEV_*); 0 when clean
   // scratch of the tiled line path, sized for the largest tile list
   size_t tile_cap = 0;               // tiles
   void *tile_rows = nullptr;         // 2 reduced rows per lane per tile (FP64 sized)

@@ -41,7 +41,8 @@ TRAFFIC = os.path.join(ROOT, "profiles", "tweed_pass_f32_4097_traffic.json")
 # the tiled kernels, their setup and layout, the launch helpers, and the tiled-path part
 # of the internal header (from its "Tiled line path" comment to the Level
 # struct, less the cluster pass's structs); the rest of that header (other
-# paths' structs, declarations) does not enter the tiled kernels
+# paths' structs, declarations) and the checked build's part of device_util.cuh
+# do not enter the tiled kernels of the timed build
 TRAFFIC_SOURCES = ["tiles.cu", "tile_setup.cu", "tile_host.h", "device_util.cuh", "mg_internal.h#tiled"]
 
 
@@ -57,6 +58,10 @@ def traffic_key():
             b = text.index(b"// Cluster pass", a)
             c = text.index(b"// Shapes of the line-solve kernel", b)
             text = text[a:b] + text[c:text.index(b"struct Level {", c)]
+        elif fn == "device_util.cuh":
+            # the checked build's part (compiled only with -DMG_CHECK)
+            a = text.index(b"#ifdef MG_CHECK\n")
+            text = text[:a] + text[text.index(b"#else\n", a):]
         h.update(text)
     return h.hexdigest()
 

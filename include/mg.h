@@ -282,6 +282,18 @@ void mg_default_params(mg_params *params);
 const char *mg_status_string(mg_status status);
 const char *mg_last_error(void);
 
+/* Checked builds.  The library built with -DMG_CHECK (build.py --checked)
+ * has every kernel validate the indices it decodes from its descriptors --
+ * node positions, junctions, tiles, chunk runs, sequences -- against its
+ * level before it uses them, in place of a memory checker (compute-sanitizer
+ * is not available everywhere).  A bad index is recorded in a device word and
+ * replaced by a safe one; every entry that launches kernels then waits for
+ * them and returns MG_ERR_INVALID_ARG.  mg_check_word() waits for the device
+ * and returns, and clears, the recorded bits: 0x80000000 marks a checked
+ * build, bit 0 a bad index since the last call.  Other builds return 0
+ * without waiting.  The paper has no counterpart; this is a test aid.       */
+unsigned mg_check_word(void);
+
 /* Residual norms for callers that cannot allocate device memory (the paper has
  * no counterpart; this is a deployment aid).  Some callers must not call
  * cudaMalloc at all -- code that runs inside a memory pool it does not own, a

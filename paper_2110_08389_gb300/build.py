@@ -4,6 +4,12 @@
 ``csrc/*.cu`` translation unit with nvcc in parallel and links
 ``_build/libtweedmg.so``.  Rebuilds only when a source or header is newer
 than the library.
+
+``build(checked=True)`` (``--checked``) builds the checked variant into
+``_build_check/libtweedmg.so``: compiled with ``-DMG_CHECK``, its kernels
+validate the indices they decode from their descriptors and record any that
+is out of range (see csrc/device_util.cuh); mg.py loads it when the
+environment variable TWEEDMG_LIB names it.
 """
 from __future__ import annotations
 
@@ -17,6 +23,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtweedmg.so")
+OUT_CHECK = os.path.join(HERE, "_build_check")
+LIB_CHECK = os.path.join(OUT_CHECK, "libtweedmg.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", f"-I{INCLUDE}"]
@@ -37,17 +45,19 @@ def _stale(srcs, target) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, checked: bool = False) -> str:
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    if not force and not _stale(srcs, LIB):
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+    out, lib = (OUT_CHECK, LIB_CHECK) if checked else (OUT, LIB)
+    if not force and not _stale(srcs, lib):
+        return lib
+    os.makedirs(out, exist_ok=True)
     cc = nvcc()
-    flags = FLAGS + (extra or [])
+    flags = FLAGS + (["-DMG_CHECK"] if checked else []) + (extra or [])
 
     def compile_one(src):
-        obj = os.path.join(OUT, os.path.basename(src) + ".o")
-        cmd = [cc, *ARCH, *flags, "-c", src, "-o", obj]
+        obj = os.path.join(out, os.path.basename(src) + ".o")
+        tu = [f'-DMG_CHECK_TU="{os.path.basename(src)}"'] if checked else []
+        cmd = [cc, *ARCH, *flags, *tu, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {os.path.basename(src)}:\n{r.stderr}")
@@ -57,16 +67,16 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
 
     print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None, checked="--checked" in sys.argv))

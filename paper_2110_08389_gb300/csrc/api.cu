@@ -543,7 +543,57 @@ static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params
 
 using namespace tmg;
 
+namespace tmg {
+
+struct CheckReader {
+  const char *tu;
+  unsigned (*read)(unsigned *line);
+};
+static std::vector<CheckReader> &check_readers() {
+  static std::vector<CheckReader> r;
+  return r;
+}
+void register_check_reader(const char *tu, unsigned (*reader)(unsigned *line)) {
+  check_readers().push_back({tu, reader});
+}
+unsigned check_words(std::string *where) {
+  unsigned w = 0;
+  for (const CheckReader &r : check_readers()) {
+    unsigned line = 0;
+    const unsigned v = r.read(&line);
+    if (v != 0u && where && where->empty()) *where = std::string(r.tu) + ", line " + std::to_string(line);
+    w |= v;
+  }
+  return w;
+}
+
+// In checked builds (-DMG_CHECK) every entry that launches kernels waits for
+// them and turns a recorded out-of-range index into MG_ERR_INVALID_ARG.
+mg_status checked(mg_status st) {
+#ifdef MG_CHECK
+  const cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_status("checked build: synchronize", e);
+  std::string where;
+  if (check_words(&where) != 0u) {
+    set_error_text(("checked build: a kernel met an index out of its level's range (" + where + ")").c_str());
+    return MG_ERR_INVALID_ARG;
+  }
+#endif
+  return st;
+}
+
+}  // namespace tmg
+
 extern "C" {
+
+unsigned mg_check_word(void) {
+#ifdef MG_CHECK
+  cudaDeviceSynchronize();
+  return check_words() | 0x80000000u;
+#else
+  return 0u;
+#endif
+}
 
 void mg_default_params(mg_params *p) {
   if (!p) return;
@@ -656,44 +706,44 @@ static bool bad_dtype(const mg_grid *g, int dtype) {
 
 mg_status mg_colour_pass(mg_grid *g, int level, int smoother, int colour, void *u, const void *f, int dtype,
                          void *stream) {
-  if (bad_level(g, level) || !u || !f || colour < 0 || colour > 1 || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
+  if (bad_level(g, level) || !u || !f || colour < 0 || colour > 1 || bad_dtype(g, dtype)) return checked(MG_ERR_INVALID_ARG);
   if (smoother == MG_SMOOTH_ALT_ZEBRA || smoother == MG_SMOOTH_ALT_TW || smoother < 0 || smoother > MG_SMOOTH_ALT_TW)
-    return MG_ERR_INVALID_ARG;
+    return checked(MG_ERR_INVALID_ARG);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (g->dim == 3) {
-    if (smoother != MG_SMOOTH_TWEED && smoother != MG_SMOOTH_WIREFRAME) return MG_ERR_UNSUPPORTED;
+    if (smoother != MG_SMOOTH_TWEED && smoother != MG_SMOOTH_WIREFRAME) return checked(MG_ERR_UNSUPPORTED);
     const int sm = smoother == MG_SMOOTH_WIREFRAME ? SM3_WIREFRAME : SM3_TWEED;
-    if (dtype == MG_F64) return colour_pass3<double>(*g, level, sm, colour, (double *)u, (const double *)f, s);
-    return colour_pass3<float>(*g, level, sm, colour, (float *)u, (const float *)f, s);
+    if (dtype == MG_F64) return checked(colour_pass3<double>(*g, level, sm, colour, (double *)u, (const double *)f, s));
+    return checked(colour_pass3<float>(*g, level, sm, colour, (float *)u, (const float *)f, s));
   }
-  if (dtype == MG_F64) return colour_pass<double>(*g, level, smoother, colour, (double *)u, (const double *)f, s);
-  return colour_pass<float>(*g, level, smoother, colour, (float *)u, (const float *)f, s);
+  if (dtype == MG_F64) return checked(colour_pass<double>(*g, level, smoother, colour, (double *)u, (const double *)f, s));
+  return checked(colour_pass<float>(*g, level, smoother, colour, (float *)u, (const float *)f, s));
 }
 
 mg_status mg_smooth(mg_grid *g, int level, int smoother, void *u, const void *f, int sweeps, int dtype,
                     void *stream) {
-  if (bad_level(g, level) || !u || !f || sweeps < 0 || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
-  if (smoother < 0 || smoother > MG_SMOOTH_ALT_TW) return MG_ERR_INVALID_ARG;
+  if (bad_level(g, level) || !u || !f || sweeps < 0 || bad_dtype(g, dtype)) return checked(MG_ERR_INVALID_ARG);
+  if (smoother < 0 || smoother > MG_SMOOTH_ALT_TW) return checked(MG_ERR_INVALID_ARG);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (g->dim == 3) {
     if (smoother != MG_SMOOTH_TWEED && smoother != MG_SMOOTH_WIREFRAME && smoother != MG_SMOOTH_ALT_TW)
-      return MG_ERR_UNSUPPORTED;
+      return checked(MG_ERR_UNSUPPORTED);
     const int order[2] = {smoother == MG_SMOOTH_WIREFRAME ? MG_SMOOTH_WIREFRAME : MG_SMOOTH_TWEED,
                           smoother == MG_SMOOTH_ALT_TW ? MG_SMOOTH_WIREFRAME : -1};
     for (int k = 0; k < sweeps; ++k)
       for (int m = 0; m < 2 && order[m] >= 0; ++m)
         for (int c = 0; c < 2; ++c) {
           const mg_status st = mg_colour_pass(g, level, order[m], c, u, f, dtype, stream);
-          if (st != MG_OK) return st;
+          if (st != MG_OK) return checked(st);
         }
-    return MG_OK;
+    return checked(MG_OK);
   }
   for (int k = 0; k < sweeps; ++k) {
     mg_status st = dtype == MG_F64 ? smooth<double>(*g, level, smoother, (double *)u, (const double *)f, s)
                                    : smooth<float>(*g, level, smoother, (float *)u, (const float *)f, s);
-    if (st != MG_OK) return st;
+    if (st != MG_OK) return checked(st);
   }
-  return MG_OK;
+  return checked(MG_OK);
 }
 
 mg_status mg_smooth_tweed(mg_grid *g, int level, void *u, const void *f, int sweeps, int dtype, void *stream) {
@@ -706,14 +756,14 @@ mg_status mg_smooth_wireframe(mg_grid *g, int level, void *u, const void *f, int
 
 mg_status mg_residual_restrict(mg_grid *g, int level, int restriction, const void *u, const void *f, void *fc,
                                void *uc, int dtype, void *stream) {
-  if (bad_level(g, level) || level + 1 >= g->nlev || !u || !f || !fc || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
-  if (restriction != MG_RESTRICT_HW && restriction != MG_RESTRICT_FW) return MG_ERR_INVALID_ARG;
+  if (bad_level(g, level) || level + 1 >= g->nlev || !u || !f || !fc || bad_dtype(g, dtype)) return checked(MG_ERR_INVALID_ARG);
+  if (restriction != MG_RESTRICT_HW && restriction != MG_RESTRICT_FW) return checked(MG_ERR_INVALID_ARG);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (g->dim == 3) {
-    if (restriction != MG_RESTRICT_FW) return MG_ERR_UNSUPPORTED;
+    if (restriction != MG_RESTRICT_FW) return checked(MG_ERR_UNSUPPORTED);
     if (dtype == MG_F64)
-      return residual_restrict3<double>(*g, level, (const double *)u, (const double *)f, (double *)fc, (double *)uc, s);
-    return residual_restrict3<float>(*g, level, (const float *)u, (const float *)f, (float *)fc, (float *)uc, s);
+      return checked(residual_restrict3<double>(*g, level, (const double *)u, (const double *)f, (double *)fc, (double *)uc, s));
+    return checked(residual_restrict3<float>(*g, level, (const float *)u, (const float *)f, (float *)fc, (float *)uc, s));
   }
   const Level &F = g->lev[level], &C = g->lev[level + 1];
   cudaError_t e = dtype == MG_F64
@@ -721,107 +771,107 @@ mg_status mg_residual_restrict(mg_grid *g, int level, int restriction, const voi
                                                          (double *)fc, (double *)uc, s)
                       : launch_residual_restrict<float>(F, C, restriction, (const float *)u, (const float *)f,
                                                         (float *)fc, (float *)uc, s);
-  return cuda_status("residual+restrict", e);
+  return checked(cuda_status("residual+restrict", e));
 }
 
 mg_status mg_prolong_add(mg_grid *g, int level, const void *uc, void *u, int dtype, void *stream) {
-  if (bad_level(g, level) || level + 1 >= g->nlev || !u || !uc || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
+  if (bad_level(g, level) || level + 1 >= g->nlev || !u || !uc || bad_dtype(g, dtype)) return checked(MG_ERR_INVALID_ARG);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (g->dim == 3) {
-    if (dtype == MG_F64) return prolong_add3<double>(*g, level, (const double *)uc, (double *)u, s);
-    return prolong_add3<float>(*g, level, (const float *)uc, (float *)u, s);
+    if (dtype == MG_F64) return checked(prolong_add3<double>(*g, level, (const double *)uc, (double *)u, s));
+    return checked(prolong_add3<float>(*g, level, (const float *)uc, (float *)u, s));
   }
   const Level &F = g->lev[level], &C = g->lev[level + 1];
   cudaError_t e = dtype == MG_F64 ? launch_prolong_add<double>(F, C, (const double *)uc, (double *)u, s)
                                   : launch_prolong_add<float>(F, C, (const float *)uc, (float *)u, s);
-  return cuda_status("prolong+correct", e);
+  return checked(cuda_status("prolong+correct", e));
 }
 
 mg_status mg_residual(mg_grid *g, int level, const void *u, const void *f, void *d, int dtype, void *stream) {
-  if (bad_level(g, level) || !u || !f || !d || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
+  if (bad_level(g, level) || !u || !f || !d || bad_dtype(g, dtype)) return checked(MG_ERR_INVALID_ARG);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (g->dim == 3) {
-    if (dtype == MG_F64) return residual3<double>(*g, level, (const double *)u, (const double *)f, (double *)d, s);
-    return residual3<float>(*g, level, (const float *)u, (const float *)f, (float *)d, s);
+    if (dtype == MG_F64) return checked(residual3<double>(*g, level, (const double *)u, (const double *)f, (double *)d, s));
+    return checked(residual3<float>(*g, level, (const float *)u, (const float *)f, (float *)d, s));
   }
   const Level &L = g->lev[level];
   cudaError_t e = dtype == MG_F64 ? launch_residual<double>(L, (const double *)u, (const double *)f, (double *)d, s)
                                   : launch_residual<float>(L, (const float *)u, (const float *)f, (float *)d, s);
-  return cuda_status("residual", e);
+  return checked(cuda_status("residual", e));
 }
 
 mg_status mg_coarse_solve(mg_grid *g, void *u, const void *f, int dtype, void *stream) {
-  if (!g || !u || !f || bad_dtype(g, dtype)) return MG_ERR_INVALID_ARG;
+  if (!g || !u || !f || bad_dtype(g, dtype)) return checked(MG_ERR_INVALID_ARG);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (g->dim == 3) {
-    if (dtype == MG_F64) return coarse_solve3<double>(*g, (double *)u, (const double *)f, s);
-    return coarse_solve3<float>(*g, (float *)u, (const float *)f, s);
+    if (dtype == MG_F64) return checked(coarse_solve3<double>(*g, (double *)u, (const double *)f, s));
+    return checked(coarse_solve3<float>(*g, (float *)u, (const float *)f, s));
   }
   cudaError_t e = dtype == MG_F64 ? launch_coarse_solve<double>(*g, (double *)u, (const double *)f, s)
                                   : launch_coarse_solve<float>(*g, (float *)u, (const float *)f, s);
-  return cuda_status("coarse solve", e);
+  return checked(cuda_status("coarse solve", e));
 }
 
 int mg_direct_level(const mg_grid *g) { return g && g->dim == 2 ? g->fd_level : -1; }
 
 mg_status mg_direct_solve(mg_grid *g, void *u, const void *f, void *stream) {
-  if (!g || !u || !f) return MG_ERR_INVALID_ARG;
-  if (g->dim != 2 || g->fd_level < 0) return MG_ERR_UNSUPPORTED;
-  return cuda_status("direct level solve",
-                     launch_direct_level(*g, (float *)u, (const float *)f, static_cast<cudaStream_t>(stream)));
+  if (!g || !u || !f) return checked(MG_ERR_INVALID_ARG);
+  if (g->dim != 2 || g->fd_level < 0) return checked(MG_ERR_UNSUPPORTED);
+  return checked(cuda_status("direct level solve",
+                     launch_direct_level(*g, (float *)u, (const float *)f, static_cast<cudaStream_t>(stream))));
 }
 
 mg_status mg_vcycle(mg_grid *g, void *u, const void *f, const mg_params *p, void *stream) {
-  if (!g || !u || !f) return MG_ERR_INVALID_ARG;
+  if (!g || !u || !f) return checked(MG_ERR_INVALID_ARG);
   mg_status st = check_params(g, p);
-  if (st != MG_OK) return st;
+  if (st != MG_OK) return checked(st);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (p->precision == MG_PREC_F64) return cycle_rec<double>(*g, *p, 0, (double *)u, (const double *)f, s);
-  return cycle_rec<float>(*g, *p, 0, (float *)u, (const float *)f, s);
+  if (p->precision == MG_PREC_F64) return checked(cycle_rec<double>(*g, *p, 0, (double *)u, (const double *)f, s));
+  return checked(cycle_rec<float>(*g, *p, 0, (float *)u, (const float *)f, s));
 }
 
 mg_status mg_solve(mg_grid *g, double *u, const double *f, const mg_params *p, mg_info *info, void *stream) {
-  if (!g || !u || !f) return MG_ERR_INVALID_ARG;
+  if (!g || !u || !f) return checked(MG_ERR_INVALID_ARG);
   mg_status st = check_params(g, p);
-  if (st != MG_OK) return st;
+  if (st != MG_OK) return checked(st);
   const auto t0 = std::chrono::steady_clock::now();
   st = solve_impl(*g, u, f, *p, info, static_cast<cudaStream_t>(stream));
   if (info) info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  return st;
+  return checked(st);
 }
 
 mg_status mg_solve_adjoint(mg_grid *g, double *lambda, const double *rhs, const mg_params *p, mg_info *info,
                            void *stream) {
-  if (!g || !lambda || !rhs) return MG_ERR_INVALID_ARG;
-  if (g->dim == 3) return MG_ERR_UNSUPPORTED;
+  if (!g || !lambda || !rhs) return checked(MG_ERR_INVALID_ARG);
+  if (g->dim == 3) return checked(MG_ERR_UNSUPPORTED);
   mg_status st = check_params(g, p);
-  if (st != MG_OK) return st;
-  if (!(g->prec_mask & 1)) return MG_ERR_INVALID_ARG;
+  if (st != MG_OK) return checked(st);
+  if (!(g->prec_mask & 1)) return checked(MG_ERR_INVALID_ARG);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const auto t0 = std::chrono::steady_clock::now();
-  if (!g->r64) return MG_ERR_INVALID_ARG;  // allocated by mg_setup_grid with FP64 enabled
+  if (!g->r64) return checked(MG_ERR_INVALID_ARG);  // allocated by mg_setup_grid with FP64 enabled
   // L^T = D L D^{-1} with D = diag(dx_i dy_j):  L mu = D^{-1} rhs, lambda = D mu
   cudaError_t e = launch_diag_scale(*g, g->r64, rhs, 1, s);
-  if (e != cudaSuccess) return cuda_status("adjoint scaling", e);
+  if (e != cudaSuccess) return checked(cuda_status("adjoint scaling", e));
   mg_params q = *p;
   q.use_initial_guess = 0;
   e = launch_diag_scale(*g, lambda, lambda, 0, s);  // zero boundary (interior is reset by the solve)
-  if (e != cudaSuccess) return cuda_status("adjoint scaling", e);
+  if (e != cudaSuccess) return checked(cuda_status("adjoint scaling", e));
   st = solve_impl(*g, lambda, g->r64, q, info, s);
-  if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return st;
+  if (st != MG_OK && st != MG_ERR_NOT_CONVERGED) return checked(st);
   e = launch_diag_scale(*g, lambda, lambda, 0, s);
-  if (e != cudaSuccess) return cuda_status("adjoint scaling", e);
+  if (e != cudaSuccess) return checked(cuda_status("adjoint scaling", e));
   if (info) info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  return st;
+  return checked(st);
 }
 
 mg_status mg_boundary_adjoint(mg_grid *g, const double *lambda, const double *grad_u, double *grad_g,
                               void *stream) {
-  if (!g || !lambda || !grad_u || !grad_g) return MG_ERR_INVALID_ARG;
-  if (g->dim == 3) return MG_ERR_UNSUPPORTED;
+  if (!g || !lambda || !grad_u || !grad_g) return checked(MG_ERR_INVALID_ARG);
+  if (g->dim == 3) return checked(MG_ERR_UNSUPPORTED);
   cudaError_t e = launch_boundary_adjoint(*g, lambda, grad_u, grad_g, static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) return cuda_status("boundary adjoint", e);
-  return MG_OK;
+  if (e != cudaSuccess) return checked(cuda_status("boundary adjoint", e));
+  return checked(MG_OK);
 }
 
 mg_status mg_pass_timer_begin(mg_grid *g, int level, int max_passes) {

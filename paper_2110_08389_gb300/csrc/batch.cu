@@ -435,7 +435,7 @@ mg_status mg_batch_solve(mg_batch *b, double *const *u, const double *const *f, 
     TRY_CUDA("cudaEventRecord(batch join)", cudaEventRecord(b->joins[i], b->streams[i]));
     TRY_CUDA("cudaStreamWaitEvent(batch join)", cudaStreamWaitEvent(s, b->joins[i], 0));
   }
-  return worst;
+  return checked(worst);
 }
 
 }  // extern "C"

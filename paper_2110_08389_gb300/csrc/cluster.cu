@@ -105,8 +105,14 @@ __device__ __forceinline__ void tile_rows(Smem &sm, const Args &a, int t, const 
                                           int lane) {
   const int nx1 = a.nx + 1;
   const Geo g(td.dir, a.cp, a.nx, a.ny);
-  const int m = ln.q1, fl = ln.flags;
+  const int fl = ln.flags;
+  // checked builds: a lane's run must lie inside the level (else it is skipped)
   const int base = COMPACT ? (int)ln.cbase : (int)td.base;
+  const int m = (ln.q1 == 0 || MG_OK_IF(ln.q1 <= 32 && ln.line >= 1 && ln.line <= (g.xrun ? a.ny : a.nx) - 1 &&
+                                        base >= 1 && base <= g.vmax - 1 && base + (ln.q1 - 1) * g.step >= 1 &&
+                                        base + (ln.q1 - 1) * g.step <= g.vmax - 1))
+                    ? ln.q1
+                    : 0;
   if (!COMPACT) {
     const int v = g.clampv(base + lane * g.step);
     sm.co[t][0][lane] = __ldg(g.lo_arr + v);
@@ -190,8 +196,14 @@ __device__ __forceinline__ void tile_expand(Smem &sm, const Args &a, int t, cons
                                             int lane) {
   const int nx1 = a.nx + 1;
   const Geo g(td.dir, a.cp, a.nx, a.ny);
-  const int m = ln.q1, fl = ln.flags;
+  const int fl = ln.flags;
+  // checked builds: a lane's run must lie inside the level (else it is skipped)
   const int base = COMPACT ? (int)ln.cbase : (int)td.base;
+  const int m = (ln.q1 == 0 || MG_OK_IF(ln.q1 <= 32 && ln.line >= 1 && ln.line <= (g.xrun ? a.ny : a.nx) - 1 &&
+                                        base >= 1 && base <= g.vmax - 1 && base + (ln.q1 - 1) * g.step >= 1 &&
+                                        base + (ln.q1 - 1) * g.step <= g.vmax - 1))
+                    ? ln.q1
+                    : 0;
   const int slot = t * 32 + lane;
   if (m > 0) {
     float d[32], x[32], cpv[32];
@@ -268,14 +280,23 @@ __global__ void __launch_bounds__(NT, 2) cluster_pass_kernel(const Args a) {
     const bool act = l < 4 && l < bd.nleg;
     CChain ch;
     ch.nseg = 0;
-    if (act) ch = a.chain[(size_t)cd.group * 128 + l * 32 + b];
+    if (act) {
+      ch = a.chain[(size_t)cd.group * 128 + l * 32 + b];
+      // checked builds: the leg's segments must be CTAs of this cluster and
+      // its rows must fit the (c', d') store (else the leg is skipped)
+      bool ok = ch.nseg <= CL_MAXSEG && (int)ch.roff + ch.nrow <= CL_LEGROWS;
+      for (int s = 0; s < CL_MAXSEG && ok; ++s) ok = s >= ch.nseg || ch.rank[s] < CL_CTAS;
+      if (!MG_OK_IF(ok)) ch.nseg = 0;
+    }
     // forward: normalised rows, pivot 1 - a c'_prev.  The rows are read where
     // they lie (remote loads only); (c', d') go to this CTA's own store.
     float cpv = 0.0f, dpv = 0.0f;
     int kr = ch.roff;
     for (int s = 0; s < ch.nseg; ++s) {
       const int rk = ch.rank[s];
-      const CSeg sg = a.seg[pseg0[rk] + ch.slot[s]];
+      CSeg sg = a.seg[pseg0[rk] + ch.slot[s]];
+      // checked builds: the segment's chunks must be slots of its CTA
+      if (!MG_OK_IF(sg.nchunk >= 1 && sg.slot0 + (sg.nchunk - 1) * sg.stride < SLOTS && sg.one <= 1)) sg.nchunk = 0;
       const int R = 2 * sg.nchunk - sg.one;
       const float4(*rows)[2] = prow[rk];
       for (int k0 = 0; k0 < R; k0 += LEG_BATCH) {
@@ -300,8 +321,9 @@ __global__ void __launch_bounds__(NT, 2) cluster_pass_kernel(const Args a) {
     }
     __syncthreads();
     // the junction row of Eq. mLThomas with each leg's last unknown
-    // x_last = d' - c' x_junction substituted
-    if (l == 0 && bd.junc) {
+    // x_last = d' - c' x_junction substituted (checked builds: the junction
+    // must lie inside the level, else the block's junction is skipped)
+    if (l == 0 && bd.junc && MG_OK_IF(bd.ji >= 1 && bd.ji <= a.nx - 1 && bd.jj >= 1 && bd.jj <= a.ny - 1)) {
       const int nx1 = a.nx + 1, i = bd.ji, j = bd.jj;
       const size_t p = (size_t)j * nx1 + i;
       unsigned att = 0;
@@ -331,7 +353,9 @@ __global__ void __launch_bounds__(NT, 2) cluster_pass_kernel(const Args a) {
     kr = ch.roff + ch.nrow;
     for (int s = ch.nseg - 1; s >= 0; --s) {
       const int rk = ch.rank[s];
-      const CSeg sg = a.seg[pseg0[rk] + ch.slot[s]];
+      CSeg sg = a.seg[pseg0[rk] + ch.slot[s]];
+      // checked builds: the segment's chunks must be slots of its CTA
+      if (!MG_OK_IF(sg.nchunk >= 1 && sg.slot0 + (sg.nchunk - 1) * sg.stride < SLOTS && sg.one <= 1)) sg.nchunk = 0;
       const int R = 2 * sg.nchunk - sg.one;
       float2 *chx = pchx[rk];
       kr -= R;

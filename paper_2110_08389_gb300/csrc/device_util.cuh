@@ -6,6 +6,59 @@
 
 namespace tmg {
 
+// Checked builds (compiled with -DMG_CHECK, see build.py): every kernel
+// validates the indices it decodes from its descriptors (node positions,
+// junctions, tiles, sequences) and the ranges it derives from the level's
+// shape before it touches memory with them.  A value out of range is
+// recorded in this translation unit's check word, with the source line of
+// the first check that failed, and replaced by the lower bound, so that the
+// access stays inside the arrays and the kernel runs on (no trap, no early
+// exit); the C ABI reads and clears the words after each call (mg_check_word)
+// and returns MG_ERR_INVALID_ARG.  In other builds MG_RANGE is the value
+// itself.
+#ifdef MG_CHECK
+#ifndef MG_CHECK_TU
+#define MG_CHECK_TU "?"
+#endif
+static __device__ unsigned g_check_word;
+static __device__ unsigned g_check_line;
+__device__ __forceinline__ void mg_check_fail(unsigned line) {
+  atomicOr(&g_check_word, 1u);
+  atomicCAS(&g_check_line, 0u, line);
+}
+__device__ __forceinline__ int mg_range(int v, int lo, int hi, unsigned line) {
+  if (v < lo || v > hi) {
+    mg_check_fail(line);
+    return lo;
+  }
+  return v;
+}
+#define MG_RANGE(v, lo, hi) ::tmg::mg_range((int)(v), (int)(lo), (int)(hi), __LINE__)
+// true if c holds; else records it (the caller then skips the work)
+__device__ __forceinline__ bool mg_ok_if(bool c, unsigned line) {
+  if (!c) mg_check_fail(line);
+  return c;
+}
+#define MG_OK_IF(c) ::tmg::mg_ok_if((c), __LINE__)
+namespace {
+unsigned read_check_word_tu(unsigned *line) {
+  unsigned v = 0, l = 0, z = 0;
+  if (cudaMemcpyFromSymbol(&v, g_check_word, sizeof(v)) != cudaSuccess) return ~0u;
+  cudaMemcpyFromSymbol(&l, g_check_line, sizeof(l));
+  cudaMemcpyToSymbol(g_check_word, &z, sizeof(z));
+  cudaMemcpyToSymbol(g_check_line, &z, sizeof(z));
+  *line = l;
+  return v;
+}
+struct CheckWordReg {
+  CheckWordReg() { register_check_reader(MG_CHECK_TU, &read_check_word_tu); }
+} g_check_word_reg;
+}  // namespace
+#else
+#define MG_RANGE(v, lo, hi) (v)
+#define MG_OK_IF(c) true
+#endif
+
 // The four coefficient arrays of a level (W_i, E_i over x; S_j, N_j over y).
 template <typename T>
 struct Coefs {

@@ -439,6 +439,15 @@ struct Grid {
 // colour pass; 1024^2: 45 vs 41 us).
 constexpr int TILE_MIN_SIDE = 1024;
 
+// Checked builds (-DMG_CHECK): each translation unit with kernels registers,
+// under its file name, a reader of its device check word and of the source
+// line of its first failed check (device_util.cuh); check_words() ORs and
+// clears them all (0 in other builds) and names the first site in *where.
+void register_check_reader(const char *tu, unsigned (*reader)(unsigned *line));
+unsigned check_words(std::string *where = nullptr);
+// st, or in checked builds MG_ERR_INVALID_ARG once a kernel recorded a bad index
+mg_status checked(mg_status st);
+
 // Kernels launched by this library in this process (mg_kernel_launches).
 extern std::atomic<unsigned long long> g_launches;
 inline void count_launch(unsigned long long n = 1) { g_launches.fetch_add(n, std::memory_order_relaxed); }

@@ -221,7 +221,8 @@ __device__ __forceinline__ void skel_cta(const WSkel3 *__restrict__ S, T *__rest
 template <typename T, int K, int W>
 __global__ void __launch_bounds__(32 * W) seq3_single_kernel(const WNode3 *__restrict__ nodes,
                                                              const WJunc3 *__restrict__ juncs, C6<T> cp, int nx1,
-                                                             int ny1, T *__restrict__ u, const T *__restrict__ f) {
+                                                             int ny1, int nz1, T *__restrict__ u,
+                                                             const T *__restrict__ f) {
   constexpr int NT = 32 * W, N = NT * K;
   extern __shared__ __align__(16) unsigned char sm3[];
   T *sa = reinterpret_cast<T *>(sm3);
@@ -241,7 +242,13 @@ __global__ void __launch_bounds__(32 * W) seq3_single_kernel(const WNode3 *__res
   } jb;
   jb.ijk = jbp->ijk;
   jb.adirs = jbp->adirs;
-  const int natt = jbp->natt;
+  int natt = jbp->natt;
+  // checked builds: the junction must be interior with at most 6 legs (else
+  // the sequence has none)
+  if (natt != 0 && !MG_OK_IF(natt <= 6 && (jb.ijk & 1023u) >= 1u && (int)(jb.ijk & 1023u) <= nx1 - 2 &&
+                             ((jb.ijk >> 10) & 1023u) >= 1u && (int)((jb.ijk >> 10) & 1023u) <= ny1 - 2 &&
+                             (jb.ijk >> 20) >= 1u && (int)(jb.ijk >> 20) <= nz1 - 2))
+    natt = 0;
   const bool has_j = natt != 0;
   T kp = T(0), cJ = T(1);
   int ji = 0, jj = 0, jk = 0;
@@ -257,7 +264,12 @@ __global__ void __launch_bounds__(32 * W) seq3_single_kernel(const WNode3 *__res
   // ---- 1. staging (thread t: nodes NT*q + t)
 #pragma unroll
   for (int q = 0; q < K; ++q) {
-    const uint2 dsc = __ldg(nd + NT * q + t);
+    uint2 dsc = __ldg(nd + NT * q + t);
+    // checked builds: a node must be an interior node (else its slot is unused)
+    if ((dsc.y & WN3_VALID) && !MG_OK_IF((dsc.x & 1023u) >= 1u && (int)(dsc.x & 1023u) <= nx1 - 2 &&
+                                          ((dsc.x >> 10) & 1023u) >= 1u && (int)((dsc.x >> 10) & 1023u) <= ny1 - 2 &&
+                                          (dsc.x >> 20) >= 1u && (int)(dsc.x >> 20) <= nz1 - 2))
+      dsc = make_uint2(0u, 0u);
     const unsigned fl = dsc.y;
     const bool valid = (fl & WN3_VALID) != 0u;
     const int i = (int)(dsc.x & 1023u), j = (int)((dsc.x >> 10) & 1023u), k = (int)(dsc.x >> 20);
@@ -383,7 +395,7 @@ __global__ void __launch_bounds__(32 * W) seq3_single_kernel(const WNode3 *__res
 template <typename T, int K, int W>
 __global__ void __launch_bounds__(32 * W, sizeof(T) == 4 ? 32 / W : 1) seq3_multi_kernel(const WNode3 *__restrict__ nodes,
                                                       const WJunc3 *__restrict__ juncs, const int *__restrict__ jofs,
-                                                      C6<T> cp, int nx1, int ny1, T *__restrict__ u,
+                                                      C6<T> cp, int nx1, int ny1, int nz1, T *__restrict__ u,
                                                       const T *__restrict__ f, const SkelArgs<T> sk) {
   pdl_trigger();
   if ((int)blockIdx.x < sk.nskel) {
@@ -403,12 +415,19 @@ __global__ void __launch_bounds__(32 * W, sizeof(T) == 4 ? 32 / W : 1) seq3_mult
   const int t = threadIdx.x, lane = t & 31, cta = (int)blockIdx.x - sk.nskel;
   const size_t plane = (size_t)nx1 * ny1;
   const uint2 *nd = reinterpret_cast<const uint2 *>(nodes) + (size_t)cta * N;
-  const int j0 = __ldg(jofs + cta), nj = __ldg(jofs + cta + 1) - j0;
+  const int j0 = __ldg(jofs + cta), nj_list = __ldg(jofs + cta + 1) - j0;
+  // checked builds: at most WJ3_MAX junctions per sequence (else none)
+  const int nj = MG_OK_IF(nj_list >= 0 && nj_list <= WJ3_MAX) ? nj_list : 0;
   pdl_wait();  // u and f from here on
   // ---- 1. staging (thread t: nodes NT*q + t)
 #pragma unroll
   for (int q = 0; q < K; ++q) {
-    const uint2 dsc = __ldg(nd + NT * q + t);
+    uint2 dsc = __ldg(nd + NT * q + t);
+    // checked builds: a node must be an interior node (else its slot is unused)
+    if ((dsc.y & WN3_VALID) && !MG_OK_IF((dsc.x & 1023u) >= 1u && (int)(dsc.x & 1023u) <= nx1 - 2 &&
+                                          ((dsc.x >> 10) & 1023u) >= 1u && (int)((dsc.x >> 10) & 1023u) <= ny1 - 2 &&
+                                          (dsc.x >> 20) >= 1u && (int)(dsc.x >> 20) <= nz1 - 2))
+      dsc = make_uint2(0u, 0u);
     const unsigned fl = dsc.y;
     const bool valid = (fl & WN3_VALID) != 0u;
     const int i = (int)(dsc.x & 1023u), j = (int)((dsc.x >> 10) & 1023u), k = (int)(dsc.x >> 20);
@@ -551,10 +570,11 @@ cudaError_t launch3_kw(const Grid3 &G, const Level3 &L, const WarpList3 &w, T *u
     const SkelArgs<T> sk{w.skel, reinterpret_cast<T *>(G.skel_scr), G.skel_len, w.nskel};
     return launch_pdl(seq3_multi_kernel<T, K, W>, dim3(w.nskel + w.nwarp), dim3(32 * W),
                       seq3_smem<T, K, W, true>(), s, (const WNode3 *)w.node, (const WJunc3 *)w.junc,
-                      (const int *)w.jofs, coefs3<T>(L), L.nx + 1, L.ny + 1, u, f, sk);
+                      (const int *)w.jofs, coefs3<T>(L), L.nx + 1, L.ny + 1, L.nz + 1, u, f, sk);
   } else {
     return launch_pdl(seq3_single_kernel<T, K, W>, dim3(w.nwarp), dim3(32 * W), seq3_smem<T, K, W, false>(), s,
-                      (const WNode3 *)w.node, (const WJunc3 *)w.junc, coefs3<T>(L), L.nx + 1, L.ny + 1, u, f);
+                      (const WNode3 *)w.node, (const WJunc3 *)w.junc, coefs3<T>(L), L.nx + 1, L.ny + 1, L.nz + 1, u,
+                      f);
   }
 }
 template <typename T, int K, bool MULTI>

@@ -280,7 +280,7 @@ template <typename T, int NT, bool SC>
 __global__ void __launch_bounds__(NT, NT == NT_SMALL ? 2 : 1)
     line_pass_kernel(const CtaWork *__restrict__ works, const ChunkDesc *__restrict__ chunks_all,
                      const JuncDesc *__restrict__ juncs_all, const VGroup *__restrict__ vgs_all, CoefP<T> cp,
-                     int nx1, T *__restrict__ u, const T *__restrict__ f) {
+                     int nx1, int ny1, T *__restrict__ u, const T *__restrict__ f) {
   using SM = LineSmem<T, NT, SC>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Row<T> *rv = reinterpret_cast<Row<T> *>(smem_raw);                        // 2*NT reduced rows
@@ -293,10 +293,27 @@ __global__ void __launch_bounds__(NT, NT == NT_SMALL ? 2 : 1)
   VGroup *svg = reinterpret_cast<VGroup *>(smem_raw + SM::rows + SM::nodes + SM::junc + SM::links + SM::descs);
 
   pdl_trigger();
-  const CtaWork w = works[blockIdx.x];
+  CtaWork w = works[blockIdx.x];
+  // checked builds: the CTA's counts must fit its shared memory (else it
+  // does nothing)
+  if (!MG_OK_IF(w.nchunk >= 0 && w.nchunk <= NT && w.nvg >= 0 && w.nvg <= NT && w.njunc >= 0 && w.njunc <= NT))
+    w.nchunk = w.nvg = w.njunc = 0;
   const JuncDesc *juncs = juncs_all + w.junc0;
   const int tid = threadIdx.x;
-  for (int t = tid; t < w.nchunk; t += NT) sc[t] = chunks_all[w.chunk0 + t];
+  for (int t = tid; t < w.nchunk; t += NT) {
+    ChunkDesc cd = chunks_all[w.chunk0 + t];
+#ifdef MG_CHECK
+    // checked builds: a chunk's run must lie among the interior nodes (else
+    // it is emptied)
+    const int dir = cd.flags & 3;
+    const int di = dir == DIR_PX ? 1 : dir == DIR_MX ? -1 : 0, dj = dir == DIR_PY ? 1 : dir == DIR_MY ? -1 : 0;
+    const int ie = cd.i0 + (cd.len - 1) * di, je = cd.j0 + (cd.len - 1) * dj;
+    if (cd.len > 0 && !MG_OK_IF(cd.len <= CMAX && cd.i0 >= 1 && cd.i0 <= nx1 - 2 && cd.j0 >= 1 &&
+                                cd.j0 <= ny1 - 2 && ie >= 1 && ie <= nx1 - 2 && je >= 1 && je <= ny1 - 2))
+      cd.len = 0;
+#endif
+    sc[t] = cd;
+  }
   for (int t = tid; t < w.nvg; t += NT) svg[t] = vgs_all[w.vg0 + t];
   pdl_wait();  // u and f from here on
   __syncthreads();
@@ -418,7 +435,13 @@ __global__ void __launch_bounds__(NT, NT == NT_SMALL ? 2 : 1)
 
   // ---- phase 2b: junction rows
   if (tid < w.njunc) {
-    const JuncDesc jd = juncs[tid];
+    JuncDesc jd = juncs[tid];
+    // checked builds: the junction must be interior with at most 4 chain ends
+    bool jok = jd.i >= 1 && jd.i <= nx1 - 2 && jd.j >= 1 && jd.j <= ny1 - 2 && jd.nend <= 4;
+    for (int e = 0; e < 4 && jok; ++e) jok = e >= jd.nend || jd.row[e] < 2 * NT;
+    if (!MG_OK_IF(jok)) {
+      jd.i = 1; jd.j = 1; jd.nend = 0;
+    }
     const int i = jd.i, j = jd.j;
     const size_t p = (size_t)j * nx1 + i;
     unsigned att = 0;
@@ -490,7 +513,7 @@ static cudaError_t launch_shape(const Level &L, const WorkList &w, T *u, const T
   auto kern = line_pass_kernel<T, NT, SC>;
   count_launch(1);
   return launch_pdl(kern, dim3(w.ncta), dim3(NT), smem, s, (const CtaWork *)w.cta, (const ChunkDesc *)w.chunk,
-                    (const JuncDesc *)w.junc, (const VGroup *)w.vg, level_coefs<T>(L), L.nx + 1, u, f);
+                    (const JuncDesc *)w.junc, (const VGroup *)w.vg, level_coefs<T>(L), L.nx + 1, L.ny + 1, u, f);
 }
 
 template <typename T>

@@ -203,7 +203,13 @@ __global__ void __launch_bounds__(32 * TWv<T>) tile_reduce(const TileDesc *__res
   const TileDesc td = tiles[t];
   const TileLane ln = lanes[(size_t)t * 32 + lane];
   const TileGeom<T> g(td, cp, nx, ny);
-  const int m = ln.q1, fl = ln.flags;
+  const int fl = ln.flags;
+  // checked builds: a lane's run must lie inside the level (else it is skipped)
+  const int m = (ln.q1 == 0 || MG_OK_IF(ln.q1 <= CMAX && td.dir < 4 && ln.line >= 1 &&
+                                        ln.line <= (g.xrun ? ny : nx) - 1 && g.v(0) >= 1 && g.v(0) <= g.vmax - 1 &&
+                                        g.v(ln.q1 - 1) >= 1 && g.v(ln.q1 - 1) <= g.vmax - 1))
+                    ? ln.q1
+                    : 0;
   T d[CMAX];
   stage_coefs(g, lane, cos[warp]);
   const T(&co)[2][32] = cos[warp];
@@ -278,13 +284,23 @@ __global__ void __launch_bounds__(32 * TWv<T>) tile_reduce(const TileDesc *__res
 // forward sweep writes (c', d') to a separate array so that the row loads of
 // later chunks do not wait for those stores.
 template <typename T>
-__global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__ blocks, CoefT<T> cp, int nx1,
+__global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__ blocks, int ntile, size_t nn,
+                                                   CoefT<T> cp, int nx1,
                                                    const TRow<T> *__restrict__ rows, T *cdp,
                                                    T *__restrict__ xscr, T *__restrict__ u, const T *__restrict__ f) {
   __shared__ T s_cp[4][32], s_dp[4][32], s_xj[32];
   pdl_trigger();
   const int l = threadIdx.x >> 5, b = threadIdx.x & 31;
-  const BlockDesc bd = blocks[(size_t)blockIdx.x * 32 + b];
+  BlockDesc bd = blocks[(size_t)blockIdx.x * 32 + b];
+  // checked builds: a block's legs must lie in the tile list and its junction
+  // inside the level (else the block is skipped)
+  if (bd.nleg > 0 || bd.junc) {
+    bool ok = bd.nleg <= 4 && bd.lane == b &&
+              (!bd.junc || (bd.ji >= 1 && bd.ji <= nx1 - 2 && bd.jj >= 1 && (size_t)(bd.jj + 1) * nx1 < nn));
+    for (int e = 0; e < 4 && ok; ++e)
+      ok = e >= bd.nleg || (size_t)bd.leg_tile0[e] + (bd.leg_len[e] + CMAX - 1) / CMAX <= (size_t)ntile;
+    if (!MG_OK_IF(ok)) { bd.nleg = 0; bd.junc = 0; }
+  }
   const bool active = l < bd.nleg;
   const int len = active ? bd.leg_len[l] : 0;
   const int nch = (len + CMAX - 1) / CMAX;
@@ -399,7 +415,13 @@ __global__ void __launch_bounds__(32 * TWv<T>) tile_expand(const TileDesc *__res
   const TileDesc td = tiles[t];
   const TileLane ln = lanes[(size_t)t * 32 + lane];
   const TileGeom<T> g(td, cp, nx, ny);
-  const int m = ln.q1, fl = ln.flags;
+  const int fl = ln.flags;
+  // checked builds: a lane's run must lie inside the level (else it is skipped)
+  const int m = (ln.q1 == 0 || MG_OK_IF(ln.q1 <= CMAX && td.dir < 4 && ln.line >= 1 &&
+                                        ln.line <= (g.xrun ? ny : nx) - 1 && g.v(0) >= 1 && g.v(0) <= g.vmax - 1 &&
+                                        g.v(ln.q1 - 1) >= 1 && g.v(ln.q1 - 1) <= g.vmax - 1))
+                    ? ln.q1
+                    : 0;
   stage_coefs(g, lane, cos[warp]);
   const T(&co)[2][32] = cos[warp];
   pdl_wait();  // the scratch and u from here on
@@ -456,7 +478,8 @@ cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &tl, 
                    (const TileLane *)tl.lane, tl.ntile, cp, L.nx, L.ny, u, f, rows, dscr);
   if (ev) cudaEventRecord(ev[1], s);
   if (e == cudaSuccess)
-    e = launch_pdl(tile_couple<T>, dim3(tl.ngroup), dim3(128), 0, s, (const BlockDesc *)tl.block, cp, nx1,
+    e = launch_pdl(tile_couple<T>, dim3(tl.ngroup), dim3(128), 0, s, (const BlockDesc *)tl.block, tl.ntile, L.nn,
+                   cp, nx1,
                    (const TRow<T> *)rows, cdp, xscr, u, f);
   if (ev) cudaEventRecord(ev[2], s);
   if (e == cudaSuccess && tl.ntile > 0)

@@ -46,7 +46,7 @@ __device__ __forceinline__ T by_dir(unsigned d, T e, T w, T n, T s) {
 // neighbours moved over) and the node's offset in u (-1 on unused slots).
 template <typename T, int K, int NT>
 __device__ __forceinline__ void stage_nodes(const uint2 *__restrict__ nd, int t, const Coefs<T> &cp, int nx1,
-                                            const T *__restrict__ u, const T *__restrict__ f, T *sa, T *sb, T *sc,
+                                            int ny1, const T *__restrict__ u, const T *__restrict__ f, T *sa, T *sb, T *sc,
                                             T *sd, T *sz, int *sp) {
   constexpr int U = K < 8 ? K : 8;
   uint2 cur[U];
@@ -62,6 +62,11 @@ __device__ __forceinline__ void stage_nodes(const uint2 *__restrict__ nd, int t,
     T fv[U], ue[U], uw[U], un[U], us[U], ce[U], cw[U], cn[U], cs[U];
 #pragma unroll
     for (int k = 0; k < U; ++k) {
+      // checked builds: a node must be an interior node of the level (else
+      // its slot is treated as unused)
+      if ((cur[k].y & WN_VALID) && !MG_OK_IF((cur[k].x & 0xFFFFu) >= 1u && (int)(cur[k].x & 0xFFFFu) <= nx1 - 2 &&
+                                               (cur[k].x >> 16) >= 1u && (int)(cur[k].x >> 16) <= ny1 - 2))
+        cur[k] = make_uint2(0u, 0u);
       const unsigned fl = cur[k].y;
       const int i = (int)(cur[k].x & 0xFFFFu), j = (int)(cur[k].x >> 16);
       const unsigned in = ((fl & WN_PRED) ? 1u << (fl & 3u) : 0u) | ((fl & WN_SUCC) ? 1u << ((fl >> 3) & 3u) : 0u) |
@@ -107,10 +112,19 @@ struct Junction {
   unsigned att = 0;  // directions from the junction to its attached nodes
   T kp = T(0), rJ = T(0), cJ = T(1), ce = T(0), cw = T(0), cn = T(0), cs = T(0);
   size_t p = 0;
-  __device__ __forceinline__ Junction(const WBlock *__restrict__ blks, int seq, int t, const Coefs<T> &cp, int nx1) {
+  __device__ __forceinline__ Junction(const WBlock *__restrict__ blks, int seq, int t, const Coefs<T> &cp, int nx1,
+                                      int ny1, int nslot) {
     jb = __ldg(reinterpret_cast<const uint4 *>(blks) + seq);
     has_j = (jb.y & 0xFFu) != 0u;
     natt = (int)((jb.y >> 8) & 0xFFu);
+    // checked builds: the junction must be interior, with at most 4 attached
+    // nodes inside the sequence (else the sequence has no junction)
+    if (has_j && !MG_OK_IF(natt <= 4 && (jb.x & 0xFFFFu) >= 1u && (int)(jb.x & 0xFFFFu) <= nx1 - 2 &&
+                           (jb.x >> 16) >= 1u && (int)(jb.x >> 16) <= ny1 - 2 && (int)(jb.z & 0xFFFFu) < nslot &&
+                           (int)(jb.z >> 16) < nslot && (int)(jb.w & 0xFFFFu) < nslot && (int)(jb.w >> 16) < nslot)) {
+      has_j = false;
+      natt = 0;
+    }
     const unsigned adirs = (jb.y >> 16) & 0xFFu;
     if (has_j && t < 4) {
       const int ji = (int)(jb.x & 0xFFFFu), jj = (int)(jb.x >> 16);
@@ -154,7 +168,7 @@ struct Junction {
 template <typename T, int K>
 __global__ void __launch_bounds__(32) warp_line_kernel(const WNode *__restrict__ nodes,
                                                        const WBlock *__restrict__ blks, Coefs<T> cp, int nx1,
-                                                       T *__restrict__ u, const T *__restrict__ f,
+                                                       int ny1, T *__restrict__ u, const T *__restrict__ f,
                                                        const PassArgs<T> *__restrict__ tab,
                                                        const int *__restrict__ active) {
   if (tab) {  // packed launch: blockIdx.y selects the problem
@@ -174,10 +188,10 @@ __global__ void __launch_bounds__(32) warp_line_kernel(const WNode *__restrict__
 
   pdl_trigger();
   // ---- the warp's junction
-  Junction<T> jn(blks, blockIdx.x, lane, cp, nx1);
+  Junction<T> jn(blks, blockIdx.x, lane, cp, nx1, ny1, N);
 
   // ---- 1. staging (waits for the previous kernel after its first descriptors)
-  stage_nodes<T, K, 32>(nd, lane, cp, nx1, u, f, sa, sb, sc, sd, sz, sp);
+  stage_nodes<T, K, 32>(nd, lane, cp, nx1, ny1, u, f, sa, sb, sc, sd, sz, sp);
   jn.rhs(lane, nx1, u, f);
   __syncwarp();
 
@@ -247,7 +261,7 @@ __global__ void __launch_bounds__(32) warp_line_kernel(const WNode *__restrict__
 template <typename T, int K, int W>
 __global__ void __launch_bounds__(32 * W) seq_line_kernel(const WNode *__restrict__ nodes,
                                                           const WBlock *__restrict__ blks, Coefs<T> cp, int nx1,
-                                                          T *__restrict__ u, const T *__restrict__ f,
+                                                          int ny1, T *__restrict__ u, const T *__restrict__ f,
                                                           const PassArgs<T> *__restrict__ tab,
                                                           const int *__restrict__ active) {
   if (tab) {  // packed launch: blockIdx.y selects the problem
@@ -268,9 +282,9 @@ __global__ void __launch_bounds__(32 * W) seq_line_kernel(const WNode *__restric
   const int t = threadIdx.x, lane = t & 31;
   const uint2 *nd = reinterpret_cast<const uint2 *>(nodes) + (size_t)blockIdx.x * N;
   pdl_trigger();
-  Junction<T> jn(blks, blockIdx.x, t, cp, nx1);
+  Junction<T> jn(blks, blockIdx.x, t, cp, nx1, ny1, N);
 
-  stage_nodes<T, K, NT>(nd, t, cp, nx1, u, f, sa, sb, sc, sd, sz, sp);
+  stage_nodes<T, K, NT>(nd, t, cp, nx1, ny1, u, f, sa, sb, sc, sd, sz, sp);
   jn.rhs(t, nx1, u, f);
   __syncthreads();
 
@@ -357,7 +371,7 @@ cudaError_t launch_k(const Level &L, const WarpList &w, const WarpLaunch<T> &a, 
   const size_t smem = (size_t)32 * K * (5 * sizeof(T) + sizeof(int));
   count_launch(1);
   return launch_pdl(warp_line_kernel<T, K>, dim3(w.nwarp, a.pk.count), dim3(32), smem, s, (const WNode *)w.node,
-                    (const WBlock *)w.blk, level_coefs<T>(L), L.nx + 1, a.u, a.f,
+                    (const WBlock *)w.blk, level_coefs<T>(L), L.nx + 1, L.ny + 1, a.u, a.f,
                     static_cast<const PassArgs<T> *>(a.pk.tab), a.pk.active);
 }
 
@@ -365,7 +379,7 @@ template <typename T, int K, int W>
 cudaError_t launch_kw(const Level &L, const WarpList &w, const WarpLaunch<T> &a, cudaStream_t s) {
   count_launch(1);
   return launch_pdl(seq_line_kernel<T, K, W>, dim3(w.nwarp, a.pk.count), dim3(32 * W), seq_smem<T, K, W>(), s,
-                    (const WNode *)w.node, (const WBlock *)w.blk, level_coefs<T>(L), L.nx + 1, a.u, a.f,
+                    (const WNode *)w.node, (const WBlock *)w.blk, level_coefs<T>(L), L.nx + 1, L.ny + 1, a.u, a.f,
                     static_cast<const PassArgs<T> *>(a.pk.tab), a.pk.active);
 }
 

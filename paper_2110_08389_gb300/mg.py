@@ -15,7 +15,8 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libtweedmg.so")
+# the library to load: the checked build when TWEEDMG_LIB says so (build.py)
+LIB_PATH = os.environ.get("TWEEDMG_LIB") or os.path.join(_HERE, "_build", "libtweedmg.so")
 
 # enums (include/mg.h)
 OK, ERR_INVALID_ARG, ERR_SIZE, ERR_CUDA, ERR_NOT_CONVERGED, ERR_NONFINITE, ERR_TIMEOUT, ERR_ALLOC, \
@@ -38,7 +39,7 @@ EXPORTS = ["mg_setup_grid", "mg_destroy", "mg_num_levels", "mg_level_shape", "mg
            "mg_default_params", "mg_status_string", "mg_last_error", "mg_kernel_launches",
            "mg_residual_norm_static", "mg_pass_timer_begin", "mg_pass_timer_end", "mg_boundary_adjoint", "mg_batch_create",
            "mg_batch_destroy", "mg_batch_solve", "mg_set_line_path", "mg_get_line_path", "mg_autotune",
-           "mg_level_dims", "mg_grid_dim", "mg_direct_level", "mg_direct_solve"]
+           "mg_level_dims", "mg_grid_dim", "mg_direct_level", "mg_direct_solve", "mg_check_word"]
 
 
 class MGError(RuntimeError):
@@ -111,6 +112,7 @@ def load(path: str = LIB_PATH):
         "mg_autotune": (i, [vp, i, i, i, ctypes.POINTER(ctypes.c_double), vp]),
         "mg_level_dims": (i, [vp, i, i64p]),
         "mg_grid_dim": (i, [vp]),
+        "mg_check_word": (ctypes.c_uint, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

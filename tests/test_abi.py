@@ -91,3 +91,15 @@ def test_default_params():
     from paper_2110_08389_gb300 import mg
     p = mg.default_params()
     assert (p.smoother, p.nu1, p.nu2, p.inner_cycles, p.early_stop, p.coarse_direct) == (mg.TWEED, 2, 2, 3, 0, 0)
+
+
+def test_checked_build_exports_and_reports_itself():
+    """The checked variant (build.py --checked) exports the same entry points;
+    mg_check_word needs no GPU in the plain build (returns 0)."""
+    from paper_2110_08389_gb300 import build
+    lib = ctypes.CDLL(build.build())
+    lib.mg_check_word.restype = ctypes.c_uint
+    assert lib.mg_check_word() == 0
+    checked = ctypes.CDLL(build.build(checked=True))
+    missing = [n for n in declared_functions() if not hasattr(checked, n)]
+    assert not missing, missing

@@ -80,6 +80,7 @@ static void free_grid(Grid *g) {
   cudaFree(g->cinv);
   cudaFree(g->fd_tr);
   cudaFree(g->r64); cudaFree(g->e32); cudaFree(g->r32);
+  cudaFree(g->u2); cudaFree(g->cd64); cudaFree(g->rpart);
   cudaFree(g->partial); cudaFree(g->scal); cudaFree(g->dev_status);
   cudaFree(g->tile_rows); cudaFree(g->tile_d); cudaFree(g->tile_x);
   if (g->hpinned) cudaFreeHost(g->hpinned);
@@ -221,6 +222,7 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
   if (want64) TRY(dalloc(&g->r64, nn0, "cudaMalloc(adjoint scratch)"));
   TRY(setup_direct_level(*g));
   TRY(setup_solver_state(g));
+  if (want32 && g->dim == 2) TRY(setup_refine_residual(*g));
   // block work lists of every line smoother on every level, so that no later
   // call allocates
   TRY_CUDA("setup scratch (latched error)", cudaGetLastError());
@@ -467,13 +469,21 @@ mg_status enqueue(SolveState &q) {
   } else {
     // FP32 cycles on the correction equation L e = r (e zeroed by the
     // residual kernel), FP64 residual and update
-    if (q.phase == 2) {
+    if (d3) {
+      if (q.phase == 2) {
+        TRY(run_cycles<float>(g, p, p.inner_cycles, g.e32, g.r32, q.s));
+        TRY(ir_update3(g, q.u, g.e32, q.s));
+      }
+      TRY(norms3(g, q.u, q.f, 0, g.r32, g.e32, q.s));
+    } else if (q.phase == 2) {
+      // the update u + e and the next residual in one launch, into the other iterate
       TRY(run_cycles<float>(g, p, p.inner_cycles, g.e32, g.r32, q.s));
-      if (d3) TRY(ir_update3(g, q.u, g.e32, q.s));
-      else TRY_CUDA("refinement update", launch_ir_update(g, q.u, g.e32, q.s));
+      double *cur = q.alt ? g.u2 : q.u, *nxt = q.alt ? q.u : g.u2;
+      TRY_CUDA("refinement update and residual", launch_refine_residual(g, cur, g.e32, nxt, q.f, q.s));
+      q.alt = !q.alt;
+    } else {
+      TRY_CUDA("refinement residual", launch_refine_residual(g, q.u, nullptr, nullptr, q.f, q.s));
     }
-    if (d3) TRY(norms3(g, q.u, q.f, 0, g.r32, g.e32, q.s));
-    else TRY_CUDA("refinement residual", launch_ir_residual(g, q.u, q.f, g.r32, g.e32, q.s));
   }
   return copy_norm(g, q.s);
 }
@@ -527,6 +537,20 @@ void consume_value(SolveState &q, double v) {
   }
 }
 
+// A finished solve whose iterate ended in Grid::u2 copies its interior back
+// into u (u keeps its own boundary: the data, corners included, which the
+// five-point stencil never reads and the refinement never writes into u2).
+mg_status finish_iterate(SolveState &q) {
+  if (!q.alt) return MG_OK;
+  q.alt = false;
+  const Level &L = q.g->lev[0];
+  const size_t pitch = (size_t)(L.nx + 1) * sizeof(double), first = (size_t)(L.nx + 1) + 1;
+  TRY_CUDA("cudaMemcpy2DAsync(iterate)",
+           cudaMemcpy2DAsync(q.u + first, pitch, q.g->u2 + first, pitch, (size_t)(L.nx - 1) * sizeof(double),
+                             (size_t)(L.ny - 1), cudaMemcpyDeviceToDevice, q.s));
+  return MG_OK;
+}
+
 static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params &p, mg_info *info,
                             cudaStream_t s) {
   SolveState q;
@@ -535,6 +559,10 @@ static mg_status solve_impl(Grid &g, double *u, const double *f, const mg_params
     TRY(enqueue(q));
     TRY_CUDA("cudaStreamSynchronize", cudaStreamSynchronize(s));
     consume(q);
+  }
+  if (q.alt) {
+    TRY(finish_iterate(q));
+    TRY_CUDA("cudaStreamSynchronize", cudaStreamSynchronize(s));
   }
   return q.st;
 }

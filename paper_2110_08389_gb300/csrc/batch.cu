@@ -30,9 +30,10 @@ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 // Table bytes one problem can take in a packed group (every array of a group
 // starts on 16 bytes: at most 16 bytes of padding per array).
 size_t problem_table_bytes(const Grid &g) {
-  const size_t L = (size_t)g.nlev, arrays = 3 * L + 8;
+  const size_t L = (size_t)g.nlev, arrays = 3 * L + 9;
   return L * (sizeof(PassArgs<float>) + sizeof(RRArgs<float>) + sizeof(ProlongArgs<float>)) +
-         sizeof(CoarseArgs<float>) + sizeof(NormArgs) + sizeof(UpdateArgs) + sizeof(int) + sizeof(double) +
+         sizeof(CoarseArgs<float>) + sizeof(NormArgs) + sizeof(UpdateArgs) + sizeof(RefineArgs) + sizeof(int) +
+         sizeof(double) +
          16 * arrays;
 }
 
@@ -83,7 +84,7 @@ struct Group {
   mg_params p{};
   size_t base = 0;           // region of the batch's tables
   std::vector<size_t> pass, rr, pr;  // per-level table offsets within the region
-  size_t coarse = 0, norm = 0, upd = 0, active = 0, out = 0, end = 0;
+  size_t coarse = 0, norm = 0, upd = 0, refine = 0, active = 0, out = 0, end = 0;
   cudaStream_t s = nullptr;
   cudaGraphExec_t exec = nullptr;
   unsigned long long graph_launches = 0;
@@ -183,6 +184,7 @@ void build_tables(mg_batch &b, Group &G, double *const *u, const double *const *
   G.coarse = take(P * sizeof(CoarseArgs<float>));
   G.norm = take(P * sizeof(NormArgs));
   G.upd = take(P * sizeof(UpdateArgs));
+  G.refine = take(P * sizeof(RefineArgs));
   G.active = take(P * sizeof(int));
   G.out = take(P * sizeof(double));
   G.end = o;
@@ -202,9 +204,12 @@ void build_tables(mg_batch &b, Group &G, double *const *u, const double *const *
     reinterpret_cast<CoarseArgs<float> *>(h + G.coarse)[k] =
         CoarseArgs<float>{level_coefs<double>(Lc), g.cinv, lu(nl - 1), lf(nl - 1)};
     reinterpret_cast<NormArgs *>(h + G.norm)[k] =
-        NormArgs{level_coefs<double>(g.lev[0]), g.lev[0].WE64, u[i], f[i], g.r32, g.e32, g.partial,
+        NormArgs{level_coefs<double>(g.lev[0]), g.lev[0].WE64, u[i], f[i], g.partial,
                  reinterpret_cast<double *>(b.dev + G.base + G.out) + k};
     reinterpret_cast<UpdateArgs *>(h + G.upd)[k] = UpdateArgs{u[i], g.e32};
+    reinterpret_cast<RefineArgs *>(h + G.refine)[k] =
+        RefineArgs{level_coefs<double>(g.lev[0]), g.cd64, u[i], g.u2, g.e32, f[i], g.r32, g.e32, g.rpart,
+                   reinterpret_cast<double *>(b.dev + G.base + G.out) + k};
     reinterpret_cast<int *>(h + G.active)[k] = 1;
   }
 }
@@ -256,7 +261,8 @@ mg_status group_enqueue(mg_batch &b, Group &G) {
   char *h = b.host + G.base;
   int phase = -1;
   for (int k = 0; k < P; ++k) {
-    reinterpret_cast<int *>(h + G.active)[k] = G.q[k].done ? 0 : 1;
+    // 2: the member's iterate is in its Grid::u2 (refine_residual_kernel)
+    reinterpret_cast<int *>(h + G.active)[k] = G.q[k].done ? 0 : (G.q[k].alt ? 2 : 1);
     if (!G.q[k].done) phase = G.q[k].phase;
   }
   cudaStream_t s = G.s;
@@ -269,14 +275,23 @@ mg_status group_enqueue(mg_batch &b, Group &G) {
     for (auto &x : G.q)
       if (x.info) { x.info->cycles = 0; x.info->outer_iters = 0; x.info->history_len = 0; x.info->rel_res = 0; x.info->conv_factor = 0; }
     if (!G.p.use_initial_guess) st = cuda_status("zero u (packed)", launch_zero_interior_packed(g, pk(b, G, G.upd), s));
-    if (st == MG_OK) st = cuda_status("norm(f - B g) (packed)", launch_norms_packed(g, 1, 0, pk(b, G, G.norm), s));
+    if (st == MG_OK) st = cuda_status("norm(f - B g) (packed)", launch_norms_packed(g, 1, pk(b, G, G.norm), s));
   } else {
     if (phase == 2) {
       st = cuda_status("cudaGraphLaunch (packed cycles)", cudaGraphLaunch(G.exec, s));
       if (st == MG_OK) count_launch(G.graph_launches);
-      if (st == MG_OK) st = cuda_status("refinement update (packed)", launch_ir_update_packed(g, pk(b, G, G.upd), s));
+      std::vector<float *> e32s(P, nullptr);
+      for (int k = 0; k < P; ++k)
+        if (!G.q[k].done) e32s[k] = G.q[k].g->e32;
+      if (st == MG_OK)
+        st = cuda_status("refinement update and residual (packed)",
+                         launch_refine_residual_packed(g, true, pk(b, G, G.refine), e32s.data(), s));
+      for (auto &x : G.q)
+        if (!x.done) x.alt = !x.alt;
+    } else if (st == MG_OK) {
+      st = cuda_status("refinement residual (packed)", launch_refine_residual_packed(g, false, pk(b, G, G.refine),
+                                                                                   nullptr, s));
     }
-    if (st == MG_OK) st = cuda_status("refinement residual (packed)", launch_norms_packed(g, 0, 1, pk(b, G, G.norm), s));
   }
   if (st != MG_OK) return st;
   return cuda_status("cudaMemcpyAsync(norms, packed)", cudaMemcpyAsync(h + G.out, b.dev + G.base + G.out,
@@ -351,7 +366,8 @@ mg_status mg_batch_solve(mg_batch *b, double *const *u, const double *const *f, 
     for (int i = 0; i < n; ++i) {
       if (used[i]) continue;
       const mg_params &p = q[i].p;
-      const bool packable = p.precision == MG_PREC_F32_REFINE && !p.coarse_direct && warp_everywhere(*q[i].g, p.smoother);
+      const bool packable = p.precision == MG_PREC_F32_REFINE && !p.coarse_direct && q[i].g->dim == 2 &&
+                            warp_everywhere(*q[i].g, p.smoother);
       Group G;
       G.members.push_back(i);
       used[i] = true;
@@ -424,6 +440,10 @@ mg_status mg_batch_solve(mg_batch *b, double *const *u, const double *const *f, 
         active += q[i].done ? 0 : 1;
       }
   }
+  // iterates that ended in a member's Grid::u2 go back to its u, on its stream
+  for (auto &G : groups)
+    for (auto &x : G.q) TRY(finish_iterate(x));
+  for (int i : single) TRY(finish_iterate(q[i]));
   for (auto &G : groups)
     for (size_t m = 0; m < G.members.size(); ++m) q[G.members[m]] = G.q[m];
   for (int i = 0; i < n; ++i)

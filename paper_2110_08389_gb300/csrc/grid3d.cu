@@ -25,6 +25,7 @@
 // exactly: lines, stars and rings on the warp path (a ring as the line left
 // when one node is taken out, that node then a junction with two attached
 // ends), skeletons by one CTA each (Thomas per edge, then the corners).
+#include "fp_bits.h"
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(N3_THREADS) norm3_stage1(C6<double> c, int nx,
         r -= cw * u[p - 1] + ce * u[p + 1] + cs * u[p - nx1] + cn * u[p + nx1] + cb * u[p - plane] +
              ct * u[p + plane] - cc * u[p];
       }
-      if (r32) { r32[p] = (float)r; e32[p] = 0.0f; }
+      if (r32) { r32[p] = narrow_rne(r); e32[p] = 0.0f; }
       s = fma(r, r, s);
     }
   }
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(T3) interior3_kernel(int nx, int ny, double *_
   const int i = 1 + blockIdx.x * T3 + threadIdx.x, j = 1 + blockIdx.y, k = 1 + blockIdx.z;
   if (i >= nx) return;
   const size_t p = ((size_t)k * (ny + 1) + j) * (nx + 1) + i;
-  u[p] = update ? u[p] + (double)e[p] : 0.0;
+  u[p] = update ? u[p] + widen_exact(e[p]) : 0.0;
 }
 
 dim3 interior_grid(const Level3 &L) { return dim3((L.nx - 1 + T3 - 1) / T3, L.ny - 1, L.nz - 1); }

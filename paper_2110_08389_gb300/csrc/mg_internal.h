@@ -404,6 +404,12 @@ struct Grid {
   // finest-level FP64/FP32 scratch for the refinement loop and norms
   double *r64 = nullptr;             // adjoint scratch: the scaled right-hand side (finest)
   float *e32 = nullptr, *r32 = nullptr;
+  // FP32+refine on 2D grids: the second FP64 iterate (the refinement writes
+  // u + e here, then back, alternately), the diagonal W_i + E_i + S_j + N_j
+  // per node, and the tiling of the fused residual kernel (rows per CTA, CTA
+  // grid) with its own partial sums
+  double *u2 = nullptr, *cd64 = nullptr, *rpart = nullptr;
+  int rr_rows = 0, rr_gx = 0, rr_gy = 0;
   double *partial = nullptr;         // per-CTA partial sums (deterministic norm)
   double *hpinned = nullptr;         // pinned host mirror of the norm results
   int npartial = 0;
@@ -543,11 +549,14 @@ cudaError_t launch_coarse_solve(const Grid &g, T *u, const T *f, cudaStream_t s)
 cudaError_t launch_resnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s);
 // ||f - B u_b||^2: the right-hand side of the interior system (u's interior taken as 0)
 cudaError_t launch_rhsnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s);
-// Refinement: r32 = float(f - L u64) and the FP64 norms of f - L u64 into scal.
-cudaError_t launch_ir_residual(const Grid &g, const double *u, const double *f, float *r32, float *e32,
-                               cudaStream_t s);
-// u64 += e32 on interior nodes.
-cudaError_t launch_ir_update(const Grid &g, double *u, const float *e, cudaStream_t s);
+// Refinement residual of the finest 2D level with the update fused: v = u + e
+// (e NULL: v = u), r = f - L v in FP64, r32 = float(r), the FP64 norms of r
+// into scal; with e, v goes to uo and e32 is zeroed afterwards, else e32 is
+// zeroed in the kernel.  setup_refine_residual sizes its tiling and computes
+// cd64 (setup time).
+cudaError_t launch_refine_residual(const Grid &g, const double *u, const float *e, double *uo, const double *f,
+                                   cudaStream_t s);
+mg_status setup_refine_residual(Grid &g);
 cudaError_t launch_boundary_adjoint(const Grid &g, const double *lam, const double *gu, double *gg, cudaStream_t s);
 // a[interior] *= scale_x[i]*scale_y[j] (adjoint diagonal scalings), boundary := 0.
 cudaError_t launch_diag_scale(const Grid &g, double *out, const double *in, int inverse,

@@ -37,10 +37,18 @@ struct NormArgs {  // FP64 norms (and refinement residual) of the finest level
   Coefs<double> c;
   const double *we;  // W_i + E_i per column
   const double *u, *f;
+  double *part, *out;
+};
+struct RefineArgs {  // refinement residual with the update fused (transfer.cu)
+  Coefs<double> c;
+  const double *cd;  // W_i + E_i + S_j + N_j per node (Grid::cd64)
+  double *ua, *ub;   // the two FP64 iterates: read one, write the other
+  const float *e;    // FP32 correction (NULL: residual of the iterate alone)
+  const double *f;
   float *r32, *e32;
   double *part, *out;
 };
-struct UpdateArgs {  // u64 += e32, or u64 interior := 0
+struct UpdateArgs {  // u64 interior := 0 (e unused)
   double *u;
   const float *e;
 };
@@ -64,8 +72,12 @@ cudaError_t launch_prolong_add_packed(const Level &F, const Level &C, const Pack
 template <typename T>
 cudaError_t launch_coarse_solve_packed(const Grid &g, const PackedLaunch &pk, cudaStream_t s);
 // norms: bnd_only as launch_rhsnorm64; with_r32: the refinement residual
-cudaError_t launch_norms_packed(const Grid &g, int bnd_only, int with_r32, const PackedLaunch &pk, cudaStream_t s);
-cudaError_t launch_ir_update_packed(const Grid &g, const PackedLaunch &pk, cudaStream_t s);
+cudaError_t launch_norms_packed(const Grid &g, int bnd_only, const PackedLaunch &pk, cudaStream_t s);
+// The refinement residual of every active member (update: the FP32
+// correction added first; active flag 1 reads ua and writes ub, 2 the
+// reverse), its r32 and FP64 norm; then each member's e32 zeroed.
+cudaError_t launch_refine_residual_packed(const Grid &g, bool update, const PackedLaunch &pk,
+                                          float *const *e32s, cudaStream_t s);
 cudaError_t launch_zero_interior_packed(const Grid &g, const PackedLaunch &pk, cudaStream_t s);
 
 }  // namespace tmg

@@ -25,6 +25,7 @@ struct SolveState {
   mg_status st = MG_OK;
   double fn = 0.0, rel = 0.0, rel0 = 0.0, prev = 0.0;  // prev: rel before the last step
   int cycles = 0, outer = 0;
+  bool alt = false;  // FP32+refine, 2D: the iterate lives in Grid::u2, not in u
 };
 
 // The early stop (mg_params.early_stop): from the third step on, true when
@@ -57,6 +58,9 @@ mg_status enqueue(SolveState &q);
 // read back otherwise (consume_value)
 void consume(SolveState &q);
 void consume_value(SolveState &q, double v);
+// Enqueues the copy of a finished solve's iterate from Grid::u2 back into u
+// when it ended there (SolveState::alt).
+mg_status finish_iterate(SolveState &q);
 mg_status cuda_status(const char *where, cudaError_t e);
 
 }  // namespace tmg

@@ -9,13 +9,15 @@
 //                            (5), fused as the paper suggests)
 //   coarse_solve_kernel      u = L_0^{-1} (f - boundary terms) with the dense
 //                            inverse prepared at setup (FP64)
-//   resnorm / ir_residual    FP64 sum of squares of the defect with a
-//                            fixed-order reduction (deterministic), optionally
-//                            writing the FP32 copy of the defect and zeroing
-//                            the FP32 correction for the refinement loop
-//   ir_update                u64 += e32
+//   resnorm                  FP64 sum of squares of the defect with a
+//                            fixed-order reduction (deterministic)
+//   refine_residual          the refinement step's update and FP64 residual
+//                            in one launch (u + e, f - L(u + e), its FP32
+//                            copy and norm), the iterate alternating between
+//                            two FP64 arrays
 #include <algorithm>
 
+#include "fp_bits.h"
 #include "packed.h"
 
 namespace tmg {
@@ -317,18 +319,16 @@ __device__ __forceinline__ double block_sum(double s) {
 // bnd_only: r = f - B u_b, the boundary neighbours alone, i.e. the residual of
 // u with its interior taken as zero -- the scale of the relative residual).
 // CTA b takes interior rows 1 + b, 1 + b + gridDim.x, ...; every thread its
-// columns in order, so the result does not depend on timing.  With r32 set
-// (refinement mode) it also stores float(r) and zeroes the FP32 correction
-// e32 for the cycles that follow.  FP64 issue is the bound on GB300 (about
-// two FP64 operations per SM per clock): the defect takes 7 per node, with
-// W_i + E_i per column precomputed (we) and f folded into the FMA chain,
+// columns in order, so the result does not depend on timing.  FP64 issue is
+// the bound on GB300 (about two FP64 operations per SM per clock): the defect
+// takes 6 per node, with W_i + E_i per column precomputed (we) and f folded
+// into the FMA chain,
 //   r = f + C u_c - W u_w - E u_e - S u_s - N u_n,  C = (W + E) + (S + N),
 // and the sum of squares one more.
 __global__ void __launch_bounds__(NORM_THREADS) norm_stage1(CoefQ<double> c, const double *__restrict__ we,
                                                             int nx, int ny,
                                                             const double *__restrict__ u,
                                                             const double *__restrict__ f, int bnd_only,
-                                                            float *__restrict__ r32, float *__restrict__ e32,
                                                             double *__restrict__ part,
                                                             const NormArgs *__restrict__ tab,
                                                             const int *__restrict__ active) {
@@ -336,23 +336,52 @@ __global__ void __launch_bounds__(NORM_THREADS) norm_stage1(CoefQ<double> c, con
     if (!active[blockIdx.y]) return;
     const NormArgs a = tab[blockIdx.y];
     c = a.c; we = a.we; u = a.u; f = a.f; part = a.part;
-    if (r32) { r32 = a.r32; e32 = a.e32; }
   }
   const int nx1 = nx + 1;
   double s = 0.0;
+  // f - B g: only the boundary neighbours of u (its interior taken as 0), at
+  // the nodes next to the boundary; elsewhere r = f.  Those nodes take their
+  // own loops (rows 1 and ny - 1; columns 1 and nx - 1 by thread 0), so that
+  // the FP64 operations of the boundary terms are not issued, predicated off,
+  // at every node.
+  auto rhs_edge = [&](int i, int j) {
+    const size_t p = (size_t)j * nx1 + i;
+    double r = f[p];
+    if (i == 1) r -= __ldg(c.W + i) * u[p - 1];
+    if (i == nx - 1) r -= __ldg(c.E + i) * u[p + 1];
+    if (j == 1) r -= __ldg(c.S + j) * u[p - nx1];
+    if (j == ny - 1) r -= __ldg(c.N + j) * u[p + nx1];
+    return r;
+  };
   for (int j = 1 + blockIdx.x; j < ny; j += gridDim.x) {
     const double sj = __ldg(c.S + j), nj = __ldg(c.N + j), snj = sj + nj;
     const size_t row = (size_t)j * nx1;
+    if (bnd_only) {
+      if (j == 1 || j == ny - 1) {
+        for (int i = 1 + threadIdx.x; i < nx; i += NORM_THREADS) {
+          const double r = rhs_edge(i, j);
+          s = fma(r, r, s);
+        }
+      } else {
+        for (int i = 2 + threadIdx.x; i < nx - 1; i += NORM_THREADS) {
+          const double r = f[row + i];
+          s = fma(r, r, s);
+        }
+        if (threadIdx.x == 0) {
+          const double r1 = rhs_edge(1, j);
+          s = fma(r1, r1, s);
+          if (nx - 1 > 1) {
+            const double r2 = rhs_edge(nx - 1, j);
+            s = fma(r2, r2, s);
+          }
+        }
+      }
+      continue;
+    }
     for (int i = 1 + threadIdx.x; i < nx; i += NORM_THREADS) {
       const size_t p = row + i;
       double r = f[p];
-      if (bnd_only) {
-        // f - B g: only the boundary neighbours of u (its interior taken as 0)
-        if (i == 1) r -= __ldg(c.W + i) * u[p - 1];
-        if (i == nx - 1) r -= __ldg(c.E + i) * u[p + 1];
-        if (j == 1) r -= sj * u[p - nx1];
-        if (j == ny - 1) r -= nj * u[p + nx1];
-      } else if (u) {
+      if (u) {
         const double cc = __ldg(we + i) + snj;
         r = fma(cc, u[p], r);
         r = fma(-__ldg(c.W + i), u[p - 1], r);
@@ -360,7 +389,6 @@ __global__ void __launch_bounds__(NORM_THREADS) norm_stage1(CoefQ<double> c, con
         r = fma(-sj, u[p - nx1], r);
         r = fma(-nj, u[p + nx1], r);
       }
-      if (r32) { r32[p] = (float)r; e32[p] = 0.0f; }
       s = fma(r, r, s);
     }
   }
@@ -383,40 +411,42 @@ __global__ void __launch_bounds__(NORM_THREADS) norm_stage2(const double *__rest
   if (threadIdx.x == 0) out[0] = s;
 }
 
-static cudaError_t norms(const Grid &g, const double *u, const double *f, int bnd_only, float *r32, float *e32,
-                         cudaStream_t s) {
+// norm_stage2 for packed refinement launches: each member's partials and output
+__global__ void __launch_bounds__(NORM_THREADS) norm_stage2_refine(int npart, const RefineArgs *__restrict__ tab,
+                                                                   const int *__restrict__ active) {
+  if (!active[blockIdx.x]) return;
+  const double *part = tab[blockIdx.x].part;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < npart; k += NORM_THREADS) s += part[k];
+  s = block_sum(s);
+  if (threadIdx.x == 0) tab[blockIdx.x].out[0] = s;
+}
+
+static cudaError_t norms(const Grid &g, const double *u, const double *f, int bnd_only, cudaStream_t s) {
   const Level &L = g.lev[0];
-  norm_stage1<<<g.npartial, NORM_THREADS, 0, s>>>(cq<double>(L), L.WE64, L.nx, L.ny, u, f, bnd_only, r32, e32,
-                                                  g.partial, nullptr, nullptr);
+  norm_stage1<<<g.npartial, NORM_THREADS, 0, s>>>(cq<double>(L), L.WE64, L.nx, L.ny, u, f, bnd_only, g.partial,
+                                                  nullptr, nullptr);
   norm_stage2<<<1, NORM_THREADS, 0, s>>>(g.partial, g.npartial, g.scal, nullptr, nullptr);
   count_launch(2);
   return cudaGetLastError();
 }
 
-// Packed: with_r32 selects the refinement residual (r32 and e32 from each
-// problem's arguments; a non-null placeholder tells the kernel to write them).
-cudaError_t launch_norms_packed(const Grid &g, int bnd_only, int with_r32, const PackedLaunch &pk, cudaStream_t s) {
+cudaError_t launch_norms_packed(const Grid &g, int bnd_only, const PackedLaunch &pk, cudaStream_t s) {
   if (pk.count == 0) return cudaSuccess;
   const Level &L = g.lev[0];
   const NormArgs *tab = static_cast<const NormArgs *>(pk.tab);
-  float *mark = with_r32 ? reinterpret_cast<float *>(g.r32) : nullptr;
   norm_stage1<<<dim3(g.npartial, pk.count), NORM_THREADS, 0, s>>>(cq<double>(L), L.WE64, L.nx, L.ny, nullptr,
-                                                                  nullptr, bnd_only, mark, mark, nullptr, tab,
-                                                                  pk.active);
+                                                                  nullptr, bnd_only, nullptr, tab, pk.active);
   norm_stage2<<<pk.count, NORM_THREADS, 0, s>>>(nullptr, g.npartial, nullptr, tab, pk.active);
   count_launch(2);
   return cudaGetLastError();
 }
 
 cudaError_t launch_resnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s) {
-  return norms(g, u, f, 0, nullptr, nullptr, s);
+  return norms(g, u, f, 0, s);
 }
 cudaError_t launch_rhsnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s) {
-  return norms(g, u, f, 1, nullptr, nullptr, s);
-}
-cudaError_t launch_ir_residual(const Grid &g, const double *u, const double *f, float *r32, float *e32,
-                               cudaStream_t s) {
-  return norms(g, u, f, 0, r32, e32, s);
+  return norms(g, u, f, 1, s);
 }
 
 // Row-wise elementwise kernels: CTA (x, j) covers interior row j + 1 with a
@@ -424,48 +454,169 @@ cudaError_t launch_ir_residual(const Grid &g, const double *u, const double *f, 
 constexpr int EW_THREADS = 256;
 static dim3 row_grid(const Level &L) { return dim3(std::min((L.nx - 1 + EW_THREADS - 1) / EW_THREADS, 4), L.ny - 1); }
 
-// Exact widening of a float to a double from the IEEE-754 fields: the sign,
-// the exponent rebiased from 127 to 1023, the 23 mantissa bits moved up by 29.
-// Integer instructions only, which leaves GB300's scarce FP64 pipe to the
-// addition; zero and subnormal floats (exponent field 0) and Inf / NaN (255)
-// take the conversion instruction instead.
-__device__ __forceinline__ double widen(float x) {
-  const unsigned b = __float_as_uint(x);
-  const unsigned ex = (b >> 23) & 0xffu;
-  if (ex == 0u || ex == 0xffu) return (double)x;
-  const unsigned long long bits = ((unsigned long long)(b & 0x80000000u) << 32) |
-                                  ((unsigned long long)(ex + 896u) << 52) |
-                                  ((unsigned long long)(b & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)bits);
+// ---- Refinement residual with the update fused (Sec. 4 step (6) on the
+// FP64 iterate of the FP32+FP64 refinement).  v = u + e, the correction of
+// the FP32 cycles just run widened exactly (none on the first step);
+// r = f - L v in FP64; r32 = float(r) by the integer-pipe rounding of
+// fp_bits.h; the sum of r^2 per CTA (fixed order, deterministic).  v goes to
+// a second array, not back into u: the CTAs next to a tile read u and e along
+// its edges while the launch runs.  The host alternates the iterate between
+// the caller's u and Grid::u2.
+//
+// CTA (bx, by) owns columns [i0, i0 + RR_TW) and rows [j0, j0 + rows): one
+// column per thread, marching down its rows with v of the rows above, at and
+// below in registers and the current row's v (with the halo columns left and
+// right of the tile) in shared memory, three row buffers and one barrier per
+// row.  Halo values are computed, not exchanged.  FP64 work per node: the
+// update's add, the five FMAs of the defect (its diagonal read from cd64),
+// the FMA of the norm; nothing else touches the FP64 pipe.
+constexpr int RR_TW = NORM_THREADS;
+
+template <bool UPD>
+__global__ void __launch_bounds__(RR_TW) refine_residual_kernel(RefineArgs a, int nx, int ny, int rows,
+                                                                const RefineArgs *__restrict__ tab,
+                                                                const int *__restrict__ active) {
+  const double *in = a.ua;
+  double *out = a.ub;
+  if (tab) {  // packed launch: blockIdx.z selects the problem; flag 2 swaps the iterates
+    const int act = active[blockIdx.z];
+    if (!act) return;
+    a = tab[blockIdx.z];
+    in = act == 2 ? a.ub : a.ua;
+    out = act == 2 ? a.ua : a.ub;
+  }
+  __shared__ double sv[3][RR_TW + 2];
+  const int nx1 = nx + 1, t = threadIdx.x;
+  const int i0 = 1 + blockIdx.x * RR_TW, iend = min(i0 + RR_TW, nx);
+  const int j0 = 1 + blockIdx.y * rows, jend = min(j0 + rows, ny);
+  const int i = i0 + t;
+  const bool own = i < iend;
+  const bool edge_l = t == 0, edge_r = t == 1;  // the two halo columns
+  const int ih = edge_l ? i0 - 1 : iend;
+  const int kh = edge_l ? 0 : iend - i0 + 1;
+  // v at (ii, jj): u + e inside, u on the boundary
+  auto vat = [&](int ii, int jj) {
+    const size_t p = (size_t)jj * nx1 + ii;
+    double x = in[p];
+    if (UPD && ii >= 1 && ii < nx && jj >= 1 && jj < ny) x += widen_exact(a.e[p]);
+    return x;
+  };
+  double vm = 0.0, vc = 0.0, vn = 0.0, s = 0.0;
+  if (own) {
+    vm = vat(i, j0 - 1);
+    vc = vat(i, j0);
+    sv[j0 % 3][t + 1] = vc;
+    if (UPD && j0 == 1) out[i] = vm;  // boundary row 0 of the other iterate
+  }
+  if (edge_l || edge_r) {
+    const double x = vat(ih, j0);
+    sv[j0 % 3][kh] = x;
+    if (UPD && (ih == 0 || ih == nx)) out[(size_t)j0 * nx1 + ih] = x;
+  }
+  const double wi = own ? __ldg(a.c.W + i) : 0.0, ei = own ? __ldg(a.c.E + i) : 0.0;
+  for (int j = j0; j < jend; ++j) {
+    const int b0 = j % 3, b1 = (j + 1) % 3;
+    if (own) {
+      vn = vat(i, j + 1);
+      sv[b1][t + 1] = vn;
+    }
+    if (edge_l || edge_r) {
+      const double x = vat(ih, j + 1);
+      sv[b1][kh] = x;
+      if (UPD && (ih == 0 || ih == nx)) out[(size_t)(j + 1) * nx1 + ih] = x;
+    }
+    __syncthreads();
+    if (own) {
+      const size_t p = (size_t)j * nx1 + i;
+      double r = fma(a.cd[p], vc, a.f[p]);
+      r = fma(-wi, sv[b0][t], r);
+      r = fma(-ei, sv[b0][t + 2], r);
+      r = fma(-__ldg(a.c.S + j), vm, r);
+      r = fma(-__ldg(a.c.N + j), vn, r);
+      a.r32[p] = narrow_rne(r);
+      if (UPD) out[p] = vc;
+      else a.e32[p] = 0.0f;
+      s = fma(r, r, s);
+    }
+    vm = vc;
+    vc = vn;
+  }
+  if (UPD && own && jend == ny) out[(size_t)ny * nx1 + i] = vc;  // boundary row ny
+  s = block_sum(s);
+  if (t == 0) a.part[blockIdx.y * gridDim.x + blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(EW_THREADS) ir_update_kernel(int nx, double *__restrict__ u,
-                                                               const float *__restrict__ e,
-                                                               const UpdateArgs *__restrict__ tab,
-                                                               const int *__restrict__ active) {
-  if (tab) {  // packed launch: blockIdx.z selects the problem
-    if (!active[blockIdx.z]) return;
-    u = tab[blockIdx.z].u;
-    e = tab[blockIdx.z].e;
-  }
-  const size_t row = (size_t)(blockIdx.y + 1) * (nx + 1);
-  for (int i = 1 + blockIdx.x * EW_THREADS + threadIdx.x; i < nx; i += gridDim.x * EW_THREADS)
-    u[row + i] += widen(e[row + i]);
+// cd[p] = W_i + E_i + S_j + N_j at interior nodes, 0 on the boundary, summed
+// as norm_stage1 sums it ((W_i + E_i) + (S_j + N_j)), so both give the same
+// defect bit for bit.
+__global__ void diag_sum_kernel(CoefQ<double> c, const double *__restrict__ we, int nx, int ny,
+                                double *__restrict__ cd) {
+  const int j = blockIdx.y;
+  const size_t row = (size_t)j * (nx + 1);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= nx; i += gridDim.x * blockDim.x)
+    cd[row + i] = (i >= 1 && i < nx && j >= 1 && j < ny) ? we[i] + (c.S[j] + c.N[j]) : 0.0;
 }
-cudaError_t launch_ir_update(const Grid &g, double *u, const float *e, cudaStream_t s) {
+
+mg_status setup_refine_residual(Grid &g) {
   const Level &L = g.lev[0];
-  ir_update_kernel<<<row_grid(L), EW_THREADS, 0, s>>>(L.nx, u, e, nullptr, nullptr);
-  count_launch(1);
+  const size_t nn = L.nn;
+  if (cudaMalloc(&g.u2, nn * sizeof(double)) != cudaSuccess || cudaMalloc(&g.cd64, nn * sizeof(double)) != cudaSuccess ||
+      cudaMemset(g.u2, 0, nn * sizeof(double)) != cudaSuccess)
+    return MG_ERR_CUDA;
+  diag_sum_kernel<<<dim3(std::max(1, std::min(8, (L.nx + 256) / 256)), L.ny + 1), 256>>>(cq<double>(L), L.WE64, L.nx,
+                                                                                          L.ny, g.cd64);
+  if (cudaGetLastError() != cudaSuccess) return MG_ERR_CUDA;
+  // about four waves of CTAs, at least 8 rows each
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, refine_residual_kernel<true>, RR_TW, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int gx = (L.nx - 1 + RR_TW - 1) / RR_TW;
+  const int target = std::max(1, 4 * per_sm * std::max(1, g.sms) / gx);
+  int rows = std::max(8, (L.ny - 1 + target - 1) / target);
+  rows = std::min(rows, L.ny - 1);
+  g.rr_rows = rows;
+  g.rr_gx = gx;
+  g.rr_gy = (L.ny - 1 + rows - 1) / rows;
+  if (cudaMalloc(&g.rpart, (size_t)g.rr_gx * g.rr_gy * sizeof(double)) != cudaSuccess) return MG_ERR_CUDA;
+  return MG_OK;
+}
+
+cudaError_t launch_refine_residual(const Grid &g, const double *u, const float *e, double *uo, const double *f,
+                                   cudaStream_t s) {
+  const Level &L = g.lev[0];
+  const RefineArgs a{cq<double>(L), g.cd64, const_cast<double *>(u), uo, e, f, g.r32, g.e32, g.rpart, nullptr};
+  const dim3 grid(g.rr_gx, g.rr_gy);
+  if (e) refine_residual_kernel<true><<<grid, RR_TW, 0, s>>>(a, L.nx, L.ny, g.rr_rows, nullptr, nullptr);
+  else refine_residual_kernel<false><<<grid, RR_TW, 0, s>>>(a, L.nx, L.ny, g.rr_rows, nullptr, nullptr);
+  norm_stage2<<<1, NORM_THREADS, 0, s>>>(g.rpart, g.rr_gx * g.rr_gy, g.scal, nullptr, nullptr);
+  count_launch(2);
+  if (e) {
+    // the next cycles start from e = 0; zeroed only now, since the kernel
+    // read e along the tile edges of every CTA
+    const cudaError_t z = cudaMemsetAsync(g.e32, 0, L.nn * sizeof(float), s);
+    if (z != cudaSuccess) return z;
+  }
   return cudaGetLastError();
 }
-cudaError_t launch_ir_update_packed(const Grid &g, const PackedLaunch &pk, cudaStream_t s) {
+
+cudaError_t launch_refine_residual_packed(const Grid &g, bool update, const PackedLaunch &pk, float *const *e32s,
+                                          cudaStream_t s) {
   if (pk.count == 0) return cudaSuccess;
   const Level &L = g.lev[0];
-  dim3 gr = row_grid(L);
-  gr.z = pk.count;
-  ir_update_kernel<<<gr, EW_THREADS, 0, s>>>(L.nx, nullptr, nullptr, static_cast<const UpdateArgs *>(pk.tab),
-                                             pk.active);
-  count_launch(1);
+  const RefineArgs none{};
+  const RefineArgs *tab = static_cast<const RefineArgs *>(pk.tab);
+  const dim3 grid(g.rr_gx, g.rr_gy, pk.count);
+  if (update) refine_residual_kernel<true><<<grid, RR_TW, 0, s>>>(none, L.nx, L.ny, g.rr_rows, tab, pk.active);
+  else refine_residual_kernel<false><<<grid, RR_TW, 0, s>>>(none, L.nx, L.ny, g.rr_rows, tab, pk.active);
+  norm_stage2_refine<<<pk.count, NORM_THREADS, 0, s>>>(g.rr_gx * g.rr_gy, tab, pk.active);
+  count_launch(2);
+  if (update)
+    for (int k = 0; k < pk.count; ++k)
+      if (e32s[k]) {
+        const cudaError_t z = cudaMemsetAsync(e32s[k], 0, L.nn * sizeof(float), s);
+        if (z != cudaSuccess) return z;
+      }
   return cudaGetLastError();
 }
 

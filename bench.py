@@ -38,12 +38,12 @@ HEADLINE = dict(smoother="tweed", nu1=1, nu2=1, precision="f32_refine", tol=TOL,
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "tweed_pass_f32_4097_traffic.json")
 # sources whose change invalidates the stored ncu traffic of the tiled pass:
-# the tiled kernels, their setup and layout, the launch helpers, and the tiled-path part
+# the tiled kernels and their chunk arithmetic, their setup and layout, the launch helpers, and the tiled-path part
 # of the internal header (from its "Tiled line path" comment to the Level
 # struct, less the cluster pass's structs); the rest of that header (other
 # paths' structs, declarations) and the checked build's part of device_util.cuh
 # do not enter the tiled kernels of the timed build
-TRAFFIC_SOURCES = ["tiles.cu", "tile_setup.cu", "tile_host.h", "device_util.cuh", "mg_internal.h#tiled"]
+TRAFFIC_SOURCES = ["tiles.cu", "tile_math.cuh", "tile_setup.cu", "tile_host.h", "device_util.cuh", "mg_internal.h#tiled"]
 
 
 def traffic_key():
@@ -525,6 +525,7 @@ def run_3d(args):
     e1.record(stream)
     torch.cuda.synchronize()
     pass_ms = e0.elapsed_time(e1) / npass
+    tiled = grid.line_path(0, "tweed", "f32")[0] == "tiled"
     nn = (n + 1) ** 3
     algo_bytes = 2 * 4 * nn
     peaks = json.load(open(PEAKS)) if os.path.exists(PEAKS) else {}
@@ -545,9 +546,11 @@ def run_3d(args):
             "speedup_vs_fp64": ms64 / ms, "f32_refine_vs_f64_solution_maxrel": err32,
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 2 * 8 * nn, "d2h_bytes_per_step": 8 * nn},
             "gpu_launches": int(launches),
-            "roofline": {"kernel": "FP32 3D tweed colour pass, finest level (seq3_single_kernel)", "bound": "hbm",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "pass_ms": pass_ms, "passes_timed": npass, "launches_per_pass": 1,
+            "roofline": {"kernel": "FP32 3D tweed colour pass, finest level (" +
+                                   ("tile3_reduce + tile3_couple + tile3_expand" if tiled else "seq3_single_kernel") + ")",
+                         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "pass_ms": pass_ms, "passes_timed": npass,
+                         "launches_per_pass": 4 if tiled else 1,
                          "algo_bytes_per_pass": algo_bytes,
                          "peak_source": "hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"},
             "clocks": clk.summary()}

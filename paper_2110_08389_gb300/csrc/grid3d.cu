@@ -25,7 +25,6 @@
 // exactly: lines, stars and rings on the warp path (a ring as the line left
 // when one node is taken out, that node then a junction with two attached
 // ends), skeletons by one CTA each (Thomas per edge, then the corners).
-#include "fp_bits.h"
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -35,6 +34,7 @@
 #include <thread>
 #include <vector>
 
+#include "fp_bits.h"
 #include "pack3_host.h"
 #include "seq3.cuh"
 
@@ -360,6 +360,7 @@ mg_status setup3(Grid &g, const int64_t *n, const double *const *coords) {
         return MG_ERR_UNSUPPORTED;
       }
       for (int c = 0; c < 2; ++c) TRY(warp_list3(L, blocks, c, false, L.wp[SM3_TWEED][c]));
+      if (std::min(L.nx, std::min(L.ny, L.nz)) >= T3_MIN_SIDE) TRY(build_tiles3(g, L, blocks, &L.t3_ok));
       L.wf_ok = wf_ok;
       if (L.wf_ok)
         for (int c = 0; c < 2; ++c) {
@@ -392,6 +393,12 @@ mg_status setup3(Grid &g, const int64_t *n, const double *const *coords) {
     TRY_CUDA("cudaMemcpy(3D coarse)", cudaMemcpy(G.cinv, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice));
   }
   const size_t nn0 = G.lev[0].nn;
+  if (g.tile_cap > 0) {
+    // scratch of the 3D tiled path, laid out as the 2D one's (api.cu), FP64 sized
+    TRY_CUDA("cudaMalloc(tile rows)", cudaMalloc(&g.tile_rows, g.tile_cap * 32 * 2 * 6 * sizeof(double)));
+    TRY_CUDA("cudaMalloc(tile rhs)", cudaMalloc(&g.tile_d, g.tile_cap * 32 * 32 * sizeof(double)));
+    TRY_CUDA("cudaMalloc(tile ends)", cudaMalloc(&g.tile_x, g.tile_cap * 32 * 2 * sizeof(double)));
+  }
   if (G.skel_len > 0)
     TRY_CUDA("cudaMalloc(3D skeleton scratch)", cudaMalloc(&G.skel_scr, sizeof(double) * 6 * G.skel_len));
   if (want64) TRY_CUDA("cudaMalloc(3D defect)", cudaMalloc(&G.d64, sizeof(double) * nn0));
@@ -412,6 +419,7 @@ void free3(Grid &g) {
     cudaFree(L.u64); cudaFree(L.f64); cudaFree(L.u32); cudaFree(L.f32);
     for (int m = 0; m < 2; ++m)
       for (int c = 0; c < 2; ++c) cudaFree(L.wp[m][c].mem);
+    for (int c = 0; c < 2; ++c) cudaFree(L.t3[c].mem);
   }
   cudaFree(g.g3->cinv);
   cudaFree(g.g3->skel_scr);
@@ -421,6 +429,10 @@ void free3(Grid &g) {
   g.g3 = nullptr;
 }
 
+// The 3D tweed passes of a level take the tiled path when its lists exist,
+// unless mg_set_line_path chose the warp path.
+static bool tiled3(const Level3 &L) { return L.t3_ok && L.t3_path != 1; }
+
 template <typename T>
 mg_status colour_pass3(Grid &g, int l, int sm, int colour, T *u, const T *f, cudaStream_t s) {
   Level3 &L = g.g3->lev[l];
@@ -429,6 +441,8 @@ mg_status colour_pass3(Grid &g, int l, int sm, int colour, T *u, const T *f, cud
     set_error_text("3D wireframe: a block of this level is not a ring, line, point or cuboid edge skeleton");
     return MG_ERR_UNSUPPORTED;
   }
+  if (sm == SM3_TWEED && tiled3(L))
+    return cuda_status("3D tweed pass (tiled)", launch_tile3_pass<T>(g, L, L.t3[colour], u, f, s));
   return cuda_status(sm == SM3_WIREFRAME ? "3D wireframe pass" : "3D tweed pass",
                      L.wp[sm][colour].multi ? launch_seq3_multi<T>(*g.g3, L, L.wp[sm][colour], u, f, s)
                                             : launch_warp3_t<T, false>(*g.g3, L, L.wp[sm][colour], u, f, s));

@@ -188,6 +188,48 @@ struct WarpList3 {
   WSkel3 *skel = nullptr;
 };
 enum { SM3_TWEED = 0, SM3_WIREFRAME = 1 };
+// 3D tiled tweed path (tiles3.cu; layout by tile3_host.h): every 3D tweed
+// block of a colour (Sec. 7) as straight legs plus at most one junction, the
+// legs cut into 32-node chunks from their first node.  A tile holds 32 such
+// chunks of parallel legs, one per lane, at the same 32 positions (same run
+// direction and start); the chunks of one leg may sit in different tiles and
+// lanes, so every leg lists its chunks' lane slots.  Runs along y and z have
+// consecutive x across lanes where the blocks allow (coalesced); runs along
+// x are read and written through a per-warp shared-memory transpose.  Lane
+// flags are the 2D ones (TL_*): the node before the first / after the last
+// is outside the block (its value is known), or the last node's successor is
+// the junction.
+struct Tile3Desc {
+  uint16_t base;  // run coordinate of slot 0
+  uint8_t dir;    // 0..5: +x, -x, +y, -y, +z, -z
+  uint8_t pad;
+};
+static_assert(sizeof(Tile3Desc) == 4, "Tile3Desc layout");
+struct Tile3Lane {
+  uint16_t c1, c2;  // fixed coordinates of the run: (j, k) along x, (i, k) along y, (i, j) along z
+  uint8_t q1;       // active slots [0, q1) (0: unused lane)
+  uint8_t flags;    // TL_*
+  uint16_t pad;
+};
+static_assert(sizeof(Tile3Lane) == 8, "Tile3Lane layout");
+struct Block3Desc {
+  uint16_t ji, jj, jk;   // junction node
+  uint8_t nleg, junc;    // legs; 1 if the block has a junction
+  uint32_t jdirs;        // 3 bits per leg: direction from the junction to the leg's last node
+  uint32_t leg_slot0[6]; // chunk r of leg l is lane slot[leg_slot0[l] + r] (= tile * 32 + lane)
+  uint16_t leg_len[6];
+  uint8_t pad[16];
+};
+static_assert(sizeof(Block3Desc) == 64, "Block3Desc layout");
+struct Tile3List {
+  int ntile = 0, nblock = 0, ngroup = 0, nslot = 0, max_leg_chunks = 0;
+  int ngroup2 = 0;              // the leading groups whose blocks have at most two legs
+  void *mem = nullptr;
+  Tile3Desc *tile = nullptr;
+  Tile3Lane *lane = nullptr;    // 32 per tile
+  Block3Desc *block = nullptr;  // 32 per group (unused entries: nleg = junc = 0)
+  uint32_t *slot = nullptr;     // the chunks of every leg, in order
+};
 struct Level3 {
   int nx = 0, ny = 0, nz = 0;
   size_t nn = 0;
@@ -200,6 +242,9 @@ struct Level3 {
   float *u32 = nullptr, *f32 = nullptr;
   WarpList3 wp[2][2];                 // [SM3_*][colour]: shared by both precisions
   bool wf_ok = false;                 // wireframe blocks are all rings, lines, points and skeletons
+  Tile3List t3[2];                    // tweed tiles per colour (t3_ok: built)
+  bool t3_ok = false;
+  int t3_path = 0;                    // 0: built-in rule, 1: warp path, 2: tiled path (mg_set_line_path)
 };
 struct Grid3 {
   std::vector<Level3> lev;
@@ -525,6 +570,16 @@ cudaError_t launch_cluster_pass(const Level &L, const ClusterPlan &cp, float *u,
 cudaError_t prepare_cluster_kernel();
 // Clusters of the cluster pass the current device holds at once (0: none).
 int cluster_pass_capacity();
+// 3D tiled tweed path (tiles3.cu): one colour pass, and the setup-time build
+// of a level's tile lists from its tweed blocks (false in *ok if a block does
+// not fit the layout; the level then keeps the warp path).
+struct HBlock3;
+template <typename T>
+cudaError_t launch_tile3_pass(const Grid &g, const Level3 &L, const Tile3List &t, T *u, const T *f, cudaStream_t s);
+mg_status build_tiles3(Grid &g, Level3 &L, const std::vector<HBlock3> &tweed_blocks, bool *ok);
+// Levels whose sides are all at least this many intervals get 3D tile lists;
+// the built-in rule takes the tiled path on them.
+constexpr int T3_MIN_SIDE = 64;
 
 // ---- kernel launchers (smooth.cu, transfer.cu).  All return cudaError_t of
 // the launch (cudaGetLastError).

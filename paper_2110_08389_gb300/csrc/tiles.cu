@@ -20,6 +20,7 @@
 #include <algorithm>
 
 #include "device_util.cuh"
+#include "tile_math.cuh"
 
 namespace tmg {
 
@@ -41,21 +42,6 @@ CoefT<double> coefs<double>(const Level &L) { return {L.W64, L.E64, L.S64, L.N64
 template <>
 CoefT<float> coefs<float>(const Level &L) { return {L.W32, L.E32, L.S32, L.N32}; }
 
-__device__ __forceinline__ float rcp_t(float x) { return __fdividef(1.0f, x); }
-// Newton-Raphson reciprocal from the FP32 one (see smooth.cu)
-__device__ __forceinline__ double rcp_t(double x) {
-  double r = (double)__frcp_rn((float)x);
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
-}
-
-template <typename T>
-struct __align__(4 * sizeof(T)) TRow {
-  T a, c, y, z;  // a x_prev + x + c x_next = y   (z unused)
-};
-
 // Per-tile constants: run direction, step, which coefficient array is the
 // predecessor / successor coupling along the run, and the lane's
 // perpendicular coefficient sum.
@@ -76,18 +62,6 @@ struct TileGeom {
   __device__ __forceinline__ int v(int q) const { return base + q * step; }
 };
 
-// Coefficients of slot q for a lane with m active slots and flags fl:
-// a (predecessor), c (successor), b (diagonal).  The along coefficients of
-// the tile's 32 positions are the same for every lane; each warp stages them
-// once in shared memory (co[0][q] = predecessor side, co[1][q] = successor).
-template <typename T>
-__device__ __forceinline__ void abc(const T (&co)[2][32], int q, int m, int fl, T cross, T &a, T &b, T &c) {
-  const T lo = co[0][q], hi = co[1][q];
-  b = -(cross + (lo + hi));
-  a = (q == 0 && (fl & TL_FIRST)) ? T(0) : lo;
-  c = (q == m - 1 && (fl & TL_LAST_W)) ? T(0) : hi;
-}
-
 // Positions of unused slots past the end of the axis (ragged last tiles of
 // lines from wall to wall) are clamped into the coefficient arrays.
 template <typename T>
@@ -96,94 +70,6 @@ __device__ __forceinline__ void stage_coefs(const TileGeom<T> &g, int lane, T (&
   co[0][lane] = __ldg(g.lo_arr + v);
   co[1][lane] = __ldg(g.hi_arr + v);
   __syncwarp();
-}
-
-// The chunk's two reduced rows: eliminate nodes 1..m-2 towards node m-1 (hi
-// row, in terms of x_0 and x_m) and nodes m-2..1 towards node 0 (lo row, in
-// terms of x_{-1} and x_{m-1}); the two sweeps are interleaved.  FULL: m is
-// CMAX, so every guard resolves at compile time.
-template <typename T, bool FULL>
-__device__ __forceinline__ void reduce_rows(const T (&co)[2][32], int m_rt, int fl, T cross, const T (&d)[CMAX],
-                                            TRow<T> &rlo, TRow<T> &rhi) {
-  const int m = FULL ? CMAX : m_rt;
-  T a0, b0, c0;
-  abc(co, 0, m, fl, cross, a0, b0, c0);
-  rhi.a = T(0); rhi.c = T(0); rhi.y = T(0); rhi.z = T(0);
-  rlo.z = T(0);
-  if (m <= 2) {
-    const T rb = rcp_t(b0);
-    rlo.a = a0 * rb; rlo.c = c0 * rb; rlo.y = d[0] * rb;
-  }
-  if (m >= 2) {
-    T a1, b1, c1;
-    abc(co, 1, m, fl, cross, a1, b1, c1);
-    T ri = rcp_t(b1);
-    T al = a1 * ri, ga = c1 * ri, de = d[1] * ri;
-    T ah = T(0), ch = T(0), dh = T(0);
-#pragma unroll
-    for (int k = 1; k <= CMAX - 2; ++k) {
-      const int qf = k + 1;
-      if (qf < m) {
-        T a, b, c;
-        abc(co, qf, m, fl, cross, a, b, c);
-        const T r = rcp_t(b - a * ga);
-        al = -a * al * r;
-        ga = c * r;
-        de = (d[qf] - a * de) * r;
-      }
-      const int qb = CMAX - 1 - k;
-      if (qb <= m - 2) {
-        T a, b, c;
-        abc(co, qb, m, fl, cross, a, b, c);
-        if (qb == m - 2) {
-          const T r = rcp_t(b);
-          ah = a * r; ch = c * r; dh = d[qb] * r;
-        } else {
-          const T r = rcp_t(b - c * ah);
-          ah = a * r;
-          ch = -c * ch * r;
-          dh = (d[qb] - c * dh) * r;
-        }
-      }
-    }
-    rhi.a = al; rhi.c = ga; rhi.y = de;
-    if (m >= 3) {
-      const T r = rcp_t(b0 - c0 * ah);
-      rlo.a = a0 * r; rlo.c = -c0 * ch * r; rlo.y = (d[0] - c0 * dh) * r;
-    }
-  }
-}
-
-// Interior nodes 1..m-2 of a chunk by Thomas between the known end values
-// xlo (node 0) and xhi (node m-1), into x (cpv: the multipliers).
-template <typename T, bool FULL>
-__device__ __forceinline__ void expand_rows(const T (&co)[2][32], int m_rt, int fl, T cross, const T (&dv)[CMAX],
-                                            T xlo, T xhi, T *x, T *cpv) {
-  const int m = FULL ? CMAX : m_rt;
-  T dprev = xlo;
-#pragma unroll
-  for (int q = 1; q < CMAX - 1; ++q) {
-    if (q <= m - 2) {
-      T a, b, c;
-      abc(co, q, m, fl, cross, a, b, c);
-      T dq = dv[q] - a * dprev;
-      if (q == m - 2) dq -= c * xhi;
-      const T r = (q == 1) ? rcp_t(b) : rcp_t(b - a * cpv[q - 1]);
-      cpv[q] = c * r;
-      dprev = dq * r;
-      x[q] = dprev;
-    }
-  }
-  T xn = dprev;
-#pragma unroll
-  for (int q = CMAX - 3; q >= 1; --q) {
-    if (q <= m - 3) {
-      xn = x[q] - cpv[q] * xn;
-      x[q] = xn;
-    }
-  }
-  x[0] = xlo;
-  x[m - 1] = xhi;
 }
 
 template <typename T>
@@ -291,20 +177,24 @@ __global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__
   __shared__ T s_cp[4][32], s_dp[4][32], s_xj[32];
   pdl_trigger();
   const int l = threadIdx.x >> 5, b = threadIdx.x & 31;
-  BlockDesc bd = blocks[(size_t)blockIdx.x * 32 + b];
+  // the record's fields are read where they lie (a copy indexed by the
+  // thread's leg would live in local memory)
+  const BlockDesc *bp = blocks + (size_t)blockIdx.x * 32 + b;
+  int nleg = bp->nleg, junc = bp->junc;
+  const int lane = bp->lane, ji = bp->ji, jj = bp->jj;
+  const unsigned jdirs = bp->jdirs;
   // checked builds: a block's legs must lie in the tile list and its junction
   // inside the level (else the block is skipped)
-  if (bd.nleg > 0 || bd.junc) {
-    bool ok = bd.nleg <= 4 && bd.lane == b &&
-              (!bd.junc || (bd.ji >= 1 && bd.ji <= nx1 - 2 && bd.jj >= 1 && (size_t)(bd.jj + 1) * nx1 < nn));
-    for (int e = 0; e < 4 && ok; ++e)
-      ok = e >= bd.nleg || (size_t)bd.leg_tile0[e] + (bd.leg_len[e] + CMAX - 1) / CMAX <= (size_t)ntile;
-    if (!MG_OK_IF(ok)) { bd.nleg = 0; bd.junc = 0; }
+  if (nleg > 0 || junc) {
+    bool ok = nleg <= 4 && lane == b && (!junc || (ji >= 1 && ji <= nx1 - 2 && jj >= 1 && (size_t)(jj + 1) * nx1 < nn));
+    for (int e = 0; e < nleg && ok; ++e)
+      ok = (size_t)bp->leg_tile0[e] + (bp->leg_len[e] + CMAX - 1) / CMAX <= (size_t)ntile;
+    if (!MG_OK_IF(ok)) { nleg = 0; junc = 0; }
   }
-  const bool active = l < bd.nleg;
-  const int len = active ? bd.leg_len[l] : 0;
+  const bool active = l < nleg;
+  const int len = active ? bp->leg_len[l] : 0;
   const int nch = (len + CMAX - 1) / CMAX;
-  const size_t t0 = active ? bd.leg_tile0[l] : 0;
+  const size_t t0 = active ? bp->leg_tile0[l] : 0;
   pdl_wait();  // the reduced rows, u and f from here on
   T cpv = T(0), dpv = T(0);
   constexpr int B = 16;  // chunks whose rows are loaded together
@@ -313,7 +203,7 @@ __global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__
 #pragma unroll
     for (int k = 0; k < B; ++k)
       if (r0 + k < nch) {
-        const size_t idx = ((t0 + r0 + k) * 32 + bd.lane) * 2;
+        const size_t idx = ((t0 + r0 + k) * 32 + lane) * 2;
         lo[k] = rows[idx];
         hi[k] = rows[idx + 1];
       }
@@ -321,7 +211,7 @@ __global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__
     for (int k = 0; k < B; ++k) {
       const int r = r0 + k;
       if (r < nch) {
-        const size_t idx = ((t0 + r) * 32 + bd.lane) * 2;
+        const size_t idx = ((t0 + r) * 32 + lane) * 2;
         const int mlen = min(CMAX, len - CMAX * r);
         T den = rcp_t(T(1) - lo[k].a * cpv);
         cpv = lo[k].c * den;
@@ -339,11 +229,11 @@ __global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__
   s_cp[l][b] = cpv;
   s_dp[l][b] = dpv;
   __syncthreads();
-  if (l == 0 && bd.junc) {
-    const int i = bd.ji, j = bd.jj;
+  if (l == 0 && junc) {
+    const int i = ji, j = jj;
     const size_t p = (size_t)j * nx1 + i;
     unsigned att = 0;
-    for (int e = 0; e < bd.nleg; ++e) att |= 1u << ((bd.jdirs >> (2 * e)) & 3);
+    for (int e = 0; e < nleg; ++e) att |= 1u << ((jdirs >> (2 * e)) & 3);
     const T w = __ldg(cp.W + i), e_ = __ldg(cp.E + i), s = __ldg(cp.S + j), n = __ldg(cp.N + j);
     T num = f[p];
     if (!(att & 2u)) num -= w * u[p - 1];
@@ -351,8 +241,8 @@ __global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__
     if (!(att & 8u)) num -= s * u[p - nx1];
     if (!(att & 4u)) num -= n * u[p + nx1];
     T den = -((w + e_) + (s + n));
-    for (int e = 0; e < bd.nleg; ++e) {
-      const int d = (bd.jdirs >> (2 * e)) & 3;
+    for (int e = 0; e < nleg; ++e) {
+      const int d = (jdirs >> (2 * e)) & 3;
       const T k = d == DIR_PX ? e_ : d == DIR_MX ? w : d == DIR_PY ? n : s;
       num -= k * s_dp[e][b];
       den -= k * s_cp[e][b];
@@ -363,14 +253,14 @@ __global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__
   }
   __syncthreads();
   if (!active) return;
-  T xn = bd.junc ? s_xj[b] : T(0);
+  T xn = junc ? s_xj[b] : T(0);
   // back-substitution, chunk by chunk towards the wall, B chunks per batch
   for (int r1 = nch - 1; r1 >= 0; r1 -= B) {
     T v[B][4];
 #pragma unroll
     for (int k = 0; k < B; ++k)
       if (r1 - k >= 0) {
-        const size_t idx = ((t0 + r1 - k) * 32 + bd.lane) * 2;
+        const size_t idx = ((t0 + r1 - k) * 32 + lane) * 2;
 #pragma unroll
         for (int e = 0; e < 4; ++e) v[k][e] = cdp[2 * idx + e];
       }
@@ -387,8 +277,8 @@ __global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__
         const T xlo = v[k][1] - v[k][0] * xn;
         xn = xlo;
         if (mlen < 2) xhi = xlo;
-        xscr[((t0 + r) * 32 + bd.lane) * 2] = xlo;
-        xscr[((t0 + r) * 32 + bd.lane) * 2 + 1] = xhi;
+        xscr[((t0 + r) * 32 + lane) * 2] = xlo;
+        xscr[((t0 + r) * 32 + lane) * 2 + 1] = xhi;
       }
     }
   }

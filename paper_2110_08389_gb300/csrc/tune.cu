@@ -125,7 +125,27 @@ mg_status time_passes(mg_grid *g, int level, int smoother, int dtype, int reps, 
 
 extern "C" {
 
+// 3D grids: tweed passes take the warp path or the 3D tiled path (both
+// precisions alike); wireframe passes have the warp path alone.
+static mg_status set_path3(mg_grid *g, int level, int smoother, int path) {
+  if (level < 0 || level + 1 >= g->nlev || !(path == MG_PATH_AUTO || path == MG_PATH_WARP || path == MG_PATH_TILED))
+    return MG_ERR_INVALID_ARG;
+  if (smoother != MG_SMOOTH_TWEED) return smoother == MG_SMOOTH_WIREFRAME ? MG_ERR_UNSUPPORTED : MG_ERR_INVALID_ARG;
+  Level3 &L = g->g3->lev[level];
+  if (path == MG_PATH_TILED && !L.t3_ok) return MG_ERR_UNSUPPORTED;
+  const cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    set_error("cudaDeviceSynchronize (line path)", e);
+    return MG_ERR_CUDA;
+  }
+  L.t3_path = path == MG_PATH_AUTO ? 0 : path == MG_PATH_WARP ? 1 : 2;
+  ++g->gen;
+  drop_graphs(*g);
+  return MG_OK;
+}
+
 mg_status mg_set_line_path(mg_grid *g, int level, int smoother, int dtype, int path, int k) {
+  if (g && g->dim == 3) return set_path3(g, level, smoother, path);
   if (bad_args(g, level, dtype) || path < MG_PATH_AUTO || path > MG_PATH_CLUSTER) return MG_ERR_INVALID_ARG;
   if (!(k == 0 || k == 1 || k == 2 || k == 4 || k == 8 || k == 16)) return MG_ERR_INVALID_ARG;
   const int wl = wl_of(smoother);
@@ -134,6 +154,17 @@ mg_status mg_set_line_path(mg_grid *g, int level, int smoother, int dtype, int p
 }
 
 mg_status mg_get_line_path(const mg_grid *g, int level, int smoother, int dtype, int *path, int *k, int *w) {
+  if (g && g->dim == 3) {
+    if (level < 0 || level + 1 >= g->nlev || (smoother != MG_SMOOTH_TWEED && smoother != MG_SMOOTH_WIREFRAME))
+      return MG_ERR_INVALID_ARG;
+    const Level3 &L = g->g3->lev[level];
+    const bool tiled = smoother == MG_SMOOTH_TWEED && L.t3_ok && L.t3_path != 1;
+    const WarpList3 &wp = L.wp[smoother == MG_SMOOTH_TWEED ? SM3_TWEED : SM3_WIREFRAME][0];
+    if (path) *path = tiled ? MG_PATH_TILED : MG_PATH_WARP;
+    if (k) *k = tiled ? 0 : wp.K;
+    if (w) *w = tiled ? 0 : wp.W;
+    return MG_OK;
+  }
   if (bad_args(g, level, dtype)) return MG_ERR_INVALID_ARG;
   const int wl = wl_of(smoother);
   if (wl < 0) return MG_ERR_INVALID_ARG;

@@ -1,6 +1,6 @@
 """3D grids (Sec. 7) through the C ABI against the 3D oracle: tweed and
 wireframe colour passes on every smoothed level (FP64 to 1e-10, FP32 to the
-FP32 smoothing tolerance), the 7-point defect, full-weighting restriction,
+FP32 smoothing tolerance), the tiled tweed path of the large levels, the 7-point defect, full-weighting restriction,
 trilinear prolongation and coarsest solve, the FP64 solve history per cycle
 (1e-12 on the relative residual, 1 % on the convergence factor) and FP32
 cycles with FP64 refinement to 1e-10."""
@@ -66,6 +66,62 @@ def test_colour_pass_3d(mg, oracle_mod, grid, smoother):
         assert rel_err(host(ud), ref) <= 2e-4, (lev, rel_err(host(ud), ref))
 
 
+TILED3 = [(64, 64, 64, "wall", 200.0), (64, 96, 128, "centre", 10.0), (128, 64, 96, "wall", 50.0)]
+
+
+@pytest.mark.parametrize("grid", TILED3, ids=lambda t: f"{t[0]}x{t[1]}x{t[2]}-{t[3]}")
+def test_tiled_tweed_pass_3d(mg, oracle_mod, grid):
+    """The 3D tiled tweed path (32 chunks of parallel legs per warp, one per
+    lane) on every level whose sides are all at least 64 intervals, where the
+    built-in rule takes it: each colour pass against the oracle (FP64 to
+    1e-10; FP32 on FP32-rounded data to 2e-4), and against the same pass
+    forced onto the warp path (FP64, 1e-10)."""
+    g, P = pair(mg, oracle_mod, grid)
+    rng = np.random.default_rng(15)
+    tiled = [lev for lev in range(g.nlev - 1) if min(P.dims(lev)) >= 64]
+    assert tiled
+    for lev in tiled:
+        assert g.line_path(lev, "tweed", "f64")[0] == "tiled"
+        u0, f = rng.standard_normal(P.shape(lev)), rng.standard_normal(P.shape(lev))
+        u32 = u0.astype(np.float32).astype(np.float64)
+        f32 = f.astype(np.float32).astype(np.float64)
+        for colour in (0, 1):
+            ref = P.colour_pass(u0.copy(), f, colour, lev)
+            ud = cuda(u0)
+            g.colour_pass(ud, cuda(f), "tweed", colour, level=lev)
+            got = host(ud)
+            assert rel_err(got, ref) <= 1e-10, (lev, colour, rel_err(got, ref))
+            g.set_line_path(lev, "tweed", "f64", "warp")
+            assert g.line_path(lev, "tweed", "f64")[0] == "warp"
+            uw = cuda(u0)
+            g.colour_pass(uw, cuda(f), "tweed", colour, level=lev)
+            g.set_line_path(lev, "tweed", "f64", "auto")
+            assert rel_err(host(uw), got) <= 1e-10
+            ref32 = P.colour_pass(u32.copy(), f32, colour, lev)
+            u3 = cuda(u32, "f32")
+            g.colour_pass(u3, cuda(f32, "f32"), "tweed", colour, level=lev)
+            assert rel_err(host(u3), ref32) <= 2e-4, (lev, colour, rel_err(host(u3), ref32))
+
+
+def test_tiled_path_requests_3d(mg):
+    """mg_set_line_path on 3D grids: the tiled path exists for tweed on levels
+    whose sides are all at least 64 intervals; wireframe has the warp path
+    alone; the coarsest level has no passes."""
+    g = mg.Grid(*coords3(64, 64, 64, "wall", 20.0))
+    g.set_line_path(0, "tweed", "f32", "tiled")
+    assert g.line_path(0, "tweed", "f32")[0] == "tiled"
+    with pytest.raises(mg.MGError) as e:
+        g.set_line_path(1, "tweed", "f32", "tiled")  # 32^3
+    assert e.value.status == mg.ERR_UNSUPPORTED
+    with pytest.raises(mg.MGError) as e:
+        g.set_line_path(0, "wireframe", "f32", "tiled")
+    assert e.value.status == mg.ERR_UNSUPPORTED
+    with pytest.raises(mg.MGError) as e:
+        g.set_line_path(g.nlev - 1, "tweed", "f32", "warp")
+    assert e.value.status == mg.ERR_INVALID_ARG
+    assert g.line_path(1, "tweed", "f32")[0] == "warp"
+
+
 @pytest.mark.parametrize("grid", GRIDS3[1:], ids=lambda t: f"{t[0]}x{t[1]}x{t[2]}-{t[3]}")
 def test_transfers_and_coarse_3d(mg, oracle_mod, grid):
     import torch
@@ -98,6 +154,7 @@ def test_transfers_and_coarse_3d(mg, oracle_mod, grid):
 
 
 @pytest.mark.parametrize("grid,smoother", [((32, 32, 32, "wall", 200.0), "tweed"), ((16, 12, 10, "wall", 50.0), "tweed"),
+                                           ((64, 64, 64, "wall", 200.0), "tweed"),
                                            ((32, 32, 32, "centre", 10.0), "wireframe"),
                                            ((24, 16, 32, "centre", 5.0), "wireframe"),
                                            ((32, 32, 32, "wall", 50.0), "alt_tw")],

@@ -373,7 +373,13 @@ typedef enum {
  * does, the device runs clusters of 8 CTAs, and every group of the tiled
  * path fits 8 CTAs of 16 tiles.  The previous choice then stays.  May allocate and
  * free device memory (work lists); synchronises the device and drops the
- * grid's captured cycle graphs.                                              */
+ * grid's captured cycle graphs.
+ * On 3D grids (Sec. 7) the choice is for MG_SMOOTH_TWEED only, and for both
+ * dtypes at once: MG_PATH_WARP, or MG_PATH_TILED on levels whose sides are
+ * all at least 64 intervals (32 chunks of parallel legs per warp; the
+ * built-in rule takes it where the sides are all at least 256); k is
+ * ignored.  The 3D wireframe has the warp path alone (MG_ERR_UNSUPPORTED for
+ * any other); the coarsest level has no passes (MG_ERR_INVALID_ARG).       */
 mg_status mg_set_line_path(mg_grid *grid, int level, int smoother, int dtype, int path, int k);
 
 /* The path the colour passes of (level, smoother, dtype) take now, resolved

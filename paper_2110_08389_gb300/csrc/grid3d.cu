@@ -429,10 +429,6 @@ void free3(Grid &g) {
   g.g3 = nullptr;
 }
 
-// The 3D tweed passes of a level take the tiled path when its lists exist,
-// unless mg_set_line_path chose the warp path.
-static bool tiled3(const Level3 &L) { return L.t3_ok && L.t3_path != 1; }
-
 template <typename T>
 mg_status colour_pass3(Grid &g, int l, int sm, int colour, T *u, const T *f, cudaStream_t s) {
   Level3 &L = g.g3->lev[l];

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <atomic>
 #include <string>
 #include <vector>
@@ -223,7 +224,6 @@ struct Block3Desc {
 static_assert(sizeof(Block3Desc) == 64, "Block3Desc layout");
 struct Tile3List {
   int ntile = 0, nblock = 0, ngroup = 0, nslot = 0, max_leg_chunks = 0;
-  int ngroup2 = 0;              // the leading groups whose blocks have at most two legs
   void *mem = nullptr;
   Tile3Desc *tile = nullptr;
   Tile3Lane *lane = nullptr;    // 32 per tile
@@ -577,9 +577,16 @@ struct HBlock3;
 template <typename T>
 cudaError_t launch_tile3_pass(const Grid &g, const Level3 &L, const Tile3List &t, T *u, const T *f, cudaStream_t s);
 mg_status build_tiles3(Grid &g, Level3 &L, const std::vector<HBlock3> &tweed_blocks, bool *ok);
-// Levels whose sides are all at least this many intervals get 3D tile lists;
-// the built-in rule takes the tiled path on them.
-constexpr int T3_MIN_SIDE = 64;
+// Levels whose sides are all at least T3_MIN_SIDE intervals get 3D tile
+// lists; the built-in rule takes the tiled path on those whose sides are all
+// at least T3_AUTO_SIDE (measured on GB300, FP32 tweed relaxation: 257^3
+// 0.29 ms tiled against 0.42 ms on the warp path; 129^3 0.089 against
+// 0.056 ms; 65^3 0.064 against 0.017 ms).
+constexpr int T3_MIN_SIDE = 64, T3_AUTO_SIDE = 256;
+// The 3D tweed passes of a level take the tiled path (see T3_AUTO_SIDE).
+inline bool tiled3(const Level3 &L) {
+  return L.t3_ok && (L.t3_path == 2 || (L.t3_path == 0 && std::min(L.nx, std::min(L.ny, L.nz)) >= T3_AUTO_SIDE));
+}
 
 // ---- kernel launchers (smooth.cu, transfer.cu).  All return cudaError_t of
 // the launch (cudaGetLastError).

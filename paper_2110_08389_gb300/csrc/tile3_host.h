@@ -37,7 +37,6 @@ struct Tile3Host {
   std::vector<Block3Desc> blocks; // 32 per group
   std::vector<uint32_t> slots;    // chunk lane slots of every leg, leg by leg
   int max_chunks = 0, ngroup = 0;
-  int ngroup2 = 0;                // the leading groups whose blocks have at most two legs
 };
 
 // run coordinate and fixed coordinates of node (i, j, k) for a run along dir
@@ -134,8 +133,8 @@ inline bool specs(const Level3 &L, const std::vector<HBlock3> &blocks, int colou
 // along x by (z, y).  Each class is packed densely, 32 lanes per tile, so a
 // short leg's chunk shares its tile with chunks of other blocks.  The block
 // records list their legs' chunk slots; blocks are grouped 32 per record
-// group in order of their number of legs, so that the groups of blocks with
-// at most two legs come first (tile3_couple runs them with two warps).
+// group in order of their number of legs, so that a group's blocks take
+// about the same time in tile3_couple.
 inline bool layout(const Level3 &L, const std::vector<HBlock3> &blocks, int colour, Tile3Host &out) {
   out = Tile3Host();
   std::vector<Spec3> sp;
@@ -215,7 +214,6 @@ inline bool layout(const Level3 &L, const std::vector<HBlock3> &blocks, int colo
     }
     out.blocks.insert(out.blocks.end(), bd.begin(), bd.end());
     ++out.ngroup;
-    if (sp[ord[std::min(g0 + 31, ord.size() - 1)]].legs.size() <= 2) out.ngroup2 = out.ngroup;
   }
   return true;
 }

@@ -9,11 +9,10 @@
 //                 side (f minus the four neighbours across the run, and the
 //                 known node before the leg or after a free end) and its two
 //                 reduced rows (partition method, tile_math.cuh);
-//   tile3_couple  one thread per leg (up to six), its chunks found through
-//                 the leg's slot list: Thomas on those rows towards the
-//                 junction; the junction row with its six neighbours fixes
-//                 the junction value; back-substitution gives every chunk's
-//                 end values;
+//   tile3_couple  per leg (up to six), its chunks found through the leg's
+//                 slot list: Thomas on those rows towards the junction; the
+//                 junction row with its six neighbours fixes the junction
+//                 value; back-substitution gives every chunk's end values;
 //   tile3_expand  one lane per chunk: the interior by Thomas between the
 //                 known ends, written to u.
 // Lanes of a tile are chunks of parallel legs over the same 32 positions, so
@@ -186,24 +185,24 @@ __global__ void __launch_bounds__(32 * TW3<T>) tile3_reduce(const Tile3Desc *__r
     if (q < m) dscr[((size_t)t * 32 + q) * 32 + lane] = d[q];
 }
 
-// One CTA per group: thread (leg l, lane b), NL warps for at most NL legs
-// (2 for the groups of lines and L-blocks, 6 for the stars).  Thomas on the
-// leg's reduced rows from its first chunk towards the junction (normalised
-// rows, so the pivot of row k is 1 - a_k c'_{k-1}); the block's junction row
-// with the substitutions x_last = d' - c' x_junction of its legs;
-// back-substitution to every chunk's end values.
-template <typename T, int NL>
-__global__ void __launch_bounds__(32 * NL) tile3_couple(const Block3Desc *__restrict__ blocks,
-                                                        const uint32_t *__restrict__ slots, int nslot, int ntile,
-                                                        Coef3T<T> cp, int nx, int ny, int nz,
-                                                        const TRow<T> *__restrict__ rows, T *cdp,
-                                                        T *__restrict__ xscr, T *__restrict__ u,
-                                                        const T *__restrict__ f) {
-  __shared__ T s_cp[NL][32], s_dp[NL][32], s_xj[32];
+// One CTA of two warps per group: lane b is block b, and warp w takes legs
+// w, w + 2, w + 4 of it in turn (most blocks have two legs; the stars'
+// groups take longer but run beside the others, in the same launch).  Per
+// leg: Thomas on its reduced rows from its first chunk towards the junction
+// (normalised rows, so the pivot of row k is 1 - a_k c'_{k-1}); then the
+// block's junction row with the substitutions x_last = d' - c' x_junction
+// of its legs; then back-substitution to every chunk's end values.
+template <typename T>
+__global__ void __launch_bounds__(64) tile3_couple(const Block3Desc *__restrict__ blocks,
+                                                   const uint32_t *__restrict__ slots, int nslot, int ntile,
+                                                   Coef3T<T> cp, int nx, int ny, int nz,
+                                                   const TRow<T> *__restrict__ rows, T *cdp, T *__restrict__ xscr,
+                                                   T *__restrict__ u, const T *__restrict__ f) {
+  __shared__ T s_cp[6][32], s_dp[6][32], s_xj[32];
   pdl_trigger();
-  const int l = threadIdx.x >> 5, b = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5, b = threadIdx.x & 31;
   // the record's fields are read where they lie (a copy indexed by the
-  // thread's leg would live in local memory)
+  // leg would live in local memory)
   const Block3Desc *bp = blocks + (size_t)blockIdx.x * 32 + b;
   int nleg = bp->nleg, junc = bp->junc;
   const unsigned jdirs = bp->jdirs;
@@ -211,7 +210,7 @@ __global__ void __launch_bounds__(32 * NL) tile3_couple(const Block3Desc *__rest
   // checked builds: a block's chunk slots must lie in the lists and its
   // junction inside the level (else the block is skipped)
   if (nleg > 0 || junc) {
-    bool ok = nleg <= NL && (!junc || (ji >= 1 && ji <= nx - 1 && jj >= 1 && jj <= ny - 1 && jk >= 1 && jk <= nz - 1));
+    bool ok = nleg <= 6 && (!junc || (ji >= 1 && ji <= nx - 1 && jj >= 1 && jj <= ny - 1 && jk >= 1 && jk <= nz - 1));
     for (int e = 0; e < nleg && ok; ++e) {
       const int nc = (bp->leg_len[e] + CMAX - 1) / CMAX;
       ok = (size_t)bp->leg_slot0[e] + nc <= (size_t)nslot;
@@ -219,45 +218,46 @@ __global__ void __launch_bounds__(32 * NL) tile3_couple(const Block3Desc *__rest
     }
     if (!MG_OK_IF(ok)) { nleg = 0; junc = 0; }
   }
-  const bool active = l < nleg;
-  const int len = active ? bp->leg_len[l] : 0;
-  const int nch = (len + CMAX - 1) / CMAX;
-  const uint32_t *sl = slots + (active ? bp->leg_slot0[l] : 0);
   pdl_wait();  // the reduced rows, u and f from here on
-  T cpv = T(0), dpv = T(0);
   constexpr int B = 4;  // chunks whose rows are loaded together (legs of at most a few chunks)
-  for (int r0 = 0; r0 < nch; r0 += B) {
-    TRow<T> lo[B], hi[B];
+  for (int l = w; l < nleg; l += 2) {
+    const int len = bp->leg_len[l];
+    const int nch = (len + CMAX - 1) / CMAX;
+    const uint32_t *sl = slots + bp->leg_slot0[l];
+    T cpv = T(0), dpv = T(0);
+    for (int r0 = 0; r0 < nch; r0 += B) {
+      TRow<T> lo[B], hi[B];
 #pragma unroll
-    for (int k = 0; k < B; ++k)
-      if (r0 + k < nch) {
-        const size_t idx = (size_t)__ldg(sl + r0 + k) * 2;
-        lo[k] = rows[idx];
-        hi[k] = rows[idx + 1];
-      }
+      for (int k = 0; k < B; ++k)
+        if (r0 + k < nch) {
+          const size_t idx = (size_t)__ldg(sl + r0 + k) * 2;
+          lo[k] = rows[idx];
+          hi[k] = rows[idx + 1];
+        }
 #pragma unroll
-    for (int k = 0; k < B; ++k) {
-      const int r = r0 + k;
-      if (r < nch) {
-        const size_t idx = (size_t)__ldg(sl + r) * 2;
-        const int mlen = min(CMAX, len - CMAX * r);
-        T den = rcp_t(T(1) - lo[k].a * cpv);
-        cpv = lo[k].c * den;
-        dpv = (lo[k].y - lo[k].a * dpv) * den;
-        cdp[2 * idx] = cpv; cdp[2 * idx + 1] = dpv;
-        if (mlen >= 2) {
-          den = rcp_t(T(1) - hi[k].a * cpv);
-          cpv = hi[k].c * den;
-          dpv = (hi[k].y - hi[k].a * dpv) * den;
-          cdp[2 * idx + 2] = cpv; cdp[2 * idx + 3] = dpv;
+      for (int k = 0; k < B; ++k) {
+        const int r = r0 + k;
+        if (r < nch) {
+          const size_t idx = (size_t)__ldg(sl + r) * 2;
+          const int mlen = min(CMAX, len - CMAX * r);
+          T den = rcp_t(T(1) - lo[k].a * cpv);
+          cpv = lo[k].c * den;
+          dpv = (lo[k].y - lo[k].a * dpv) * den;
+          cdp[2 * idx] = cpv; cdp[2 * idx + 1] = dpv;
+          if (mlen >= 2) {
+            den = rcp_t(T(1) - hi[k].a * cpv);
+            cpv = hi[k].c * den;
+            dpv = (hi[k].y - hi[k].a * dpv) * den;
+            cdp[2 * idx + 2] = cpv; cdp[2 * idx + 3] = dpv;
+          }
         }
       }
     }
+    s_cp[l][b] = cpv;
+    s_dp[l][b] = dpv;
   }
-  s_cp[l][b] = cpv;
-  s_dp[l][b] = dpv;
   __syncthreads();
-  if (l == 0 && junc) {
+  if (w == 0 && junc) {
     const long long nx1 = nx + 1, plane = nx1 * (ny + 1);
     const long long p = jk * plane + jj * nx1 + ji;
     unsigned att = 0;
@@ -283,21 +283,25 @@ __global__ void __launch_bounds__(32 * NL) tile3_couple(const Block3Desc *__rest
     s_xj[b] = x;
   }
   __syncthreads();
-  if (!active) return;
-  T xn = junc ? s_xj[b] : T(0);
-  for (int r = nch - 1; r >= 0; --r) {
-    const size_t idx = (size_t)__ldg(sl + r) * 2;
-    const int mlen = min(CMAX, len - CMAX * r);
-    T xhi = T(0);
-    if (mlen >= 2) {
-      xhi = cdp[2 * idx + 3] - cdp[2 * idx + 2] * xn;
-      xn = xhi;
+  for (int l = w; l < nleg; l += 2) {
+    const int len = bp->leg_len[l];
+    const int nch = (len + CMAX - 1) / CMAX;
+    const uint32_t *sl = slots + bp->leg_slot0[l];
+    T xn = junc ? s_xj[b] : T(0);
+    for (int r = nch - 1; r >= 0; --r) {
+      const size_t idx = (size_t)__ldg(sl + r) * 2;
+      const int mlen = min(CMAX, len - CMAX * r);
+      T xhi = T(0);
+      if (mlen >= 2) {
+        xhi = cdp[2 * idx + 3] - cdp[2 * idx + 2] * xn;
+        xn = xhi;
+      }
+      const T xlo = cdp[2 * idx + 1] - cdp[2 * idx] * xn;
+      xn = xlo;
+      if (mlen < 2) xhi = xlo;
+      xscr[idx] = xlo;
+      xscr[idx + 1] = xhi;
     }
-    const T xlo = cdp[2 * idx + 1] - cdp[2 * idx] * xn;
-    xn = xlo;
-    if (mlen < 2) xhi = xlo;
-    xscr[idx] = xlo;
-    xscr[idx + 1] = xhi;
   }
 }
 
@@ -385,7 +389,6 @@ mg_status build_tiles3(Grid &g, Level3 &L, const std::vector<HBlock3> &tweed_blo
     T.nblock = (int)th[c].blocks.size();
     T.nslot = (int)th[c].slots.size();
     T.ngroup = th[c].ngroup;
-    T.ngroup2 = th[c].ngroup2;
     T.max_leg_chunks = th[c].max_chunks;
     g.tile_cap = std::max(g.tile_cap, (size_t)T.ntile);
   }
@@ -407,19 +410,14 @@ cudaError_t launch_tile3_pass(const Grid &g, const Level3 &L, const Tile3List &t
   if (tl.ntile > 0)
     e = launch_pdl(tile3_reduce<T>, dim3(ctas), dim3(32 * TW), 0, s, (const Tile3Desc *)tl.tile,
                    (const Tile3Lane *)tl.lane, tl.ntile, cp, L.nx, L.ny, L.nz, (const T *)u, f, rows, dscr);
-  // the groups of blocks with at most two legs come first
-  if (e == cudaSuccess && tl.ngroup2 > 0)
-    e = launch_pdl(tile3_couple<T, 2>, dim3(tl.ngroup2), dim3(64), 0, s, (const Block3Desc *)tl.block,
+  if (e == cudaSuccess && tl.ngroup > 0)
+    e = launch_pdl(tile3_couple<T>, dim3(tl.ngroup), dim3(64), 0, s, (const Block3Desc *)tl.block,
                    (const uint32_t *)tl.slot, tl.nslot, tl.ntile, cp, L.nx, L.ny, L.nz, (const TRow<T> *)rows, cdp,
                    xscr, u, f);
-  if (e == cudaSuccess && tl.ngroup > tl.ngroup2)
-    e = launch_pdl(tile3_couple<T, 6>, dim3(tl.ngroup - tl.ngroup2), dim3(192), 0, s,
-                   (const Block3Desc *)tl.block + (size_t)32 * tl.ngroup2, (const uint32_t *)tl.slot, tl.nslot,
-                   tl.ntile, cp, L.nx, L.ny, L.nz, (const TRow<T> *)rows, cdp, xscr, u, f);
   if (e == cudaSuccess && tl.ntile > 0)
     e = launch_pdl(tile3_expand<T>, dim3(ctas), dim3(32 * TW), 0, s, (const Tile3Desc *)tl.tile,
                    (const Tile3Lane *)tl.lane, tl.ntile, cp, L.nx, L.ny, L.nz, (const T *)dscr, (const T *)xscr, u);
-  count_launch((tl.ntile > 0 ? 2 : 0) + (tl.ngroup2 > 0 ? 1 : 0) + (tl.ngroup > tl.ngroup2 ? 1 : 0));
+  count_launch((tl.ntile > 0 ? 2 : 0) + (tl.ngroup > 0 ? 1 : 0));
   return e;
 }
 template cudaError_t launch_tile3_pass<double>(const Grid &, const Level3 &, const Tile3List &, double *,

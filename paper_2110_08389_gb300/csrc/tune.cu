@@ -158,7 +158,7 @@ mg_status mg_get_line_path(const mg_grid *g, int level, int smoother, int dtype,
     if (level < 0 || level + 1 >= g->nlev || (smoother != MG_SMOOTH_TWEED && smoother != MG_SMOOTH_WIREFRAME))
       return MG_ERR_INVALID_ARG;
     const Level3 &L = g->g3->lev[level];
-    const bool tiled = smoother == MG_SMOOTH_TWEED && L.t3_ok && L.t3_path != 1;
+    const bool tiled = smoother == MG_SMOOTH_TWEED && tiled3(L);
     const WarpList3 &wp = L.wp[smoother == MG_SMOOTH_TWEED ? SM3_TWEED : SM3_WIREFRAME][0];
     if (path) *path = tiled ? MG_PATH_TILED : MG_PATH_WARP;
     if (k) *k = tiled ? 0 : wp.K;

@@ -30,7 +30,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--ratio", type=float, default=1000.0)
     ap.add_argument("--dim", type=int, default=2, choices=[2, 3])
-    ap.add_argument("--path", default="auto", help="line-solve path of the finest level (2D)")
+    ap.add_argument("--path", default="auto", help="line-solve path of the finest level (3D: tiled or warp)")
     ap.add_argument("--solve", default=None, choices=["f32_refine", "f64"])
     args = ap.parse_args()
     import torch

@@ -72,15 +72,17 @@ TILED3 = [(64, 64, 64, "wall", 200.0), (64, 96, 128, "centre", 10.0), (128, 64, 
 @pytest.mark.parametrize("grid", TILED3, ids=lambda t: f"{t[0]}x{t[1]}x{t[2]}-{t[3]}")
 def test_tiled_tweed_pass_3d(mg, oracle_mod, grid):
     """The 3D tiled tweed path (32 chunks of parallel legs per warp, one per
-    lane) on every level whose sides are all at least 64 intervals, where the
-    built-in rule takes it: each colour pass against the oracle (FP64 to
-    1e-10; FP32 on FP32-rounded data to 2e-4), and against the same pass
-    forced onto the warp path (FP64, 1e-10)."""
+    lane) on every level whose sides are all at least 64 intervals, selected
+    with mg_set_line_path (the built-in rule takes it from 256 intervals on):
+    each colour pass against the oracle (FP64 to 1e-10; FP32 on FP32-rounded
+    data to 2e-4), and against the same pass on the warp path (FP64, 1e-10)."""
     g, P = pair(mg, oracle_mod, grid)
     rng = np.random.default_rng(15)
     tiled = [lev for lev in range(g.nlev - 1) if min(P.dims(lev)) >= 64]
     assert tiled
     for lev in tiled:
+        assert g.line_path(lev, "tweed", "f64")[0] == "warp"
+        g.set_line_path(lev, "tweed", "f64", "tiled")
         assert g.line_path(lev, "tweed", "f64")[0] == "tiled"
         u0, f = rng.standard_normal(P.shape(lev)), rng.standard_normal(P.shape(lev))
         u32 = u0.astype(np.float32).astype(np.float64)
@@ -92,10 +94,9 @@ def test_tiled_tweed_pass_3d(mg, oracle_mod, grid):
             got = host(ud)
             assert rel_err(got, ref) <= 1e-10, (lev, colour, rel_err(got, ref))
             g.set_line_path(lev, "tweed", "f64", "warp")
-            assert g.line_path(lev, "tweed", "f64")[0] == "warp"
             uw = cuda(u0)
             g.colour_pass(uw, cuda(f), "tweed", colour, level=lev)
-            g.set_line_path(lev, "tweed", "f64", "auto")
+            g.set_line_path(lev, "tweed", "f64", "tiled")
             assert rel_err(host(uw), got) <= 1e-10
             ref32 = P.colour_pass(u32.copy(), f32, colour, lev)
             u3 = cuda(u32, "f32")
@@ -163,6 +164,8 @@ def test_solve_history_3d(mg, oracle_mod, grid, smoother):
     """FP64 V(2,2) cycles: the relative residual after every cycle within
     1e-12 of the oracle's and the convergence factor within 1 %."""
     g, P = pair(mg, oracle_mod, grid)
+    if min(grid[:3]) >= 64 and smoother == "tweed":
+        g.set_line_path(0, "tweed", "f64", "tiled")  # the 3D tiled path inside the cycles
     rng = np.random.default_rng(13)
     f = rng.standard_normal(P.shape())
     bnd = rng.standard_normal(P.shape())

@@ -5,11 +5,10 @@ record's legs, through their chunks' lane slots (each the tile's run base
 and direction, the lane's fixed coordinates and active slots), must be
 straight chains of adjacent nodes whose first node follows a node outside
 the block, ending at the junction (TL_LAST_J) or before a node outside the
-block (TL_LAST_W); every used lane belongs to exactly one chunk; the leading
-groups that the couple kernel runs with two warps hold blocks of at most two
-legs.  The system assembled from that layout alone (each node's row of Eq.
-(prob:DP) with the block's nodes unknown and every other neighbour known),
-solved densely, must give the oracle's 3D tweed colour pass (Sec. 7) at every
+block (TL_LAST_W); every used lane belongs to exactly one chunk.  The system
+assembled from that layout alone (each node's row of Eq. (prob:DP) with the
+block's nodes unknown and every other neighbour known), solved densely, must
+give the oracle's 3D tweed colour pass (Sec. 7) at every
 node: a node the layout lost, doubled, misplaced or coupled wrongly fails
 it."""
 import os
@@ -39,15 +38,12 @@ def _layout(dumper, nx, ny, nz, colour):
                           check=True).stdout.split()
     assert toks[0] == "ok", toks[:2]
     it = iter(int(t) for t in toks[1:])
-    nt, nb, ng, ns, ng2 = next(it), next(it), next(it), next(it), next(it)
+    nt, nb, ng, ns = next(it), next(it), next(it), next(it)
     tiles = [(next(it), next(it)) for _ in range(nt)]
     lanes = [tuple(next(it) for _ in range(4)) for _ in range(32 * nt)]
     blocks = [tuple(next(it) for _ in range(18)) for _ in range(nb)]
     slots = [next(it) for _ in range(ns)]
-    assert nb == 32 * ng and 0 <= ng2 <= ng
-    # the leading ng2 groups (run by two warps each) hold blocks of at most two legs
-    assert all(b[3] <= 2 for b in blocks[:32 * ng2])
-    assert ng2 == ng or any(b[3] > 2 for b in blocks[32 * ng2:32 * ng2 + 32])
+    assert nb == 32 * ng
     return tiles, lanes, blocks, slots
 
 

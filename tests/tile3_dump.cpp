@@ -1,5 +1,5 @@
 // Prints the 3D tiled tweed layout of csrc/tile3_host.h for (nx ny nz colour)
-// read on stdin: "ok ntile nblock ngroup nslot ngroup2", every tile (base
+// read on stdin: "ok ntile nblock ngroup nslot", every tile (base
 // dir), every lane (c1 c2 q1 flags), every block record (ji jj jk nleg junc
 // jdirs leg_slot0[6] leg_len[6]), the slots; or "fail".
 #include <cstdio>
@@ -20,7 +20,7 @@ int main() {
     std::printf("fail\n");
     return 0;
   }
-  std::printf("ok %zu %zu %d %zu %d\n", th.tiles.size(), th.blocks.size(), th.ngroup, th.slots.size(), th.ngroup2);
+  std::printf("ok %zu %zu %d %zu\n", th.tiles.size(), th.blocks.size(), th.ngroup, th.slots.size());
   for (const auto &t : th.tiles) std::printf("%u %u\n", (unsigned)t.base, (unsigned)t.dir);
   for (const auto &l : th.lanes)
     std::printf("%u %u %u %u\n", (unsigned)l.c1, (unsigned)l.c2, (unsigned)l.q1, (unsigned)l.flags);

@@ -154,20 +154,26 @@ __global__ void __launch_bounds__(32 * TW3<T>) tile3_reduce(const Tile3Desc *__r
     }
   } else {
     // runs along x: for each lane's run in turn, all lanes read along it
-    // (coalesced) and the values are transposed through shared memory
+    // (coalesced) and the values are transposed through shared memory; the
+    // run's row offset and its four coefficients across (S, N of its y, B,
+    // T of its z: the lane's own am, ap, bm, bp) come from its lane by
+    // shuffle, and slots past its chunk load nothing
     const int q = lane;
+    const long long rb = (long long)c2 * g.plane + (long long)c1 * g.nx1;
 #pragma unroll 4
     for (int c = 0; c < 32; ++c) {
-      const int jc = __shfl_sync(0xffffffffu, c1, c);
-      const int kc = __shfl_sync(0xffffffffu, c2, c);
+      const long long rbc = __shfl_sync(0xffffffffu, rb, c);
       const int mc = __shfl_sync(0xffffffffu, m, c);
       const int fc = __shfl_sync(0xffffffffu, fl, c);
-      const int qq = q < mc ? q : (mc > 0 ? mc - 1 : 0);
-      const long long p = g.node(qq, jc, kc);
-      T r = f[p] - __ldg(cp.c[2] + jc) * u[p - g.nx1] - __ldg(cp.c[3] + jc) * u[p + g.nx1] -
-            __ldg(cp.c[4] + kc) * u[p - g.plane] - __ldg(cp.c[5] + kc) * u[p + g.plane];
-      if (q == 0 && (fc & TL_FIRST)) r -= co[0][0] * u[p - g.sv];
-      if (q == mc - 1 && (fc & TL_LAST_W)) r -= co[1][q] * u[p + g.sv];
+      const T amc = __shfl_sync(0xffffffffu, am, c), apc = __shfl_sync(0xffffffffu, ap, c);
+      const T bmc = __shfl_sync(0xffffffffu, bm, c), bpc = __shfl_sync(0xffffffffu, bp, c);
+      T r = T(0);
+      if (q < mc) {
+        const long long p = rbc + g.v(q);
+        r = f[p] - amc * u[p - g.nx1] - apc * u[p + g.nx1] - bmc * u[p - g.plane] - bpc * u[p + g.plane];
+        if (q == 0 && (fc & TL_FIRST)) r -= co[0][0] * u[p - g.sv];
+        if (q == mc - 1 && (fc & TL_LAST_W)) r -= co[1][q] * u[p + g.sv];
+      }
       tr[warp][c][q] = r;
     }
     __syncwarp();

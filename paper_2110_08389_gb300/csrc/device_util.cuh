@@ -2,6 +2,7 @@
 #pragma once
 #include <utility>
 
+#include "fp_bits.h"
 #include "mg_internal.h"
 
 namespace tmg {
@@ -76,10 +77,13 @@ inline Coefs<float> level_coefs<float>(const Level &L) { return {L.W32, L.E32, L
 // iteration r <- r + r (1 - x r), which doubles the number of correct bits per
 // step, started from the FP32 reciprocal (24 bits -> 48 -> 96); two fused
 // steps replace the much slower IEEE double division.  Valid while |x| and
-// 1/|x| lie inside the float range (grid spacings above ~1e-18).
+// 1/|x| lie inside the float range (grid spacings above ~1e-18).  The seed's
+// conversions to float and back use integer instructions (fp_bits.h, the
+// same values as the conversion instructions), which keeps them off the
+// FP64 pipe.
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double recip(double x) {
-  double r = (double)__frcp_rn((float)x);
+  double r = widen_exact(__frcp_rn(narrow_rne(x)));
   double e = fma(-x, r, 1.0);
   r = fma(r, e, r);
   e = fma(-x, r, 1.0);

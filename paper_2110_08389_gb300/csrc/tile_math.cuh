@@ -11,9 +11,9 @@ namespace tmg {
 namespace {
 
 __device__ __forceinline__ float rcp_t(float x) { return __fdividef(1.0f, x); }
-// Newton-Raphson reciprocal from the FP32 one (see smooth.cu)
+// Newton-Raphson reciprocal from the FP32 one (as recip, device_util.cuh)
 __device__ __forceinline__ double rcp_t(double x) {
-  double r = (double)__frcp_rn((float)x);
+  double r = widen_exact(__frcp_rn(narrow_rne(x)));
   double e = fma(-x, r, 1.0);
   r = fma(r, e, r);
   e = fma(-x, r, 1.0);

@@ -3,8 +3,8 @@ the checked build of the library (build.py --checked): the small-grid parity
 set of the GPU path, every call of which must return MG_OK with no bad index
 recorded by any kernel, on inputs poisoned with NaN where a kernel must not
 read (the relaxed colour's own nodes before a colour pass; the outputs of the
-transfers before they are written).  Prints one line "checked ok <calls>" or
-raises."""
+transfers before they are written), and the 3D tiled tweed path on a 64^3
+level.  Prints one line "checked ok <calls>" or raises."""
 import os
 import sys
 
@@ -103,6 +103,20 @@ def main():
         res = g3.solve(u3, torch.tensor(f3, device="cuda"), smoother=sm, nu1=2, nu2=2, tol=1e-10)
         calls += 1
         assert res.status == mg.OK, (sm, res.status, res.cycles, res.rel_res)
+    # the 3D tiled tweed path on a 64^3 level, both colours, FP64 and FP32
+    x3 = I.wall_coords(64, I.c_for_ratio(64, 50.0))
+    g3, P3 = mg.Grid(x3, x3, x3), oracle.Problem3(x3, x3, x3)
+    g3.set_line_path(0, "tweed", "f64", "tiled")
+    u0, f0 = rng.standard_normal(P3.shape()), rng.standard_normal(P3.shape())
+    for colour in (0, 1):
+        ref = P3.colour_pass(u0.copy(), f0, colour)
+        for dt, tol in (("f64", 1e-10), ("f32", 2e-3)):
+            tdt = torch.float64 if dt == "f64" else torch.float32
+            ud = torch.tensor(u0, dtype=tdt, device="cuda")
+            g3.colour_pass(ud, torch.tensor(f0, dtype=tdt, device="cuda"), "tweed", colour)
+            calls += 1
+            got = ud.double().cpu().numpy()
+            assert np.abs(got - ref).max() <= tol * max(1.0, np.abs(ref).max()), ("3d tiled", colour, dt)
     # a batch of two problems
     xs = [I.wall_coords(64, 2.0), I.wall_coords(128, 3.0)]
     bg = [mg.Grid(x, x) for x in xs]

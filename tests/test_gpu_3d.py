@@ -183,9 +183,12 @@ def test_solve_history_3d(mg, oracle_mod, grid, smoother):
     assert rel_err(host(ud), u_ref) <= 1e-8
 
 
-@pytest.mark.parametrize("smoother,kind,ratio", [("tweed", "wall", 200.0), ("wireframe", "centre", 10.0)])
-def test_f32_refine_3d(mg, oracle_mod, smoother, kind, ratio):
+@pytest.mark.parametrize("smoother,kind,ratio,path", [("tweed", "wall", 200.0, "warp"), ("tweed", "wall", 200.0, "tiled"),
+                                                      ("wireframe", "centre", 10.0, "warp")])
+def test_f32_refine_3d(mg, oracle_mod, smoother, kind, ratio, path):
     g, P = pair(mg, oracle_mod, (64, 64, 64, kind, ratio))
+    if path == "tiled":
+        g.set_line_path(0, "tweed", "f32", "tiled")
     f = np.random.default_rng(14).standard_normal(P.shape())
     ud = cuda(np.zeros(P.shape()))
     res = g.solve(ud, cuda(f), smoother=smoother, nu1=2, nu2=2, tol=1e-10, precision="f32_refine", max_outer=40,

@@ -460,8 +460,16 @@ mg_status enqueue(SolveState &q) {
     }
     // scale of the relative residual: ||f - B g||, the right-hand side of the
     // interior system (||f|| when the boundary data vanish)
-    if (d3) TRY(norms3(g, q.u, q.f, 1, nullptr, nullptr, q.s));
-    else TRY_CUDA("norm(f - B g)", launch_rhsnorm64(g, q.u, q.f, q.s));
+    if (d3) {
+      TRY(norms3(g, q.u, q.f, 1, nullptr, nullptr, q.s));
+    } else if (!f64 && !p.use_initial_guess) {
+      // the interior of u is zero: f - B g is also the first defect, so this
+      // launch writes its FP32 copy and the next step starts the cycles
+      TRY_CUDA("norm(f - B g) and first residual", launch_rhsnorm64(g, q.u, q.f, q.s, g.r32, g.e32));
+      q.merged = true;
+    } else {
+      TRY_CUDA("norm(f - B g)", launch_rhsnorm64(g, q.u, q.f, q.s));
+    }
   } else if (f64) {
     if (q.phase == 2) TRY(run_cycles<double>(g, p, 1, q.u, q.f, q.s));
     if (d3) TRY(norms3(g, q.u, q.f, 0, nullptr, nullptr, q.s));
@@ -507,7 +515,8 @@ void consume_value(SolveState &q, double v) {
   if (q.phase == 0) {
     q.fn = std::sqrt(v);
     q.phase = 1;
-    return;
+    if (!q.merged) return;
+    q.merged = false;  // v is also the first residual's: on to the first step
   }
   if (q.phase == 1) {
     if (q.fn == 0.0) q.fn = std::sqrt(v) > 0.0 ? std::sqrt(v) : 1.0;

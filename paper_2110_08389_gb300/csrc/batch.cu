@@ -205,7 +205,7 @@ void build_tables(mg_batch &b, Group &G, double *const *u, const double *const *
         CoarseArgs<float>{level_coefs<double>(Lc), g.cinv, lu(nl - 1), lf(nl - 1)};
     reinterpret_cast<NormArgs *>(h + G.norm)[k] =
         NormArgs{level_coefs<double>(g.lev[0]), g.lev[0].WE64, u[i], f[i], g.partial,
-                 reinterpret_cast<double *>(b.dev + G.base + G.out) + k};
+                 reinterpret_cast<double *>(b.dev + G.base + G.out) + k, g.r32, g.e32};
     reinterpret_cast<UpdateArgs *>(h + G.upd)[k] = UpdateArgs{u[i], g.e32};
     reinterpret_cast<RefineArgs *>(h + G.refine)[k] =
         RefineArgs{level_coefs<double>(g.lev[0]), g.cd64, u[i], g.u2, g.e32, f[i], g.r32, g.e32, g.rpart,
@@ -275,7 +275,11 @@ mg_status group_enqueue(mg_batch &b, Group &G) {
     for (auto &x : G.q)
       if (x.info) { x.info->cycles = 0; x.info->outer_iters = 0; x.info->history_len = 0; x.info->rel_res = 0; x.info->conv_factor = 0; }
     if (!G.p.use_initial_guess) st = cuda_status("zero u (packed)", launch_zero_interior_packed(g, pk(b, G, G.upd), s));
-    if (st == MG_OK) st = cuda_status("norm(f - B g) (packed)", launch_norms_packed(g, 1, pk(b, G, G.norm), s));
+    // a zeroed guess: f - B g is also the first defect (its FP32 copy written here)
+    const bool merged = !G.p.use_initial_guess;
+    if (st == MG_OK)
+      st = cuda_status("norm(f - B g) (packed)", launch_norms_packed(g, 1, pk(b, G, G.norm), s, merged));
+    for (auto &x : G.q) x.merged = merged;
   } else {
     if (phase == 2) {
       st = cuda_status("cudaGraphLaunch (packed cycles)", cudaGraphLaunch(G.exec, s));

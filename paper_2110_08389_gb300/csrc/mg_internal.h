@@ -609,8 +609,11 @@ cudaError_t launch_coarse_solve(const Grid &g, T *u, const T *f, cudaStream_t s)
 // FP64 norms: out[0] = sum (f-Lu)^2 over interior, out[1] = max |f-Lu|,
 // written to the device scalars g.scal[0..1] (u may be NULL: residual = f).
 cudaError_t launch_resnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s);
-// ||f - B u_b||^2: the right-hand side of the interior system (u's interior taken as 0)
-cudaError_t launch_rhsnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s);
+// ||f - B u_b||^2: the right-hand side of the interior system (u's interior
+// taken as 0); with r32 and e32 also float(f - B u_b), the defect of a zero
+// interior, and e32 = 0 (the first refinement step of a zeroed guess)
+cudaError_t launch_rhsnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s,
+                             float *r32 = nullptr, float *e32 = nullptr);
 // Refinement residual of the finest 2D level with the update fused: v = u + e
 // (e NULL: v = u), r = f - L v in FP64, r32 = float(r), the FP64 norms of r
 // into scal; with e, v goes to uo and e32 is zeroed afterwards, else e32 is

@@ -38,6 +38,7 @@ struct NormArgs {  // FP64 norms (and refinement residual) of the finest level
   const double *we;  // W_i + E_i per column
   const double *u, *f;
   double *part, *out;
+  float *r32, *e32;  // the first refinement step of a zeroed guess (launch_norms_packed with_r32)
 };
 struct RefineArgs {  // refinement residual with the update fused (transfer.cu)
   Coefs<double> c;
@@ -72,7 +73,8 @@ cudaError_t launch_prolong_add_packed(const Level &F, const Level &C, const Pack
 template <typename T>
 cudaError_t launch_coarse_solve_packed(const Grid &g, const PackedLaunch &pk, cudaStream_t s);
 // norms: bnd_only as launch_rhsnorm64; with_r32: the refinement residual
-cudaError_t launch_norms_packed(const Grid &g, int bnd_only, const PackedLaunch &pk, cudaStream_t s);
+cudaError_t launch_norms_packed(const Grid &g, int bnd_only, const PackedLaunch &pk, cudaStream_t s,
+                                bool with_r32 = false);
 // The refinement residual of every active member (update: the FP32
 // correction added first; active flag 1 reads ua and writes ub, 2 the
 // reverse), its r32 and FP64 norm; then each member's e32 zeroed.

@@ -26,6 +26,9 @@ struct SolveState {
   double fn = 0.0, rel = 0.0, rel0 = 0.0, prev = 0.0;  // prev: rel before the last step
   int cycles = 0, outer = 0;
   bool alt = false;  // FP32+refine, 2D: the iterate lives in Grid::u2, not in u
+  // the scale norm ||f - B g|| also served as the first residual (a zeroed
+  // guess: f - B g is its defect); its FP32 copy is already in r32
+  bool merged = false;
 };
 
 // The early stop (mg_params.early_stop): from the third step on, true when

@@ -329,13 +329,15 @@ __global__ void __launch_bounds__(NORM_THREADS) norm_stage1(CoefQ<double> c, con
                                                             int nx, int ny,
                                                             const double *__restrict__ u,
                                                             const double *__restrict__ f, int bnd_only,
-                                                            double *__restrict__ part,
+                                                            double *__restrict__ part, float *__restrict__ r32,
+                                                            float *__restrict__ e32,
                                                             const NormArgs *__restrict__ tab,
                                                             const int *__restrict__ active) {
   if (tab) {  // packed launch: blockIdx.y selects the problem
     if (!active[blockIdx.y]) return;
     const NormArgs a = tab[blockIdx.y];
     c = a.c; we = a.we; u = a.u; f = a.f; part = a.part;
+    if (r32) { r32 = a.r32; e32 = a.e32; }
   }
   const int nx1 = nx + 1;
   double s = 0.0;
@@ -357,21 +359,30 @@ __global__ void __launch_bounds__(NORM_THREADS) norm_stage1(CoefQ<double> c, con
     const double sj = __ldg(c.S + j), nj = __ldg(c.N + j), snj = sj + nj;
     const size_t row = (size_t)j * nx1;
     if (bnd_only) {
+      // with r32: also the FP32 copy of f - B g, the defect of a zero
+      // interior, and a zero FP32 correction (the first refinement step)
+      auto keep = [&](int i, double r) {
+        if (r32) { r32[row + i] = narrow_rne(r); e32[row + i] = 0.0f; }
+      };
       if (j == 1 || j == ny - 1) {
         for (int i = 1 + threadIdx.x; i < nx; i += NORM_THREADS) {
           const double r = rhs_edge(i, j);
+          keep(i, r);
           s = fma(r, r, s);
         }
       } else {
         for (int i = 2 + threadIdx.x; i < nx - 1; i += NORM_THREADS) {
           const double r = f[row + i];
+          keep(i, r);
           s = fma(r, r, s);
         }
         if (threadIdx.x == 0) {
           const double r1 = rhs_edge(1, j);
+          keep(1, r1);
           s = fma(r1, r1, s);
           if (nx - 1 > 1) {
             const double r2 = rhs_edge(nx - 1, j);
+            keep(nx - 1, r2);
             s = fma(r2, r2, s);
           }
         }
@@ -422,21 +433,25 @@ __global__ void __launch_bounds__(NORM_THREADS) norm_stage2_refine(int npart, co
   if (threadIdx.x == 0) tab[blockIdx.x].out[0] = s;
 }
 
-static cudaError_t norms(const Grid &g, const double *u, const double *f, int bnd_only, cudaStream_t s) {
+static cudaError_t norms(const Grid &g, const double *u, const double *f, int bnd_only, cudaStream_t s,
+                         float *r32 = nullptr, float *e32 = nullptr) {
   const Level &L = g.lev[0];
   norm_stage1<<<g.npartial, NORM_THREADS, 0, s>>>(cq<double>(L), L.WE64, L.nx, L.ny, u, f, bnd_only, g.partial,
-                                                  nullptr, nullptr);
+                                                  r32, e32, nullptr, nullptr);
   norm_stage2<<<1, NORM_THREADS, 0, s>>>(g.partial, g.npartial, g.scal, nullptr, nullptr);
   count_launch(2);
   return cudaGetLastError();
 }
 
-cudaError_t launch_norms_packed(const Grid &g, int bnd_only, const PackedLaunch &pk, cudaStream_t s) {
+cudaError_t launch_norms_packed(const Grid &g, int bnd_only, const PackedLaunch &pk, cudaStream_t s, bool with_r32) {
   if (pk.count == 0) return cudaSuccess;
   const Level &L = g.lev[0];
   const NormArgs *tab = static_cast<const NormArgs *>(pk.tab);
+  // a non-null placeholder tells the kernel to take each problem's r32 and e32
+  float *mark = with_r32 ? g.r32 : nullptr;
   norm_stage1<<<dim3(g.npartial, pk.count), NORM_THREADS, 0, s>>>(cq<double>(L), L.WE64, L.nx, L.ny, nullptr,
-                                                                  nullptr, bnd_only, nullptr, tab, pk.active);
+                                                                  nullptr, bnd_only, nullptr, mark, mark, tab,
+                                                                  pk.active);
   norm_stage2<<<pk.count, NORM_THREADS, 0, s>>>(nullptr, g.npartial, nullptr, tab, pk.active);
   count_launch(2);
   return cudaGetLastError();
@@ -445,8 +460,9 @@ cudaError_t launch_norms_packed(const Grid &g, int bnd_only, const PackedLaunch 
 cudaError_t launch_resnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s) {
   return norms(g, u, f, 0, s);
 }
-cudaError_t launch_rhsnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s) {
-  return norms(g, u, f, 1, s);
+cudaError_t launch_rhsnorm64(const Grid &g, const double *u, const double *f, cudaStream_t s, float *r32,
+                             float *e32) {
+  return norms(g, u, f, 1, s, r32, e32);
 }
 
 // Row-wise elementwise kernels: CTA (x, j) covers interior row j + 1 with a

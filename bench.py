@@ -656,7 +656,7 @@ def main():
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, pg, dev)
 
     # roofline of the dominant kernel: the FP32 tweed colour pass on the finest
-    # level (tile_reduce + tile_couple + tile_expand), timed live in the solves
+    # level (tile_reduce + tile_couple_pc + tile_expand), timed live in the solves
     # (each stage includes the event-record gap of about 2 us)
     npass = max(timer["passes"], 1)
     stage_ms = [v / npass for v in timer["stage_ms"]]
@@ -684,11 +684,11 @@ def main():
             "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": 2 * 8 * n1 * n1,
                     "d2h_bytes_per_step": 8 * n1 * n1},
             "gpu_launches": int(launches),
-            "roofline": {"kernel": "FP32 tweed colour pass, finest level (tile_reduce + tile_couple + tile_expand)",
+            "roofline": {"kernel": "FP32 tweed colour pass, finest level (tile_reduce + tile_couple_pc + tile_expand)",
                          "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "pass_ms": pass_ms,
                          "passes_timed": timer["passes"], "launches_per_pass": 3,
-                         "stage_ms": {"tile_reduce": stage_ms[0], "tile_couple": stage_ms[1],
+                         "stage_ms": {"tile_reduce": stage_ms[0], "tile_couple_pc": stage_ms[1],
                                       "tile_expand": stage_ms[2]},
                          "algo_bytes_per_pass": algo_bytes,
                          "peak_source": "hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s"},

@@ -164,6 +164,7 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
   g->nlev = (int)g->lev.size();
   TRY_CUDA("setup start (latched error)", cudaGetLastError());
   TRY_CUDA("line kernel attributes", prepare_line_kernels());
+  TRY_CUDA("tile kernel attributes", prepare_tile_kernels());
   TRY_CUDA("warp kernel attributes", prepare_warp_kernels());
   TRY_CUDA("cluster kernel attributes", prepare_cluster_kernel());
   g->cluster_ok = (g->prec_mask & 2) && cluster_pass_capacity() > 0;
@@ -242,6 +243,7 @@ static mg_status setup(Grid *g, int nx, int ny, const double *x, const double *y
     TRY_CUDA("cudaMalloc(tile rows)", cudaMalloc(&g->tile_rows, g->tile_cap * 32 * 2 * 6 * sizeof(double)));
     TRY_CUDA("cudaMalloc(tile rhs)", cudaMalloc(&g->tile_d, g->tile_cap * 32 * 32 * sizeof(double)));
     TRY_CUDA("cudaMalloc(tile ends)", cudaMalloc(&g->tile_x, g->tile_cap * 32 * 2 * sizeof(double)));
+    if (want32) TRY_CUDA("tile couple constants", setup_couple_consts(*g));
   }
   TRY_CUDA("setup (latched error)", cudaGetLastError());
   return MG_OK;

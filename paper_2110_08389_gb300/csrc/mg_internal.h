@@ -298,6 +298,10 @@ struct BlockDesc {
 };
 static_assert(sizeof(BlockDesc) == 32, "BlockDesc layout");
 
+// Legs of at most this many chunks take the FP32 couple with precomputed
+// pivots (tiles.cu, tile_couple_pc).
+constexpr int TILE_PC_CHUNKS = 64;
+
 struct TileList {
   int ntile = 0, nblock = 0, ngroup = 0;
   int max_leg_chunks = 0;       // longest leg, in chunks
@@ -306,6 +310,13 @@ struct TileList {
   TileDesc *tile = nullptr;
   TileLane *lane = nullptr;     // 32 per tile
   BlockDesc *block = nullptr;   // 32 per group (unused entries have nleg = junc = 0)
+  // FP32 grids with legs of at most TILE_PC_CHUNKS chunks: per lane and
+  // chunk (index tile * 32 + lane), the couple's forward-sweep constants of
+  // the reduced lo and hi rows: a float4 (pivot 1 / (1 - a c'_prev) and a
+  // times it, lo then hi) for every lane chunk, followed by a float2 (c' of
+  // lo and hi) for every lane chunk; set once at setup (setup_couple_consts).
+  // nullptr otherwise.
+  void *cconst = nullptr;
 };
 
 // Cluster pass (FP32 tweed and zebra on the tiled levels): the three stages of
@@ -557,6 +568,10 @@ mg_status build_cluster_plans(Grid &g, int level, int wl);
 // Dynamic shared memory opt-in of the line kernels on the current device
 // (called by mg_setup_grid).
 cudaError_t prepare_line_kernels();
+cudaError_t prepare_tile_kernels();
+// The couple constants of every FP32 tile list of the grid (after its tiled
+// scratch is allocated).
+cudaError_t setup_couple_consts(Grid &g);
 cudaError_t prepare_warp_kernels();
 // ev: nullptr, or 4 events recorded before tile_reduce, tile_couple,
 // tile_expand and after tile_expand

@@ -183,5 +183,14 @@ inline void layout(int nx, int ny, int wl, int colour, TileHost &out) {
   }
 }
 
+// True if every block of more than two legs is alone in its group (lane 0):
+// tile_couple_pc then gives each leg of a group its own shared-memory slot
+// among 64.
+inline bool pc_slots_ok(const TileHost &th) {
+  for (size_t k = 0; k < th.blocks.size(); ++k)
+    if (th.blocks[k].nleg > 2 && k % 32 != 0) return false;
+  return true;
+}
+
 }  // namespace tile
 }  // namespace tmg

@@ -50,13 +50,16 @@ mg_status build_tiles(Grid &g, int level, int wl) {
     const size_t s0 = align16<TileDesc>(std::max<size_t>(tiles.size(), 1)),
                  s1 = align16<TileLane>(std::max<size_t>(lanes.size(), 1)),
                  s2 = align16<BlockDesc>(std::max<size_t>(blocks.size(), 1));
+    const bool consts = (g.prec_mask & 2) && max_chunks <= TILE_PC_CHUNKS && !tiles.empty() && tile::pc_slots_ok(th);
+    const size_t s3 = consts ? tiles.size() * 32 * (16 + 8) : 0;  // per lane chunk: float4 + float2
     char *mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, s0 + s1 + s2);
+    cudaError_t e = cudaMalloc(&mem, s0 + s1 + s2 + s3);
     if (e != cudaSuccess) { set_error("cudaMalloc(tiles)", e); return MG_ERR_ALLOC; }
     T.mem = mem;
     T.tile = reinterpret_cast<TileDesc *>(mem);
     T.lane = reinterpret_cast<TileLane *>(mem + s0);
     T.block = reinterpret_cast<BlockDesc *>(mem + s0 + s1);
+    T.cconst = consts ? mem + s0 + s1 + s2 : nullptr;
     if (!tiles.empty()) e = cudaMemcpy(T.tile, tiles.data(), sizeof(TileDesc) * tiles.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !lanes.empty())
       e = cudaMemcpy(T.lane, lanes.data(), sizeof(TileLane) * lanes.size(), cudaMemcpyHostToDevice);

@@ -10,7 +10,9 @@
 //                coupling its first and last node to the neighbouring chunks;
 //   tile_couple  one thread per leg: Thomas on those rows from the wall
 //                towards the junction; the junction row fixes the junction
-//                value; back-substitution gives every chunk's end values;
+//                value; back-substitution gives every chunk's end values
+//                (FP32 levels whose legs have at most 64 chunks: the
+//                pivots of that Thomas come from setup, tile_couple_pc);
 //   tile_expand  one lane per chunk: the interior by Thomas between the known
 //                ends, written to u.
 // Lanes of a tile are parallel legs at the same stretch of 32 positions, so
@@ -284,6 +286,193 @@ __global__ void __launch_bounds__(128) tile_couple(const BlockDesc *__restrict__
   }
 }
 
+// ---- FP32 couple with precomputed pivots.  In the forward sweep of
+// tile_couple only d' depends on the right-hand sides: the pivots
+// p = 1 / (1 - a c'_prev) and c' of every reduced row are fixed by the
+// level's coefficients, so couple_consts_kernel computes them once at setup
+// (from the rows tile_reduce gives for any right-hand side) and the sweep per
+// pass is one dependent FMA per row, d' = y p - (a p) d'_prev.  A group's
+// legs are carried by at most 64 threads (two legs per block; a block of
+// three or four legs is alone in its group), so every chunk of every leg fits
+// in shared memory at once: each thread copies its leg's constants with
+// cp.async before waiting for the previous kernel, then the rows' right-hand
+// sides in four copy groups, and eliminates each group as it lands; the
+// back-substitution reads (c', d') from shared memory; the junction's
+// neighbour values are loaded before the sweep.  Legs of at most
+// TILE_PC_CHUNKS chunks.
+constexpr int CCH = TILE_PC_CHUNKS, CSLOT = 64, CSEG = 4;
+static_assert(CCH % CSEG == 0, "whole copy groups");
+constexpr size_t COUPLE_PC_SMEM = (size_t)CCH * CSLOT * (16 + 16 + 8);
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Shared-memory slot of thread (leg l, lane b) in tile_couple_pc: legs 0 and
+// 1 of the group's blocks, and legs 2 and 3 of a block alone in its group.
+__device__ __forceinline__ int couple_slot(int l, int b) { return l < 2 ? l * 32 + b : (l - 2) * 32 + b + 1; }
+
+// One CTA per group, thread (leg l, lane b) as in tile_couple: the forward
+// sweep of the leg's reduced rows without right-hand sides.  Per lane and
+// chunk: ca = (p_lo, a_lo p_lo, p_hi, a_hi p_hi), cb = (c'_lo, c'_hi).
+__global__ void __launch_bounds__(128) couple_consts_kernel(const BlockDesc *__restrict__ blocks, int ntile,
+                                                           const TRow<float> *__restrict__ rows,
+                                                           float4 *__restrict__ ca, float2 *__restrict__ cb) {
+  const int l = threadIdx.x >> 5, b = threadIdx.x & 31;
+  const BlockDesc *bp = blocks + (size_t)blockIdx.x * 32 + b;
+  const int nleg = bp->nleg;
+  if (l >= nleg || l >= 4 || bp->lane != b) return;
+  const int len = bp->leg_len[l], nch = (len + CMAX - 1) / CMAX;
+  const size_t t0 = bp->leg_tile0[l];
+  if (!MG_OK_IF(t0 + nch <= (size_t)ntile)) return;
+  float cpv = 0.f;
+  for (int r = 0; r < nch; ++r) {
+    const size_t i = (t0 + r) * 32 + b;
+    const TRow<float> lo = rows[2 * i], hi = rows[2 * i + 1];
+    float4 A = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 B;
+    float p = rcp_t(1.f - lo.a * cpv);
+    cpv = lo.c * p;
+    A.x = p; A.y = lo.a * p; B.x = cpv; B.y = cpv;
+    if (min(CMAX, len - CMAX * r) >= 2) {
+      p = rcp_t(1.f - hi.a * cpv);
+      cpv = hi.c * p;
+      A.z = p; A.w = hi.a * p; B.y = cpv;
+    }
+    ca[i] = A;
+    cb[i] = B;
+  }
+}
+
+__global__ void __launch_bounds__(128) tile_couple_pc(const BlockDesc *__restrict__ blocks, int ntile, size_t nn,
+                                                     CoefT<float> cp, int nx1, const TRow<float> *__restrict__ rows,
+                                                     const float4 *__restrict__ ca, const float2 *__restrict__ cb,
+                                                     float *__restrict__ xscr, float *__restrict__ u,
+                                                     const float *__restrict__ f) {
+  extern __shared__ float4 couple_smem[];
+  // chunk r of slot s: sA (p_lo, a_lo p_lo, p_hi, a_hi p_hi), sB (c'_lo,
+  // c'_hi, d'_lo, d'_hi), sY (y_lo, y_hi) at [r * CSLOT + s]
+  float4 *sA = couple_smem, *sB = couple_smem + CCH * CSLOT;
+  float2 *sY = reinterpret_cast<float2 *>(couple_smem + 2 * CCH * CSLOT);
+  __shared__ float s_cp[4][32], s_dp[4][32], s_xj[32];
+  pdl_trigger();
+  const int l = threadIdx.x >> 5, b = threadIdx.x & 31;
+  const BlockDesc *bp = blocks + (size_t)blockIdx.x * 32 + b;
+  int nleg = bp->nleg, junc = bp->junc;
+  const int lane = bp->lane, ji = bp->ji, jj = bp->jj;
+  const unsigned jdirs = bp->jdirs;
+  // checked builds: a block's legs must lie in the tile list, within the
+  // chunk cap, a block of more than two legs alone in its group (lane 0), and
+  // its junction inside the level (else it is skipped)
+  if (nleg > 0 || junc) {
+    bool ok = nleg <= 4 && lane == b && (nleg <= 2 || b == 0) &&
+              (!junc || (ji >= 1 && ji <= nx1 - 2 && jj >= 1 && (size_t)(jj + 1) * nx1 < nn));
+    for (int e = 0; e < nleg && ok; ++e)
+      ok = (size_t)bp->leg_tile0[e] + (bp->leg_len[e] + CMAX - 1) / CMAX <= (size_t)ntile &&
+           (bp->leg_len[e] + CMAX - 1) / CMAX <= CCH;
+    if (!MG_OK_IF(ok)) { nleg = 0; junc = 0; }
+  }
+  const bool active = l < nleg;
+  const int len = active ? bp->leg_len[l] : 0;
+  const int nch = (len + CMAX - 1) / CMAX;
+  const size_t t0 = active ? bp->leg_tile0[l] : 0;
+  const int sl = couple_slot(l, b);
+  const size_t i0 = t0 * 32 + lane;  // lane-chunk index of chunk r: i0 + 32 r
+  // the constants (setup data) while the previous kernel may still run
+  for (int r = 0; r < nch; ++r) {
+    cp_async16(&sA[r * CSLOT + sl], ca + i0 + 32 * (size_t)r);
+    cp_async8(&sB[r * CSLOT + sl], cb + i0 + 32 * (size_t)r);
+  }
+  pdl_wait();  // the reduced rows, u and f from here on
+  // the junction row's terms outside the block (loaded now, summed in the
+  // order tile_couple sums them)
+  float jnum = 0.f, jw = 0.f, je = 0.f, js = 0.f, jn = 0.f;
+  if (l == 0 && junc) {
+    const size_t p = (size_t)jj * nx1 + ji;
+    unsigned att = 0;
+    for (int e = 0; e < nleg; ++e) att |= 1u << ((jdirs >> (2 * e)) & 3);
+    jw = __ldg(cp.W + ji); je = __ldg(cp.E + ji); js = __ldg(cp.S + jj); jn = __ldg(cp.N + jj);
+    jnum = f[p];
+    if (!(att & 2u)) jnum -= jw * u[p - 1];
+    if (!(att & 1u)) jnum -= je * u[p + 1];
+    if (!(att & 8u)) jnum -= js * u[p - nx1];
+    if (!(att & 4u)) jnum -= jn * u[p + nx1];
+  }
+  // the rows' right-hand sides (y of the lo and hi row), CSEG copy groups
+  // (the first also holds the constants)
+#pragma unroll
+  for (int g = 0; g < CSEG; ++g) {
+    for (int r = g * (CCH / CSEG); r < min(nch, (g + 1) * (CCH / CSEG)); ++r) {
+      const TRow<float> *row = rows + 2 * (i0 + 32 * (size_t)r);
+      cp_async4(&sY[r * CSLOT + sl].x, &row[0].y);
+      cp_async4(&sY[r * CSLOT + sl].y, &row[1].y);
+    }
+    cp_async_commit();
+  }
+  float dpv = 0.f;
+#pragma unroll
+  for (int g = 0; g < CSEG; ++g) {
+    if (g == 0) cp_async_wait<CSEG - 1>();
+    else if (g == 1) cp_async_wait<CSEG - 2>();
+    else if (g == 2) cp_async_wait<CSEG - 3>();
+    else cp_async_wait<0>();
+    for (int r = g * (CCH / CSEG); r < min(nch, (g + 1) * (CCH / CSEG)); ++r) {
+      const float4 A = sA[r * CSLOT + sl];
+      const float2 y = sY[r * CSLOT + sl];
+      dpv = fmaf(-A.y, dpv, y.x * A.x);
+      const float dlo = dpv;
+      if (min(CMAX, len - CMAX * r) >= 2) dpv = fmaf(-A.w, dpv, y.y * A.z);
+      *reinterpret_cast<float2 *>(&sB[r * CSLOT + sl].z) = make_float2(dlo, dpv);
+    }
+  }
+  // c' of the leg's last row: c'_hi of its last chunk (= c'_lo for a chunk of one node)
+  s_cp[l][b] = nch > 0 ? sB[(nch - 1) * CSLOT + sl].y : 0.f;
+  s_dp[l][b] = dpv;
+  __syncthreads();
+  if (l == 0 && junc) {
+    float num = jnum, den = -((jw + je) + (js + jn));
+    for (int e = 0; e < nleg; ++e) {
+      const int d = (jdirs >> (2 * e)) & 3;
+      const float k = d == DIR_PX ? je : d == DIR_MX ? jw : d == DIR_PY ? jn : js;
+      num -= k * s_dp[e][b];
+      den -= k * s_cp[e][b];
+    }
+    const float xj = num / den;
+    u[(size_t)jj * nx1 + ji] = xj;
+    s_xj[b] = xj;
+  }
+  __syncthreads();
+  if (!active) return;
+  float xn = junc ? s_xj[b] : 0.f;
+  // back-substitution, chunk by chunk towards the wall
+  for (int r = nch - 1; r >= 0; --r) {
+    const float4 v = sB[r * CSLOT + sl];  // (c'_lo, c'_hi, d'_lo, d'_hi)
+    const int mlen = min(CMAX, len - CMAX * r);
+    float xhi = 0.f;
+    if (mlen >= 2) {
+      xhi = v.w - v.y * xn;
+      xn = xhi;
+    }
+    const float xlo = v.z - v.x * xn;
+    xn = xlo;
+    if (mlen < 2) xhi = xlo;
+    xscr[(i0 + 32 * (size_t)r) * 2] = xlo;
+    xscr[(i0 + 32 * (size_t)r) * 2 + 1] = xhi;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(32 * TWv<T>) tile_expand(const TileDesc *__restrict__ tiles,
                                                        const TileLane *__restrict__ lanes, int ntile, CoefT<T> cp,
@@ -350,6 +539,39 @@ __global__ void __launch_bounds__(32 * TWv<T>) tile_expand(const TileDesc *__res
 
 }  // namespace
 
+// the two constant arrays of a tile list (TileList.cconst)
+static float4 *couple_ca(const TileList &tl) { return static_cast<float4 *>(tl.cconst); }
+static float2 *couple_cb(const TileList &tl) {
+  return reinterpret_cast<float2 *>(static_cast<char *>(tl.cconst) + (size_t)tl.ntile * 32 * sizeof(float4));
+}
+
+cudaError_t prepare_tile_kernels() {
+  return cudaFuncSetAttribute(tile_couple_pc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)COUPLE_PC_SMEM);
+}
+
+cudaError_t setup_couple_consts(Grid &g) {
+  // the rows' couplings do not depend on u and f: reduce zero arrays
+  float *z = static_cast<float *>(g.e32);
+  cudaError_t e = cudaMemset(z, 0, g.lev[0].nn * sizeof(float));
+  TRow<float> *rows = static_cast<TRow<float> *>(g.tile_rows);
+  float *dscr = static_cast<float *>(g.tile_d);
+  for (int l = 0; l < g.nlev && e == cudaSuccess; ++l)
+    for (int wl = 0; wl < WL_COUNT && e == cudaSuccess; ++wl)
+      for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+        const Level &L = g.lev[l];
+        const TileList &tl = L.tl[wl][c];
+        if (!tl.cconst) continue;
+        constexpr int TW = TWv<float>;
+        tile_reduce<float><<<(tl.ntile + TW - 1) / TW, 32 * TW>>>(tl.tile, tl.lane, tl.ntile, coefs<float>(L), L.nx,
+                                                                 L.ny, z, z, rows, dscr);
+        couple_consts_kernel<<<tl.ngroup, 128>>>(tl.block, tl.ntile, rows, couple_ca(tl), couple_cb(tl));
+        count_launch(2);
+        e = cudaGetLastError();
+      }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e;
+}
+
 template <typename T>
 cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &tl, T *u, const T *f, cudaStream_t s,
                              cudaEvent_t *ev) {
@@ -367,13 +589,18 @@ cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &tl, 
     e = launch_pdl(tile_reduce<T>, dim3(ctas), dim3(32 * TW), 0, s, (const TileDesc *)tl.tile,
                    (const TileLane *)tl.lane, tl.ntile, cp, L.nx, L.ny, u, f, rows, dscr);
   if (ev) cudaEventRecord(ev[1], s);
-  if (e == cudaSuccess)
-    e = launch_pdl(tile_couple<T>, dim3(tl.ngroup), dim3(128), 0, s, (const BlockDesc *)tl.block, tl.ntile, L.nn,
-                   cp, nx1,
-                   (const TRow<T> *)rows, cdp, xscr, u, f);
+  if (e == cudaSuccess) {
+    if (sizeof(T) == 4 && tl.cconst)
+      e = launch_pdl(tile_couple_pc, dim3(tl.ngroup), dim3(128), COUPLE_PC_SMEM, s, (const BlockDesc *)tl.block,
+                     tl.ntile, L.nn, coefs<float>(L), nx1, (const TRow<float> *)rows, couple_ca(tl), couple_cb(tl),
+                     (float *)xscr, (float *)u, (const float *)f);
+    else
+      e = launch_pdl(tile_couple<T>, dim3(tl.ngroup), dim3(128), 0, s, (const BlockDesc *)tl.block, tl.ntile, L.nn,
+                     cp, nx1, (const TRow<T> *)rows, cdp, xscr, u, f);
+  }
   if (ev) cudaEventRecord(ev[2], s);
   if (e == cudaSuccess && tl.ntile > 0)
-    e = launch_pdl(tile_expand<T>, dim3(ctas), dim3(32 * TW), 0, s, (const TileDesc *)tl.tile,
+    e = launch_ex(true, tile_expand<T>, dim3(ctas), dim3(32 * TW), 0, s, (const TileDesc *)tl.tile,
                    (const TileLane *)tl.lane, tl.ntile, cp, L.nx, L.ny, (const T *)dscr, (const T *)xscr, u);
   if (ev) cudaEventRecord(ev[3], s);
   count_launch(tl.ntile > 0 ? 3 : 1);

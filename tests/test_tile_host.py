@@ -118,3 +118,25 @@ def test_tile_layout_encodes_the_block_systems(dumper, nx, ny, kind, smoother):
                 got[p[1], p[0]] = xs[r]
         assert covered.max() <= 1 and (covered[ref != u0] == 1).all()
         assert np.abs(got - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max()), (colour, np.abs(got - ref).max())
+
+
+@pytest.mark.parametrize("smoother", list(WL))
+@pytest.mark.parametrize("nx,ny", [(64, 64), (128, 64), (64, 160), (96, 96), (256, 128)])
+def test_wide_blocks_alone_in_their_group(dumper, nx, ny, smoother):
+    """The FP32 couple with precomputed pivots gives every leg of a group one
+    of 64 shared-memory slots: legs 0 and 1 of the group's 32 blocks, and legs
+    2 and 3 only of a block alone in its group.  So a block of three or four
+    legs (the centre cross, the T-blocks) must sit at lane 0 of a group whose
+    other 31 records are empty; the setup checks the same (pc_slots_ok) and
+    keeps the plain couple otherwise."""
+    for colour in (0, 1):
+        _, _, blocks = _layout(dumper, nx, ny, WL[smoother], colour)
+        assert len(blocks) % 32 == 0
+        for g0 in range(0, len(blocks), 32):
+            grp = blocks[g0:g0 + 32]
+            for q, bd in enumerate(grp):
+                ji, jj, nleg, junc, jdirs, lane = bd[:6]
+                assert nleg <= 4
+                if nleg > 2:
+                    assert q == 0 and lane == 0
+                    assert all(o[2] == 0 and o[3] == 0 for o in grp[1:])

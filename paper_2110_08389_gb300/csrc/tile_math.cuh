@@ -40,8 +40,10 @@ __device__ __forceinline__ void abc(const T (&co)[2][32], int q, int m, int fl, 
 // The chunk's two reduced rows: eliminate nodes 1..m-2 towards node m-1 (hi
 // row, in terms of x_0 and x_m) and nodes m-2..1 towards node 0 (lo row, in
 // terms of x_{-1} and x_{m-1}); the two sweeps are interleaved.  FULL: m is
-// CMAX, so every guard resolves at compile time.
-template <typename T, bool FULL>
+// CMAX, so every guard resolves at compile time.  COUP: also the rows'
+// couplings a and c (they depend only on the coefficients; without COUP
+// only the right-hand sides y are formed, a and c are left 0).
+template <typename T, bool FULL, bool COUP = true>
 __device__ __forceinline__ void reduce_rows(const T (&co)[2][32], int m_rt, int fl, T cross, const T (&d)[CMAX],
                                             TRow<T> &rlo, TRow<T> &rhi) {
   const int m = FULL ? CMAX : m_rt;
@@ -49,15 +51,17 @@ __device__ __forceinline__ void reduce_rows(const T (&co)[2][32], int m_rt, int 
   abc(co, 0, m, fl, cross, a0, b0, c0);
   rhi.a = T(0); rhi.c = T(0); rhi.y = T(0); rhi.z = T(0);
   rlo.z = T(0);
+  if (!COUP) { rlo.a = T(0); rlo.c = T(0); }
   if (m <= 2) {
     const T rb = rcp_t(b0);
-    rlo.a = a0 * rb; rlo.c = c0 * rb; rlo.y = d[0] * rb;
+    if (COUP) { rlo.a = a0 * rb; rlo.c = c0 * rb; }
+    rlo.y = d[0] * rb;
   }
   if (m >= 2) {
     T a1, b1, c1;
     abc(co, 1, m, fl, cross, a1, b1, c1);
     T ri = rcp_t(b1);
-    T al = a1 * ri, ga = c1 * ri, de = d[1] * ri;
+    T al = COUP ? a1 * ri : T(0), ga = c1 * ri, de = d[1] * ri;
     T ah = T(0), ch = T(0), dh = T(0);
 #pragma unroll
     for (int k = 1; k <= CMAX - 2; ++k) {
@@ -66,7 +70,7 @@ __device__ __forceinline__ void reduce_rows(const T (&co)[2][32], int m_rt, int 
         T a, b, c;
         abc(co, qf, m, fl, cross, a, b, c);
         const T r = rcp_t(b - a * ga);
-        al = -a * al * r;
+        if (COUP) al = -a * al * r;
         ga = c * r;
         de = (d[qf] - a * de) * r;
       }
@@ -76,19 +80,21 @@ __device__ __forceinline__ void reduce_rows(const T (&co)[2][32], int m_rt, int 
         abc(co, qb, m, fl, cross, a, b, c);
         if (qb == m - 2) {
           const T r = rcp_t(b);
-          ah = a * r; ch = c * r; dh = d[qb] * r;
+          ah = a * r; dh = d[qb] * r;
+          if (COUP) ch = c * r;
         } else {
           const T r = rcp_t(b - c * ah);
           ah = a * r;
-          ch = -c * ch * r;
+          if (COUP) ch = -c * ch * r;
           dh = (d[qb] - c * dh) * r;
         }
       }
     }
-    rhi.a = al; rhi.c = ga; rhi.y = de;
+    rhi.a = COUP ? al : T(0); rhi.c = COUP ? ga : T(0); rhi.y = de;
     if (m >= 3) {
       const T r = rcp_t(b0 - c0 * ah);
-      rlo.a = a0 * r; rlo.c = -c0 * ch * r; rlo.y = (d[0] - c0 * dh) * r;
+      if (COUP) { rlo.a = a0 * r; rlo.c = -c0 * ch * r; }
+      rlo.y = (d[0] - c0 * dh) * r;
     }
   }
 }

@@ -74,7 +74,10 @@ __device__ __forceinline__ void stage_coefs(const TileGeom<T> &g, int lane, T (&
   __syncwarp();
 }
 
-template <typename T>
+// YONLY (FP32 levels whose couple takes precomputed pivots): the rows'
+// couplings are not formed, and only the pair (y_lo, y_hi) of each lane's
+// chunk is written, as a 2-vector at tile * 32 + lane of `rows`.
+template <typename T, bool YONLY = false>
 __global__ void __launch_bounds__(32 * TWv<T>) tile_reduce(const TileDesc *__restrict__ tiles,
                                                        const TileLane *__restrict__ lanes, int ntile, CoefT<T> cp,
                                                        int nx, int ny, const T *__restrict__ u,
@@ -153,9 +156,14 @@ __global__ void __launch_bounds__(32 * TWv<T>) tile_reduce(const TileDesc *__res
   // as tile_expand has, doubled the registers here to 150 and was slower on
   // GB300: 79 vs 50 us per pass at 4097^2.)
   TRow<T> rlo, rhi;
-  reduce_rows<T, false>(co, m, fl, cross, d, rlo, rhi);
-  rows[((size_t)t * 32 + lane) * 2] = rlo;
-  rows[((size_t)t * 32 + lane) * 2 + 1] = rhi;
+  reduce_rows<T, false, !YONLY>(co, m, fl, cross, d, rlo, rhi);
+  if constexpr (YONLY) {
+    static_assert(sizeof(T) == 4, "the y-only rows are FP32");
+    reinterpret_cast<float2 *>(rows)[(size_t)t * 32 + lane] = make_float2(rlo.y, rhi.y);
+  } else {
+    rows[((size_t)t * 32 + lane) * 2] = rlo;
+    rows[((size_t)t * 32 + lane) * 2 + 1] = rhi;
+  }
   if (m == CMAX) {
 #pragma unroll
     for (int q = 0; q < CMAX; ++q) dscr[((size_t)t * 32 + q) * 32 + lane] = d[q];
@@ -312,10 +320,6 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
 }
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
-               : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -357,7 +361,7 @@ __global__ void __launch_bounds__(128) couple_consts_kernel(const BlockDesc *__r
 }
 
 __global__ void __launch_bounds__(128) tile_couple_pc(const BlockDesc *__restrict__ blocks, int ntile, size_t nn,
-                                                     CoefT<float> cp, int nx1, const TRow<float> *__restrict__ rows,
+                                                     CoefT<float> cp, int nx1, const float2 *__restrict__ ys,
                                                      const float4 *__restrict__ ca, const float2 *__restrict__ cb,
                                                      float *__restrict__ xscr, float *__restrict__ u,
                                                      const float *__restrict__ f) {
@@ -410,15 +414,12 @@ __global__ void __launch_bounds__(128) tile_couple_pc(const BlockDesc *__restric
     if (!(att & 8u)) jnum -= js * u[p - nx1];
     if (!(att & 4u)) jnum -= jn * u[p + nx1];
   }
-  // the rows' right-hand sides (y of the lo and hi row), CSEG copy groups
-  // (the first also holds the constants)
+  // the rows' right-hand sides (y of the lo and hi row, tile_reduce<float,
+  // true>), CSEG copy groups (the first also holds the constants)
 #pragma unroll
   for (int g = 0; g < CSEG; ++g) {
-    for (int r = g * (CCH / CSEG); r < min(nch, (g + 1) * (CCH / CSEG)); ++r) {
-      const TRow<float> *row = rows + 2 * (i0 + 32 * (size_t)r);
-      cp_async4(&sY[r * CSLOT + sl].x, &row[0].y);
-      cp_async4(&sY[r * CSLOT + sl].y, &row[1].y);
-    }
+    for (int r = g * (CCH / CSEG); r < min(nch, (g + 1) * (CCH / CSEG)); ++r)
+      cp_async8(&sY[r * CSLOT + sl], ys + i0 + 32 * (size_t)r);
     cp_async_commit();
   }
   float dpv = 0.f;
@@ -585,14 +586,24 @@ cudaError_t launch_tile_pass(const Grid &g, const Level &L, const TileList &tl, 
   const int ctas = (tl.ntile + TW - 1) / TW;
   if (ev) cudaEventRecord(ev[0], s);
   cudaError_t e = cudaSuccess;
-  if (tl.ntile > 0)
-    e = launch_pdl(tile_reduce<T>, dim3(ctas), dim3(32 * TW), 0, s, (const TileDesc *)tl.tile,
-                   (const TileLane *)tl.lane, tl.ntile, cp, L.nx, L.ny, u, f, rows, dscr);
+  if (tl.ntile > 0) {
+    if constexpr (sizeof(T) == 4) {
+      if (tl.cconst)
+        e = launch_pdl(tile_reduce<float, true>, dim3(ctas), dim3(32 * TW), 0, s, (const TileDesc *)tl.tile,
+                       (const TileLane *)tl.lane, tl.ntile, cp, L.nx, L.ny, u, f, rows, dscr);
+      else
+        e = launch_pdl(tile_reduce<float, false>, dim3(ctas), dim3(32 * TW), 0, s, (const TileDesc *)tl.tile,
+                       (const TileLane *)tl.lane, tl.ntile, cp, L.nx, L.ny, u, f, rows, dscr);
+    } else {
+      e = launch_pdl(tile_reduce<T>, dim3(ctas), dim3(32 * TW), 0, s, (const TileDesc *)tl.tile,
+                     (const TileLane *)tl.lane, tl.ntile, cp, L.nx, L.ny, u, f, rows, dscr);
+    }
+  }
   if (ev) cudaEventRecord(ev[1], s);
   if (e == cudaSuccess) {
     if (sizeof(T) == 4 && tl.cconst)
       e = launch_pdl(tile_couple_pc, dim3(tl.ngroup), dim3(128), COUPLE_PC_SMEM, s, (const BlockDesc *)tl.block,
-                     tl.ntile, L.nn, coefs<float>(L), nx1, (const TRow<float> *)rows, couple_ca(tl), couple_cb(tl),
+                     tl.ntile, L.nn, coefs<float>(L), nx1, (const float2 *)rows, couple_ca(tl), couple_cb(tl),
                      (float *)xscr, (float *)u, (const float *)f);
     else
       e = launch_pdl(tile_couple<T>, dim3(tl.ngroup), dim3(128), 0, s, (const BlockDesc *)tl.block, tl.ntile, L.nn,

@@ -108,6 +108,27 @@ def test_smooth_f32(mg, oracle_mod, grid, smoother):
     assert rel_err(host(ud), ref) <= 2e-4, rel_err(host(ud), ref)
 
 
+@pytest.mark.parametrize("smoother", ["zebra_x", "zebra_y", "tweed", "alt_zebra"])
+def test_smooth_f32_long_lines(mg, oracle_mod, smoother):
+    """4096 x 1024 intervals, level 0 on the tiled path: the zebra-x lines have 4095
+    nodes, 128 chunks, more than the 64 a leg may have for the FP32 couple
+    with setup-time pivots, so that list keeps the plain couple; the zebra-y
+    lines (32 chunks) and the tweed blocks (L-blocks, T-blocks, straight
+    lines) take the pivots from setup.  Each against the oracle as
+    test_smooth_f32."""
+    g, P = setup_pair(mg, oracle_mod, 4096, 1024, "wall", 2.0)
+    for sm in (("zebra_x", "zebra_y") if smoother == "alt_zebra" else (smoother,)):
+        g.set_line_path(0, sm, "f32", "tiled")
+        assert g.line_path(0, sm, "f32")[0] == "tiled"
+    rng = np.random.default_rng(3)
+    u0 = rng.standard_normal(P.shape()).astype(np.float32).astype(np.float64)
+    f = rng.standard_normal(P.shape()).astype(np.float32).astype(np.float64)
+    ref = P.smooth(u0.copy(), f, smoother, 1)
+    ud = cuda(u0, "f32")
+    g.smooth(ud, cuda(f, "f32"), smoother, 1)
+    assert rel_err(host(ud), ref) <= 2e-4, rel_err(host(ud), ref)
+
+
 @pytest.mark.parametrize("grid", GRIDS[3:], ids=lambda t: f"{t[0]}x{t[1]}-{t[2]}")
 @pytest.mark.parametrize("restriction", [0, 1])
 def test_residual_restrict_prolong(mg, oracle_mod, grid, restriction):

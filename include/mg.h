@@ -139,9 +139,9 @@ typedef struct {
  * MG_ERR_UNSUPPORTED (their middle blocks would close loops).
  * precision_mask: bit 0 = FP64 workspaces, bit 1 = FP32 workspaces (0 means
  * both).  The block work lists of every smoother are built here too, and
- * with FP32 workspaces the coefficient-only part of the tiled line solves
- * (the pivots of the reduced systems of Sec. 3's partition into chunks),
- * which runs kernels on the device and waits for them.
+ * with FP32 workspaces the part of the tiled line solves that only the
+ * coefficients fix (the pivots of the reduced system each leg's 32-node
+ * chunks form), which runs kernels on the device and waits for them.
  * On success *out owns device memory until mg_destroy.                       */
 mg_status mg_setup_grid(mg_grid **out, int dim, const int64_t *n_intervals,
                         const double *const *coords, int precision_mask, void *stream);

@@ -408,6 +408,7 @@ mg_status setup3(Grid &g, const int64_t *n, const double *const *coords) {
     TRY_CUDA("cudaMalloc(r32)", cudaMalloc(&g.r32, sizeof(float) * nn0));
     TRY_CUDA("cudaMemset(e32)", cudaMemset(g.e32, 0, sizeof(float) * nn0));
     TRY_CUDA("cudaMemset(r32)", cudaMemset(g.r32, 0, sizeof(float) * nn0));
+    if (g.tile_cap > 0) TRY_CUDA("3D tile couple constants", setup_couple_consts3(g));
   }
   return MG_OK;
 }

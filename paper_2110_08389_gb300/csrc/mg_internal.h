@@ -229,6 +229,11 @@ struct Tile3List {
   Tile3Lane *lane = nullptr;    // 32 per tile
   Block3Desc *block = nullptr;  // 32 per group (unused entries: nleg = junc = 0)
   uint32_t *slot = nullptr;     // the chunks of every leg, in order
+  // FP32 grids: per lane slot (tile * 32 + lane), the couple's forward-sweep
+  // constants of the reduced lo and hi rows, laid out as TileList.cconst
+  // (a float4 per slot, then a float2 per slot); set at setup
+  // (setup_couple_consts3).  nullptr otherwise.
+  void *cconst = nullptr;
 };
 struct Level3 {
   int nx = 0, ny = 0, nz = 0;
@@ -592,6 +597,9 @@ struct HBlock3;
 template <typename T>
 cudaError_t launch_tile3_pass(const Grid &g, const Level3 &L, const Tile3List &t, T *u, const T *f, cudaStream_t s);
 mg_status build_tiles3(Grid &g, Level3 &L, const std::vector<HBlock3> &tweed_blocks, bool *ok);
+// The couple constants of every FP32 3D tile list (after the tiled scratch
+// and e32 are allocated).
+cudaError_t setup_couple_consts3(Grid &g);
 // Levels whose sides are all at least T3_MIN_SIDE intervals get 3D tile
 // lists; the built-in rule takes the tiled path on those whose sides are all
 // at least T3_AUTO_SIDE (measured on GB300, FP32 tweed relaxation: 257^3

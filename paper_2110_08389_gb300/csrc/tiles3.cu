@@ -12,7 +12,9 @@
 //   tile3_couple  per leg (up to six), its chunks found through the leg's
 //                 slot list: Thomas on those rows towards the junction; the
 //                 junction row with its six neighbours fixes the junction
-//                 value; back-substitution gives every chunk's end values;
+//                 value; back-substitution gives every chunk's end values
+//                 (FP32: tile3_couple_pc, with the pivots from setup, after
+//                 a tile3_reduce that forms only the rows' right-hand sides);
 //   tile3_expand  one lane per chunk: the interior by Thomas between the
 //                 known ends, written to u.
 // Lanes of a tile are chunks of parallel legs over the same 32 positions, so
@@ -105,7 +107,10 @@ __device__ __forceinline__ void stage_coefs3(const Geo3<T> &g, int lane, T (&co)
   __syncwarp();
 }
 
-template <typename T>
+// YONLY (FP32 lists whose couple takes setup-time pivots): the rows'
+// couplings are not formed; only (y_lo, y_hi) of each lane slot is written,
+// as a 2-vector at tile * 32 + lane of `rows`.
+template <typename T, bool YONLY = false>
 __global__ void __launch_bounds__(32 * TW3<T>) tile3_reduce(const Tile3Desc *__restrict__ tiles,
                                                         const Tile3Lane *__restrict__ lanes, int ntile,
                                                         Coef3T<T> cp, int nx, int ny, int nz,
@@ -183,9 +188,14 @@ __global__ void __launch_bounds__(32 * TW3<T>) tile3_reduce(const Tile3Desc *__r
   if (m == 0) return;
   const T cross = (am + ap) + (bm + bp);
   TRow<T> rlo, rhi;
-  reduce_rows<T, false>(co, m, fl, cross, d, rlo, rhi);
-  rows[((size_t)t * 32 + lane) * 2] = rlo;
-  rows[((size_t)t * 32 + lane) * 2 + 1] = rhi;
+  reduce_rows<T, false, !YONLY>(co, m, fl, cross, d, rlo, rhi);
+  if constexpr (YONLY) {
+    static_assert(sizeof(T) == 4, "the y-only rows are FP32");
+    reinterpret_cast<float2 *>(rows)[(size_t)t * 32 + lane] = make_float2(rlo.y, rhi.y);
+  } else {
+    rows[((size_t)t * 32 + lane) * 2] = rlo;
+    rows[((size_t)t * 32 + lane) * 2 + 1] = rhi;
+  }
 #pragma unroll
   for (int q = 0; q < CMAX; ++q)
     if (q < m) dscr[((size_t)t * 32 + q) * 32 + lane] = d[q];
@@ -311,6 +321,154 @@ __global__ void __launch_bounds__(64) tile3_couple(const Block3Desc *__restrict_
   }
 }
 
+// ---- FP32 couple with setup-time pivots, as tiles.cu's tile_couple_pc:
+// the pivots p = 1 / (1 - a c'_prev), a p and c' of every reduced row depend
+// only on the coefficients, so couple3_consts_kernel forms them once from the
+// rows tile3_reduce gives for any right-hand side; per pass the forward sweep
+// is d' = y p - (a p) d'_prev on the rows' right-hand sides alone.
+__global__ void __launch_bounds__(64) couple3_consts_kernel(const Block3Desc *__restrict__ blocks,
+                                                            const uint32_t *__restrict__ slots,
+                                                            const TRow<float> *__restrict__ rows,
+                                                            float4 *__restrict__ ca, float2 *__restrict__ cb) {
+  const int w = threadIdx.x >> 5, b = threadIdx.x & 31;
+  const Block3Desc *bp = blocks + (size_t)blockIdx.x * 32 + b;
+  const int nleg = min((int)bp->nleg, 6);
+  for (int l = w; l < nleg; l += 2) {
+    const int len = bp->leg_len[l];
+    const int nch = (len + CMAX - 1) / CMAX;
+    const uint32_t *sl = slots + bp->leg_slot0[l];
+    float cpv = 0.f;
+    for (int r = 0; r < nch; ++r) {
+      const size_t i = sl[r];
+      const TRow<float> lo = rows[2 * i], hi = rows[2 * i + 1];
+      float4 A = make_float4(0.f, 0.f, 0.f, 0.f);
+      float2 B;
+      float p = rcp_t(1.f - lo.a * cpv);
+      cpv = lo.c * p;
+      A.x = p; A.y = lo.a * p; B.x = cpv; B.y = cpv;
+      if (min(CMAX, len - CMAX * r) >= 2) {
+        p = rcp_t(1.f - hi.a * cpv);
+        cpv = hi.c * p;
+        A.z = p; A.w = hi.a * p; B.y = cpv;
+      }
+      ca[i] = A;
+      cb[i] = B;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(64) tile3_couple_pc(const Block3Desc *__restrict__ blocks,
+                                                      const uint32_t *__restrict__ slots, int nslot, int ntile,
+                                                      Coef3T<float> cp, int nx, int ny, int nz,
+                                                      const float2 *__restrict__ ys, const float4 *__restrict__ ca,
+                                                      const float2 *__restrict__ cb, float *cdp,
+                                                      float *__restrict__ xscr, float *__restrict__ u,
+                                                      const float *__restrict__ f) {
+  __shared__ float s_cp[6][32], s_dp[6][32], s_xj[32];
+  pdl_trigger();
+  const int w = threadIdx.x >> 5, b = threadIdx.x & 31;
+  const Block3Desc *bp = blocks + (size_t)blockIdx.x * 32 + b;
+  int nleg = bp->nleg, junc = bp->junc;
+  const unsigned jdirs = bp->jdirs;
+  const int ji = bp->ji, jj = bp->jj, jk = bp->jk;
+  // checked builds: a block's chunk slots must lie in the lists and its
+  // junction inside the level (else the block is skipped)
+  if (nleg > 0 || junc) {
+    bool ok = nleg <= 6 && (!junc || (ji >= 1 && ji <= nx - 1 && jj >= 1 && jj <= ny - 1 && jk >= 1 && jk <= nz - 1));
+    for (int e = 0; e < nleg && ok; ++e) {
+      const int nc = (bp->leg_len[e] + CMAX - 1) / CMAX;
+      ok = (size_t)bp->leg_slot0[e] + nc <= (size_t)nslot;
+      for (int r = 0; r < nc && ok; ++r) ok = slots[bp->leg_slot0[e] + r] < 32u * ntile;
+    }
+    if (!MG_OK_IF(ok)) { nleg = 0; junc = 0; }
+  }
+  pdl_wait();  // the rows' right-hand sides, u and f from here on
+  constexpr int B = 4;  // chunks whose loads are issued together (legs of at most a few chunks)
+  for (int l = w; l < nleg; l += 2) {
+    const int len = bp->leg_len[l];
+    const int nch = (len + CMAX - 1) / CMAX;
+    const uint32_t *sl = slots + bp->leg_slot0[l];
+    float cpv = 0.f, dpv = 0.f;
+    for (int r0 = 0; r0 < nch; r0 += B) {
+      float2 y[B], c2[B];
+      float4 A[B];
+#pragma unroll
+      for (int k = 0; k < B; ++k)
+        if (r0 + k < nch) {
+          const size_t i = __ldg(sl + r0 + k);
+          y[k] = ys[i];
+          A[k] = ca[i];
+          c2[k] = cb[i];
+        }
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        const int r = r0 + k;
+        if (r < nch) {
+          const size_t idx = (size_t)__ldg(sl + r) * 2;
+          const int mlen = min(CMAX, len - CMAX * r);
+          dpv = fmaf(-A[k].y, dpv, y[k].x * A[k].x);
+          cpv = c2[k].x;
+          cdp[2 * idx] = cpv; cdp[2 * idx + 1] = dpv;
+          if (mlen >= 2) {
+            dpv = fmaf(-A[k].w, dpv, y[k].y * A[k].z);
+            cpv = c2[k].y;
+            cdp[2 * idx + 2] = cpv; cdp[2 * idx + 3] = dpv;
+          }
+        }
+      }
+    }
+    s_cp[l][b] = cpv;
+    s_dp[l][b] = dpv;
+  }
+  __syncthreads();
+  if (w == 0 && junc) {
+    const long long nx1 = nx + 1, plane = nx1 * (ny + 1);
+    const long long p = jk * plane + jj * nx1 + ji;
+    unsigned att = 0;
+    for (int e = 0; e < nleg; ++e) att |= 1u << ((jdirs >> (3 * e)) & 7u);
+    const float cw = __ldg(cp.c[0] + ji), ce = __ldg(cp.c[1] + ji), cs = __ldg(cp.c[2] + jj),
+                cn = __ldg(cp.c[3] + jj), cbo = __ldg(cp.c[4] + jk), ct = __ldg(cp.c[5] + jk);
+    float num = f[p];
+    if (!(att & 1u)) num -= ce * u[p + 1];
+    if (!(att & 2u)) num -= cw * u[p - 1];
+    if (!(att & 4u)) num -= cn * u[p + nx1];
+    if (!(att & 8u)) num -= cs * u[p - nx1];
+    if (!(att & 16u)) num -= ct * u[p + plane];
+    if (!(att & 32u)) num -= cbo * u[p - plane];
+    float den = -(((cw + ce) + (cs + cn)) + (cbo + ct));
+    for (int e = 0; e < nleg; ++e) {
+      const unsigned d = (jdirs >> (3 * e)) & 7u;
+      const float kc = d == 0 ? ce : d == 1 ? cw : d == 2 ? cn : d == 3 ? cs : d == 4 ? ct : cbo;
+      num -= kc * s_dp[e][b];
+      den -= kc * s_cp[e][b];
+    }
+    const float x = num / den;
+    u[p] = x;
+    s_xj[b] = x;
+  }
+  __syncthreads();
+  for (int l = w; l < nleg; l += 2) {
+    const int len = bp->leg_len[l];
+    const int nch = (len + CMAX - 1) / CMAX;
+    const uint32_t *sl = slots + bp->leg_slot0[l];
+    float xn = junc ? s_xj[b] : 0.f;
+    for (int r = nch - 1; r >= 0; --r) {
+      const size_t idx = (size_t)__ldg(sl + r) * 2;
+      const int mlen = min(CMAX, len - CMAX * r);
+      float xhi = 0.f;
+      if (mlen >= 2) {
+        xhi = cdp[2 * idx + 3] - cdp[2 * idx + 2] * xn;
+        xn = xhi;
+      }
+      const float xlo = cdp[2 * idx + 1] - cdp[2 * idx] * xn;
+      xn = xlo;
+      if (mlen < 2) xhi = xlo;
+      xscr[idx] = xlo;
+      xscr[idx + 1] = xhi;
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(32 * TW3<T>) tile3_expand(const Tile3Desc *__restrict__ tiles,
                                                         const Tile3Lane *__restrict__ lanes, int ntile,
@@ -379,9 +537,12 @@ mg_status build_tiles3(Grid &g, Level3 &L, const std::vector<HBlock3> &tweed_blo
     const size_t s0 = th[c].tiles.size() * sizeof(Tile3Desc), s1 = th[c].lanes.size() * sizeof(Tile3Lane),
                  s2 = th[c].blocks.size() * sizeof(Block3Desc), s3 = th[c].slots.size() * sizeof(uint32_t);
     const size_t o1 = (s0 + 255) / 256 * 256, o2 = o1 + (s1 + 255) / 256 * 256, o3 = o2 + (s2 + 255) / 256 * 256;
+    const size_t o4 = o3 + (s3 + 255) / 256 * 256;
+    const size_t s4 = (g.prec_mask & 2) ? th[c].tiles.size() * 32 * (16 + 8) : 0;  // couple constants
     char *mem = nullptr;
-    if (cudaMalloc(&mem, o3 + s3 + 16) != cudaSuccess) return MG_ERR_ALLOC;
+    if (cudaMalloc(&mem, o4 + s4 + 16) != cudaSuccess) return MG_ERR_ALLOC;
     T.mem = mem;
+    T.cconst = s4 ? mem + o4 : nullptr;
     T.tile = reinterpret_cast<Tile3Desc *>(mem);
     T.lane = reinterpret_cast<Tile3Lane *>(mem + o1);
     T.block = reinterpret_cast<Block3Desc *>(mem + o2);
@@ -402,6 +563,34 @@ mg_status build_tiles3(Grid &g, Level3 &L, const std::vector<HBlock3> &tweed_blo
   return MG_OK;
 }
 
+// the two constant arrays of a 3D tile list (Tile3List.cconst)
+static float4 *couple3_ca(const Tile3List &tl) { return static_cast<float4 *>(tl.cconst); }
+static float2 *couple3_cb(const Tile3List &tl) {
+  return reinterpret_cast<float2 *>(static_cast<char *>(tl.cconst) + (size_t)tl.ntile * 32 * sizeof(float4));
+}
+
+cudaError_t setup_couple_consts3(Grid &g) {
+  // the rows' couplings do not depend on u and f: reduce zero arrays
+  float *z = static_cast<float *>(g.e32);
+  cudaError_t e = cudaMemset(z, 0, g.g3->lev[0].nn * sizeof(float));
+  TRow<float> *rows = static_cast<TRow<float> *>(g.tile_rows);
+  float *dscr = static_cast<float *>(g.tile_d);
+  for (Level3 &L : g.g3->lev)
+    for (int c = 0; c < 2 && e == cudaSuccess && L.t3_ok; ++c) {
+      const Tile3List &tl = L.t3[c];
+      if (!tl.cconst || tl.ntile == 0) continue;
+      constexpr int TW = TW3<float>;
+      tile3_reduce<float><<<(tl.ntile + TW - 1) / TW, 32 * TW>>>(tl.tile, tl.lane, tl.ntile, coef3t<float>(L), L.nx,
+                                                                 L.ny, L.nz, z, z, rows, dscr);
+      if (tl.ngroup > 0)
+        couple3_consts_kernel<<<tl.ngroup, 64>>>(tl.block, tl.slot, rows, couple3_ca(tl), couple3_cb(tl));
+      count_launch(tl.ngroup > 0 ? 2 : 1);
+      e = cudaGetLastError();
+    }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return e;
+}
+
 template <typename T>
 cudaError_t launch_tile3_pass(const Grid &g, const Level3 &L, const Tile3List &tl, T *u, const T *f,
                               cudaStream_t s) {
@@ -413,13 +602,27 @@ cudaError_t launch_tile3_pass(const Grid &g, const Level3 &L, const Tile3List &t
   constexpr int TW = TW3<T>;
   const int ctas = (tl.ntile + TW - 1) / TW;
   cudaError_t e = cudaSuccess;
-  if (tl.ntile > 0)
-    e = launch_pdl(tile3_reduce<T>, dim3(ctas), dim3(32 * TW), 0, s, (const Tile3Desc *)tl.tile,
-                   (const Tile3Lane *)tl.lane, tl.ntile, cp, L.nx, L.ny, L.nz, (const T *)u, f, rows, dscr);
-  if (e == cudaSuccess && tl.ngroup > 0)
-    e = launch_pdl(tile3_couple<T>, dim3(tl.ngroup), dim3(64), 0, s, (const Block3Desc *)tl.block,
-                   (const uint32_t *)tl.slot, tl.nslot, tl.ntile, cp, L.nx, L.ny, L.nz, (const TRow<T> *)rows, cdp,
-                   xscr, u, f);
+  const bool pc = sizeof(T) == 4 && tl.cconst;  // FP32 with setup-time pivots
+  if (tl.ntile > 0) {
+    if (pc)
+      e = launch_pdl(tile3_reduce<float, true>, dim3(ctas), dim3(32 * TW), 0, s, (const Tile3Desc *)tl.tile,
+                     (const Tile3Lane *)tl.lane, tl.ntile, coef3t<float>(L), L.nx, L.ny, L.nz, (const float *)u,
+                     (const float *)f, (TRow<float> *)rows, (float *)dscr);
+    else
+      e = launch_pdl(tile3_reduce<T>, dim3(ctas), dim3(32 * TW), 0, s, (const Tile3Desc *)tl.tile,
+                     (const Tile3Lane *)tl.lane, tl.ntile, cp, L.nx, L.ny, L.nz, (const T *)u, f, rows, dscr);
+  }
+  if (e == cudaSuccess && tl.ngroup > 0) {
+    if (pc)
+      e = launch_pdl(tile3_couple_pc, dim3(tl.ngroup), dim3(64), 0, s, (const Block3Desc *)tl.block,
+                     (const uint32_t *)tl.slot, tl.nslot, tl.ntile, coef3t<float>(L), L.nx, L.ny, L.nz,
+                     (const float2 *)rows, couple3_ca(tl), couple3_cb(tl), (float *)cdp, (float *)xscr, (float *)u,
+                     (const float *)f);
+    else
+      e = launch_pdl(tile3_couple<T>, dim3(tl.ngroup), dim3(64), 0, s, (const Block3Desc *)tl.block,
+                     (const uint32_t *)tl.slot, tl.nslot, tl.ntile, cp, L.nx, L.ny, L.nz, (const TRow<T> *)rows,
+                     cdp, xscr, u, f);
+  }
   if (e == cudaSuccess && tl.ntile > 0)
     e = launch_pdl(tile3_expand<T>, dim3(ctas), dim3(32 * TW), 0, s, (const Tile3Desc *)tl.tile,
                    (const Tile3Lane *)tl.lane, tl.ntile, cp, L.nx, L.ny, L.nz, (const T *)dscr, (const T *)xscr, u);

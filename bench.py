@@ -547,7 +547,7 @@ def run_3d(args):
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": 2 * 8 * nn, "d2h_bytes_per_step": 8 * nn},
             "gpu_launches": int(launches),
             "roofline": {"kernel": "FP32 3D tweed colour pass, finest level (" +
-                                   ("tile3_reduce + tile3_couple + tile3_expand" if tiled else "seq3_single_kernel") + ")",
+                                   ("tile3_reduce + tile3_couple_pc + tile3_expand" if tiled else "seq3_single_kernel") + ")",
                          "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "pass_ms": pass_ms, "passes_timed": npass,
                          "launches_per_pass": 3 if tiled else 1,
